@@ -1,0 +1,260 @@
+/*
+ * phfem.h -- C ABI of the GB300 (sm_103a) primal hybrid finite element library.
+ *
+ * Lowest-order primal hybrid FEM for 2D second-order elliptic problems and
+ * their Crank-Nicolson parabolic counterparts with mixed Dirichlet/Neumann
+ * boundaries (Nagula Mallesham, Porwal, Valdman, Acharya, "Vectorized
+ * implementation of primal hybrid FEM in MATLAB", arXiv 2401.15557):
+ * discontinuous P1 unknowns on every triangle, one piecewise-constant Lagrange
+ * multiplier per non-Neumann edge (Section 3.2, Eqs. ph21-ph22).
+ *
+ * The library eliminates every element's three P1 unknowns in favour of its
+ * three edge-midpoint values w_T = R u_T (R from Definition 3.1: the rows R_k
+ * of lambda_j at the midpoints).  The multiplier constraint (Eq. ph22) makes
+ * these midpoint values single-valued, so the solve runs on one SPD system
+ * over the edges; U and Lambda are recovered exactly from w per element.
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers to arrays are DEVICE pointers (CUDA global memory of the current
+ *     device) unless the comment says "host".  Arrays are 0-based, row-major.
+ *   - The caller owns every array it passes; the library reads inputs and
+ *     writes outputs only during the call, ordered on the context's stream,
+ *     and keeps no pointer to them after the call returns.
+ *   - Handles (phfem_ctx/_mesh/_sys/_cn) own their device buffers (allocated
+ *     stream-ordered on the context stream) until the matching *_destroy.
+ *   - Every function returns a phfem_status (0 = success, < 0 = error); the
+ *     message of the last error of the calling thread is phfem_last_error().
+ *     On error no output is guaranteed to be written and no handle is created.
+ *   - Edge numbering follows the paper's nodes2edge (Listing 2): edges are
+ *     numbered by increasing (larger vertex, smaller vertex).
+ *   - Local edge k of a triangle (P1, P2, P3) = (tri[t][0], tri[t][1],
+ *     tri[t][2]) is the edge opposite P_{k+1} (E1, E2, E3 of Section 2).
+ */
+#ifndef PHFEM_H
+#define PHFEM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define PHFEM_API __attribute__((visibility("default")))
+#else
+#define PHFEM_API
+#endif
+
+typedef enum {
+  PHFEM_OK = 0,
+  PHFEM_EINVAL = -1,      /* bad argument (NULL handle, negative size, ...)        */
+  PHFEM_EMESH = -2,       /* mesh rejected (see phfem_mesh_build)                   */
+  PHFEM_ENOMEM = -3,      /* device allocation failed                                */
+  PHFEM_ENOCONV = -4,     /* iteration limits reached before the tolerance           */
+  PHFEM_EBREAKDOWN = -5,  /* conjugate gradients met p.Ap <= 0                       */
+  PHFEM_ENAN = -6,        /* a NaN or Inf appeared in coefficients or iterates       */
+  PHFEM_ECUDA = -7        /* a CUDA runtime call failed                               */
+} phfem_status;
+
+enum { PHFEM_FP64 = 0, PHFEM_FP32_IR = 1 };
+enum { PHFEM_EDGE_INTERIOR = 0, PHFEM_EDGE_DIRICHLET = 1, PHFEM_EDGE_NEUMANN = 2 };
+
+typedef struct phfem_ctx_s* phfem_ctx;
+typedef struct phfem_mesh_s* phfem_mesh;
+typedef struct phfem_sys_s* phfem_sys;
+typedef struct phfem_cn_s* phfem_cn;
+
+/* ------------------------------------------------------------------------ */
+/* Context                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Creates a context bound to the current CUDA device and to `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  All work of handles
+ * made from this context is ordered on that stream. */
+PHFEM_API int phfem_ctx_create(void* cuda_stream, phfem_ctx* out);
+PHFEM_API int phfem_ctx_destroy(phfem_ctx ctx);
+PHFEM_API const char* phfem_status_str(int status);
+PHFEM_API const char* phfem_last_error(void);
+/* Number of kernels the library launched on this context so far. */
+PHFEM_API int64_t phfem_ctx_launches(phfem_ctx ctx);
+/* Instrumentation (not part of the method): when enabled, launches of the
+ * kernels "cg_spmv", "cg_update", "cg_dir", "residual", "asm_tri", "asm_rows"
+ * and "recover" are bracketed by CUDA events on the context
+ * stream.  phfem_ctx_kernel_time synchronises on the last event and returns
+ * the summed device time (ms) and the number of timed launches of one kernel;
+ * reset != 0 starts a new accumulation. */
+PHFEM_API int phfem_ctx_profile(phfem_ctx ctx, int enable);
+PHFEM_API int phfem_ctx_kernel_time(phfem_ctx ctx, const char* kernel, double* total_ms,
+                                    int64_t* launches, int reset);
+
+/* ------------------------------------------------------------------------ */
+/* Mesh tables (Section 2.2: edge_vec; Listings 1-3, Eqs. n2el/n2ed/ed2el)   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  int32_t nV, nT;  /* vertices, triangles                                   */
+  int32_t nE;      /* edges (nrEdges of the paper)                           */
+  int32_t nF;      /* free edges = interior + Neumann (unknowns of the solve) */
+  int32_t nL;      /* multiplier edges = interior + Dirichlet (L, Sec. 2)   */
+  int32_t nD, nN;  /* Dirichlet / Neumann edges                              */
+  int32_t nnz;     /* nonzeros of the free-edge system (CSR pattern)         */
+} phfem_mesh_info;
+
+/* Builds every table of the mesh on the device.
+ *   xy        [nV][2] double   vertex coordinates (coordinates.dat, Table 1)
+ *   tri       [nT][3] int32    counter-clockwise triangles (elements.dat)
+ *   dirichlet [nD][2] int32    vertex pairs of the Dirichlet edges (Dirichlet.dat)
+ *   neumann   [nN][2] int32    vertex pairs of the Neumann edges (Neumann.dat)
+ * Rules (the paper's definitions):
+ *   - edge e's T+ is the first triangle, in the element-major order of the
+ *     directed edges P1P2, P2P3, P3P1, that holds it; (initial, end) is its
+ *     direction in T+; T- is the other triangle (ed2el, Eq. ed2el);
+ *   - sigma = +1 on the T+ side of an edge and -1 on the T- side (psi_E, Sec. 3.2).
+ * Returns PHFEM_EMESH when a vertex id is out of range, a triangle is
+ * clockwise or degenerate, an edge lies in more than two triangles or twice in
+ * the same direction, a boundary edge is listed in neither or both lists or
+ * twice, or a listed pair is not a boundary edge.  The mesh handle copies xy
+ * and tri (the caller's arrays may be freed after the call). */
+PHFEM_API int phfem_mesh_build(phfem_ctx ctx, int32_t nV, const double* xy, int32_t nT,
+                               const int32_t* tri, int32_t nD, const int32_t* dirichlet,
+                               int32_t nN, const int32_t* neumann, phfem_mesh* out);
+PHFEM_API int phfem_mesh_info_get(phfem_mesh mesh, phfem_mesh_info* out);
+/* Copies tables into caller device buffers; any pointer may be NULL.
+ *   ed2el   [nE][4] int32  initial node, end node, T+, T- (-1 on the boundary)
+ *   t2e     [nT][3] int32  edge opposite local vertex k (E_{k+1})
+ *   sigma   [nT][3] int8   +1 if the triangle is T+ of that edge, else -1
+ *   eclass  [nE]    uint8  PHFEM_EDGE_INTERIOR / _DIRICHLET / _NEUMANN
+ *   free_id [nE]    int32  row of the edge in the free-edge system, -1 on Dirichlet
+ *   lam_id  [nE]    int32  index of the edge's multiplier (Redges order of
+ *                          Main.m: non-Neumann edges by increasing number), -1 on Neumann
+ *   row_ptr [nF+1]  int32  CSR row pointer of the free-edge system
+ *   col     [nnz]   int32  CSR columns (sorted in each row; every pair of free
+ *                          edges sharing a triangle, exact zeros kept) */
+PHFEM_API int phfem_mesh_tables(phfem_mesh mesh, int32_t* ed2el, int32_t* t2e, int8_t* sigma,
+                                uint8_t* eclass, int32_t* free_id, int32_t* lam_id,
+                                int32_t* row_ptr, int32_t* col);
+PHFEM_API int phfem_mesh_destroy(phfem_mesh mesh);
+
+/* ------------------------------------------------------------------------ */
+/* Assembly (Definition 3.1; Eqs. right_b, right_g, DirichletEqn; Sec. 3.5)  */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  const double* a_T;  /* [nT] per-triangle coefficient (A = a_T I), or NULL      */
+  double a;           /* coefficient used when a_T == NULL                       */
+  double delta;       /* reaction coefficient delta >= 0 (Eq. eq1)                */
+  double dt;          /* 0: elliptic; > 0: Crank-Nicolson matrix M + dt/2 K (Sec. 4) */
+  int32_t precision;  /* PHFEM_FP64 or PHFEM_FP32_IR (FP32 inner solve + FP64 refinement) */
+  int32_t reserved;
+} phfem_coeffs;
+
+/* Assembles, per triangle, the stiffness/reaction blocks of Definition 3.1
+ * condensed to the edge midpoints, K^CR_T = R^-T (a_T B_T + delta M_T) R^-1
+ * = a_T |T|^-1 (e_k . e_j) + delta |T|/3 I (e_k the edge vectors), and the
+ * edge right-hand side of the midpoint quadrature of Eqs. right_b/right_g:
+ *   rhs_e = sum_{T owning e} |T|/3 f(m_e) + [e Neumann] |E| g(m_e).
+ * Dirichlet values enter through the matrix (lifting) at solve time.
+ *   f_mid  [nE] double  f at the edge midpoints
+ *   bc_mid [nE] double  u_D(m_E) on Dirichlet edges, g(m_E) (outward normal
+ *                       flux) on Neumann edges, ignored elsewhere
+ * For dt > 0 the matrix is M^CR + dt/2 K^CR (M^CR = |T|/3 I per triangle) and
+ * f_mid/bc_mid may be NULL (the source comes with phfem_cn_create).
+ * Returns PHFEM_EINVAL for delta < 0, dt < 0 or a nonpositive a; PHFEM_ENAN
+ * when a coefficient is not finite. */
+PHFEM_API int phfem_assemble(phfem_mesh mesh, const phfem_coeffs* coeffs, const double* f_mid,
+                             const double* bc_mid, phfem_sys* out);
+/* The assembled free-edge system in CSR form (pattern of phfem_mesh_tables):
+ *   val [nnz] double  matrix values; rhs [nF] double  right-hand side with
+ *   the Dirichlet lifting applied.  Either pointer may be NULL. */
+PHFEM_API int phfem_sys_csr(phfem_sys sys, double* val, double* rhs);
+PHFEM_API int phfem_sys_destroy(phfem_sys sys);
+
+/* ------------------------------------------------------------------------ */
+/* Solve                                                                     */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+  double rtol;          /* stop when ||b - S w||_2 <= rtol ||b||_2 (FP64 S, free rows); 0 -> 1e-10 */
+  double inner_rtol;    /* reliable-update factor: the true FP64 residual replaces the
+                           recursive one whenever the latter fell by this factor;
+                           0 -> 0.1 (FP32_IR) or 0.01 (FP64)                       */
+  int32_t max_iter;     /* total inner iterations; 0 -> 200000                        */
+  int32_t max_refine;   /* outer refinement steps; 0 -> 40                            */
+  int32_t check_every;  /* inner iterations between host convergence checks; 0 -> 64  */
+  int32_t reserved;
+} phfem_solve_opts;
+
+typedef struct {
+  int32_t iterations;   /* conjugate-gradient iterations                            */
+  int32_t refinements;  /* FP64 residual evaluations (reliable updates)             */
+  int32_t converged;    /* 1: rtol met; 2: stopped at the FP64 floor (see below)   */
+  int32_t steps;        /* time steps done (phfem_cn_step)                          */
+  double rel_residual;  /* final ||b - S w|| / ||b|| in FP64 (difference form)      */
+  double seconds;       /* host wall time of the call                               */
+  double fp64_floor;    /* estimated ||b - S w|| / ||b|| that rounding w to FP64
+                           alone leaves: 2^-53 ||(|S| |w|)|| / ||b||              */
+} phfem_stats;
+
+/* Solves the condensed system by Jacobi-preconditioned conjugate gradients
+ * (FP64, or FP32 iterations with FP64-accumulated dot products whose residual
+ * is replaced by the true FP64 residual at every reliable update, the FP64
+ * solution accumulating the corrections), then recovers the paper's unknowns.
+ * The solve stops when rtol is met, or when the residual reaches twice the
+ * FP64 floor (converged = 2): on fine meshes b scales like h^2 while S does
+ * not, and below that level no FP64 vector w satisfies the system better.
+ *   w0     [nE] double  initial midpoint values (NULL = zero); Dirichlet
+ *                       entries are ignored (u_D is imposed)
+ *   w      [nE] double  out: midpoint values of u_h on every edge (or NULL)
+ *   U      [3 nT] double out: u_h at the vertices, element-major (3t + k;
+ *                       Wvec(1:N) of Main.m) (or NULL)
+ *   Lambda [nL] double  out: multipliers in Redges order (Wvec(N+1:N+L)) (or NULL)
+ * Recovery: u_T = R^-1 w_T and Lambda_E = (K^CR_T w_T - F^CR_T)_k / |E| read on
+ * the T+ side.  Blocks until the result is known (one host synchronisation
+ * per check).  Returns PHFEM_ENOCONV when the limits are reached (outputs are
+ * still written), PHFEM_EBREAKDOWN or PHFEM_ENAN on numerical failure. */
+PHFEM_API int phfem_solve(phfem_sys sys, const phfem_solve_opts* opts, const double* w0,
+                          double* w, double* U, double* Lambda, phfem_stats* stats);
+
+/* ------------------------------------------------------------------------ */
+/* Crank-Nicolson (Section 4, Eq. MatrixformParabolic)                       */
+/* ------------------------------------------------------------------------ */
+
+#define PHFEM_MAX_TERMS 4
+/* Source of separable form f(x, t) = sum_q phi_q(t) f_q(x) (same for u_D and g):
+ *   f_mid  [nterms][nE] double  f_q at the edge midpoints
+ *   bc_mid [nterms][nE] double  u_D,q on Dirichlet edges, g_q on Neumann edges
+ *   phi    host [nterms][nt] double  phi_q(t_n), t_n = n dt, n = 0 .. nt-1 */
+typedef struct {
+  int32_t nterms;
+  int32_t nt;
+  const double* f_mid;
+  const double* bc_mid;
+  const double* phi;
+} phfem_source;
+
+/* Starts a time integration with the system of phfem_assemble(dt > 0).
+ *   w0      [nE] double  u0 at the edge midpoints (U^0 = R^-1 w0 per element)
+ *   Lambda0 [nL] double  initial multipliers, or NULL for zero
+ * The source arrays are copied. */
+PHFEM_API int phfem_cn_create(phfem_sys sys, const phfem_source* src, const double* w0,
+                              const double* Lambda0, phfem_cn* out);
+/* Advances nsteps steps: per step the edge right-hand side
+ * (M - dt/2 K) w^{n-1} + dt (F^n + F^{n-1})/2 (trapezoid average of the
+ * sources, Sec. 4), the solve of (M + dt/2 K) w^n with w^n = u_D(t_n) on
+ * Dirichlet edges (warm start w^{n-1}), and the recovery of Lambda^{n-1/2}
+ * and Lambda^n = 2 Lambda^{n-1/2} - Lambda^{n-1}.  Fails with PHFEM_EINVAL if
+ * the source has no phi for a requested step. */
+PHFEM_API int phfem_cn_step(phfem_cn cn, int32_t nsteps, const phfem_solve_opts* opts,
+                            phfem_stats* stats);
+/* Reads the state after the last step (any pointer may be NULL):
+ *   w [nE], U [3 nT], Lambda_n [nL], Lambda_half [nL] (Lambda^{n-1/2}),
+ *   step: host int32, number of steps done. */
+PHFEM_API int phfem_cn_read(phfem_cn cn, double* w, double* U, double* Lambda_n,
+                            double* Lambda_half, int32_t* step);
+PHFEM_API int phfem_cn_destroy(phfem_cn cn);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PHFEM_H */

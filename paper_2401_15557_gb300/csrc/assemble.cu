@@ -1,0 +1,323 @@
+// Assembly of the condensed edge system (Definition 3.1 condensed to the edge
+// midpoints; Eqs. right_b, right_g) and its CSR export.
+//
+// With u_T = R^-1 w_T (R of Definition 3.1, R^-1 = J - 2I), the element block
+// a_T B_T + delta M_T becomes
+//     K^CR_T[k][j] = (a_T / |T|) e_k . e_j + delta |T|/3 [k == j]
+// where e_k = P_{k+2} - P_{k+1} is the edge vector opposite P_k (cyclic), since
+// |T| grad(lambda_k) . grad(lambda_j) = e_k . e_j / (4 |T|) and
+// R^-T M_T R^-1 = delta |T|/3 I.  The load |T|/3 sum_i f(m_i) R_i of Eq. right_b
+// becomes |T|/3 f(m_k) on edge k, and the Neumann term |E| g(m_E) R_k of
+// Eq. right_g becomes |E| g(m_E) on that edge.
+//
+// Two passes, none with atomics:
+//   k_asm_tri   one thread per triangle: geometry and the 6 distinct entries of
+//               K^CR_T (FP64), plus |T|/3;
+//   k_asm_rows  one thread per edge: its row = the rows of K^CR_{T+} and
+//               K^CR_{T-} at the edge (diagonal summed T+ then T-), the rhs, and
+//               the operator, in FP64 and in the inner precision, in difference form
+//                 (S p)_e = r_e p_e + sum_s l_es (p_e - p_s),  l_es = -S_es,
+//               with r_e the reaction/mass part of the diagonal.  The stiffness
+//               rows of K^CR sum to zero (e_0 + e_1 + e_2 = 0), so the diagonal
+//               is sum_s l_es + r_e exactly; storing l and r instead of S keeps
+//               constants in the kernel of the rounded operator, and rounding
+//               l and r to FP32 perturbs S by a relative 2^-24 in the energy
+//               norm whatever its condition number -- which is what lets the
+//               FP32 inner solve drive an FP64 refinement on fine meshes.
+#include <cmath>
+
+#include "internal.cuh"
+
+namespace phfem {
+namespace {
+
+__global__ void k_asm_tri(int nT, const int32_t* __restrict__ tri, const double2* __restrict__ xy,
+                          const double* __restrict__ aT, double a_const, double delta,
+                          double* __restrict__ Kt, int* __restrict__ bad) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nT; t += gridDim.x * blockDim.x) {
+    const int v0 = tri[3 * t], v1 = tri[3 * t + 1], v2 = tri[3 * t + 2];
+    const double2 p0 = __ldg(xy + v0), p1 = __ldg(xy + v1), p2 = __ldg(xy + v2);
+    const double a = aT ? aT[t] : a_const;
+    if (!(a > 0.0) || !isfinite(a)) atomicOr(bad, isfinite(a) ? 1 : 2);
+    const double e0x = p2.x - p1.x, e0y = p2.y - p1.y;
+    const double e1x = p0.x - p2.x, e1y = p0.y - p2.y;
+    const double e2x = p1.x - p0.x, e2y = p1.y - p0.y;
+    const double area2 = e1x * e2y - e1y * e2x;  // 2|T| = cross(P1 - P0, P2 - P0)
+    const double mT = area2 * (1.0 / 6.0);       // |T|/3
+    const double c = (a + a) / area2;            // a / |T|
+    const double dm = delta * mT;
+    const size_t n = (size_t)nT;
+    Kt[0 * n + t] = c * (e0x * e0x + e0y * e0y) + dm;
+    Kt[1 * n + t] = c * (e1x * e1x + e1y * e1y) + dm;
+    Kt[2 * n + t] = c * (e2x * e2x + e2y * e2y) + dm;
+    Kt[3 * n + t] = c * (e0x * e1x + e0y * e1y);
+    Kt[4 * n + t] = c * (e1x * e2x + e1y * e2y);
+    Kt[5 * n + t] = c * (e2x * e0x + e2y * e0y);
+    Kt[6 * n + t] = mT;
+  }
+}
+
+// Entries of row k of K^CR_T: diagonal, (k, k+1), (k, k+2).
+__device__ __forceinline__ void tri_row(const double* __restrict__ Kt, size_t n, int t, int k, double& d,
+                                        double& o1, double& o2, double& mT) {
+  const int k2 = (k == 0) ? 2 : k - 1;  // k + 2 mod 3
+  d = __ldg(Kt + (size_t)k * n + t);
+  o1 = __ldg(Kt + (size_t)(3 + k) * n + t);   // pair (k, k+1)
+  o2 = __ldg(Kt + (size_t)(3 + k2) * n + t);  // pair (k+2, k)
+  mT = __ldg(Kt + 6 * n + t);
+}
+
+// sK scales K^CR and sM the mass |T|/3 (elliptic: 1, 0; Crank-Nicolson: dt/2, 1).
+template <typename T>
+__global__ void k_asm_rows(int nE, int nT, const int32_t* __restrict__ ed2el, const uint8_t* __restrict__ lk,
+                           const uint8_t* __restrict__ eclass, const double* __restrict__ Kt,
+                           const double* __restrict__ f_mid, const double* __restrict__ bc_mid,
+                           const double* __restrict__ elen, double sK, double sM, double delta,
+                           double* __restrict__ val, double* __restrict__ b, double* __restrict__ me,
+                           T* __restrict__ lval, T* __restrict__ rdiag, T* __restrict__ dinv) {
+  const size_t n = (size_t)nT, m = (size_t)nE;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    const int4 q = reinterpret_cast<const int4*>(ed2el)[e];
+    const int tp = q.z, tm = q.w;
+    const int kk = lk[e];
+    double d, o1, o2, mT;
+    tri_row(Kt, n, tp, kk & 3, d, o1, o2, mT);
+    double diag = sK * d + sM * mT, v1 = sK * o1, v2 = sK * o2, v3 = 0.0, v4 = 0.0, mass = mT;
+    if (tm >= 0) {
+      tri_row(Kt, n, tm, (kk >> 2) & 3, d, o1, o2, mT);
+      diag += sK * d + sM * mT;
+      v3 = sK * o1;
+      v4 = sK * o2;
+      mass += mT;
+    }
+    const uint8_t cls = eclass[e];
+    double rhs, rpart;
+    if (cls == PHFEM_EDGE_DIRICHLET) {
+      diag = 1.0;
+      v1 = v2 = v3 = v4 = 0.0;
+      rhs = bc_mid ? bc_mid[e] : 0.0;
+      rpart = 1.0;
+    } else {
+      rhs = f_mid ? mass * f_mid[e] : 0.0;
+      if (cls == PHFEM_EDGE_NEUMANN && bc_mid) rhs += elen[e] * bc_mid[e];
+      rpart = (sK * delta + sM) * mass;
+    }
+    val[0 * m + e] = rpart;
+    val[1 * m + e] = -v1;
+    val[2 * m + e] = -v2;
+    val[3 * m + e] = -v3;
+    val[4 * m + e] = -v4;
+    b[e] = rhs;
+    me[e] = mass;
+    lval[0 * m + e] = (T)(-v1);
+    lval[1 * m + e] = (T)(-v2);
+    lval[2 * m + e] = (T)(-v3);
+    lval[3 * m + e] = (T)(-v4);
+    rdiag[e] = (T)rpart;
+    dinv[e] = (T)(1.0 / diag);
+  }
+}
+
+// CSR export of the free-edge system: the row of free edge e lists (column,
+// value) for e and its free neighbours, sorted by column; rhs subtracts the
+// Dirichlet couplings times u_D (the lifting).
+__global__ void k_export(int nE, const int32_t* __restrict__ nbr, const int32_t* __restrict__ free_id,
+                         const uint8_t* __restrict__ eclass, const int32_t* __restrict__ row_ptr,
+                         const double* __restrict__ val, const double* __restrict__ b, double* __restrict__ out_val,
+                         double* __restrict__ out_rhs) {
+  const size_t m = (size_t)nE;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    const int r = free_id[e];
+    if (r < 0) continue;
+    int c[5];
+    double v[5];
+    int len = 0;
+    double diag = val[e];  // r_e + sum of l_es over every neighbour slot
+    for (int s = 0; s < 4; ++s) diag += val[(s + 1) * m + e];
+    c[len] = r;
+    v[len++] = diag;
+    double rhs = b[e];
+    for (int s = 0; s < 4; ++s) {
+      const int n = nbr[s * m + e];
+      if (n == e) continue;
+      const double a = -val[(s + 1) * m + e];
+      const int f = free_id[n];
+      if (f >= 0) {
+        c[len] = f;
+        v[len++] = a;
+      } else if (eclass[n] == PHFEM_EDGE_DIRICHLET) {
+        rhs -= a * b[n];
+      }
+    }
+    for (int i = 1; i < len; ++i) {
+      int ck = c[i];
+      double vk = v[i];
+      int j = i - 1;
+      while (j >= 0 && c[j] > ck) {
+        c[j + 1] = c[j];
+        v[j + 1] = v[j];
+        --j;
+      }
+      c[j + 1] = ck;
+      v[j + 1] = vk;
+    }
+    if (out_val) {
+      const int base = row_ptr[r];
+      for (int i = 0; i < len; ++i) out_val[base + i] = v[i];
+    }
+    if (out_rhs) out_rhs[r] = rhs;
+  }
+}
+
+void sys_free(phfem_sys s) {
+  phfem_ctx c = s->mesh->ctx;
+  dfree(c, s->Kt);
+  dfree(c, s->val);
+  dfree(c, s->b);
+  dfree(c, s->me);
+  dfree(c, s->lval);
+  dfree(c, s->rdiag);
+  dfree(c, s->dinv);
+  dfree(c, s->f);
+  dfree(c, s->x);
+  dfree(c, s->r64);
+  dfree(c, s->xi);
+  dfree(c, s->ri);
+  dfree(c, s->pi);
+  dfree(c, s->qi);
+  dfree(c, s->partials);
+  dfree(c, s->st);
+  if (s->st_host) cudaFreeHost(s->st_host);
+  delete s;
+}
+
+}  // namespace
+
+// Runs the three assembly passes (also used to re-assemble in place).
+int assemble_into(phfem_sys sys, const double* f_mid, const double* bc_mid, int* d_bad) {
+  phfem_mesh m = sys->mesh;
+  phfem_ctx ctx = m->ctx;
+  cudaStream_t s = ctx->stream;
+  const int nT = m->info.nT, nE = m->info.nE;
+  const phfem_coeffs& c = sys->c;
+  prof_start(ctx, kProfAsmTri);
+  k_asm_tri<<<grid_for(ctx, nT), kBlock, 0, s>>>(nT, m->tri, reinterpret_cast<const double2*>(m->xy), c.a_T, c.a,
+                                                 c.delta, sys->Kt, d_bad);
+  prof_stop(ctx, kProfAsmTri);
+  PH_TRY(check_launch(ctx, "k_asm_tri"));
+  const double sK = c.dt > 0 ? 0.5 * c.dt : 1.0, sM = c.dt > 0 ? 1.0 : 0.0;
+  prof_start(ctx, kProfAsmRows);
+  if (sys->fp32)
+    k_asm_rows<float><<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, nT, m->ed2el, m->lk, m->eclass, sys->Kt, f_mid,
+                                                           bc_mid, m->elen, sK, sM, c.delta, sys->val, sys->b,
+                                                           sys->me, (float*)sys->lval, (float*)sys->rdiag,
+                                                           (float*)sys->dinv);
+  else
+    k_asm_rows<double><<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, nT, m->ed2el, m->lk, m->eclass, sys->Kt, f_mid,
+                                                            bc_mid, m->elen, sK, sM, c.delta, sys->val, sys->b,
+                                                            sys->me, (double*)sys->lval, (double*)sys->rdiag,
+                                                            (double*)sys->dinv);
+  prof_stop(ctx, kProfAsmRows);
+  return check_launch(ctx, "k_asm_rows");
+}
+
+}  // namespace phfem
+
+using namespace phfem;
+
+extern "C" {
+
+PHFEM_API int phfem_assemble(phfem_mesh mesh, const phfem_coeffs* coeffs, const double* f_mid,
+                             const double* bc_mid, phfem_sys* out) {
+  if (!out) return fail(PHFEM_EINVAL, "phfem_assemble: out is NULL");
+  *out = nullptr;
+  if (!mesh || !coeffs) return fail(PHFEM_EINVAL, "phfem_assemble: NULL argument");
+  const phfem_coeffs& c = *coeffs;
+  if (!(c.delta >= 0.0) || !(c.dt >= 0.0)) return fail(PHFEM_EINVAL, "phfem_assemble: delta and dt must be >= 0");
+  if (!c.a_T && !(c.a > 0.0)) return fail(PHFEM_EINVAL, "phfem_assemble: coefficient a must be > 0");
+  if (c.precision != PHFEM_FP64 && c.precision != PHFEM_FP32_IR)
+    return fail(PHFEM_EINVAL, "phfem_assemble: unknown precision");
+  if (c.delta == 0.0 && c.dt == 0.0 && mesh->info.nD == 0)
+    return fail(PHFEM_EINVAL, "phfem_assemble: no Dirichlet edge and no reaction term (singular system)");
+  if (!std::isfinite(c.delta) || !std::isfinite(c.dt) || (!c.a_T && !std::isfinite(c.a)))
+    return fail(PHFEM_ENAN, "phfem_assemble: non-finite coefficient");
+  phfem_ctx ctx = mesh->ctx;
+  cudaStream_t s = ctx->stream;
+  const size_t nT = mesh->info.nT, nE = mesh->info.nE;
+  phfem_sys sys = new phfem_sys_s();
+  sys->mesh = mesh;
+  sys->c = c;
+  sys->c.a_T = nullptr;  // the pointer is only valid during this call
+  sys->fp32 = c.precision == PHFEM_FP32_IR;
+  const size_t isz = sys->fp32 ? sizeof(float) : sizeof(double);
+  int st = PHFEM_OK;
+  int* d_bad = nullptr;
+  auto chk = [&](int r) {
+    if (st == PHFEM_OK) st = r;
+  };
+  chk(dalloc_n(ctx, &sys->Kt, 7 * nT));
+  chk(dalloc_n(ctx, &sys->val, 5 * nE));
+  chk(dalloc_n(ctx, &sys->b, nE));
+  chk(dalloc_n(ctx, &sys->me, nE));
+  chk(dalloc(ctx, &sys->lval, 4 * nE * isz));
+  chk(dalloc(ctx, &sys->rdiag, nE * isz));
+  chk(dalloc(ctx, &sys->dinv, nE * isz));
+  chk(dalloc_n(ctx, &sys->f, nE));
+  chk(dalloc_n(ctx, &sys->x, nE));
+  chk(dalloc_n(ctx, &sys->r64, nE));
+  chk(dalloc(ctx, &sys->xi, nE * isz));
+  chk(dalloc(ctx, &sys->ri, nE * isz));
+  chk(dalloc(ctx, &sys->pi, nE * isz));
+  chk(dalloc(ctx, &sys->qi, nE * isz));
+  chk(dalloc_n(ctx, &sys->partials, 4 * (size_t)kMaxGrid));
+  chk(dalloc_n(ctx, &sys->st, 1));
+  chk(dalloc_n(ctx, &d_bad, 1));
+  if (st == PHFEM_OK && cudaMallocHost((void**)&sys->st_host, sizeof(SolveState)) != cudaSuccess) {
+    cudaGetLastError();
+    sys->st_host = nullptr;
+    st = fail(PHFEM_ENOMEM, "phfem_assemble: pinned host allocation failed");
+  }
+  if (st == PHFEM_OK) {
+    cudaMemsetAsync(sys->st, 0, sizeof(SolveState), s);
+    cudaMemsetAsync(d_bad, 0, sizeof(int), s);
+    if (f_mid) cudaMemcpyAsync(sys->f, f_mid, nE * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    else cudaMemsetAsync(sys->f, 0, nE * sizeof(double), s);
+    sys->c.a_T = c.a_T;
+    st = assemble_into(sys, f_mid, bc_mid, d_bad);
+    sys->c.a_T = nullptr;
+  }
+  if (st == PHFEM_OK) {
+    int bad = 0;
+    cudaError_t e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "phfem_assemble", __FILE__, __LINE__);
+    else if (bad & 2) st = fail(PHFEM_ENAN, "phfem_assemble: non-finite coefficient a_T");
+    else if (bad & 1) st = fail(PHFEM_EINVAL, "phfem_assemble: coefficient a_T must be > 0");
+  }
+  dfree(ctx, d_bad);
+  if (st != PHFEM_OK) {
+    cudaStreamSynchronize(s);
+    sys_free(sys);
+    return st;
+  }
+  *out = sys;
+  return PHFEM_OK;
+}
+
+PHFEM_API int phfem_sys_csr(phfem_sys sys, double* val, double* rhs) {
+  if (!sys) return fail(PHFEM_EINVAL, "phfem_sys_csr: NULL system");
+  phfem_mesh m = sys->mesh;
+  phfem_ctx ctx = m->ctx;
+  const int nE = m->info.nE;
+  k_export<<<grid_for(ctx, nE), kBlock, 0, ctx->stream>>>(nE, m->nbr, m->free_id, m->eclass, m->row_ptr, sys->val,
+                                                          sys->b, val, rhs);
+  return check_launch(ctx, "k_export");
+}
+
+PHFEM_API int phfem_sys_destroy(phfem_sys sys) {
+  if (!sys) return fail(PHFEM_EINVAL, "phfem_sys_destroy: NULL system");
+  sys_free(sys);
+  return PHFEM_OK;
+}
+
+}  // extern "C"

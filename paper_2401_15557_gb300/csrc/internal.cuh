@@ -1,0 +1,197 @@
+// Internal declarations of the sm_103a primal hybrid FEM library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "phfem.h"
+
+namespace phfem {
+
+constexpr int kBlock = 256;          // threads per block of every grid-stride kernel
+constexpr int kBlocksPerSM = 8;      // resident blocks per SM targeted by the grids
+constexpr int kMaxGrid = 152 * 16;   // upper bound of reduction partials per reduction
+
+// Error plumbing ------------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int status, const std::string& msg);
+int cuda_fail(cudaError_t err, const char* what, const char* file, int line);
+
+#define PH_CUDA(call)                                                          \
+  do {                                                                         \
+    cudaError_t _e = (call);                                                   \
+    if (_e != cudaSuccess) return ::phfem::cuda_fail(_e, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define PH_TRY(call)                \
+  do {                              \
+    int _s = (call);                \
+    if (_s != PHFEM_OK) return _s;  \
+  } while (0)
+
+// Device-visible status word of a multi-kernel computation.
+struct DevStatus {
+  int code;      // 0 ok, else a negative phfem_status
+  int index;     // first offending index (for messages)
+  int detail;    // extra information
+  int pad;
+};
+
+// Scalar state of one conjugate-gradient solve (device resident).
+struct SolveState {
+  double rz;       // r.r of the current inner residual (unit-diagonal system)
+  double rz0;      // r.r at the start of the inner solve
+  double tol2;     // inner stopping threshold on rz
+  double alpha, beta;
+  double rr64;     // ||b - S x||^2 of the outer FP64 residual
+  double bb;       // ||b||^2 of the free-edge system (with lifting)
+  double floor2;   // squared estimate of the residual that rounding x to FP64 alone leaves
+  int it;          // inner iterations done
+  int done;        // 1: inner converged, 2: outer converged, 3: failure
+  int status;      // phfem_status of a failure
+  int dir_pending; // set by the update kernel, cleared by the next SpMV: gates the direction kernel
+  unsigned int counter[4];  // last-block counters of the reductions
+};
+
+}  // namespace phfem
+
+namespace phfem {
+// Kernels whose launches can be timed with CUDA events (phfem_ctx_profile).
+enum ProfKernel { kProfSpmv = 0, kProfUpdate, kProfDir, kProfResidual, kProfAsmTri, kProfAsmRows,
+                  kProfRecover, kNumProf };
+struct ProfSlot {
+  std::vector<cudaEvent_t> ev;  // start/stop pairs
+  size_t used = 0;
+};
+}  // namespace phfem
+
+// Handles --------------------------------------------------------------------
+struct phfem_ctx_s {
+  cudaStream_t stream;
+  int device;
+  int num_sms;
+  int grid;              // blocks of the grid-stride kernels
+  int64_t launches;
+  bool profile = false;
+  phfem::ProfSlot prof[phfem::kNumProf];
+};
+
+struct phfem_mesh_s {
+  phfem_ctx ctx;
+  phfem_mesh_info info;
+  double* xy;            // [nV][2]
+  int32_t* tri;          // [nT][3]
+  int32_t* ed2el;        // [nE][4]
+  int32_t* t2e;          // [nT][3]
+  int8_t* sigma;         // [nT][3]
+  uint8_t* eclass;       // [nE]
+  uint8_t* lk;           // [nE]: local index of the edge in T+ | (in T-) << 2
+  int32_t* free_id;      // [nE]
+  int32_t* lam_id;       // [nE]
+  int32_t* nbr;          // [4][nE] neighbour edges: T+ (k+1, k+2), T- (k+1, k+2); self if absent
+  double* elen;          // [nE] edge lengths
+  int32_t* row_ptr;      // [nF + 1]
+  int32_t* col;          // [nnz]
+};
+
+struct phfem_sys_s {
+  phfem_mesh mesh;
+  phfem_coeffs c;
+  bool fp32;
+  double* Kt;            // [7][nT]: K^CR_T entries (00, 11, 22, 01, 12, 20) and |T|/3
+  double* val;           // [5][nE]: FP64 row in difference form: slot 0 = r_e (reaction/mass
+                         //          part of the diagonal), slots 1..4 = l_es = -S_{e,nbr_s}
+  double* b;             // [nE]: right-hand side; u_D on Dirichlet rows
+  double* me;            // [nE]: mass diagonal sum_T |T|/3
+  // inner operator in difference form (float or double):
+  //   (S p)_e = rdiag_e p_e + sum_s lval[s][e] (p_e - p[nbr[s][e]])
+  void* lval;            // [4][nE]: -S_{e, nbr_s}
+  void* rdiag;           // [nE]: row sum (reaction / mass part)
+  void* dinv;            // [nE]: 1 / S_ee (Jacobi)
+  double* f;             // [nE]: copy of f at the midpoints (elliptic recovery)
+  // solver workspace
+  double* x;             // [nE] current midpoint values (FP64)
+  double* r64;           // [nE]
+  void* xi;              // [nE] inner vectors (float or double)
+  void* ri;
+  void* pi;
+  void* qi;
+  double* partials;      // [4][kMaxGrid]
+  phfem::SolveState* st;       // device
+  phfem::SolveState* st_host;  // pinned host mirror
+};
+
+namespace phfem {
+
+// Allocation on the context stream (stream-ordered allocator).
+int dalloc(phfem_ctx ctx, void** p, size_t bytes);
+void dfree(phfem_ctx ctx, void* p);
+template <typename T>
+int dalloc_n(phfem_ctx ctx, T** p, size_t n) {
+  return dalloc(ctx, reinterpret_cast<void**>(p), n * sizeof(T) + (n == 0 ? 16 : 0));
+}
+
+int grid_for(phfem_ctx ctx, int64_t n);
+// Event pair around one launch of kernel k when profiling is on (no-op otherwise).
+void prof_start(phfem_ctx ctx, int k);
+void prof_stop(phfem_ctx ctx, int k);
+int check_launch(phfem_ctx ctx, const char* what);
+
+// Device-wide exclusive scan of int32 (out may alias in); returns the total
+// through *total_dev (device int) if non-NULL.
+int exclusive_scan(phfem_ctx ctx, const int32_t* in, int32_t* out, int n, int32_t* total_dev);
+
+// Solve helpers shared by the elliptic and Crank-Nicolson drivers.
+int solve_system(phfem_sys sys, const phfem_solve_opts* opts, phfem_stats* stats, bool warm);
+int sys_init_x(phfem_sys sys, const double* w0);
+int recover(phfem_sys sys, const double* x_new, const double* x_old, const double* f_eff,
+            double inv_dt, double theta, double* U, double* Lambda);
+
+// Device helpers ---------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of v (blockDim.x == kBlock); result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v, double* smem) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) smem[w] = v;
+  __syncthreads();
+  v = 0.0;
+  if (w == 0) {
+    v = (lane < kBlock / 32) ? smem[lane] : 0.0;
+    v = warp_sum(v);
+  }
+  __syncthreads();
+  return v;
+}
+
+// Call after thread 0 wrote this block's partial(s): reports whether this is
+// the last block to finish.  The last block can then read every partial (in a
+// fixed order, hence a deterministic result) and must reset *counter to 0.
+__device__ __forceinline__ bool arrive_last(unsigned int* counter) {
+  __shared__ bool am_last;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    unsigned int t = atomicAdd(counter, 1u);
+    am_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last;
+}
+
+// Sum of the partials in fixed order by the last block; result in thread 0.
+__device__ __forceinline__ double sum_partials(const double* partials, double* smem) {
+  double v = 0.0;
+  for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) v += __ldcg(partials + i);
+  return block_sum(v, smem);
+}
+
+}  // namespace phfem

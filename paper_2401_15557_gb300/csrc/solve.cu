@@ -1,0 +1,453 @@
+// Jacobi-preconditioned conjugate gradients on the condensed edge system,
+// with an FP64 iterative refinement around FP32 (or FP64) inner iterations,
+// and the recovery of the paper's unknowns U and Lambda (Wvec of Main.m).
+//
+// The system is stored per edge row (all nE edges; Dirichlet rows are identity
+// rows holding u_D) in difference form (S p)_e = r_e p_e + sum_s l_es (p_e -
+// p[nbr_s]) with l_es = -S_{e,nbr_s} and r_e the reaction/mass part of the
+// diagonal: in FP64 (val[5][nE]) for the outer residual, and in the inner
+// precision with the Jacobi inverse diagonal for the inner iterations.  The inner search direction is
+// zero on Dirichlet rows, so the Dirichlet columns (kept in the free rows for
+// the lifting) never act inside the iteration.
+//
+// Jacobi-PCG with reliable updates: the iteration runs on the correction d
+// (FP32 vectors with FP64-accumulated dot products, or FP64) from the FP64
+// solution x.  Whenever the recursive residual has fallen by the factor
+// inner_rtol since the last update, x += d (FP64), the true residual
+// r = b - S x is recomputed in FP64 (difference form) and replaces the
+// recursive one while the search direction is kept, so the Krylov space is
+// not lost as in restarted refinement.  The solve stops when
+// ||r|| <= rtol ||b_free||, or when ||r|| reaches the level that rounding x to
+// FP64 alone leaves (estimated from |l| |x| per row), which on fine meshes can
+// exceed rtol because b scales like h^2 while S does not.
+// Every kernel is a grid-stride loop; reductions write one partial per block
+// and the last block to arrive sums the partials in a fixed order
+// (deterministic results, no floating-point atomics).
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+
+#include "internal.cuh"
+
+namespace phfem {
+namespace {
+
+// r = b - S x (FP64); inner start vectors r' = r, p = D^-1 r', d = 0; two
+// reductions (||r||^2 and r'.D^-1 r').  mode 0 replaces x by (0 on free rows,
+// u_D on Dirichlet rows): ||b_free||^2 with the Dirichlet lifting.
+// mode 1 starts the iteration (p = D^-1 r); mode 2 is a reliable update (p kept).
+template <typename T>
+__global__ void k_residual(int nE, const int32_t* __restrict__ nbr, const double* __restrict__ val,
+                           const double* __restrict__ b, const double* __restrict__ x,
+                           const uint8_t* __restrict__ eclass, const T* __restrict__ dinv,
+                           T* __restrict__ xi, T* __restrict__ ri, T* __restrict__ pi, double* partials,
+                           SolveState* st, double rtol2, double inner_rtol2, int mode) {
+  __shared__ double smem[kBlock / 32];
+  const size_t m = (size_t)nE;
+  double acc_r = 0.0, acc_z = 0.0, acc_f = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    double r;
+    if (mode == 0) {
+      if (eclass[e] == PHFEM_EDGE_DIRICHLET) {
+        r = 0.0;
+      } else {
+        r = b[e];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+          const int c = nbr[s * m + e];
+          if (c != e && eclass[c] == PHFEM_EDGE_DIRICHLET) r += val[(s + 1) * m + e] * b[c];
+        }
+      }
+      acc_r += r * r;
+    } else {
+      // difference form: S x = r_e x_e + sum_s l_es (x_e - x_s); the differences
+      // of nearby values are exact or nearly so, which keeps the FP64 residual
+      // accurate where the naive row product would cancel ~1/h^2 digits
+      const double xe = x[e];
+      double sx = val[e] * xe;
+      double fl = fabs(val[e] * xe);  // |S| |x| of the row: scale of the FP64 rounding of x
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        const double l = val[(s + 1) * m + e], xs = x[nbr[s * m + e]];
+        sx += l * (xe - xs);
+        fl += fabs(l) * (fabs(xe) + fabs(xs));
+      }
+      r = b[e] - sx;
+      acc_r += r * r;
+      fl *= 0x1p-53;
+      acc_f += fl * fl;
+      const T rs = (T)r;
+      const T zs = dinv[e] * rs;
+      ri[e] = rs;
+      if (mode == 1) pi[e] = zs;
+      xi[e] = (T)0;
+      acc_z += (double)rs * (double)zs;
+    }
+  }
+  acc_r = block_sum(acc_r, smem);
+  acc_z = block_sum(acc_z, smem);
+  acc_f = block_sum(acc_f, smem);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = acc_r;
+    partials[kMaxGrid + blockIdx.x] = acc_z;
+    partials[2 * kMaxGrid + blockIdx.x] = acc_f;
+  }
+  if (!arrive_last(&st->counter[0])) return;
+  const double rr = sum_partials(partials, smem);
+  const double rz = sum_partials(partials + kMaxGrid, smem);
+  const double ff = sum_partials(partials + 2 * kMaxGrid, smem);
+  if (threadIdx.x == 0) {
+    st->counter[0] = 0;
+    if (mode == 0) {
+      st->bb = rr;
+    } else {
+      st->rr64 = rr;
+      st->floor2 = ff;
+      st->rz = rz;
+      if (mode == 1) {
+        st->rz0 = rz;
+        st->it = 0;
+      }
+      st->tol2 = inner_rtol2 * rz;
+      st->status = 0;
+      if (!isfinite(rr) || !isfinite(rz)) {
+        st->done = 3;
+        st->status = PHFEM_ENAN;
+      } else {
+        st->done = (rr <= rtol2 * st->bb) ? 2 : 0;
+      }
+    }
+  }
+}
+
+// q = S p in difference form, p.q -> alpha = rz / p.q
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cg_spmv(int nE, const int32_t* __restrict__ nbr,
+                                                    const T* __restrict__ lval, const T* __restrict__ rdiag,
+                                                    const T* __restrict__ p, T* __restrict__ q, double* partials,
+                                                    SolveState* st) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->dir_pending = 0;  // no block of this kernel reads it
+  if (st->done) return;
+  __shared__ double smem[kBlock / 32];
+  const size_t m = (size_t)nE;
+  double acc = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    const int c0 = nbr[e], c1 = nbr[m + e], c2 = nbr[2 * m + e], c3 = nbr[3 * m + e];
+    const T l0 = lval[e], l1 = lval[m + e], l2 = lval[2 * m + e], l3 = lval[3 * m + e];
+    const T pe = p[e];
+    T s = rdiag[e] * pe;
+    s += l0 * (pe - __ldg(p + c0));
+    s += l1 * (pe - __ldg(p + c1));
+    s += l2 * (pe - __ldg(p + c2));
+    s += l3 * (pe - __ldg(p + c3));
+    q[e] = s;
+    acc += (double)pe * (double)s;
+  }
+  acc = block_sum(acc, smem);
+  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  if (!arrive_last(&st->counter[1])) return;
+  const double pq = sum_partials(partials, smem);
+  if (threadIdx.x == 0) {
+    st->counter[1] = 0;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      st->done = 3;
+      st->status = isfinite(pq) ? PHFEM_EBREAKDOWN : PHFEM_ENAN;
+    } else {
+      st->alpha = st->rz / pq;
+    }
+  }
+}
+
+// x += alpha p, r -= alpha q, r.D^-1 r -> beta
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cg_update(int nE, T* __restrict__ x, const T* __restrict__ p,
+                                                      T* __restrict__ r, const T* __restrict__ q,
+                                                      const T* __restrict__ dinv, double* partials,
+                                                      SolveState* st) {
+  if (st->done) return;
+  __shared__ double smem[kBlock / 32];
+  const T alpha = (T)st->alpha;
+  double acc = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    x[e] += alpha * p[e];
+    const T re = r[e] - alpha * q[e];
+    r[e] = re;
+    acc += (double)re * (double)(dinv[e] * re);
+  }
+  acc = block_sum(acc, smem);
+  if (threadIdx.x == 0) partials[kMaxGrid + blockIdx.x] = acc;
+  if (!arrive_last(&st->counter[2])) return;
+  const double rz = sum_partials(partials + kMaxGrid, smem);
+  if (threadIdx.x == 0) {
+    st->counter[2] = 0;
+    st->beta = rz / st->rz;
+    st->rz = rz;
+    st->it += 1;
+    st->dir_pending = 1;
+    if (!isfinite(rz)) {
+      st->done = 3;
+      st->status = PHFEM_ENAN;
+    }
+  }
+}
+
+// p = D^-1 r + beta p; then the test of the recursive residual, so that the
+// direction is always complete when the iteration pauses for an update.  The
+// kernel runs only after an update kernel that did run (dir_pending), and the
+// done flag it sets is read only by later kernels.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cg_dir(int nE, const T* __restrict__ r, const T* __restrict__ dinv,
+                                                   T* __restrict__ p, SolveState* st) {
+  if (!st->dir_pending) return;
+  const T beta = (T)st->beta;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x)
+    p[e] = dinv[e] * r[e] + beta * p[e];
+  if (blockIdx.x == 0 && threadIdx.x == 0 && st->done == 0 && st->rz <= st->tol2) st->done = 1;
+}
+
+// Restart of the direction after a reliable update whose true residual is far
+// from the recursive one (the kept direction would no longer fit it).
+template <typename T>
+__global__ void k_cg_restart(int nE, const T* __restrict__ r, const T* __restrict__ dinv, T* __restrict__ p) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) p[e] = dinv[e] * r[e];
+}
+
+template <typename T>
+__global__ void k_ir_update(int nE, const T* __restrict__ xi, double* __restrict__ x) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x)
+    x[e] += (double)xi[e];
+}
+
+__global__ void k_init_x(int nE, const uint8_t* __restrict__ eclass, const double* __restrict__ b,
+                         const double* __restrict__ w0, double* __restrict__ x) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x)
+    x[e] = (eclass[e] == PHFEM_EDGE_DIRICHLET) ? b[e] : (w0 ? w0[e] : 0.0);
+}
+
+// U = R^-1 w per triangle (u at the vertices); with Lambda: the element row
+// residual mT (wa - wb)/dt + K^CR_T (theta wa + (1 - theta) wb) - mT f, divided
+// by |E_k|, on the T+ side of every multiplier edge.
+__global__ void k_recover(int nT, const int32_t* __restrict__ t2e, const int8_t* __restrict__ sigma,
+                          const int32_t* __restrict__ lam_id, const double* __restrict__ Kt,
+                          const double* __restrict__ elen, const double* __restrict__ wa,
+                          const double* __restrict__ wb, const double* __restrict__ f, double inv_dt,
+                          double theta, double* __restrict__ U, double* __restrict__ Lambda) {
+  const size_t n = (size_t)nT;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nT; t += gridDim.x * blockDim.x) {
+    const int e0 = t2e[3 * t], e1 = t2e[3 * t + 1], e2 = t2e[3 * t + 2];
+    const double a0 = wa[e0], a1 = wa[e1], a2 = wa[e2];
+    if (U) {
+      const double s = a0 + a1 + a2;
+      U[3 * t] = s - 2.0 * a0;
+      U[3 * t + 1] = s - 2.0 * a1;
+      U[3 * t + 2] = s - 2.0 * a2;
+    }
+    if (!Lambda) continue;
+    double b0 = 0.0, b1 = 0.0, b2 = 0.0;
+    if (wb) {
+      b0 = wb[e0];
+      b1 = wb[e1];
+      b2 = wb[e2];
+    }
+    const double m0 = theta * a0 + (1.0 - theta) * b0;
+    const double m1 = theta * a1 + (1.0 - theta) * b1;
+    const double m2 = theta * a2 + (1.0 - theta) * b2;
+    const double K00 = Kt[t], K11 = Kt[n + t], K22 = Kt[2 * n + t];
+    const double K01 = Kt[3 * n + t], K12 = Kt[4 * n + t], K20 = Kt[5 * n + t], mT = Kt[6 * n + t];
+    const double res[3] = {K00 * m0 + K01 * m1 + K20 * m2, K01 * m0 + K11 * m1 + K12 * m2,
+                           K20 * m0 + K12 * m1 + K22 * m2};
+    const double dw[3] = {a0 - b0, a1 - b1, a2 - b2};
+    const int ee[3] = {e0, e1, e2};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int li = lam_id[ee[k]];
+      if (li < 0 || sigma[3 * t + k] < 0) continue;
+      double r = res[k] - mT * (f ? f[ee[k]] : 0.0);
+      if (inv_dt > 0.0) r += mT * inv_dt * dw[k];
+      Lambda[li] = r / elen[ee[k]];
+    }
+  }
+}
+
+int read_state(phfem_sys sys) {
+  cudaStream_t s = sys->mesh->ctx->stream;
+  PH_CUDA(cudaMemcpyAsync(sys->st_host, sys->st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+  PH_CUDA(cudaStreamSynchronize(s));
+  return PHFEM_OK;
+}
+
+template <typename T>
+int solve_typed(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats) {
+  phfem_mesh m = sys->mesh;
+  phfem_ctx ctx = m->ctx;
+  cudaStream_t s = ctx->stream;
+  const int nE = m->info.nE;
+  const int g = grid_for(ctx, nE);
+  T* xi = (T*)sys->xi;
+  T* ri = (T*)sys->ri;
+  T* pi = (T*)sys->pi;
+  T* qi = (T*)sys->qi;
+  const T* lval = (const T*)sys->lval;
+  const T* rdiag = (const T*)sys->rdiag;
+  const T* dinv = (const T*)sys->dinv;
+  const double rtol2 = o.rtol * o.rtol, irtol2 = o.inner_rtol * o.inner_rtol;
+  static const bool verbose = getenv("PHFEM_VERBOSE") != nullptr;
+  auto residual = [&](int mode) -> int {
+    prof_start(ctx, kProfResidual);
+    k_residual<T><<<g, kBlock, 0, s>>>(nE, m->nbr, sys->val, sys->b, sys->x, m->eclass, dinv, xi, ri, pi,
+                                       sys->partials, sys->st, rtol2, irtol2, mode);
+    prof_stop(ctx, kProfResidual);
+    return check_launch(ctx, "k_residual");
+  };
+  // ||b|| of the free-edge system (with the Dirichlet lifting), then the start
+  PH_TRY(residual(0));
+  PH_TRY(residual(1));
+  int iters = 0, updates = 1, converged = 0, status = PHFEM_OK, stagnant = 0, restarts = 0;
+  double rel = 0.0, best = 1e300;
+  PH_TRY(read_state(sys));
+  for (;;) {
+    const SolveState& h = *sys->st_host;
+    if (h.done == 3) {
+      status = h.status;
+      break;
+    }
+    rel = h.bb > 0 ? std::sqrt(h.rr64 / h.bb) : 0.0;
+    const double floor_rel = h.bb > 0 ? std::sqrt(h.floor2 / h.bb) : 0.0;
+    if (verbose)
+      fprintf(stderr, "phfem: update %d  iterations %d  relative residual %.3e  fp64 floor %.3e  restarts %d\n",
+              updates, iters, rel, floor_rel, restarts);
+    if (h.rr64 <= rtol2 * h.bb || h.rr64 == 0.0) {
+      converged = 1;
+      break;
+    }
+    // at the level where rounding x to FP64 dominates, further work cannot help
+    if (rel <= 2.0 * floor_rel) {
+      converged = 2;
+      break;
+    }
+    stagnant = (rel > 0.5 * best) ? stagnant + 1 : 0;
+    best = rel < best ? rel : best;
+    if (iters >= o.max_iter || updates > o.max_refine || stagnant >= 8) {
+      status = PHFEM_ENOCONV;
+      break;
+    }
+    // iterate until the recursive residual fell by inner_rtol (or the limits)
+    int run = sys->st_host->it;
+    for (;;) {
+      int chunk = o.check_every;
+      if (iters + chunk > o.max_iter) chunk = o.max_iter - iters;
+      if (chunk <= 0) break;
+      for (int k = 0; k < chunk; ++k) {
+        prof_start(ctx, kProfSpmv);
+        k_cg_spmv<T><<<g, kBlock, 0, s>>>(nE, m->nbr, lval, rdiag, pi, qi, sys->partials, sys->st);
+        prof_stop(ctx, kProfSpmv);
+        prof_start(ctx, kProfUpdate);
+        k_cg_update<T><<<g, kBlock, 0, s>>>(nE, xi, pi, ri, qi, dinv, sys->partials, sys->st);
+        prof_stop(ctx, kProfUpdate);
+        prof_start(ctx, kProfDir);
+        k_cg_dir<T><<<g, kBlock, 0, s>>>(nE, ri, dinv, pi, sys->st);
+        prof_stop(ctx, kProfDir);
+        ctx->launches += 2;
+        PH_TRY(check_launch(ctx, "k_cg"));
+      }
+      PH_TRY(read_state(sys));
+      const int done_it = sys->st_host->it - run;
+      run = sys->st_host->it;
+      iters += done_it;
+      if (sys->st_host->done || iters >= o.max_iter) break;
+    }
+    if (sys->st_host->done == 3) {
+      status = sys->st_host->status;
+      break;
+    }
+    // reliable update: fold the correction into x, recompute the true residual
+    const double rz_recursive = sys->st_host->rz;
+    k_ir_update<T><<<g, kBlock, 0, s>>>(nE, xi, sys->x);
+    PH_TRY(check_launch(ctx, "k_ir_update"));
+    PH_TRY(residual(2));
+    ++updates;
+    PH_TRY(read_state(sys));
+    if (sys->st_host->done == 0 && sys->st_host->rz > 4.0 * rz_recursive) {
+      k_cg_restart<T><<<g, kBlock, 0, s>>>(nE, ri, dinv, pi);
+      PH_TRY(check_launch(ctx, "k_cg_restart"));
+      ++restarts;
+    }
+  }
+  if (stats) {
+    stats->iterations += iters;
+    stats->refinements += updates;
+    stats->converged = converged;
+    stats->rel_residual = rel;
+    const SolveState& h = *sys->st_host;
+    stats->fp64_floor = h.bb > 0 ? std::sqrt(h.floor2 / h.bb) : 0.0;
+  }
+  if (status != PHFEM_OK) {
+    char buf[200];
+    snprintf(buf, sizeof(buf), "solve: %s after %d iterations, %d residual updates, relative residual %.3e",
+             phfem_status_str(status), iters, updates, rel);
+    return fail(status, buf);
+  }
+  return PHFEM_OK;
+}
+
+}  // namespace
+
+int sys_init_x(phfem_sys sys, const double* w0) {
+  phfem_mesh m = sys->mesh;
+  phfem_ctx ctx = m->ctx;
+  const int nE = m->info.nE;
+  k_init_x<<<grid_for(ctx, nE), kBlock, 0, ctx->stream>>>(nE, m->eclass, sys->b, w0, sys->x);
+  return check_launch(ctx, "k_init_x");
+}
+
+int solve_system(phfem_sys sys, const phfem_solve_opts* opts, phfem_stats* stats, bool /*warm*/) {
+  phfem_solve_opts o{};
+  if (opts) o = *opts;
+  if (o.rtol <= 0) o.rtol = 1e-10;
+  if (o.inner_rtol <= 0) o.inner_rtol = sys->fp32 ? 0.1 : 0.01;
+  if (o.max_iter <= 0) o.max_iter = 200000;
+  if (o.max_refine <= 0) o.max_refine = 1000;
+  if (o.check_every <= 0) o.check_every = 64;
+  return sys->fp32 ? solve_typed<float>(sys, o, stats) : solve_typed<double>(sys, o, stats);
+}
+
+int recover(phfem_sys sys, const double* x_new, const double* x_old, const double* f_eff, double inv_dt,
+            double theta, double* U, double* Lambda) {
+  phfem_mesh m = sys->mesh;
+  phfem_ctx ctx = m->ctx;
+  const int nT = m->info.nT;
+  if (!U && !Lambda) return PHFEM_OK;
+  prof_start(ctx, kProfRecover);
+  k_recover<<<grid_for(ctx, nT), kBlock, 0, ctx->stream>>>(nT, m->t2e, m->sigma, m->lam_id, sys->Kt, m->elen,
+                                                           x_new, x_old, f_eff, inv_dt, theta, U, Lambda);
+  prof_stop(ctx, kProfRecover);
+  return check_launch(ctx, "k_recover");
+}
+
+}  // namespace phfem
+
+using namespace phfem;
+
+extern "C" {
+
+PHFEM_API int phfem_solve(phfem_sys sys, const phfem_solve_opts* opts, const double* w0, double* w, double* U,
+                          double* Lambda, phfem_stats* stats) {
+  if (!sys) return fail(PHFEM_EINVAL, "phfem_solve: NULL system");
+  auto t0 = std::chrono::steady_clock::now();
+  phfem_stats st{};
+  PH_TRY(sys_init_x(sys, w0));
+  int status = solve_system(sys, opts, &st, false);
+  if (status == PHFEM_OK || status == PHFEM_ENOCONV) {
+    phfem_mesh m = sys->mesh;
+    cudaStream_t s = m->ctx->stream;
+    if (w) PH_CUDA(cudaMemcpyAsync(w, sys->x, sizeof(double) * m->info.nE, cudaMemcpyDeviceToDevice, s));
+    PH_TRY(recover(sys, sys->x, nullptr, sys->f, 0.0, 1.0, U, Lambda));
+    PH_CUDA(cudaStreamSynchronize(s));
+  }
+  st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = st;
+  return status;
+}
+
+}  // extern "C"

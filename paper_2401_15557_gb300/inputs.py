@@ -168,15 +168,16 @@ def red_refine(m: Mesh) -> Mesh:
     out[nT + 1::3] = np.stack([P2, M1, M3], axis=1)
     out[nT + 2::3] = np.stack([P3, M2, M1], axis=1)
 
-    lookup = {int(k): int(i) for i, k in enumerate(ukey)}
-
     def refine_edges(pairs):
         if len(pairs) == 0:
             return _as_pairs([])
         pairs = pairs.astype(np.int64)
         a, b = pairs[:, 0], pairs[:, 1]
         k = np.minimum(a, b) * nV + np.maximum(a, b)
-        mid = np.array([nV + lookup[int(x)] for x in k], dtype=np.int64)
+        pos = np.searchsorted(ukey, k)
+        if np.any(pos >= ukey.size) or np.any(ukey[np.minimum(pos, ukey.size - 1)] != k):
+            raise ValueError("a boundary pair is not an edge of the mesh")
+        mid = nV + pos
         return _as_pairs(np.concatenate([np.stack([a, mid], 1), np.stack([mid, b], 1)], 0))
 
     meta = dict(m.meta)
@@ -447,3 +448,32 @@ def poisson_arrivals(count: int, rate: float, seed: int | None = None) -> np.nda
         seed = seed_for(4, 0)
     u = uniform(seed, count)
     return np.cumsum(-np.log(1.0 - u) / rate)
+
+
+# ----------------------------------------------------------------------------
+# Problem data at the edges of a numbered mesh
+# ----------------------------------------------------------------------------
+
+def edge_data(xy: np.ndarray, ed2el: np.ndarray, eclass: np.ndarray, f, g=None, uD=None, t=None):
+    """Sample the problem data at the midpoints of the edges of a mesh whose
+    edge table ``ed2el`` ([initial, end, T+, T-]) and classes (0 interior,
+    1 Dirichlet, 2 Neumann) are given: ``f_mid`` = f(m_E) on every edge and
+    ``bc_mid`` = u_D(m_E) on Dirichlet edges, g(m_E, nu) on Neumann edges with
+    nu the outward unit normal (initial -> end runs counter-clockwise around
+    the only triangle of a boundary edge), 0 elsewhere."""
+    a = xy[ed2el[:, 0]]
+    b = xy[ed2el[:, 1]]
+    mid = 0.5 * (a + b)
+    x, y = mid[:, 0], mid[:, 1]
+    targs = () if t is None else (t,)
+    f_mid = np.broadcast_to(np.asarray(f(x, y, *targs), dtype=np.float64), x.shape).copy()
+    bc = np.zeros(x.shape)
+    D = eclass == 1
+    N = eclass == 2
+    if uD is not None and D.any():
+        bc[D] = uD(x[D], y[D], *targs)
+    if g is not None and N.any():
+        d = b[N] - a[N]
+        L = np.sqrt(d[:, 0] ** 2 + d[:, 1] ** 2)
+        bc[N] = g(x[N], y[N], d[:, 1] / L, -d[:, 0] / L, *targs)
+    return f_mid, bc

@@ -1,0 +1,275 @@
+"""Thin Python binding of the C ABI in include/phfem.h (argument marshalling only).
+
+Every function carries the name of the C entry point it calls, takes CUDA
+tensors (device pointers) and ints, and raises :class:`PhfemError` on a
+non-zero status.  All computation happens in the CUDA library; if the library
+has not been built this module raises instead of falling back to anything.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import torch
+
+from . import build as _build
+
+PHFEM_FP64, PHFEM_FP32_IR = 0, 1
+EDGE_INTERIOR, EDGE_DIRICHLET, EDGE_NEUMANN = 0, 1, 2
+MAX_TERMS = 4
+
+
+class PhfemError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(msg)
+        self.status = status
+
+
+class MeshInfo(C.Structure):
+    _fields_ = [(n, C.c_int32) for n in ("nV", "nT", "nE", "nF", "nL", "nD", "nN", "nnz")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class Coeffs(C.Structure):
+    _fields_ = [("a_T", C.c_void_p), ("a", C.c_double), ("delta", C.c_double), ("dt", C.c_double),
+                ("precision", C.c_int32), ("reserved", C.c_int32)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("inner_rtol", C.c_double), ("max_iter", C.c_int32),
+                ("max_refine", C.c_int32), ("check_every", C.c_int32), ("reserved", C.c_int32)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("refinements", C.c_int32), ("converged", C.c_int32),
+                ("steps", C.c_int32), ("rel_residual", C.c_double), ("seconds", C.c_double),
+                ("fp64_floor", C.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class Source(C.Structure):
+    _fields_ = [("nterms", C.c_int32), ("nt", C.c_int32), ("f_mid", C.c_void_p), ("bc_mid", C.c_void_p),
+                ("phi", C.c_void_p)]
+
+
+_lib = None
+_H = C.c_void_p
+_P = C.c_void_p
+
+
+def lib() -> C.CDLL:
+    """The loaded library (``_build/libphfem.so``); raises if it is missing."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        L = C.CDLL(path)
+        sig = {
+            "phfem_ctx_create": (C.c_int, [_P, C.POINTER(_H)]),
+            "phfem_ctx_destroy": (C.c_int, [_H]),
+            "phfem_status_str": (C.c_char_p, [C.c_int]),
+            "phfem_last_error": (C.c_char_p, []),
+            "phfem_ctx_launches": (C.c_int64, [_H]),
+            "phfem_ctx_profile": (C.c_int, [_H, C.c_int]),
+            "phfem_ctx_kernel_time": (C.c_int, [_H, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64),
+                                                C.c_int]),
+            "phfem_mesh_build": (C.c_int, [_H, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P, C.c_int32, _P,
+                                           C.POINTER(_H)]),
+            "phfem_mesh_info_get": (C.c_int, [_H, C.POINTER(MeshInfo)]),
+            "phfem_mesh_tables": (C.c_int, [_H, _P, _P, _P, _P, _P, _P, _P, _P]),
+            "phfem_mesh_destroy": (C.c_int, [_H]),
+            "phfem_assemble": (C.c_int, [_H, C.POINTER(Coeffs), _P, _P, C.POINTER(_H)]),
+            "phfem_sys_csr": (C.c_int, [_H, _P, _P]),
+            "phfem_sys_destroy": (C.c_int, [_H]),
+            "phfem_solve": (C.c_int, [_H, C.POINTER(SolveOpts), _P, _P, _P, _P, C.POINTER(Stats)]),
+            "phfem_cn_create": (C.c_int, [_H, C.POINTER(Source), _P, _P, C.POINTER(_H)]),
+            "phfem_cn_step": (C.c_int, [_H, C.c_int32, C.POINTER(SolveOpts), C.POINTER(Stats)]),
+            "phfem_cn_read": (C.c_int, [_H, _P, _P, _P, _P, C.POINTER(C.c_int32)]),
+            "phfem_cn_destroy": (C.c_int, [_H]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        L = lib()
+        raise PhfemError(status, f"{what}: {L.phfem_status_str(status).decode()}: "
+                                 f"{L.phfem_last_error().decode()}")
+
+
+def _ptr(t, dtype=None, n=None):
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"expected at least {n} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+def _stream_ptr(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+# --- context -----------------------------------------------------------------
+
+def phfem_ctx_create(stream=None):
+    h = _H()
+    _check(lib().phfem_ctx_create(_stream_ptr(stream), C.byref(h)), "phfem_ctx_create")
+    return h
+
+
+def phfem_ctx_destroy(ctx):
+    _check(lib().phfem_ctx_destroy(ctx), "phfem_ctx_destroy")
+
+
+def phfem_ctx_launches(ctx) -> int:
+    return int(lib().phfem_ctx_launches(ctx))
+
+
+def phfem_ctx_profile(ctx, enable: bool):
+    _check(lib().phfem_ctx_profile(ctx, int(bool(enable))), "phfem_ctx_profile")
+
+
+def phfem_ctx_kernel_time(ctx, kernel: str, reset: bool = True):
+    """(total device ms, number of timed launches) of one instrumented kernel."""
+    ms, n = C.c_double(), C.c_int64()
+    _check(lib().phfem_ctx_kernel_time(ctx, kernel.encode(), C.byref(ms), C.byref(n), int(reset)),
+           "phfem_ctx_kernel_time")
+    return float(ms.value), int(n.value)
+
+
+# --- mesh --------------------------------------------------------------------
+
+def phfem_mesh_build(ctx, xy, tri, dirichlet, neumann):
+    nV, nT = xy.shape[0], tri.shape[0]
+    nD = dirichlet.shape[0] if dirichlet is not None else 0
+    nN = neumann.shape[0] if neumann is not None else 0
+    h = _H()
+    _check(lib().phfem_mesh_build(ctx, nV, _ptr(xy, torch.float64, 2 * nV), nT, _ptr(tri, torch.int32, 3 * nT),
+                                  nD, _ptr(dirichlet, torch.int32) if nD else None,
+                                  nN, _ptr(neumann, torch.int32) if nN else None, C.byref(h)),
+           "phfem_mesh_build")
+    return h
+
+
+def phfem_mesh_info_get(mesh) -> dict:
+    info = MeshInfo()
+    _check(lib().phfem_mesh_info_get(mesh, C.byref(info)), "phfem_mesh_info_get")
+    return info.as_dict()
+
+
+def phfem_mesh_tables(mesh, device=None) -> dict:
+    """All tables of the mesh as new device tensors."""
+    I = phfem_mesh_info_get(mesh)
+    dev = device or torch.device("cuda", torch.cuda.current_device())
+    i32 = dict(dtype=torch.int32, device=dev)
+    out = dict(
+        ed2el=torch.empty((I["nE"], 4), **i32), t2e=torch.empty((I["nT"], 3), **i32),
+        sigma=torch.empty((I["nT"], 3), dtype=torch.int8, device=dev),
+        eclass=torch.empty(I["nE"], dtype=torch.uint8, device=dev),
+        free_id=torch.empty(I["nE"], **i32), lam_id=torch.empty(I["nE"], **i32),
+        row_ptr=torch.empty(I["nF"] + 1, **i32), col=torch.empty(max(I["nnz"], 1), **i32))
+    _check(lib().phfem_mesh_tables(mesh, *(out[k].data_ptr() for k in
+                                           ("ed2el", "t2e", "sigma", "eclass", "free_id", "lam_id",
+                                            "row_ptr", "col"))), "phfem_mesh_tables")
+    out["col"] = out["col"][:I["nnz"]]
+    return out
+
+
+def phfem_mesh_destroy(mesh):
+    _check(lib().phfem_mesh_destroy(mesh), "phfem_mesh_destroy")
+
+
+# --- assembly ----------------------------------------------------------------
+
+def phfem_assemble(mesh, f_mid=None, bc_mid=None, a_T=None, a=1.0, delta=0.0, dt=0.0, precision=PHFEM_FP64):
+    I = phfem_mesh_info_get(mesh)
+    c = Coeffs(_ptr(a_T, torch.float64, I["nT"]), float(a), float(delta), float(dt), int(precision), 0)
+    h = _H()
+    _check(lib().phfem_assemble(mesh, C.byref(c), _ptr(f_mid, torch.float64, I["nE"]),
+                                _ptr(bc_mid, torch.float64, I["nE"]), C.byref(h)), "phfem_assemble")
+    return h
+
+
+def phfem_sys_csr(sys, val, rhs):
+    _check(lib().phfem_sys_csr(sys, _ptr(val, torch.float64), _ptr(rhs, torch.float64)), "phfem_sys_csr")
+
+
+def phfem_sys_destroy(sys):
+    _check(lib().phfem_sys_destroy(sys), "phfem_sys_destroy")
+
+
+def solve_opts(rtol=1e-10, inner_rtol=0.0, max_iter=0, max_refine=0, check_every=0) -> SolveOpts:
+    return SolveOpts(float(rtol), float(inner_rtol), int(max_iter), int(max_refine), int(check_every), 0)
+
+
+def phfem_solve(sys, opts=None, w0=None, w=None, U=None, Lambda=None, raise_on_noconv=True) -> dict:
+    st = Stats()
+    o = opts if opts is not None else solve_opts()
+    status = lib().phfem_solve(sys, C.byref(o), _ptr(w0, torch.float64), _ptr(w, torch.float64),
+                               _ptr(U, torch.float64), _ptr(Lambda, torch.float64), C.byref(st))
+    if status != 0 and (raise_on_noconv or status != -4):
+        _check(status, "phfem_solve")
+    d = st.as_dict()
+    d["status"] = status
+    return d
+
+
+# --- Crank-Nicolson ------------------------------------------------------------
+
+def phfem_cn_create(sys, f_mid, bc_mid, phi, w0, Lambda0=None):
+    """f_mid, bc_mid: [Q, nE] CUDA float64; phi: [Q, nt] host float64 (numpy or tensor)."""
+    import numpy as np
+    phi = np.ascontiguousarray(np.asarray(phi, dtype=np.float64))
+    if phi.ndim == 1:
+        phi = phi[None, :]
+    Q, nt = phi.shape
+    src = Source(Q, nt, _ptr(f_mid, torch.float64), _ptr(bc_mid, torch.float64),
+                 phi.ctypes.data_as(C.c_void_p).value)
+    h = _H()
+    _check(lib().phfem_cn_create(sys, C.byref(src), _ptr(w0, torch.float64), _ptr(Lambda0, torch.float64),
+                                 C.byref(h)), "phfem_cn_create")
+    return h
+
+
+def phfem_cn_step(cn, nsteps, opts=None) -> dict:
+    st = Stats()
+    o = opts if opts is not None else solve_opts()
+    _check(lib().phfem_cn_step(cn, int(nsteps), C.byref(o), C.byref(st)), "phfem_cn_step")
+    return st.as_dict()
+
+
+def phfem_cn_read(cn, w=None, U=None, Lambda_n=None, Lambda_half=None) -> int:
+    step = C.c_int32()
+    _check(lib().phfem_cn_read(cn, _ptr(w, torch.float64), _ptr(U, torch.float64), _ptr(Lambda_n, torch.float64),
+                               _ptr(Lambda_half, torch.float64), C.byref(step)), "phfem_cn_read")
+    return int(step.value)
+
+
+def phfem_cn_destroy(cn):
+    _check(lib().phfem_cn_destroy(cn), "phfem_cn_destroy")
+
+
+def phfem_status_str(status: int) -> str:
+    return lib().phfem_status_str(int(status)).decode()
+
+
+def phfem_last_error() -> str:
+    return lib().phfem_last_error().decode()

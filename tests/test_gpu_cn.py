@@ -1,0 +1,93 @@
+"""Crank-Nicolson stepping of the CUDA path against the oracle's stepping of
+the paper's saddle-point system (Section 4)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import phfem_oracle as O
+from paper_2401_15557_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_2401_15557_gb300 import phfem as P
+    c = P.phfem_ctx_create()
+    yield c
+    P.phfem_ctx_destroy(c)
+
+
+def _run_gpu(ctx, mesh, terms, phi_fn, dt, nsteps, u0, delta, aT=None, precision=0, rtol=1e-13, Lambda0=None):
+    """terms: list of (f_q, g_q, uD_q) spatial functions; phi_fn(t) -> [Q]."""
+    from paper_2401_15557_gb300 import phfem as P
+    from phfem_gpu import GpuMesh, dev
+    gm = GpuMesh(mesh, ctx)
+    fs, bcs = [], []
+    for fq, gq, uq in terms:
+        fm, bc = gm.edge_data(fq, gq, uq)
+        fs.append(fm)
+        bcs.append(bc)
+    F = torch.stack(fs).contiguous()
+    B = torch.stack(bcs).contiguous()
+    phi = np.array([phi_fn(n * dt) for n in range(nsteps + 1)]).T.copy()
+    sysh = P.phfem_assemble(gm.h, None, None, a_T=None if aT is None else dev(aT, torch.float64), delta=delta,
+                            dt=dt, precision=precision)
+    w0, _ = gm.edge_data(u0)
+    cn = P.phfem_cn_create(sysh, F, B, phi, w0, Lambda0=None if Lambda0 is None else dev(Lambda0, torch.float64))
+    st = P.phfem_cn_step(cn, nsteps, P.solve_opts(rtol=rtol))
+    I_ = gm.info
+    U = torch.empty(3 * I_["nT"], dtype=torch.float64, device="cuda")
+    Ln = torch.empty(I_["nL"], dtype=torch.float64, device="cuda")
+    Lh = torch.empty(I_["nL"], dtype=torch.float64, device="cuda")
+    step = P.phfem_cn_read(cn, U=U, Lambda_n=Ln, Lambda_half=Lh)
+    P.phfem_cn_destroy(cn)
+    P.phfem_sys_destroy(sysh)
+    gm.close()
+    return dict(U=U.cpu().numpy(), Lambda=Ln.cpu().numpy(), Lambda_half=Lh.cpu().numpy(), step=step, stats=st)
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32ir"])
+def test_heat_sine_matches_oracle(ctx, precision):
+    pi = np.pi
+    s = lambda x, y: np.sin(pi * x) * np.sin(pi * y)
+    pb = I.problem_heat_sine()
+    mesh = I.square_mesh(10)
+    dt, n = 1.0 / 10, 10
+    terms = [(lambda x, y: (2 * pi * pi - 1.0) * s(x, y),
+              lambda x, y, nx, ny: pi * (np.cos(pi * x) * np.sin(pi * y) * nx + np.sin(pi * x) * np.cos(pi * y) * ny),
+              lambda x, y: 0 * x)]
+    out = _run_gpu(ctx, mesh, terms, lambda t: [np.exp(-t)], dt, n, s, 0.0, precision=precision,
+                   rtol=1e-13 if precision == 0 else 1e-10)
+    ref = O.cn_solve(mesh, pb, dt, n)
+    assert out["step"] == n
+    tol = 1e-10 if precision == 0 else 1e-7
+    assert np.max(np.abs(out["U"] - ref["U"])) <= tol * np.max(np.abs(ref["U"]))
+    assert np.max(np.abs(out["Lambda_half"] - ref["Lambda_half"])) <= 10 * tol * np.max(np.abs(ref["Lambda_half"]))
+    assert np.max(np.abs(out["Lambda"] - ref["Lambda"])) <= 100 * tol * np.max(np.abs(ref["Lambda"]))
+
+
+def test_two_term_source_reaction_variable_coefficient(ctx):
+    """u = t s(x) with s = (x - x^2)(y - y^2) + 0.2 x: f = s + t (L s) has two
+    separable terms; Dirichlet on x = 0, 1, Neumann elsewhere, delta > 0,
+    variable a_T (the oracle gets the same a_T)."""
+    mesh = I.lshape_mesh(n=4, seed=I.seed_for(1, 51))
+    delta = 0.7
+    aT = I.element_mean_at_midpoints(mesh.xy, mesh.tri, I.coeff_lshape)
+    s = lambda x, y: (x - x * x) * (y - y * y) + 0.2 * x
+    # L s = -div(a grad s) + delta s evaluated with the element coefficient is
+    # not needed: any smooth f is a valid source; use f1 = sin(x) cos(y)
+    f1 = lambda x, y: np.sin(x) * np.cos(y)
+    g1 = lambda x, y, nx, ny: 0.3 * nx - 0.1 * ny
+    uD1 = lambda x, y: 0.2 * x + 0.1
+    terms = [(s, lambda x, y, nx, ny: 0 * x, lambda x, y: 0 * x), (f1, g1, uD1)]
+    phi = lambda t: [1.0, t]
+    pb = I.Problem(f=lambda x, y, t: s(x, y) + t * f1(x, y), g=lambda x, y, nx, ny, t: t * g1(x, y, nx, ny),
+                   uD=lambda x, y, t: t * uD1(x, y), delta=delta, u0=lambda x, y: 0 * x)
+    dt, n = 0.05, 8
+    L0 = np.linspace(-1, 1, O.setup(mesh)["bsets"]["Redges"].size)
+    out = _run_gpu(ctx, mesh, terms, phi, dt, n, lambda x, y: 0 * x, delta, aT=aT, Lambda0=L0)
+    ref = O.cn_solve(mesh, pb, dt, n, aT=aT, Lambda0=L0)
+    assert np.max(np.abs(out["U"] - ref["U"])) <= 1e-10 * np.max(np.abs(ref["U"]))
+    assert np.max(np.abs(out["Lambda_half"] - ref["Lambda_half"])) <= 1e-8 * np.max(np.abs(ref["Lambda_half"]))
+    assert np.max(np.abs(out["Lambda"] - ref["Lambda"])) <= 1e-7 * np.max(np.abs(ref["Lambda"]))

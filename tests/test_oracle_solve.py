@@ -210,3 +210,36 @@ def test_manufactured_rates_sine_exp():
     r1 = np.log2(np.array(h1[:-1]) / np.array(h1[1:]))
     assert np.all(np.abs(r2 - 2.0) < 0.1), r2
     assert np.all(np.abs(r1 - 1.0) < 0.1), r1
+
+
+def test_relative_residual_against_exact_rationals():
+    """The difference-form residual equals the residual computed exactly in
+    rational arithmetic from the same FP64 matrix, vector and rhs; the plain
+    FP64 row product does not on a fine mesh (cancellation)."""
+    from fractions import Fraction
+    mesh = I.square_mesh(48)
+    pb = I.Problem(f=lambda x, y: 1.0 + 0 * x, g=lambda x, y, nx, ny: 0 * x, uD=lambda x, y: 0 * x, delta=0.0)
+    cs = O.condensed_system(mesh, pb)
+    S, b = cs["S"], cs["rhs"]
+    x = spla.spsolve(S.tocsc(), b)
+    Fx = [Fraction(v) for v in x]
+    r2 = Fraction(0)
+    for i in range(S.shape[0]):
+        acc = Fraction(b[i])
+        for k in range(S.indptr[i], S.indptr[i + 1]):
+            acc -= Fraction(S.data[k]) * Fx[S.indices[k]]
+        r2 += acc * acc
+    exact = float(np.sqrt(float(r2))) / np.linalg.norm(b)
+    stable = O.relative_residual(S, b, x)
+    assert abs(stable - exact) <= 0.05 * exact + 1e-16
+    # a perturbed vector: both agree at a larger residual too
+    xp = x * (1 + 1e-9 * np.sin(np.arange(x.size)))
+    Fp = [Fraction(v) for v in xp]
+    r2 = Fraction(0)
+    for i in range(S.shape[0]):
+        acc = Fraction(b[i])
+        for k in range(S.indptr[i], S.indptr[i + 1]):
+            acc -= Fraction(S.data[k]) * Fp[S.indices[k]]
+        r2 += acc * acc
+    exact_p = float(np.sqrt(float(r2))) / np.linalg.norm(b)
+    assert abs(O.relative_residual(S, b, xp) - exact_p) <= 1e-3 * exact_p
