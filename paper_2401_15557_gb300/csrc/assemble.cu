@@ -181,7 +181,6 @@ void sys_free(phfem_sys s) {
   dfree(c, s->f);
   dfree(c, s->x);
   dfree(c, s->r64);
-  dfree(c, s->xi);
   dfree(c, s->ri);
   dfree(c, s->pi);
   dfree(c, s->qi);
@@ -265,7 +264,6 @@ PHFEM_API int phfem_assemble(phfem_mesh mesh, const phfem_coeffs* coeffs, const 
   chk(dalloc_n(ctx, &sys->f, nE));
   chk(dalloc_n(ctx, &sys->x, nE));
   chk(dalloc_n(ctx, &sys->r64, nE));
-  chk(dalloc(ctx, &sys->xi, nE * isz));
   chk(dalloc(ctx, &sys->ri, nE * isz));
   chk(dalloc(ctx, &sys->pi, nE * isz));
   chk(dalloc(ctx, &sys->qi, nE * isz));

@@ -115,8 +115,7 @@ struct phfem_sys_s {
   // solver workspace
   double* x;             // [nE] current midpoint values (FP64)
   double* r64;           // [nE]
-  void* xi;              // [nE] inner vectors (float or double)
-  void* ri;
+  void* ri;              // [nE] inner vectors (float or double)
   void* pi;
   void* qi;
   double* partials;      // [4][kMaxGrid]

@@ -10,12 +10,14 @@
 // zero on Dirichlet rows, so the Dirichlet columns (kept in the free rows for
 // the lifting) never act inside the iteration.
 //
-// Jacobi-PCG with reliable updates: the iteration runs on the correction d
-// (FP32 vectors with FP64-accumulated dot products, or FP64) from the FP64
-// solution x.  Whenever the recursive residual has fallen by the factor
-// inner_rtol since the last update, x += d (FP64), the true residual
-// r = b - S x is recomputed in FP64 (difference form) and replaces the
-// recursive one while the search direction is kept, so the Krylov space is
+// Jacobi-PCG with reliable updates: the residual, direction and operator
+// product live in the inner precision (FP32 with FP64-accumulated dot
+// products, or FP64) while the solution x is accumulated in FP64 at every
+// iteration (rounding a correction vector to FP32 would leave a residual of
+// 2^-24 |S| |d|, far above |b| ~ h^2 on fine meshes).  Whenever the recursive
+// residual has fallen by the factor inner_rtol since the last update, the true
+// residual r = b - S x is recomputed in FP64 (difference form) and replaces
+// the recursive one while the search direction is kept, so the Krylov space is
 // not lost as in restarted refinement.  The solve stops when
 // ||r|| <= rtol ||b_free||, or when ||r|| reaches the level that rounding x to
 // FP64 alone leaves (estimated from |l| |x| per row), which on fine meshes can
@@ -41,7 +43,7 @@ template <typename T>
 __global__ void k_residual(int nE, const int32_t* __restrict__ nbr, const double* __restrict__ val,
                            const double* __restrict__ b, const double* __restrict__ x,
                            const uint8_t* __restrict__ eclass, const T* __restrict__ dinv,
-                           T* __restrict__ xi, T* __restrict__ ri, T* __restrict__ pi, double* partials,
+                           T* __restrict__ ri, T* __restrict__ pi, double* partials,
                            SolveState* st, double rtol2, double inner_rtol2, int mode) {
   __shared__ double smem[kBlock / 32];
   const size_t m = (size_t)nE;
@@ -81,7 +83,6 @@ __global__ void k_residual(int nE, const int32_t* __restrict__ nbr, const double
       const T zs = dinv[e] * rs;
       ri[e] = rs;
       if (mode == 1) pi[e] = zs;
-      xi[e] = (T)0;
       acc_z += (double)rs * (double)zs;
     }
   }
@@ -161,16 +162,17 @@ __global__ void __launch_bounds__(kBlock) k_cg_spmv(int nE, const int32_t* __res
 
 // x += alpha p, r -= alpha q, r.D^-1 r -> beta
 template <typename T>
-__global__ void __launch_bounds__(kBlock) k_cg_update(int nE, T* __restrict__ x, const T* __restrict__ p,
+__global__ void __launch_bounds__(kBlock) k_cg_update(int nE, double* __restrict__ x, const T* __restrict__ p,
                                                       T* __restrict__ r, const T* __restrict__ q,
                                                       const T* __restrict__ dinv, double* partials,
                                                       SolveState* st) {
   if (st->done) return;
   __shared__ double smem[kBlock / 32];
-  const T alpha = (T)st->alpha;
+  const double alpha64 = st->alpha;
+  const T alpha = (T)alpha64;
   double acc = 0.0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
-    x[e] += alpha * p[e];
+    x[e] += alpha64 * (double)p[e];
     const T re = r[e] - alpha * q[e];
     r[e] = re;
     acc += (double)re * (double)(dinv[e] * re);
@@ -211,12 +213,6 @@ __global__ void __launch_bounds__(kBlock) k_cg_dir(int nE, const T* __restrict__
 template <typename T>
 __global__ void k_cg_restart(int nE, const T* __restrict__ r, const T* __restrict__ dinv, T* __restrict__ p) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) p[e] = dinv[e] * r[e];
-}
-
-template <typename T>
-__global__ void k_ir_update(int nE, const T* __restrict__ xi, double* __restrict__ x) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x)
-    x[e] += (double)xi[e];
 }
 
 __global__ void k_init_x(int nE, const uint8_t* __restrict__ eclass, const double* __restrict__ b,
@@ -284,7 +280,6 @@ int solve_typed(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats) {
   cudaStream_t s = ctx->stream;
   const int nE = m->info.nE;
   const int g = grid_for(ctx, nE);
-  T* xi = (T*)sys->xi;
   T* ri = (T*)sys->ri;
   T* pi = (T*)sys->pi;
   T* qi = (T*)sys->qi;
@@ -295,7 +290,7 @@ int solve_typed(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats) {
   static const bool verbose = getenv("PHFEM_VERBOSE") != nullptr;
   auto residual = [&](int mode) -> int {
     prof_start(ctx, kProfResidual);
-    k_residual<T><<<g, kBlock, 0, s>>>(nE, m->nbr, sys->val, sys->b, sys->x, m->eclass, dinv, xi, ri, pi,
+    k_residual<T><<<g, kBlock, 0, s>>>(nE, m->nbr, sys->val, sys->b, sys->x, m->eclass, dinv, ri, pi,
                                        sys->partials, sys->st, rtol2, irtol2, mode);
     prof_stop(ctx, kProfResidual);
     return check_launch(ctx, "k_residual");
@@ -343,7 +338,7 @@ int solve_typed(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats) {
         k_cg_spmv<T><<<g, kBlock, 0, s>>>(nE, m->nbr, lval, rdiag, pi, qi, sys->partials, sys->st);
         prof_stop(ctx, kProfSpmv);
         prof_start(ctx, kProfUpdate);
-        k_cg_update<T><<<g, kBlock, 0, s>>>(nE, xi, pi, ri, qi, dinv, sys->partials, sys->st);
+        k_cg_update<T><<<g, kBlock, 0, s>>>(nE, sys->x, pi, ri, qi, dinv, sys->partials, sys->st);
         prof_stop(ctx, kProfUpdate);
         prof_start(ctx, kProfDir);
         k_cg_dir<T><<<g, kBlock, 0, s>>>(nE, ri, dinv, pi, sys->st);
@@ -361,10 +356,8 @@ int solve_typed(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats) {
       status = sys->st_host->status;
       break;
     }
-    // reliable update: fold the correction into x, recompute the true residual
+    // reliable update: the true residual of the FP64 x replaces the recursive one
     const double rz_recursive = sys->st_host->rz;
-    k_ir_update<T><<<g, kBlock, 0, s>>>(nE, xi, sys->x);
-    PH_TRY(check_launch(ctx, "k_ir_update"));
     PH_TRY(residual(2));
     ++updates;
     PH_TRY(read_state(sys));
