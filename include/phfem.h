@@ -254,6 +254,43 @@ PHFEM_API int phfem_cn_read(phfem_cn cn, double* w, double* U, double* Lambda_n,
                             double* Lambda_half, int32_t* step);
 PHFEM_API int phfem_cn_destroy(phfem_cn cn);
 
+/* ------------------------------------------------------------------------ */
+/* Solve without device allocation                                           */
+/* ------------------------------------------------------------------------ */
+
+/* The paper has no counterpart of this entry point; it exists for callers that
+ * cannot allocate device memory while they call the library: work being
+ * captured into a CUDA graph (an allocation inside the capture fails or is
+ * recorded into the graph), programs whose device memory belongs to another
+ * framework's pool, and latency-critical loops that must not allocate.
+ *
+ * Jacobi-preconditioned conjugate gradients (FP64) on a symmetric positive
+ * definite CSR system A x = rhs given by the caller, for instance the export
+ * of phfem_sys_csr.  It allocates nothing: its temporaries live in one
+ * fixed-size device array of the library (about 8 MB per device, reserved when
+ * the library is loaded on a device and kept until the process exits).
+ *   cuda_stream  cudaStream_t the work is ordered on (NULL = legacy stream)
+ *   n            rows, 1 <= n <= PHFEM_NOALLOC_MAX_ROWS (else PHFEM_EINVAL)
+ *   row_ptr [n+1], col [nnz] int32, val [nnz] double   the matrix (device);
+ *                every row must hold a positive diagonal entry
+ *   rhs [n] double (device); x [n] double (device): initial guess on entry,
+ *                solution on return
+ *   rtol         stop when ||rhs - A x||_2 <= rtol ||rhs||_2 (recursive
+ *                residual); <= 0 -> 1e-10
+ *   max_iter     iteration limit; <= 0 -> 100000 (PHFEM_ENOCONV when reached)
+ *   iterations, rel_residual   host outputs, may be NULL
+ * The array is shared by every call on a device and keeps the last call's
+ * contents; each call clears the state it needs at its start.  Calls whose
+ * GPU work overlaps (different streams or threads without ordering) race on
+ * it.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) with that device current: make it before any stream
+ * capture begins.  Blocks the host until the result is known. */
+#define PHFEM_NOALLOC_MAX_ROWS 262144
+PHFEM_API int phfem_csr_pcg_noalloc(void* cuda_stream, int32_t n, const int32_t* row_ptr,
+                                    const int32_t* col, const double* val, const double* rhs,
+                                    double* x, double rtol, int32_t max_iter, int32_t* iterations,
+                                    double* rel_residual);
+
 #ifdef __cplusplus
 }
 #endif

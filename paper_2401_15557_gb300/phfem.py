@@ -92,6 +92,8 @@ def lib() -> C.CDLL:
             "phfem_cn_step": (C.c_int, [_H, C.c_int32, C.POINTER(SolveOpts), C.POINTER(Stats)]),
             "phfem_cn_read": (C.c_int, [_H, _P, _P, _P, _P, C.POINTER(C.c_int32)]),
             "phfem_cn_destroy": (C.c_int, [_H]),
+            "phfem_csr_pcg_noalloc": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, C.c_double, C.c_int32,
+                                                C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -273,3 +275,20 @@ def phfem_status_str(status: int) -> str:
 
 def phfem_last_error() -> str:
     return lib().phfem_last_error().decode()
+
+
+# --- solve without device allocation -------------------------------------------
+
+NOALLOC_MAX_ROWS = 262144
+
+
+def phfem_csr_pcg_noalloc(row_ptr, col, val, rhs, x, rtol=1e-10, max_iter=0, stream=None) -> dict:
+    """Jacobi-PCG on a CSR system using only the library's fixed device scratch
+    (see include/phfem.h); x holds the initial guess and receives the solution."""
+    n = rhs.numel()
+    it, rel = C.c_int32(), C.c_double()
+    _check(lib().phfem_csr_pcg_noalloc(_stream_ptr(stream), n, _ptr(row_ptr, torch.int32, n + 1),
+                                       _ptr(col, torch.int32), _ptr(val, torch.float64), _ptr(rhs, torch.float64, n),
+                                       _ptr(x, torch.float64, n), float(rtol), int(max_iter), C.byref(it),
+                                       C.byref(rel)), "phfem_csr_pcg_noalloc")
+    return {"iterations": int(it.value), "rel_residual": float(rel.value)}
