@@ -38,10 +38,10 @@ LEVELS = 5
 CPU_SAMPLE_LEVEL = 2
 SPMV_BYTES_PER_ROW = 4 * 4 + 4 * 4 + 4 + 4 + 4   # nbr, l (FP32), r, p, q
 # DRAM traffic of one cg_spmv launch at the full workload, from the ncu capture
-# summarised in profiles/cg_spmv_lshape_l5.md; valid only for the kernel
+# summarised in profiles/cg_kernels_full_lshape_l5.md; valid only for the kernel
 # source whose hash is recorded with it.
-SPMV_TRAFFIC = None
-SPMV_TRAFFIC_SRC_SHA = None
+SPMV_TRAFFIC = 465.76e6
+SPMV_TRAFFIC_SRC_SHA = "15947392d944502d"
 
 
 def _sha_solve_src():
@@ -59,6 +59,10 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true",
+                    help="do not sample nvidia-smi clocks (profiling runs under ncu)")
+    ap.add_argument("--max-iter", type=int, default=0,
+                    help="cap the CG iterations (short runs for profiling only; not a benchmark)")
     return ap.parse_args()
 
 
@@ -202,7 +206,7 @@ def main():
     bc_mid = torch.zeros(nE, dtype=torch.float64, device=dev)  # u_D = 0, g = 0
     U = torch.empty(3 * nT, dtype=torch.float64, device=dev)
     Lam = torch.empty(nL, dtype=torch.float64, device=dev)
-    opts = P.solve_opts(rtol=1e-10)
+    opts = P.solve_opts(rtol=1e-10, max_iter=args.max_iter)
 
     def ev():
         return torch.cuda.Event(enable_timing=True)
@@ -215,7 +219,7 @@ def main():
         e1.record(stream)
         s = P.phfem_assemble(m, F_, B_, a_T=A_, delta=1.0, precision=prec)
         e2.record(stream)
-        st = P.phfem_solve(s, opts, U=U, Lambda=Lam)
+        st = P.phfem_solve(s, opts, U=U, Lambda=Lam, raise_on_noconv=args.max_iter == 0)
         e3.record(stream)
         P.phfem_sys_destroy(s)
         P.phfem_mesh_destroy(m)
@@ -242,11 +246,12 @@ def main():
         P.phfem_ctx_kernel_time(ctx, k, reset=True)
     P.phfem_ctx_profile(ctx, True)
     launches0 = P.phfem_ctx_launches(ctx)
-    clocks = ClockSampler(torch.cuda.current_device())
+    clocks = ClockSampler(torch.cuda.current_device()) if not args.no_clocks else None
     phases = []
     barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    if clocks:
+        clocks.start()
     t_start, t_stop = ev(), ev()
     t_start.record(stream)
     for _ in range(args.steps):
@@ -254,7 +259,7 @@ def main():
     t_stop.record(stream)
     torch.cuda.synchronize()
     barrier()
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     P.phfem_ctx_profile(ctx, False)
     launches = P.phfem_ctx_launches(ctx) - launches0
     ms_total = max_over_ranks(t_start.elapsed_time(t_stop))

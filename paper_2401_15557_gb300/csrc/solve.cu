@@ -11,8 +11,9 @@
 // the lifting) never act inside the iteration.
 //
 // Jacobi-PCG with reliable updates: the residual, direction and operator
-// product live in the inner precision (FP32 with FP64-accumulated dot
-// products, or FP64) while the solution x is accumulated in FP64 at every
+// product live in the inner precision (FP32, or FP64; dot products sum each
+// thread's few rows in that precision and accumulate across threads and
+// blocks in FP64) while the solution x is accumulated in FP64 at every
 // iteration (rounding a correction vector to FP32 would leave a residual of
 // 2^-24 |S| |d|, far above |b| ~ h^2 on fine meshes).  Whenever the recursive
 // residual has fallen by the factor inner_rtol since the last update, the true
@@ -132,7 +133,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_spmv(int nE, const int32_t* __res
   if (st->done) return;
   __shared__ double smem[kBlock / 32];
   const size_t m = (size_t)nE;
-  double acc = 0.0;
+  T acc = (T)0;  // this thread's few rows in T; across threads and blocks in FP64
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
     const int c0 = nbr[e], c1 = nbr[m + e], c2 = nbr[2 * m + e], c3 = nbr[3 * m + e];
     const T l0 = lval[e], l1 = lval[m + e], l2 = lval[2 * m + e], l3 = lval[3 * m + e];
@@ -143,10 +144,10 @@ __global__ void __launch_bounds__(kBlock) k_cg_spmv(int nE, const int32_t* __res
     s += l2 * (pe - __ldg(p + c2));
     s += l3 * (pe - __ldg(p + c3));
     q[e] = s;
-    acc += (double)pe * (double)s;
+    acc += pe * s;
   }
-  acc = block_sum(acc, smem);
-  if (threadIdx.x == 0) partials[blockIdx.x] = acc;
+  const double accd = block_sum((double)acc, smem);
+  if (threadIdx.x == 0) partials[blockIdx.x] = accd;
   if (!arrive_last(&st->counter[1])) return;
   const double pq = sum_partials(partials, smem);
   if (threadIdx.x == 0) {
@@ -170,15 +171,15 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(int nE, double* __restrict
   __shared__ double smem[kBlock / 32];
   const double alpha64 = st->alpha;
   const T alpha = (T)alpha64;
-  double acc = 0.0;
+  T acc = (T)0;  // this thread's few rows in T; across threads and blocks in FP64
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
     x[e] += alpha64 * (double)p[e];
     const T re = r[e] - alpha * q[e];
     r[e] = re;
-    acc += (double)re * (double)(dinv[e] * re);
+    acc += re * (dinv[e] * re);
   }
-  acc = block_sum(acc, smem);
-  if (threadIdx.x == 0) partials[kMaxGrid + blockIdx.x] = acc;
+  const double accd = block_sum((double)acc, smem);
+  if (threadIdx.x == 0) partials[kMaxGrid + blockIdx.x] = accd;
   if (!arrive_last(&st->counter[2])) return;
   const double rz = sum_partials(partials + kMaxGrid, smem);
   if (threadIdx.x == 0) {
