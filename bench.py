@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--workload", default="lshape", choices=["lshape", "batched"],
+                    help="lshape: the L-shaped 6.3M-triangle solve (default); batched: 4096 meshes in one launch")
+    ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--no-clocks", action="store_true",
                     help="do not sample nvidia-smi clocks (profiling runs under ncu)")
     ap.add_argument("--max-iter", type=int, default=0,
@@ -168,10 +171,116 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def run_batched(args):
+    """4096 unit-square meshes with sides log-uniform in [8, 256], a = exp(0.5 z)
+    (seeded Fourier field), delta ~ U[0, 2], f = 1, u = 0 on x = 0, 1, zero flux
+    on y = 0, 1: assembly + FP32/FP64-refined solve of all meshes in one
+    persistent launch (block size from the autotuner), against the single-mesh
+    FP64 path on a sample."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    from paper_2401_15557_gb300 import inputs as I
+    from paper_2401_15557_gb300 import phfem as P
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    sides = I.batch_sides(args.batch_count)
+    members = [I.batch_member(i, n) for i, n in enumerate(sides)]
+    t_gen = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    ctx = P.phfem_ctx_create(stream)
+    d = lambda a, t: torch.as_tensor(np.ascontiguousarray(a), dtype=t, device=dev)
+    t0 = time.perf_counter()
+    meshes = []
+    for m, _, _ in members:
+        meshes.append(P.phfem_mesh_build(ctx, d(m.xy, torch.float64), d(m.tri, torch.int32),
+                                         d(m.dirichlet, torch.int32), d(m.neumann, torch.int32)))
+    batch = P.phfem_batch_create(ctx, meshes)
+    torch.cuda.synchronize()
+    t_tables = time.perf_counter() - t0
+    infos = [P.phfem_mesh_info_get(h) for h in meshes[:128]]
+    for h in meshes[128:]:
+        P.phfem_mesh_destroy(h)
+    count = len(members)
+    toff, eoff, loff = P.phfem_batch_offsets(batch, count)
+    nT, nE = int(toff[-1]), int(eoff[-1])
+    aT = d(np.concatenate([a for _, a, _ in members]), torch.float64)
+    delta = d(np.array([dl for _, _, dl in members]), torch.float64)
+    f = torch.ones(nE, dtype=torch.float64, device=dev)
+    U = torch.empty(3 * nT, dtype=torch.float64, device=dev)
+    L = torch.empty(int(loff[-1]), dtype=torch.float64, device=dev)
+    opts = P.solve_opts(rtol=1e-10)
+    chosen, tune_ms = P.phfem_batch_tune(batch, delta, a_T=aT, f_mid=f, precision=P.PHFEM_FP32_IR, opts=opts)
+    res = None
+    for _ in range(args.warmup):
+        res = P.phfem_batch_solve(batch, count, delta, a_T=aT, f_mid=f, precision=P.PHFEM_FP32_IR, opts=opts,
+                                  U=U, Lambda=L)
+    clocks = ClockSampler(0) if not args.no_clocks else None
+    if clocks:
+        clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        res = P.phfem_batch_solve(batch, count, delta, a_T=aT, f_mid=f, precision=P.PHFEM_FP32_IR, opts=opts,
+                                  U=U, Lambda=L)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop() if clocks else None
+    ms = e0.elapsed_time(e1) / args.steps
+    r64 = P.phfem_batch_solve(batch, count, delta, a_T=aT, f_mid=f, precision=P.PHFEM_FP64, opts=opts, U=U)
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record(stream)
+    r64 = P.phfem_batch_solve(batch, count, delta, a_T=aT, f_mid=f, precision=P.PHFEM_FP64, opts=opts, U=U)
+    e3.record(stream)
+    torch.cuda.synchronize()
+    ms64 = e2.elapsed_time(e3)
+    # the plain FP64 single-mesh path (assemble + solve per mesh) on the first 128 meshes
+    sample = min(128, count)
+    t0 = time.perf_counter()
+    tri_sample = 0
+    for i in range(sample):
+        m, a, dl = members[i]
+        fm = torch.ones(infos[i]["nE"], dtype=torch.float64, device=dev)
+        sh = P.phfem_assemble(meshes[i], fm, None, a_T=d(a, torch.float64), delta=dl, precision=P.PHFEM_FP64)
+        P.phfem_solve(sh, opts)
+        P.phfem_sys_destroy(sh)
+        tri_sample += m.nT
+    torch.cuda.synchronize()
+    t_single = time.perf_counter() - t0
+    line = {
+        "metric": METRIC, "value": nT * 1e3 / ms, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"batched-{count}-unit-squares", "meshes": count, "triangles": nT, "edges": nE,
+                   "sides": [int(sides.min()), int(sides.max())], "block": chosen,
+                   "step": "assemble+solve+recover of every mesh, one launch"},
+        "solves_per_s": count * 1e3 / ms,
+        "iterations": {"median": float(np.median(res["iterations"])), "max": int(res["iterations"].max())},
+        "converged": {"rtol": int((res["converged"] == 1).sum()), "floor": int((res["converged"] == 2).sum())},
+        "rel_residual_max": float(res["rel_residual"].max()),
+        "fp64_batched": {"value": nT * 1e3 / ms64, "ms_per_step": ms64, "solves_per_s": count * 1e3 / ms64},
+        "single_mesh_fp64_sample": {"meshes": sample, "triangles_per_s": tri_sample / t_single,
+                                    "solves_per_s": sample / t_single},
+        "tune_ms_per_block": tune_ms, "setup_s": {"host_generation": t_gen, "tables": t_tables},
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    for h in meshes[:128]:
+        P.phfem_mesh_destroy(h)
+    P.phfem_batch_destroy(batch)
+    P.phfem_ctx_destroy(ctx)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
 
     import numpy as np
     import torch

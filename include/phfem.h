@@ -255,6 +255,47 @@ PHFEM_API int phfem_cn_read(phfem_cn cn, double* w, double* U, double* Lambda_n,
 PHFEM_API int phfem_cn_destroy(phfem_cn cn);
 
 /* ------------------------------------------------------------------------ */
+/* Batched assembly and solve of many meshes in one persistent launch       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct phfem_batch_s* phfem_batch;
+
+/* Gathers the tables of `count` meshes built by phfem_mesh_build on the same
+ * device into one batch (the meshes may be destroyed afterwards).  Arrays of a
+ * batch are the per-mesh arrays concatenated in mesh order; phfem_batch_offsets
+ * gives the start of every mesh (count + 1 entries, host int64) in triangles,
+ * edges and multipliers. */
+PHFEM_API int phfem_batch_create(phfem_ctx ctx, int32_t count, const phfem_mesh* meshes,
+                                 phfem_batch* out);
+PHFEM_API int phfem_batch_offsets(phfem_batch batch, int64_t* tri_off, int64_t* edge_off,
+                                  int64_t* lam_off);
+/* Assembles and solves every mesh of the batch in ONE kernel launch: each
+ * thread block takes the next mesh (largest first) and runs the condensed
+ * assembly (as phfem_assemble), Jacobi-PCG with reliable updates (as
+ * phfem_solve, block-wide reductions) and the recovery of U and Lambda.
+ *   a_T    [sum nT] double per-triangle coefficient, or NULL for a = 1
+ *   delta  [count] double reaction coefficient per mesh (device)
+ *   f_mid, bc_mid [sum nE] double as in phfem_assemble (either may be NULL)
+ *   precision PHFEM_FP64 or PHFEM_FP32_IR; opts as in phfem_solve
+ *   w [sum nE], U [3 sum nT], Lambda [sum nL] double outputs (each may be NULL)
+ *   block  threads per block: 128, 256, 512, 1024, or 0 for the tuned value
+ *   iterations, converged [count] int32, rel_residual [count] double: host
+ *          outputs per mesh (each may be NULL)
+ * Blocks until the batch is done.  Returns the first failing mesh's status. */
+PHFEM_API int phfem_batch_solve(phfem_batch batch, const double* a_T, const double* delta,
+                                const double* f_mid, const double* bc_mid, int32_t precision,
+                                const phfem_solve_opts* opts, double* w, double* U, double* Lambda,
+                                int32_t block, int32_t* iterations, int32_t* converged,
+                                double* rel_residual);
+/* Autotuner: times phfem_batch_solve with 128, 256, 512 and 1024 threads per
+ * block on these inputs, keeps the fastest for block = 0, and reports it
+ * (chosen, host) with the four host wall times in ms (ms_per_block[4], host). */
+PHFEM_API int phfem_batch_tune(phfem_batch batch, const double* a_T, const double* delta,
+                               const double* f_mid, const double* bc_mid, int32_t precision,
+                               const phfem_solve_opts* opts, int32_t* chosen, double* ms_per_block);
+PHFEM_API int phfem_batch_destroy(phfem_batch batch);
+
+/* ------------------------------------------------------------------------ */
 /* Solve without device allocation                                           */
 /* ------------------------------------------------------------------------ */
 

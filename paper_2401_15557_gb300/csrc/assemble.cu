@@ -26,7 +26,7 @@
 //               FP32 inner solve drive an FP64 refinement on fine meshes.
 #include <cmath>
 
-#include "internal.cuh"
+#include "kernels.cuh"
 
 namespace phfem {
 namespace {
@@ -34,37 +34,16 @@ namespace {
 __global__ void k_asm_tri(int nT, const int32_t* __restrict__ tri, const double2* __restrict__ xy,
                           const double* __restrict__ aT, double a_const, double delta,
                           double* __restrict__ Kt, int* __restrict__ bad) {
+  const size_t n = (size_t)nT;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nT; t += gridDim.x * blockDim.x) {
     const int v0 = tri[3 * t], v1 = tri[3 * t + 1], v2 = tri[3 * t + 2];
-    const double2 p0 = __ldg(xy + v0), p1 = __ldg(xy + v1), p2 = __ldg(xy + v2);
     const double a = aT ? aT[t] : a_const;
     if (!(a > 0.0) || !isfinite(a)) atomicOr(bad, isfinite(a) ? 1 : 2);
-    const double e0x = p2.x - p1.x, e0y = p2.y - p1.y;
-    const double e1x = p0.x - p2.x, e1y = p0.y - p2.y;
-    const double e2x = p1.x - p0.x, e2y = p1.y - p0.y;
-    const double area2 = e1x * e2y - e1y * e2x;  // 2|T| = cross(P1 - P0, P2 - P0)
-    const double mT = area2 * (1.0 / 6.0);       // |T|/3
-    const double c = (a + a) / area2;            // a / |T|
-    const double dm = delta * mT;
-    const size_t n = (size_t)nT;
-    Kt[0 * n + t] = c * (e0x * e0x + e0y * e0y) + dm;
-    Kt[1 * n + t] = c * (e1x * e1x + e1y * e1y) + dm;
-    Kt[2 * n + t] = c * (e2x * e2x + e2y * e2y) + dm;
-    Kt[3 * n + t] = c * (e0x * e1x + e0y * e1y);
-    Kt[4 * n + t] = c * (e1x * e2x + e1y * e2y);
-    Kt[5 * n + t] = c * (e2x * e0x + e2y * e0y);
-    Kt[6 * n + t] = mT;
+    double K[7];
+    tri_block(__ldg(xy + v0), __ldg(xy + v1), __ldg(xy + v2), a, delta, K);
+#pragma unroll
+    for (int j = 0; j < 7; ++j) Kt[j * n + t] = K[j];
   }
-}
-
-// Entries of row k of K^CR_T: diagonal, (k, k+1), (k, k+2).
-__device__ __forceinline__ void tri_row(const double* __restrict__ Kt, size_t n, int t, int k, double& d,
-                                        double& o1, double& o2, double& mT) {
-  const int k2 = (k == 0) ? 2 : k - 1;  // k + 2 mod 3
-  d = __ldg(Kt + (size_t)k * n + t);
-  o1 = __ldg(Kt + (size_t)(3 + k) * n + t);   // pair (k, k+1)
-  o2 = __ldg(Kt + (size_t)(3 + k2) * n + t);  // pair (k+2, k)
-  mT = __ldg(Kt + 6 * n + t);
 }
 
 // sK scales K^CR and sM the mass |T|/3 (elliptic: 1, 0; Crank-Nicolson: dt/2, 1).
@@ -78,43 +57,21 @@ __global__ void k_asm_rows(int nE, int nT, const int32_t* __restrict__ ed2el, co
   const size_t n = (size_t)nT, m = (size_t)nE;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
     const int4 q = reinterpret_cast<const int4*>(ed2el)[e];
-    const int tp = q.z, tm = q.w;
     const int kk = lk[e];
-    double d, o1, o2, mT;
-    tri_row(Kt, n, tp, kk & 3, d, o1, o2, mT);
-    double diag = sK * d + sM * mT, v1 = sK * o1, v2 = sK * o2, v3 = 0.0, v4 = 0.0, mass = mT;
-    if (tm >= 0) {
-      tri_row(Kt, n, tm, (kk >> 2) & 3, d, o1, o2, mT);
-      diag += sK * d + sM * mT;
-      v3 = sK * o1;
-      v4 = sK * o2;
-      mass += mT;
-    }
     const uint8_t cls = eclass[e];
-    double rhs, rpart;
-    if (cls == PHFEM_EDGE_DIRICHLET) {
-      diag = 1.0;
-      v1 = v2 = v3 = v4 = 0.0;
-      rhs = bc_mid ? bc_mid[e] : 0.0;
-      rpart = 1.0;
-    } else {
-      rhs = f_mid ? mass * f_mid[e] : 0.0;
-      if (cls == PHFEM_EDGE_NEUMANN && bc_mid) rhs += elen[e] * bc_mid[e];
-      rpart = (sK * delta + sM) * mass;
+    const EdgeRow R = edge_row(Kt, n, q.z, kk & 3, q.w, (kk >> 2) & 3, cls, f_mid ? f_mid[e] : 0.0,
+                               bc_mid ? bc_mid[e] : 0.0, cls == PHFEM_EDGE_NEUMANN ? elen[e] : 0.0, sK, sM,
+                               delta, f_mid != nullptr, bc_mid != nullptr);
+    val[e] = R.rpart;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      val[(s + 1) * m + e] = R.l[s];
+      lval[s * m + e] = (T)R.l[s];
     }
-    val[0 * m + e] = rpart;
-    val[1 * m + e] = -v1;
-    val[2 * m + e] = -v2;
-    val[3 * m + e] = -v3;
-    val[4 * m + e] = -v4;
-    b[e] = rhs;
-    me[e] = mass;
-    lval[0 * m + e] = (T)(-v1);
-    lval[1 * m + e] = (T)(-v2);
-    lval[2 * m + e] = (T)(-v3);
-    lval[3 * m + e] = (T)(-v4);
-    rdiag[e] = (T)rpart;
-    dinv[e] = (T)(1.0 / diag);
+    b[e] = R.rhs;
+    me[e] = R.mass;
+    rdiag[e] = (T)R.rpart;
+    dinv[e] = (T)(1.0 / R.diag);
   }
 }
 

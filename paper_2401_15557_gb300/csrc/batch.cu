@@ -1,0 +1,614 @@
+// Batched assembly and solve of many independent meshes in one persistent
+// launch.
+//
+// Each thread block takes the next mesh from a device work queue (meshes in
+// decreasing size, so the largest start first) and runs the whole path for it:
+// the triangle pass (condensed element blocks), the edge-row pass (difference
+// form, FP64 and inner precision), Jacobi-PCG with FP64 accumulation of the
+// solution and reliable updates, and the recovery of U and Lambda.  Block-wide
+// barriers replace the kernel boundaries of the single-mesh path, and dot
+// products are block reductions (FP64 across threads), so one launch solves
+// the whole batch.  The per-element and per-row arithmetic is the same code as
+// the single-mesh kernels (kernels.cuh).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <numeric>
+#include <vector>
+
+#include "kernels.cuh"
+
+namespace phfem {
+namespace {
+
+struct MeshDesc {
+  int nT, nE, nL, pad;
+  long long t0, e0, l0, v0;  // offsets of the mesh's triangles, edges, multipliers, vertices
+};
+
+struct BatchParams {
+  double rtol2, upd2;   // rtol^2, reliable-update factor^2
+  int max_iter, max_updates;
+  double a_const;
+};
+
+struct MeshStats {
+  int iterations, updates, converged, status;
+  double rel, floor_rel;
+  int where, pad;      // failure site: 1 residual, 2 p.q, 3 r.z
+  double dbg[4];       // pq, rz, rz of the last update, alpha at the failure
+};
+
+template <int BS>
+__device__ __forceinline__ double bsum(double v, double* smem) {
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();  // smem may still be read by the previous reduction
+  if (lane == 0) smem[w] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int i = 0; i < BS / 32; ++i) t += smem[i];  // every thread, same order
+  return t;
+}
+
+template <typename T>
+struct BatchArrays {
+  const double2* xy;
+  const int32_t* tri;
+  const int32_t* ed2el;
+  const uint8_t* lk;
+  const uint8_t* eclass;
+  const int32_t* nbr;
+  const double* elen;
+  const int32_t* t2e;
+  const int8_t* sigma;
+  const int32_t* lam_id;
+  const double* aT;      // [sum nT] or NULL
+  const double* delta;   // [count]
+  const double* f_mid;   // [sum nE] or NULL
+  const double* bc_mid;  // [sum nE] or NULL
+  double* Kt;            // [7 sum nT] slot-major per mesh
+  double* val;           // [5 sum nE]
+  double* b;
+  T* lval;               // [4 sum nE]
+  T* rdiag;
+  T* dinv;
+  double* x;
+  T* r;
+  T* p;
+  T* q;
+  double* U;             // [3 sum nT] or NULL
+  double* Lambda;        // [sum nL] or NULL
+  double* w;             // [sum nE] or NULL
+};
+
+template <typename T, int BS>
+__global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restrict__ desc,
+                                              const int* __restrict__ order, int* next, BatchArrays<T> A,
+                                              BatchParams P, MeshStats* stats) {
+  __shared__ double smem[BS / 32];
+  __shared__ int s_mesh;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_mesh = atomicAdd(next, 1);
+    __syncthreads();
+    const int k = s_mesh;
+    if (k >= count) return;
+    const int id = order[k];
+    const MeshDesc D = desc[id];
+    const int nT = D.nT, nE = D.nE;
+    const size_t n = (size_t)nT, m = (size_t)nE;
+    const double2* xy = A.xy + D.v0;
+    const int32_t* tri = A.tri + 3 * D.t0;
+    const int32_t* ed2el = A.ed2el + 4 * D.e0;
+    const uint8_t* lk = A.lk + D.e0;
+    const uint8_t* ecl = A.eclass + D.e0;
+    const int32_t* nbr = A.nbr + 4 * D.e0;
+    const double* elen = A.elen + D.e0;
+    double* Kt = A.Kt + 7 * D.t0;
+    double* val = A.val + 5 * D.e0;
+    double* b = A.b + D.e0;
+    T* lval = A.lval + 4 * D.e0;
+    T* rdiag = A.rdiag + D.e0;
+    T* dinv = A.dinv + D.e0;
+    double* x = A.x + D.e0;
+    T* r = A.r + D.e0;
+    T* p = A.p + D.e0;
+    T* q = A.q + D.e0;
+    const double delta = A.delta[id];
+    const double* f = A.f_mid ? A.f_mid + D.e0 : nullptr;
+    const double* bc = A.bc_mid ? A.bc_mid + D.e0 : nullptr;
+
+    // 1. triangle pass
+    for (int t = threadIdx.x; t < nT; t += BS) {
+      const double a = A.aT ? A.aT[D.t0 + t] : P.a_const;
+      double K[7];
+      tri_block(xy[tri[3 * t]], xy[tri[3 * t + 1]], xy[tri[3 * t + 2]], a, delta, K);
+#pragma unroll
+      for (int j = 0; j < 7; ++j) Kt[j * n + t] = K[j];
+    }
+    __syncthreads();
+    // 2. edge rows; x starts at 0 on free edges and u_D on Dirichlet edges
+    for (int e = threadIdx.x; e < nE; e += BS) {
+      const int4 qd = reinterpret_cast<const int4*>(ed2el)[e];
+      const int kk = lk[e];
+      const uint8_t cls = ecl[e];
+      const EdgeRow R = edge_row<false>(Kt, n, qd.z, kk & 3, qd.w, (kk >> 2) & 3, cls, f ? f[e] : 0.0, bc ? bc[e] : 0.0,
+                                 cls == PHFEM_EDGE_NEUMANN ? elen[e] : 0.0, 1.0, 0.0, delta, f != nullptr,
+                                 bc != nullptr);
+      val[e] = R.rpart;
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        val[(s + 1) * m + e] = R.l[s];
+        lval[s * m + e] = (T)R.l[s];
+      }
+      b[e] = R.rhs;
+      rdiag[e] = (T)R.rpart;
+      dinv[e] = (T)(1.0 / R.diag);
+      x[e] = (cls == PHFEM_EDGE_DIRICHLET) ? R.rhs : 0.0;
+    }
+    __syncthreads();
+    // ||b_free|| with the Dirichlet lifting (x is (0, u_D) now)
+    double bb = 0.0;
+    {
+      double acc = 0.0;
+      for (int e = threadIdx.x; e < nE; e += BS) {
+        if (ecl[e] == PHFEM_EDGE_DIRICHLET) continue;
+        double fl;
+        const double rr = residual_row(nbr, val, b, x, m, e, fl);
+        acc += rr * rr;
+      }
+      bb = bsum<BS>(acc, smem);
+    }
+    // 3. Jacobi-PCG with reliable updates
+    int it = 0, updates = 0, converged = 0, status = 0, stagnant = 0, where = 0;
+    double rel = 0.0, floor_rel = 0.0, best = 1e300, rz = 0.0, tol2 = 0.0, dpq = 0.0, dal = 0.0, drzt = 0.0;
+    bool first = true;
+    for (;;) {
+      // true residual (FP64, difference form), inner residual replaced
+      double a_r = 0.0, a_z = 0.0, a_f = 0.0, a_p = 0.0;
+      for (int e = threadIdx.x; e < nE; e += BS) {
+        double fl;
+        const double rr = residual_row(nbr, val, b, x, m, e, fl);
+        a_r += rr * rr;
+        fl *= 0x1p-53;
+        a_f += fl * fl;
+        const T rs = (T)rr;
+        const T zs = dinv[e] * rs;
+        r[e] = rs;
+        if (first) p[e] = zs;
+        else a_p += (double)rs * (double)p[e];
+        a_z += (double)rs * (double)zs;
+      }
+      const double rr64 = bsum<BS>(a_r, smem);
+      const double rz_true = bsum<BS>(a_z, smem);
+      const double ff = bsum<BS>(a_f, smem);
+      const double rp = bsum<BS>(a_p, smem);
+      ++updates;
+      rel = bb > 0 ? sqrt(rr64 / bb) : 0.0;
+      floor_rel = bb > 0 ? sqrt(ff / bb) : 0.0;
+      drzt = rz_true;
+      if (!isfinite(rr64) || !isfinite(rz_true)) {
+        status = PHFEM_ENAN;
+        where = 1;
+        break;
+      }
+      if (rr64 <= P.rtol2 * bb || rr64 == 0.0) {
+        converged = 1;
+        break;
+      }
+      if (rel <= 2.0 * floor_rel) {
+        converged = 2;
+        break;
+      }
+      stagnant = (rel > 0.5 * best) ? stagnant + 1 : 0;
+      best = rel < best ? rel : best;
+      if (it >= P.max_iter || updates > P.max_updates || stagnant >= 8) {
+        status = PHFEM_ENOCONV;
+        break;
+      }
+      // the first step after the replacement is a line search alpha = r.p / p.Ap;
+      // restart the direction if it no longer fits the replaced residual
+      bool line_search = !first;
+      if (!first && (rz_true > 4.0 * rz || !(rp > 0.0))) {
+        for (int e = threadIdx.x; e < nE; e += BS) p[e] = dinv[e] * r[e];
+        line_search = false;
+      }
+      first = false;
+      rz = rz_true;
+      tol2 = P.upd2 * rz;
+      __syncthreads();
+      // iterate until the recursive residual fell by the update factor
+      while (it < P.max_iter) {
+        T acc = (T)0;
+        for (int e = threadIdx.x; e < nE; e += BS) {
+          const T s = spmv_row<T, false>(nbr, lval, rdiag, p, m, e);
+          q[e] = s;
+          acc += p[e] * s;
+        }
+        const double pq = bsum<BS>((double)acc, smem);
+        dpq = pq;
+        if (!(pq > 0.0) || !isfinite(pq)) {
+          status = isfinite(pq) ? PHFEM_EBREAKDOWN : PHFEM_ENAN;
+          where = 2;
+          break;
+        }
+        const double alpha64 = (line_search ? rp : rz) / pq;
+        line_search = false;
+        dal = alpha64;
+        const T alpha = (T)alpha64;
+        T acc2 = (T)0;
+        for (int e = threadIdx.x; e < nE; e += BS) {
+          x[e] += alpha64 * (double)p[e];
+          const T re = r[e] - alpha * q[e];
+          r[e] = re;
+          acc2 += re * (dinv[e] * re);
+        }
+        const double rzn = bsum<BS>((double)acc2, smem);
+        const T beta = (T)(rz > 0.0 ? rzn / rz : 0.0);
+        rz = rzn;
+        ++it;
+        for (int e = threadIdx.x; e < nE; e += BS) p[e] = dinv[e] * r[e] + beta * p[e];
+        __syncthreads();
+        if (!isfinite(rz)) {
+          status = PHFEM_ENAN;
+          where = 3;
+          break;
+        }
+        if (rz <= tol2) break;
+      }
+      if (status) break;
+      __syncthreads();
+    }
+    __syncthreads();
+    // 4. recovery: U = R^-1 w per triangle, Lambda from the T+ rows
+    if (A.U || A.Lambda) {
+      const int32_t* t2e = A.t2e + 3 * D.t0;
+      const int8_t* sg = A.sigma + 3 * D.t0;
+      const int32_t* lam = A.lam_id + D.e0;
+      for (int t = threadIdx.x; t < nT; t += BS) {
+        const int e0 = t2e[3 * t], e1 = t2e[3 * t + 1], e2 = t2e[3 * t + 2];
+        const double a0 = x[e0], a1 = x[e1], a2 = x[e2];
+        if (A.U) {
+          const double s = a0 + a1 + a2;
+          double* U = A.U + 3 * D.t0;
+          U[3 * t] = s - 2.0 * a0;
+          U[3 * t + 1] = s - 2.0 * a1;
+          U[3 * t + 2] = s - 2.0 * a2;
+        }
+        if (A.Lambda) {
+          const double K00 = Kt[t], K11 = Kt[n + t], K22 = Kt[2 * n + t];
+          const double K01 = Kt[3 * n + t], K12 = Kt[4 * n + t], K20 = Kt[5 * n + t], mT = Kt[6 * n + t];
+          const double res[3] = {K00 * a0 + K01 * a1 + K20 * a2, K01 * a0 + K11 * a1 + K12 * a2,
+                                 K20 * a0 + K12 * a1 + K22 * a2};
+          const int ee[3] = {e0, e1, e2};
+#pragma unroll
+          for (int kk = 0; kk < 3; ++kk) {
+            const int li = lam[ee[kk]];
+            if (li < 0 || sg[3 * t + kk] < 0) continue;
+            const double rr = res[kk] - mT * (f ? f[ee[kk]] : 0.0);
+            A.Lambda[D.l0 + li] = rr / elen[ee[kk]];
+          }
+        }
+      }
+    }
+    if (A.w)
+      for (int e = threadIdx.x; e < nE; e += BS) A.w[D.e0 + e] = x[e];
+    if (threadIdx.x == 0) {
+      MeshStats s;
+      s.iterations = it;
+      s.updates = updates;
+      s.converged = converged;
+      s.status = status;
+      s.rel = rel;
+      s.floor_rel = floor_rel;
+      s.where = where;
+      s.dbg[0] = dpq;
+      s.dbg[1] = rz;
+      s.dbg[2] = drzt;
+      s.dbg[3] = dal;
+      stats[id] = s;
+    }
+  }
+}
+
+}  // namespace
+}  // namespace phfem
+
+using namespace phfem;
+
+struct phfem_batch_s {
+  phfem_ctx ctx;
+  int count;
+  std::vector<long long> toff, eoff, loff, voff;  // count + 1
+  MeshDesc* desc;
+  int* order;
+  int* next;
+  MeshStats* stats;
+  double2* xy;
+  int32_t* tri;
+  int32_t* ed2el;
+  uint8_t* lk;
+  uint8_t* eclass;
+  int32_t* nbr;
+  double* elen;
+  int32_t* t2e;
+  int8_t* sigma;
+  int32_t* lam_id;
+  int32_t nD_zero_count;  // meshes without a Dirichlet edge
+  std::vector<int> nD;
+  // system and workspace (allocated on the first solve, for both precisions)
+  double* Kt = nullptr;
+  double* val = nullptr;
+  double* b = nullptr;
+  double* x = nullptr;
+  void* lval = nullptr;
+  void* rdiag = nullptr;
+  void* dinv = nullptr;
+  void* r = nullptr;
+  void* p = nullptr;
+  void* q = nullptr;
+  int block = 0;  // 0: not tuned yet
+};
+
+namespace phfem {
+namespace {
+
+void batch_free(phfem_batch B) {
+  phfem_ctx c = B->ctx;
+  for (void* ptr : {(void*)B->desc, (void*)B->order, (void*)B->next, (void*)B->stats, (void*)B->xy, (void*)B->tri,
+                    (void*)B->ed2el, (void*)B->lk, (void*)B->eclass, (void*)B->nbr, (void*)B->elen, (void*)B->t2e,
+                    (void*)B->sigma, (void*)B->lam_id, (void*)B->Kt, (void*)B->val, (void*)B->b, (void*)B->x,
+                    B->lval, B->rdiag, B->dinv, B->r, B->p, B->q})
+    dfree(c, ptr);
+  delete B;
+}
+
+template <typename T, int BS>
+int launch_batch(phfem_batch B, const BatchArrays<T>& A, const BatchParams& P) {
+  phfem_ctx ctx = B->ctx;
+  int per_sm = 0;
+  PH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<T, BS>, BS, 0));
+  if (per_sm < 1) per_sm = 1;
+  int grid = ctx->num_sms * per_sm;
+  if (grid > B->count) grid = B->count;
+  PH_CUDA(cudaMemsetAsync(B->next, 0, sizeof(int), ctx->stream));
+  k_batch<T, BS><<<grid, BS, 0, ctx->stream>>>(B->count, B->desc, B->order, B->next, A, P, B->stats);
+  return check_launch(ctx, "k_batch");
+}
+
+template <typename T>
+int run_batch(phfem_batch B, int block, const BatchArrays<T>& A, const BatchParams& P) {
+  switch (block) {
+    case 128: return launch_batch<T, 128>(B, A, P);
+    case 256: return launch_batch<T, 256>(B, A, P);
+    case 512: return launch_batch<T, 512>(B, A, P);
+    default: return launch_batch<T, 1024>(B, A, P);
+  }
+}
+
+}  // namespace
+}  // namespace phfem
+
+extern "C" {
+
+PHFEM_API int phfem_batch_create(phfem_ctx ctx, int32_t count, const phfem_mesh* meshes, phfem_batch* out) {
+  if (!out) return fail(PHFEM_EINVAL, "phfem_batch_create: out is NULL");
+  *out = nullptr;
+  if (!ctx || count < 1 || !meshes) return fail(PHFEM_EINVAL, "phfem_batch_create: bad argument");
+  phfem_batch B = new phfem_batch_s();
+  B->ctx = ctx;
+  B->count = count;
+  B->toff.assign(count + 1, 0);
+  B->eoff.assign(count + 1, 0);
+  B->loff.assign(count + 1, 0);
+  B->voff.assign(count + 1, 0);
+  B->nD.resize(count);
+  std::vector<MeshDesc> hd(count);
+  for (int i = 0; i < count; ++i) {
+    if (!meshes[i] || meshes[i]->ctx->device != ctx->device) {
+      delete B;
+      return fail(PHFEM_EINVAL, "phfem_batch_create: NULL mesh or mesh of another device");
+    }
+    const phfem_mesh_info& I = meshes[i]->info;
+    hd[i] = MeshDesc{I.nT, I.nE, I.nL, 0, B->toff[i], B->eoff[i], B->loff[i], B->voff[i]};
+    B->toff[i + 1] = B->toff[i] + I.nT;
+    B->eoff[i + 1] = B->eoff[i] + I.nE;
+    B->loff[i + 1] = B->loff[i] + I.nL;
+    B->voff[i + 1] = B->voff[i] + I.nV;
+    B->nD[i] = I.nD;
+  }
+  const size_t sT = B->toff[count], sE = B->eoff[count], sV = B->voff[count];
+  int st = PHFEM_OK;
+  auto chk = [&](int r) {
+    if (st == PHFEM_OK) st = r;
+  };
+  chk(dalloc_n(ctx, &B->desc, count));
+  chk(dalloc_n(ctx, &B->order, count));
+  chk(dalloc_n(ctx, &B->next, 1));
+  chk(dalloc_n(ctx, &B->stats, count));
+  chk(dalloc_n(ctx, &B->xy, sV));
+  chk(dalloc_n(ctx, &B->tri, 3 * sT));
+  chk(dalloc_n(ctx, &B->ed2el, 4 * sE));
+  chk(dalloc_n(ctx, &B->lk, sE));
+  chk(dalloc_n(ctx, &B->eclass, sE));
+  chk(dalloc_n(ctx, &B->nbr, 4 * sE));
+  chk(dalloc_n(ctx, &B->elen, sE));
+  chk(dalloc_n(ctx, &B->t2e, 3 * sT));
+  chk(dalloc_n(ctx, &B->sigma, 3 * sT));
+  chk(dalloc_n(ctx, &B->lam_id, sE));
+  if (st != PHFEM_OK) {
+    cudaStreamSynchronize(ctx->stream);
+    batch_free(B);
+    return st;
+  }
+  cudaStream_t s = ctx->stream;
+  // largest meshes first
+  std::vector<int> ord(count);
+  std::iota(ord.begin(), ord.end(), 0);
+  std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return hd[a].nE > hd[c].nE; });
+  auto cp = [&](void* dst, const void* src, size_t bytes) {
+    if (st == PHFEM_OK && bytes) {
+      cudaError_t e = cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s);
+      if (e != cudaSuccess) st = cuda_fail(e, "phfem_batch_create copy", __FILE__, __LINE__);
+    }
+  };
+  for (int i = 0; i < count; ++i) {
+    phfem_mesh M = meshes[i];
+    const phfem_mesh_info& I = M->info;
+    const long long t0 = B->toff[i], e0 = B->eoff[i], v0 = B->voff[i];
+    cp(B->xy + v0, M->xy, sizeof(double2) * I.nV);
+    cp(B->tri + 3 * t0, M->tri, sizeof(int32_t) * 3 * I.nT);
+    cp(B->ed2el + 4 * e0, M->ed2el, sizeof(int32_t) * 4 * I.nE);
+    cp(B->lk + e0, M->lk, I.nE);
+    cp(B->eclass + e0, M->eclass, I.nE);
+    cp(B->nbr + 4 * e0, M->nbr, sizeof(int32_t) * 4 * I.nE);
+    cp(B->elen + e0, M->elen, sizeof(double) * I.nE);
+    cp(B->t2e + 3 * t0, M->t2e, sizeof(int32_t) * 3 * I.nT);
+    cp(B->sigma + 3 * t0, M->sigma, 3 * I.nT);
+    cp(B->lam_id + e0, M->lam_id, sizeof(int32_t) * I.nE);
+  }
+  if (st == PHFEM_OK) {
+    cudaMemcpyAsync(B->desc, hd.data(), sizeof(MeshDesc) * count, cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(B->order, ord.data(), sizeof(int) * count, cudaMemcpyHostToDevice, s);
+    if (cudaStreamSynchronize(s) != cudaSuccess) st = cuda_fail(cudaGetLastError(), "phfem_batch_create", __FILE__, __LINE__);
+  }
+  if (st != PHFEM_OK) {
+    cudaStreamSynchronize(s);
+    batch_free(B);
+    return st;
+  }
+  *out = B;
+  return PHFEM_OK;
+}
+
+PHFEM_API int phfem_batch_offsets(phfem_batch B, int64_t* tri_off, int64_t* edge_off, int64_t* lam_off) {
+  if (!B) return fail(PHFEM_EINVAL, "phfem_batch_offsets: NULL batch");
+  for (int i = 0; i <= B->count; ++i) {
+    if (tri_off) tri_off[i] = B->toff[i];
+    if (edge_off) edge_off[i] = B->eoff[i];
+    if (lam_off) lam_off[i] = B->loff[i];
+  }
+  return PHFEM_OK;
+}
+
+PHFEM_API int phfem_batch_solve(phfem_batch B, const double* a_T, const double* delta, const double* f_mid,
+                                const double* bc_mid, int32_t precision, const phfem_solve_opts* opts, double* w,
+                                double* U, double* Lambda, int32_t block, int32_t* iterations, int32_t* converged,
+                                double* rel_residual) {
+  if (!B || !delta) return fail(PHFEM_EINVAL, "phfem_batch_solve: NULL argument");
+  if (precision != PHFEM_FP64 && precision != PHFEM_FP32_IR)
+    return fail(PHFEM_EINVAL, "phfem_batch_solve: unknown precision");
+  if (block != 0 && block != 128 && block != 256 && block != 512 && block != 1024)
+    return fail(PHFEM_EINVAL, "phfem_batch_solve: block must be 0, 128, 256, 512 or 1024");
+  phfem_ctx ctx = B->ctx;
+  cudaStream_t s = ctx->stream;
+  // host copy of delta to check solvability (no Dirichlet edge needs delta > 0)
+  std::vector<double> hdel(B->count);
+  PH_CUDA(cudaMemcpyAsync(hdel.data(), delta, sizeof(double) * B->count, cudaMemcpyDeviceToHost, s));
+  PH_CUDA(cudaStreamSynchronize(s));
+  for (int i = 0; i < B->count; ++i) {
+    if (!(hdel[i] >= 0.0) || !std::isfinite(hdel[i]))
+      return fail(PHFEM_EINVAL, "phfem_batch_solve: delta must be finite and >= 0 (mesh " + std::to_string(i) + ")");
+    if (hdel[i] == 0.0 && B->nD[i] == 0)
+      return fail(PHFEM_EINVAL, "phfem_batch_solve: mesh " + std::to_string(i) +
+                                    " has no Dirichlet edge and no reaction term (singular)");
+  }
+  const size_t sT = B->toff[B->count], sE = B->eoff[B->count];
+  const bool fp32 = precision == PHFEM_FP32_IR;
+  if (!B->Kt) {
+    int st = PHFEM_OK;
+    auto chk = [&](int r) {
+      if (st == PHFEM_OK) st = r;
+    };
+    chk(dalloc_n(ctx, &B->Kt, 7 * sT));
+    chk(dalloc_n(ctx, &B->val, 5 * sE));
+    chk(dalloc_n(ctx, &B->b, sE));
+    chk(dalloc_n(ctx, &B->x, sE));
+    chk(dalloc(ctx, &B->lval, 4 * sE * sizeof(double)));
+    chk(dalloc(ctx, &B->rdiag, sE * sizeof(double)));
+    chk(dalloc(ctx, &B->dinv, sE * sizeof(double)));
+    chk(dalloc(ctx, &B->r, sE * sizeof(double)));
+    chk(dalloc(ctx, &B->p, sE * sizeof(double)));
+    chk(dalloc(ctx, &B->q, sE * sizeof(double)));
+    if (st != PHFEM_OK) return st;
+  }
+  phfem_solve_opts o{};
+  if (opts) o = *opts;
+  if (o.rtol <= 0) o.rtol = 1e-10;
+  if (o.inner_rtol <= 0) o.inner_rtol = fp32 ? 0.1 : 0.01;
+  if (o.max_iter <= 0) o.max_iter = 200000;
+  if (o.max_refine <= 0) o.max_refine = 1000;
+  BatchParams P{o.rtol * o.rtol, o.inner_rtol * o.inner_rtol, o.max_iter, o.max_refine, 1.0};
+  const int bs = block ? block : (B->block ? B->block : 256);
+  int st;
+  if (fp32) {
+    BatchArrays<float> A{B->xy, B->tri, B->ed2el, B->lk, B->eclass, B->nbr, B->elen, B->t2e, B->sigma, B->lam_id,
+                         a_T, delta, f_mid, bc_mid, B->Kt, B->val, B->b, (float*)B->lval, (float*)B->rdiag,
+                         (float*)B->dinv, B->x, (float*)B->r, (float*)B->p, (float*)B->q, U, Lambda, w};
+    st = run_batch<float>(B, bs, A, P);
+  } else {
+    BatchArrays<double> A{B->xy, B->tri, B->ed2el, B->lk, B->eclass, B->nbr, B->elen, B->t2e, B->sigma, B->lam_id,
+                          a_T, delta, f_mid, bc_mid, B->Kt, B->val, B->b, (double*)B->lval, (double*)B->rdiag,
+                          (double*)B->dinv, B->x, (double*)B->r, (double*)B->p, (double*)B->q, U, Lambda, w};
+    st = run_batch<double>(B, bs, A, P);
+  }
+  if (st != PHFEM_OK) return st;
+  std::vector<MeshStats> hs(B->count);
+  PH_CUDA(cudaMemcpyAsync(hs.data(), B->stats, sizeof(MeshStats) * B->count, cudaMemcpyDeviceToHost, s));
+  PH_CUDA(cudaStreamSynchronize(s));
+  int worst = PHFEM_OK, bad = -1;
+  for (int i = 0; i < B->count; ++i) {
+    if (iterations) iterations[i] = hs[i].iterations;
+    if (converged) converged[i] = hs[i].converged;
+    if (rel_residual) rel_residual[i] = hs[i].rel;
+    if (hs[i].status != 0 && worst == PHFEM_OK) {
+      worst = hs[i].status;
+      bad = i;
+    }
+  }
+  if (worst != PHFEM_OK) {
+    const MeshStats& w = hs[bad];
+    char buf[320];
+    snprintf(buf, sizeof(buf),
+             "phfem_batch_solve: mesh %d: %s (site %d, iteration %d, update %d, p.q %.3e, r.z %.3e, "
+             "last true r.z %.3e, alpha %.3e, relative residual %.3e)",
+             bad, phfem_status_str(worst), w.where, w.iterations, w.updates, w.dbg[0], w.dbg[1], w.dbg[2], w.dbg[3],
+             w.rel);
+    return fail(worst, buf);
+  }
+  return PHFEM_OK;
+}
+
+PHFEM_API int phfem_batch_tune(phfem_batch B, const double* a_T, const double* delta, const double* f_mid,
+                               const double* bc_mid, int32_t precision, const phfem_solve_opts* opts,
+                               int32_t* chosen, double* ms_per_block) {
+  if (!B) return fail(PHFEM_EINVAL, "phfem_batch_tune: NULL batch");
+  static const int cand[4] = {128, 256, 512, 1024};
+  double best = 1e300;
+  int pick = 256;
+  for (int i = 0; i < 4; ++i) {
+    auto t0 = std::chrono::steady_clock::now();
+    int st = phfem_batch_solve(B, a_T, delta, f_mid, bc_mid, precision, opts, nullptr, nullptr, nullptr, cand[i],
+                               nullptr, nullptr, nullptr);
+    double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    if (st != PHFEM_OK && st != PHFEM_ENOCONV) return st;
+    if (ms_per_block) ms_per_block[i] = ms;
+    if (ms < best) {
+      best = ms;
+      pick = cand[i];
+    }
+  }
+  B->block = pick;
+  if (chosen) *chosen = pick;
+  return PHFEM_OK;
+}
+
+PHFEM_API int phfem_batch_destroy(phfem_batch B) {
+  if (!B) return fail(PHFEM_EINVAL, "phfem_batch_destroy: NULL batch");
+  batch_free(B);
+  return PHFEM_OK;
+}
+
+}  // extern "C"

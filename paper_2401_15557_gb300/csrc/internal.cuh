@@ -49,6 +49,9 @@ struct SolveState {
   double rr64;     // ||b - S x||^2 of the outer FP64 residual
   double bb;       // ||b||^2 of the free-edge system (with lifting)
   double floor2;   // squared estimate of the residual that rounding x to FP64 alone leaves
+  double rp;       // r.p right after a reliable update (p kept)
+  int use_rp;      // 1: the next step is a line search alpha = r.p / p.Ap
+  int pad2;
   int it;          // inner iterations done
   int done;        // 1: inner converged, 2: outer converged, 3: failure
   int status;      // phfem_status of a failure

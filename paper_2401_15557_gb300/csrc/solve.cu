@@ -19,7 +19,11 @@
 // residual has fallen by the factor inner_rtol since the last update, the true
 // residual r = b - S x is recomputed in FP64 (difference form) and replaces
 // the recursive one while the search direction is kept, so the Krylov space is
-// not lost as in restarted refinement.  The solve stops when
+// not lost as in restarted refinement.  The first step after a replacement is
+// an exact line search alpha = r.p / p.Ap (in exact CG r.p = r.z; with the
+// replaced residual the plain formula can diverge), and the direction is
+// restarted (p = D^-1 r) when r.p <= 0 or when the true residual is far above
+// the recursive one.  The solve stops when
 // ||r|| <= rtol ||b_free||, or when ||r|| reaches the level that rounding x to
 // FP64 alone leaves (estimated from |l| |x| per row), which on fine meshes can
 // exceed rtol because b scales like h^2 while S does not.
@@ -31,7 +35,7 @@
 #include <cstdio>
 #include <cstdlib>
 
-#include "internal.cuh"
+#include "kernels.cuh"
 
 namespace phfem {
 namespace {
@@ -48,7 +52,7 @@ __global__ void k_residual(int nE, const int32_t* __restrict__ nbr, const double
                            SolveState* st, double rtol2, double inner_rtol2, int mode) {
   __shared__ double smem[kBlock / 32];
   const size_t m = (size_t)nE;
-  double acc_r = 0.0, acc_z = 0.0, acc_f = 0.0;
+  double acc_r = 0.0, acc_z = 0.0, acc_f = 0.0, acc_p = 0.0;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
     double r;
     if (mode == 0) {
@@ -67,16 +71,8 @@ __global__ void k_residual(int nE, const int32_t* __restrict__ nbr, const double
       // difference form: S x = r_e x_e + sum_s l_es (x_e - x_s); the differences
       // of nearby values are exact or nearly so, which keeps the FP64 residual
       // accurate where the naive row product would cancel ~1/h^2 digits
-      const double xe = x[e];
-      double sx = val[e] * xe;
-      double fl = fabs(val[e] * xe);  // |S| |x| of the row: scale of the FP64 rounding of x
-#pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        const double l = val[(s + 1) * m + e], xs = x[nbr[s * m + e]];
-        sx += l * (xe - xs);
-        fl += fabs(l) * (fabs(xe) + fabs(xs));
-      }
-      r = b[e] - sx;
+      double fl;  // |S| |x| of the row: scale of the FP64 rounding of x
+      r = residual_row(nbr, val, b, x, m, e, fl);
       acc_r += r * r;
       fl *= 0x1p-53;
       acc_f += fl * fl;
@@ -84,21 +80,25 @@ __global__ void k_residual(int nE, const int32_t* __restrict__ nbr, const double
       const T zs = dinv[e] * rs;
       ri[e] = rs;
       if (mode == 1) pi[e] = zs;
+      else acc_p += (double)rs * (double)pi[e];
       acc_z += (double)rs * (double)zs;
     }
   }
   acc_r = block_sum(acc_r, smem);
   acc_z = block_sum(acc_z, smem);
   acc_f = block_sum(acc_f, smem);
+  acc_p = block_sum(acc_p, smem);
   if (threadIdx.x == 0) {
     partials[blockIdx.x] = acc_r;
     partials[kMaxGrid + blockIdx.x] = acc_z;
     partials[2 * kMaxGrid + blockIdx.x] = acc_f;
+    partials[3 * kMaxGrid + blockIdx.x] = acc_p;
   }
   if (!arrive_last(&st->counter[0])) return;
   const double rr = sum_partials(partials, smem);
   const double rz = sum_partials(partials + kMaxGrid, smem);
   const double ff = sum_partials(partials + 2 * kMaxGrid, smem);
+  const double rp = sum_partials(partials + 3 * kMaxGrid, smem);
   if (threadIdx.x == 0) {
     st->counter[0] = 0;
     if (mode == 0) {
@@ -107,6 +107,8 @@ __global__ void k_residual(int nE, const int32_t* __restrict__ nbr, const double
       st->rr64 = rr;
       st->floor2 = ff;
       st->rz = rz;
+      st->rp = rp;
+      st->use_rp = (mode == 2) ? 1 : 0;
       if (mode == 1) {
         st->rz0 = rz;
         st->it = 0;
@@ -135,16 +137,9 @@ __global__ void __launch_bounds__(kBlock) k_cg_spmv(int nE, const int32_t* __res
   const size_t m = (size_t)nE;
   T acc = (T)0;  // this thread's few rows in T; across threads and blocks in FP64
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
-    const int c0 = nbr[e], c1 = nbr[m + e], c2 = nbr[2 * m + e], c3 = nbr[3 * m + e];
-    const T l0 = lval[e], l1 = lval[m + e], l2 = lval[2 * m + e], l3 = lval[3 * m + e];
-    const T pe = p[e];
-    T s = rdiag[e] * pe;
-    s += l0 * (pe - __ldg(p + c0));
-    s += l1 * (pe - __ldg(p + c1));
-    s += l2 * (pe - __ldg(p + c2));
-    s += l3 * (pe - __ldg(p + c3));
+    const T s = spmv_row(nbr, lval, rdiag, p, m, e);
     q[e] = s;
-    acc += pe * s;
+    acc += p[e] * s;
   }
   const double accd = block_sum((double)acc, smem);
   if (threadIdx.x == 0) partials[blockIdx.x] = accd;
@@ -156,7 +151,8 @@ __global__ void __launch_bounds__(kBlock) k_cg_spmv(int nE, const int32_t* __res
       st->done = 3;
       st->status = isfinite(pq) ? PHFEM_EBREAKDOWN : PHFEM_ENAN;
     } else {
-      st->alpha = st->rz / pq;
+      st->alpha = (st->use_rp ? st->rp : st->rz) / pq;
+      st->use_rp = 0;
     }
   }
 }
@@ -212,8 +208,10 @@ __global__ void __launch_bounds__(kBlock) k_cg_dir(int nE, const T* __restrict__
 // Restart of the direction after a reliable update whose true residual is far
 // from the recursive one (the kept direction would no longer fit it).
 template <typename T>
-__global__ void k_cg_restart(int nE, const T* __restrict__ r, const T* __restrict__ dinv, T* __restrict__ p) {
+__global__ void k_cg_restart(int nE, const T* __restrict__ r, const T* __restrict__ dinv, T* __restrict__ p,
+                             SolveState* st) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) p[e] = dinv[e] * r[e];
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->use_rp = 0;  // p = D^-1 r: r.p = r.z
 }
 
 __global__ void k_init_x(int nE, const uint8_t* __restrict__ eclass, const double* __restrict__ b,
@@ -362,8 +360,8 @@ int solve_typed(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats) {
     PH_TRY(residual(2));
     ++updates;
     PH_TRY(read_state(sys));
-    if (sys->st_host->done == 0 && sys->st_host->rz > 4.0 * rz_recursive) {
-      k_cg_restart<T><<<g, kBlock, 0, s>>>(nE, ri, dinv, pi);
+    if (sys->st_host->done == 0 && (sys->st_host->rz > 4.0 * rz_recursive || !(sys->st_host->rp > 0.0))) {
+      k_cg_restart<T><<<g, kBlock, 0, s>>>(nE, ri, dinv, pi, sys->st);
       PH_TRY(check_launch(ctx, "k_cg_restart"));
       ++restarts;
     }

@@ -92,6 +92,13 @@ def lib() -> C.CDLL:
             "phfem_cn_step": (C.c_int, [_H, C.c_int32, C.POINTER(SolveOpts), C.POINTER(Stats)]),
             "phfem_cn_read": (C.c_int, [_H, _P, _P, _P, _P, C.POINTER(C.c_int32)]),
             "phfem_cn_destroy": (C.c_int, [_H]),
+            "phfem_batch_create": (C.c_int, [_H, C.c_int32, C.POINTER(_H), C.POINTER(_H)]),
+            "phfem_batch_offsets": (C.c_int, [_H, _P, _P, _P]),
+            "phfem_batch_solve": (C.c_int, [_H, _P, _P, _P, _P, C.c_int32, C.POINTER(SolveOpts), _P, _P, _P,
+                                            C.c_int32, _P, _P, _P]),
+            "phfem_batch_tune": (C.c_int, [_H, _P, _P, _P, _P, C.c_int32, C.POINTER(SolveOpts), C.POINTER(C.c_int32),
+                                           _P]),
+            "phfem_batch_destroy": (C.c_int, [_H]),
             "phfem_csr_pcg_noalloc": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, C.c_double, C.c_int32,
                                                 C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
         }
@@ -275,6 +282,54 @@ def phfem_status_str(status: int) -> str:
 
 def phfem_last_error() -> str:
     return lib().phfem_last_error().decode()
+
+
+# --- batched assembly and solve --------------------------------------------------
+
+def phfem_batch_create(ctx, meshes):
+    arr = (_H * len(meshes))(*meshes)
+    h = _H()
+    _check(lib().phfem_batch_create(ctx, len(meshes), arr, C.byref(h)), "phfem_batch_create")
+    return h
+
+
+def phfem_batch_offsets(batch, count):
+    import numpy as np
+    t = np.zeros(count + 1, dtype=np.int64)
+    e = np.zeros(count + 1, dtype=np.int64)
+    l = np.zeros(count + 1, dtype=np.int64)
+    _check(lib().phfem_batch_offsets(batch, t.ctypes.data, e.ctypes.data, l.ctypes.data), "phfem_batch_offsets")
+    return t, e, l
+
+
+def phfem_batch_solve(batch, count, delta, a_T=None, f_mid=None, bc_mid=None, precision=PHFEM_FP32_IR,
+                      opts=None, w=None, U=None, Lambda=None, block=0):
+    import numpy as np
+    it = np.zeros(count, dtype=np.int32)
+    cv = np.zeros(count, dtype=np.int32)
+    rel = np.zeros(count, dtype=np.float64)
+    o = opts if opts is not None else solve_opts()
+    _check(lib().phfem_batch_solve(batch, _ptr(a_T, torch.float64), _ptr(delta, torch.float64, count),
+                                   _ptr(f_mid, torch.float64), _ptr(bc_mid, torch.float64), int(precision),
+                                   C.byref(o), _ptr(w, torch.float64), _ptr(U, torch.float64),
+                                   _ptr(Lambda, torch.float64), int(block), it.ctypes.data, cv.ctypes.data,
+                                   rel.ctypes.data), "phfem_batch_solve")
+    return {"iterations": it, "converged": cv, "rel_residual": rel}
+
+
+def phfem_batch_tune(batch, delta, a_T=None, f_mid=None, bc_mid=None, precision=PHFEM_FP32_IR, opts=None):
+    import numpy as np
+    ms = np.zeros(4, dtype=np.float64)
+    ch = C.c_int32()
+    o = opts if opts is not None else solve_opts()
+    _check(lib().phfem_batch_tune(batch, _ptr(a_T, torch.float64), _ptr(delta, torch.float64),
+                                  _ptr(f_mid, torch.float64), _ptr(bc_mid, torch.float64), int(precision),
+                                  C.byref(o), C.byref(ch), ms.ctypes.data), "phfem_batch_tune")
+    return int(ch.value), dict(zip((128, 256, 512, 1024), ms.tolist()))
+
+
+def phfem_batch_destroy(batch):
+    _check(lib().phfem_batch_destroy(batch), "phfem_batch_destroy")
 
 
 # --- solve without device allocation -------------------------------------------
