@@ -59,8 +59,10 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="lshape", choices=["lshape", "batched"],
-                    help="lshape: the L-shaped 6.3M-triangle solve (default); batched: 4096 meshes in one launch")
+    ap.add_argument("--workload", default="lshape", choices=["lshape", "batched", "heat"],
+                    help="lshape: the L-shaped 6.3M-triangle solve (default); batched: 4096 meshes in one "
+                         "launch; heat: Crank-Nicolson on 512 x 512 squares, 512 steps")
+    ap.add_argument("--heat-n", type=int, default=512)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--no-clocks", action="store_true",
                     help="do not sample nvidia-smi clocks (profiling runs under ncu)")
@@ -275,12 +277,83 @@ def run_batched(args):
     return 0
 
 
+def run_heat(args):
+    """Crank-Nicolson for u_t - Lap u = f on the unit square, n x n squares
+    (n = 512: 524,288 triangles), dt = 1/n, T = 1: u = e^-t sin(pi x) sin(pi y),
+    u = 0 on x = 0, 1 and the exact flux on y = 0, 1.  One step = right-hand
+    side, solve to 1e-10 (warm start) and multiplier recovery; steps replayed
+    from the captured CUDA graph against host-driven steps."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    from paper_2401_15557_gb300 import inputs as I
+    from paper_2401_15557_gb300 import phfem as P
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    n = args.heat_n
+    mesh = I.square_mesh(n)
+    pi = np.pi
+    sfun = lambda x, y: np.sin(pi * x) * np.sin(pi * y)
+    stream = torch.cuda.current_stream()
+    ctx = P.phfem_ctx_create(stream)
+    d = lambda a, t: torch.as_tensor(np.ascontiguousarray(a), dtype=t, device=dev)
+    mh = P.phfem_mesh_build(ctx, d(mesh.xy, torch.float64), d(mesh.tri, torch.int32),
+                            d(mesh.dirichlet, torch.int32), d(mesh.neumann, torch.int32))
+    info = P.phfem_mesh_info_get(mh)
+    T_ = {k: v.cpu().numpy() for k, v in P.phfem_mesh_tables(mh).items()}
+    f0, g0 = I.edge_data(mesh.xy, T_["ed2el"], T_["eclass"], lambda x, y: (2 * pi * pi - 1.0) * sfun(x, y),
+                         lambda x, y, nx, ny: pi * (np.cos(pi * x) * np.sin(pi * y) * nx
+                                                    + np.sin(pi * x) * np.cos(pi * y) * ny),
+                         lambda x, y: 0 * x)
+    w0, _ = I.edge_data(mesh.xy, T_["ed2el"], T_["eclass"], sfun)
+    dt = 1.0 / n
+    nsteps = n
+    phi = np.exp(-dt * np.arange(nsteps + 1))[None]
+    F, G, W0 = d(f0[None], torch.float64), d(g0[None], torch.float64), d(w0, torch.float64)
+    out = {}
+    U = torch.empty(3 * info["nT"], dtype=torch.float64, device=dev)
+    for prec, name in ((P.PHFEM_FP32_IR, "fp32_refined"), (P.PHFEM_FP64, "fp64")):
+        sysh = P.phfem_assemble(mh, None, None, delta=0.0, dt=dt, precision=prec)
+        for mode in ("graph", "host"):
+            cn = P.phfem_cn_create(sysh, F, G, phi, W0)
+            stepf = P.phfem_cn_step_graph if mode == "graph" else P.phfem_cn_step
+            stepf(cn, 2, P.solve_opts(rtol=1e-10))  # capture (graph) and warm up
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = stepf(cn, nsteps - 2, P.solve_opts(rtol=1e-10))
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            P.phfem_cn_read(cn, U=U)
+            P.phfem_cn_destroy(cn)
+            out[f"{name}_{mode}"] = {"steps_per_s": (nsteps - 2) / el, "ms_per_step": 1e3 * el / (nsteps - 2),
+                                     "iterations_per_step": st["iterations"] / max(1, nsteps - 2),
+                                     "converged": st["converged"], "rel_residual_max": st["rel_residual"]}
+        # error at t = 1 against the exact solution at the vertices
+        P_ = mesh.xy[mesh.tri]
+        ue = np.exp(-1.0) * sfun(P_[..., 0], P_[..., 1]).ravel()
+        out[f"{name}_graph"]["max_vertex_error_t1"] = float(np.max(np.abs(U.cpu().numpy() - ue)))
+        P.phfem_sys_destroy(sysh)
+    g = out["fp32_refined_graph"]
+    line = {"metric": METRIC, "value": g["steps_per_s"] * mesh.nT, "unit": UNIT + " (per CN step)", "n_gpus": 1,
+            "steps": nsteps - 2, "warmup": 2, "ms_per_step": g["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"heat-cn-{n}x{n}", "triangles": mesh.nT, "edges": info["nE"], "dt": dt,
+                       "steps": nsteps}, "cn": out}
+    print(json.dumps(line), flush=True)
+    P.phfem_mesh_destroy(mh)
+    P.phfem_ctx_destroy(ctx)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
         return run_batched(args)
+    if args.workload == "heat":
+        return run_heat(args)
 
     import numpy as np
     import torch

@@ -247,6 +247,17 @@ PHFEM_API int phfem_cn_create(phfem_sys sys, const phfem_source* src, const doub
  * the source has no phi for a requested step. */
 PHFEM_API int phfem_cn_step(phfem_cn cn, int32_t nsteps, const phfem_solve_opts* opts,
                             phfem_stats* stats);
+/* As phfem_cn_step, with every step replayed from a CUDA graph captured on
+ * first use (and again when opts change): right-hand side, Dirichlet values,
+ * the solve -- its iteration loop a conditional WHILE node whose body runs
+ * eight iterations, the conditional reliable update and a one-thread control
+ * kernel (bounded by max_iter) -- and the recovery.  The time index and the
+ * time factors are read on the device, so the host only launches the graph
+ * nsteps times and synchronises once.  Gives bitwise the results of
+ * phfem_cn_step.  Requires a context stream other than the legacy default
+ * stream for nothing: capture runs on a private stream. */
+PHFEM_API int phfem_cn_step_graph(phfem_cn cn, int32_t nsteps, const phfem_solve_opts* opts,
+                                  phfem_stats* stats);
 /* Reads the state after the last step (any pointer may be NULL):
  *   w [nE], U [3 nT], Lambda_n [nL], Lambda_half [nL] (Lambda^{n-1/2}),
  *   step: host int32, number of steps done. */

@@ -10,7 +10,9 @@
 // element rows on the T+ side:
 //   |E| Lambda^{n-1/2} = (M^CR (w^n - w^{n-1})/dt + K^CR (w^n + w^{n-1})/2 - F^{n-1/2})_k
 // and Lambda^n = 2 Lambda^{n-1/2} - Lambda^{n-1}.
+#include <algorithm>
 #include <chrono>
+#include <cstring>
 #include <vector>
 
 #include "internal.cuh"
@@ -23,10 +25,18 @@ struct phfem_cn_s {
   double* fq;        // [Q][nE]
   double* bcq;       // [Q][nE]
   std::vector<double> phi;  // [Q][nt]
+  double* phi_dev;   // [Q][nt] (the graph reads the time factors on the device)
+  int* step_dev;     // steps done, advanced on the device
+  int* it_dev;       // [nt] iterations of every step
+  int* conv_dev;     // [nt] convergence code of every step
+  double* rel_dev;   // [nt] final relative residual of every step
   double* xprev;     // [nE]
   double* f_eff;     // [nE]
   double* lam_half;  // [nL]
   double* lam_n;     // [nL]
+  // captured step
+  cudaGraphExec_t exec = nullptr;
+  phfem_solve_opts graph_opts{};
 };
 
 namespace phfem {
@@ -51,15 +61,27 @@ __global__ void k_cn_init(int nE, const uint8_t* __restrict__ eclass, const doub
   }
 }
 
+// Time factors of step n = *step + 1 from the device table.
+__device__ __forceinline__ Phi phi_dev_at(const double* phi, int Q, int nt, int n) {
+  Phi p;
+  for (int q = 0; q < Q; ++q) {
+    p.now[q] = phi[q * nt + n];
+    p.avg[q] = 0.5 * (phi[q * nt + n] + phi[q * nt + n - 1]);
+  }
+  return p;
+}
+
 // rhs = 2 M w^{n-1} - A+ w^{n-1} + dt (sum_q avg_q (m_e f_q + [Neumann] |E| g_q))
 // on free rows (A+ = M + dt/2 K; w^{n-1} holds u_D(t_{n-1}) on Dirichlet rows),
 // u_D(t_n) on Dirichlet rows; also the averaged source f^{n-1/2} per edge.
 __global__ void k_cn_rhs(int nE, const int32_t* __restrict__ nbr, const double* __restrict__ val,
                          const double* __restrict__ x, const double* __restrict__ me,
                          const uint8_t* __restrict__ eclass, const double* __restrict__ elen,
-                         const double* __restrict__ fq, const double* __restrict__ bcq, int Q, Phi ph, double dt,
+                         const double* __restrict__ fq, const double* __restrict__ bcq, int Q,
+                         const double* __restrict__ phi, int nt, const int* __restrict__ step, double dt,
                          double* __restrict__ b, double* __restrict__ f_eff) {
   const size_t m = (size_t)nE;
+  const Phi ph = phi_dev_at(phi, Q, nt, *step + 1);
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
     const uint8_t cls = eclass[e];
     double fav = 0.0;
@@ -96,10 +118,25 @@ __global__ void k_lam_update(int nL, const double* __restrict__ half, double* __
     lam[i] = 2.0 * half[i] - lam[i];
 }
 
+// Records the step's solve statistics and advances the step counter.
+__global__ void k_cn_advance(int* step, const SolveState* st, int* it, int* conv, double* rel) {
+  const int n = *step + 1;
+  it[n] = st->it;
+  conv[n] = st->done == 2 ? st->conv : (st->done == 3 ? st->status : PHFEM_ENOCONV);
+  rel[n] = st->bb > 0 ? sqrt(st->rr64 / st->bb) : 0.0;
+  *step = n;
+}
+
 void cn_free(phfem_cn cn) {
   phfem_ctx c = cn->sys->mesh->ctx;
+  if (cn->exec) cudaGraphExecDestroy(cn->exec);
   dfree(c, cn->fq);
   dfree(c, cn->bcq);
+  dfree(c, cn->phi_dev);
+  dfree(c, cn->step_dev);
+  dfree(c, cn->it_dev);
+  dfree(c, cn->conv_dev);
+  dfree(c, cn->rel_dev);
   dfree(c, cn->xprev);
   dfree(c, cn->f_eff);
   dfree(c, cn->lam_half);
@@ -114,6 +151,90 @@ Phi phi_at(const phfem_cn_s* cn, int n) {
     p.avg[q] = n > 0 ? 0.5 * (cn->phi[(size_t)q * cn->nt + n] + cn->phi[(size_t)q * cn->nt + n - 1]) : p.now[q];
   }
   return p;
+}
+
+// One step's work up to the solve, on the context stream.
+int enqueue_pre(phfem_cn cn) {
+  phfem_sys sys = cn->sys;
+  phfem_mesh m = sys->mesh;
+  phfem_ctx ctx = m->ctx;
+  cudaStream_t s = ctx->stream;
+  const int nE = m->info.nE;
+  PH_CUDA(cudaMemcpyAsync(cn->xprev, sys->x, sizeof(double) * nE, cudaMemcpyDeviceToDevice, s));
+  k_cn_rhs<<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, m->nbr, sys->val, sys->x, sys->me, m->eclass, m->elen, cn->fq,
+                                                cn->bcq, cn->Q, cn->phi_dev, cn->nt, cn->step_dev, sys->c.dt, sys->b,
+                                                cn->f_eff);
+  PH_TRY(check_launch(ctx, "k_cn_rhs"));
+  k_set_dirichlet<<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, m->eclass, sys->b, sys->x);
+  return check_launch(ctx, "k_set_dirichlet");
+}
+
+// One step's work after the solve: Lambda^{n-1/2}, Lambda^n, step statistics.
+int enqueue_post(phfem_cn cn) {
+  phfem_sys sys = cn->sys;
+  phfem_mesh m = sys->mesh;
+  phfem_ctx ctx = m->ctx;
+  cudaStream_t s = ctx->stream;
+  const int nL = m->info.nL;
+  PH_TRY(recover(sys, sys->x, cn->xprev, cn->f_eff, 1.0 / sys->c.dt, 0.5, nullptr, cn->lam_half));
+  k_lam_update<<<grid_for(ctx, nL), kBlock, 0, s>>>(nL, cn->lam_half, cn->lam_n);
+  PH_TRY(check_launch(ctx, "k_lam_update"));
+  k_cn_advance<<<1, 1, 0, s>>>(cn->step_dev, sys->st, cn->it_dev, cn->conv_dev, cn->rel_dev);
+  return check_launch(ctx, "k_cn_advance");
+}
+
+// Captures one whole step into a graph: the solve loop runs in a conditional
+// WHILE node controlled on the device, so a step needs no host round trip.
+int build_step_graph(phfem_cn cn, const phfem_solve_opts& o) {
+  phfem_ctx ctx = cn->sys->mesh->ctx;
+  PH_CUDA(cudaStreamSynchronize(ctx->stream));
+  cudaStream_t cs;
+  PH_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  const cudaStream_t saved = ctx->stream;
+  const bool saved_prof = ctx->profile;
+  ctx->stream = cs;      // every helper enqueues on ctx->stream
+  ctx->profile = false;  // no event nodes inside the graph
+  int st = PHFEM_OK;
+  cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
+  if (st == PHFEM_OK) st = enqueue_pre(cn);
+  if (st == PHFEM_OK) st = capture_solve(cn->sys, &o, cs, 8);
+  if (st == PHFEM_OK) st = enqueue_post(cn);
+  cudaGraph_t graph = nullptr;
+  e = cudaStreamEndCapture(cs, &graph);
+  if (e != cudaSuccess && st == PHFEM_OK) st = cuda_fail(e, "cudaStreamEndCapture", __FILE__, __LINE__);
+  ctx->stream = saved;
+  ctx->profile = saved_prof;
+  if (st == PHFEM_OK) {
+    if (cn->exec) cudaGraphExecDestroy(cn->exec);
+    cn->exec = nullptr;
+    e = cudaGraphInstantiate(&cn->exec, graph, 0);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaGraphInstantiate", __FILE__, __LINE__);
+  }
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  cudaGetLastError();
+  if (st == PHFEM_OK) cn->graph_opts = o;
+  return st;
+}
+
+int read_steps(phfem_cn cn, int first, int count, phfem_stats* st) {
+  if (count <= 0) return PHFEM_OK;
+  cudaStream_t s = cn->sys->mesh->ctx->stream;
+  std::vector<int> it(count), conv(count);
+  std::vector<double> rel(count);
+  PH_CUDA(cudaMemcpyAsync(it.data(), cn->it_dev + first, sizeof(int) * count, cudaMemcpyDeviceToHost, s));
+  PH_CUDA(cudaMemcpyAsync(conv.data(), cn->conv_dev + first, sizeof(int) * count, cudaMemcpyDeviceToHost, s));
+  PH_CUDA(cudaMemcpyAsync(rel.data(), cn->rel_dev + first, sizeof(double) * count, cudaMemcpyDeviceToHost, s));
+  PH_CUDA(cudaStreamSynchronize(s));
+  int worst = 1;
+  for (int i = 0; i < count; ++i) {
+    st->iterations += it[i];
+    worst = std::min(worst, conv[i]);
+    st->rel_residual = std::max(st->rel_residual, rel[i]);
+  }
+  st->converged = worst;
+  return worst > 0 ? PHFEM_OK : worst;
 }
 
 }  // namespace
@@ -147,6 +268,11 @@ PHFEM_API int phfem_cn_create(phfem_sys sys, const phfem_source* src, const doub
   };
   chk(dalloc_n(ctx, &cn->fq, cn->Q * nE));
   chk(dalloc_n(ctx, &cn->bcq, cn->Q * nE));
+  chk(dalloc_n(ctx, &cn->phi_dev, (size_t)cn->Q * cn->nt));
+  chk(dalloc_n(ctx, &cn->step_dev, 1));
+  chk(dalloc_n(ctx, &cn->it_dev, cn->nt));
+  chk(dalloc_n(ctx, &cn->conv_dev, cn->nt));
+  chk(dalloc_n(ctx, &cn->rel_dev, cn->nt));
   chk(dalloc_n(ctx, &cn->xprev, nE));
   chk(dalloc_n(ctx, &cn->f_eff, nE));
   chk(dalloc_n(ctx, &cn->lam_half, nL));
@@ -157,6 +283,11 @@ PHFEM_API int phfem_cn_create(phfem_sys sys, const phfem_source* src, const doub
     if (Lambda0) cudaMemcpyAsync(cn->lam_n, Lambda0, sizeof(double) * nL, cudaMemcpyDeviceToDevice, s);
     else cudaMemsetAsync(cn->lam_n, 0, sizeof(double) * nL, s);
     cudaMemsetAsync(cn->lam_half, 0, sizeof(double) * nL, s);
+    cudaMemcpyAsync(cn->phi_dev, cn->phi.data(), sizeof(double) * cn->phi.size(), cudaMemcpyHostToDevice, s);
+    cudaMemsetAsync(cn->step_dev, 0, sizeof(int), s);
+    cudaMemsetAsync(cn->it_dev, 0, sizeof(int) * cn->nt, s);
+    cudaMemsetAsync(cn->conv_dev, 0, sizeof(int) * cn->nt, s);
+    cudaMemsetAsync(cn->rel_dev, 0, sizeof(double) * cn->nt, s);
     k_cn_init<<<grid_for(ctx, nE), kBlock, 0, s>>>((int)nE, m->eclass, w0, cn->bcq, cn->Q, phi_at(cn, 0), sys->x);
     st = check_launch(ctx, "k_cn_init");
   }
@@ -180,31 +311,43 @@ PHFEM_API int phfem_cn_step(phfem_cn cn, int32_t nsteps, const phfem_solve_opts*
   phfem_mesh m = sys->mesh;
   phfem_ctx ctx = m->ctx;
   cudaStream_t s = ctx->stream;
-  const int nE = m->info.nE, nL = m->info.nL;
-  const double dt = sys->c.dt;
   phfem_stats st{};
   int status = PHFEM_OK;
   for (int k = 0; k < nsteps; ++k) {
-    const int n = cn->step + 1;
-    const Phi ph = phi_at(cn, n);
-    PH_CUDA(cudaMemcpyAsync(cn->xprev, sys->x, sizeof(double) * nE, cudaMemcpyDeviceToDevice, s));
-    k_cn_rhs<<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, m->nbr, sys->val, sys->x, sys->me, m->eclass, m->elen, cn->fq,
-                                                  cn->bcq, cn->Q, ph, dt, sys->b, cn->f_eff);
-    PH_TRY(check_launch(ctx, "k_cn_rhs"));
-    k_set_dirichlet<<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, m->eclass, sys->b, sys->x);
-    PH_TRY(check_launch(ctx, "k_set_dirichlet"));
+    PH_TRY(enqueue_pre(cn));
     status = solve_system(sys, opts, &st, true);
     if (status != PHFEM_OK) break;
-    PH_TRY(recover(sys, sys->x, cn->xprev, cn->f_eff, 1.0 / dt, 0.5, nullptr, cn->lam_half));
-    k_lam_update<<<grid_for(ctx, nL), kBlock, 0, s>>>(nL, cn->lam_half, cn->lam_n);
-    PH_TRY(check_launch(ctx, "k_lam_update"));
-    cn->step = n;
+    PH_TRY(enqueue_post(cn));
+    cn->step += 1;
     st.steps += 1;
   }
   PH_CUDA(cudaStreamSynchronize(s));
   st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (stats) *stats = st;
   return status;
+}
+
+PHFEM_API int phfem_cn_step_graph(phfem_cn cn, int32_t nsteps, const phfem_solve_opts* opts, phfem_stats* stats) {
+  if (!cn || nsteps < 0) return fail(PHFEM_EINVAL, "phfem_cn_step_graph: bad argument");
+  if (cn->step + nsteps >= cn->nt)
+    return fail(PHFEM_EINVAL, "phfem_cn_step_graph: the source has no time factors for the requested steps");
+  auto t0 = std::chrono::steady_clock::now();
+  phfem_solve_opts o{};
+  if (opts) o = *opts;
+  fill_opts(cn->sys, o);
+  if (!cn->exec || std::memcmp(&o, &cn->graph_opts, sizeof(o)) != 0) PH_TRY(build_step_graph(cn, o));
+  phfem_ctx ctx = cn->sys->mesh->ctx;
+  for (int k = 0; k < nsteps; ++k) PH_CUDA(cudaGraphLaunch(cn->exec, ctx->stream));
+  ctx->launches += (int64_t)nsteps;
+  phfem_stats st{};
+  const int first = cn->step + 1;
+  int status = read_steps(cn, first, nsteps, &st);
+  cn->step += nsteps;
+  st.steps = nsteps;
+  st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = st;
+  if (status != PHFEM_OK) return fail(status, "phfem_cn_step_graph: a step did not converge");
+  return PHFEM_OK;
 }
 
 PHFEM_API int phfem_cn_read(phfem_cn cn, double* w, double* U, double* Lambda_n, double* Lambda_half,

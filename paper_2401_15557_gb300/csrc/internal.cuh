@@ -51,6 +51,10 @@ struct SolveState {
   double floor2;   // squared estimate of the residual that rounding x to FP64 alone leaves
   double rp;       // r.p right after a reliable update (p kept)
   int use_rp;      // 1: the next step is a line search alpha = r.p / p.Ap
+  int restart;     // 1: the next SpMV restarts the direction, p = D^-1 r
+  int conv;        // 1: rtol met, 2: stopped at the FP64 floor
+  int updates;     // true-residual evaluations
+  int bodies;      // executions of a graph loop body (bounded)
   int pad2;
   int it;          // inner iterations done
   int done;        // 1: inner converged, 2: outer converged, 3: failure
@@ -148,7 +152,11 @@ int exclusive_scan(phfem_ctx ctx, const int32_t* in, int32_t* out, int n, int32_
 
 // Solve helpers shared by the elliptic and Crank-Nicolson drivers.
 int solve_system(phfem_sys sys, const phfem_solve_opts* opts, phfem_stats* stats, bool warm);
+// Enqueues a whole solve (start, device-controlled iteration loop in a CUDA
+// graph conditional WHILE node) into the graph being captured on `capture`.
+int capture_solve(phfem_sys sys, const phfem_solve_opts* opts, cudaStream_t capture, int iters_per_body);
 int sys_init_x(phfem_sys sys, const double* w0);
+void fill_opts(phfem_sys sys, phfem_solve_opts& o);
 int recover(phfem_sys sys, const double* x_new, const double* x_old, const double* f_eff,
             double inv_dt, double theta, double* U, double* Lambda);
 

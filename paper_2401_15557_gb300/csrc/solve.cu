@@ -40,16 +40,24 @@
 namespace phfem {
 namespace {
 
-// r = b - S x (FP64); inner start vectors r' = r, p = D^-1 r', d = 0; two
-// reductions (||r||^2 and r'.D^-1 r').  mode 0 replaces x by (0 on free rows,
-// u_D on Dirichlet rows): ||b_free||^2 with the Dirichlet lifting.
-// mode 1 starts the iteration (p = D^-1 r); mode 2 is a reliable update (p kept).
+// r = b - S x (FP64); inner start vectors; reductions ||r||^2, r.D^-1 r, the
+// FP64 floor estimate and (after an update) r.p.  Modes:
+//   0  ||b_free||^2 with the Dirichlet lifting (x replaced by (0, u_D));
+//   1  start: p = D^-1 r;
+//   2  reliable update: the true residual replaces the recursive one, p kept;
+//   3  as 2, but only if the iteration asked for an update (done == 1).
+// The last block decides on the device: converged (rtol, or twice the FP64
+// floor), the line-search step, or a restart of the direction.
 template <typename T>
 __global__ void k_residual(int nE, const int32_t* __restrict__ nbr, const double* __restrict__ val,
                            const double* __restrict__ b, const double* __restrict__ x,
                            const uint8_t* __restrict__ eclass, const T* __restrict__ dinv,
                            T* __restrict__ ri, T* __restrict__ pi, double* partials,
                            SolveState* st, double rtol2, double inner_rtol2, int mode) {
+  if (mode == 3) {
+    if (st->done != 1) return;  // every block reads done before the last block rewrites it
+    mode = 2;
+  }
   __shared__ double smem[kBlock / 32];
   const size_t m = (size_t)nE;
   double acc_r = 0.0, acc_z = 0.0, acc_f = 0.0, acc_p = 0.0;
@@ -68,9 +76,6 @@ __global__ void k_residual(int nE, const int32_t* __restrict__ nbr, const double
       }
       acc_r += r * r;
     } else {
-      // difference form: S x = r_e x_e + sum_s l_es (x_e - x_s); the differences
-      // of nearby values are exact or nearly so, which keeps the FP64 residual
-      // accurate where the naive row product would cancel ~1/h^2 digits
       double fl;  // |S| |x| of the row: scale of the FP64 rounding of x
       r = residual_row(nbr, val, b, x, m, e, fl);
       acc_r += r * r;
@@ -103,43 +108,79 @@ __global__ void k_residual(int nE, const int32_t* __restrict__ nbr, const double
     st->counter[0] = 0;
     if (mode == 0) {
       st->bb = rr;
+      return;
+    }
+    const double rz_recursive = st->rz;
+    st->rr64 = rr;
+    st->floor2 = ff;
+    st->rz = rz;
+    st->rp = rp;
+    st->tol2 = inner_rtol2 * rz;
+    st->status = 0;
+    if (mode == 1) {
+      st->rz0 = rz;
+      st->it = 0;
+      st->updates = 1;
+      st->bodies = 0;
+      st->use_rp = 0;
+      st->restart = 0;
     } else {
-      st->rr64 = rr;
-      st->floor2 = ff;
-      st->rz = rz;
-      st->rp = rp;
-      st->use_rp = (mode == 2) ? 1 : 0;
-      if (mode == 1) {
-        st->rz0 = rz;
-        st->it = 0;
-      }
-      st->tol2 = inner_rtol2 * rz;
-      st->status = 0;
-      if (!isfinite(rr) || !isfinite(rz)) {
-        st->done = 3;
-        st->status = PHFEM_ENAN;
-      } else {
-        st->done = (rr <= rtol2 * st->bb) ? 2 : 0;
-      }
+      st->updates += 1;
+      // line search along the kept direction, or restart it when it no longer
+      // fits the replaced residual
+      const int restart = (rz > 4.0 * rz_recursive) || !(rp > 0.0);
+      st->restart = restart;
+      st->use_rp = !restart;
+    }
+    st->conv = 0;
+    if (!isfinite(rr) || !isfinite(rz)) {
+      st->done = 3;
+      st->status = PHFEM_ENAN;
+    } else if (rr <= rtol2 * st->bb || rr == 0.0) {
+      st->done = 2;
+      st->conv = 1;
+    } else if (rr <= 4.0 * ff) {  // relative residual within twice the FP64 floor
+      st->done = 2;
+      st->conv = 2;
+    } else {
+      st->done = 0;
     }
   }
 }
 
-// q = S p in difference form, p.q -> alpha = rz / p.q
+// q = S p in difference form, p.q -> alpha = rz / p.q (or r.p / p.q right
+// after a reliable update).  In restart mode the direction is first set to
+// p = D^-1 r (each block writes its own rows and computes neighbours' values
+// from r and D^-1, so no block reads p being written).
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cg_spmv(int nE, const int32_t* __restrict__ nbr,
                                                     const T* __restrict__ lval, const T* __restrict__ rdiag,
-                                                    const T* __restrict__ p, T* __restrict__ q, double* partials,
-                                                    SolveState* st) {
+                                                    T* __restrict__ p, T* __restrict__ q, const T* __restrict__ r,
+                                                    const T* __restrict__ dinv, double* partials, SolveState* st) {
   if (blockIdx.x == 0 && threadIdx.x == 0) st->dir_pending = 0;  // no block of this kernel reads it
   if (st->done) return;
   __shared__ double smem[kBlock / 32];
   const size_t m = (size_t)nE;
   T acc = (T)0;  // this thread's few rows in T; across threads and blocks in FP64
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
-    const T s = spmv_row(nbr, lval, rdiag, p, m, e);
-    q[e] = s;
-    acc += p[e] * s;
+  if (st->restart) {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+      const T pe = dinv[e] * r[e];
+      T s = rdiag[e] * pe;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int c = nbr[k * m + e];
+        s += lval[k * m + e] * (pe - dinv[c] * r[c]);
+      }
+      p[e] = pe;
+      q[e] = s;
+      acc += pe * s;
+    }
+  } else {
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+      const T s = spmv_row(nbr, lval, rdiag, (const T*)p, m, e);
+      q[e] = s;
+      acc += p[e] * s;
+    }
   }
   const double accd = block_sum((double)acc, smem);
   if (threadIdx.x == 0) partials[blockIdx.x] = accd;
@@ -153,6 +194,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_spmv(int nE, const int32_t* __res
     } else {
       st->alpha = (st->use_rp ? st->rp : st->rz) / pq;
       st->use_rp = 0;
+      st->restart = 0;
     }
   }
 }
@@ -180,7 +222,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(int nE, double* __restrict
   const double rz = sum_partials(partials + kMaxGrid, smem);
   if (threadIdx.x == 0) {
     st->counter[2] = 0;
-    st->beta = rz / st->rz;
+    st->beta = st->rz > 0.0 ? rz / st->rz : 0.0;
     st->rz = rz;
     st->it += 1;
     st->dir_pending = 1;
@@ -205,13 +247,12 @@ __global__ void __launch_bounds__(kBlock) k_cg_dir(int nE, const T* __restrict__
   if (blockIdx.x == 0 && threadIdx.x == 0 && st->done == 0 && st->rz <= st->tol2) st->done = 1;
 }
 
-// Restart of the direction after a reliable update whose true residual is far
-// from the recursive one (the kept direction would no longer fit it).
-template <typename T>
-__global__ void k_cg_restart(int nE, const T* __restrict__ r, const T* __restrict__ dinv, T* __restrict__ p,
-                             SolveState* st) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) p[e] = dinv[e] * r[e];
-  if (blockIdx.x == 0 && threadIdx.x == 0) st->use_rp = 0;  // p = D^-1 r: r.p = r.z
+// Graph loop control: continue while the iteration runs and stays within the
+// iteration and body limits (every loop is bounded).
+__global__ void k_loop_control(SolveState* st, cudaGraphConditionalHandle handle, int max_iter, int max_bodies) {
+  st->bodies += 1;
+  const bool more = st->done == 0 && st->it < max_iter && st->bodies < max_bodies;
+  cudaGraphSetConditional(handle, more ? 1u : 0u);
 }
 
 __global__ void k_init_x(int nE, const uint8_t* __restrict__ eclass, const double* __restrict__ b,
@@ -273,116 +314,171 @@ int read_state(phfem_sys sys) {
 }
 
 template <typename T>
+struct Launch {
+  phfem_sys sys;
+  cudaStream_t s;
+  int g, nE;
+  double rtol2, irtol2;
+  int residual(int mode) const {
+    phfem_ctx ctx = sys->mesh->ctx;
+    prof_start(ctx, kProfResidual);
+    k_residual<T><<<g, kBlock, 0, s>>>(nE, sys->mesh->nbr, sys->val, sys->b, sys->x, sys->mesh->eclass,
+                                       (const T*)sys->dinv, (T*)sys->ri, (T*)sys->pi, sys->partials, sys->st, rtol2,
+                                       irtol2, mode);
+    prof_stop(ctx, kProfResidual);
+    return check_launch(ctx, "k_residual");
+  }
+  int iteration() const {
+    phfem_ctx ctx = sys->mesh->ctx;
+    const T* lval = (const T*)sys->lval;
+    const T* rdiag = (const T*)sys->rdiag;
+    const T* dinv = (const T*)sys->dinv;
+    T* ri = (T*)sys->ri;
+    T* pi = (T*)sys->pi;
+    T* qi = (T*)sys->qi;
+    prof_start(ctx, kProfSpmv);
+    k_cg_spmv<T><<<g, kBlock, 0, s>>>(nE, sys->mesh->nbr, lval, rdiag, pi, qi, ri, dinv, sys->partials, sys->st);
+    prof_stop(ctx, kProfSpmv);
+    prof_start(ctx, kProfUpdate);
+    k_cg_update<T><<<g, kBlock, 0, s>>>(nE, sys->x, pi, ri, qi, dinv, sys->partials, sys->st);
+    prof_stop(ctx, kProfUpdate);
+    prof_start(ctx, kProfDir);
+    k_cg_dir<T><<<g, kBlock, 0, s>>>(nE, ri, dinv, pi, sys->st);
+    prof_stop(ctx, kProfDir);
+    ctx->launches += 2;
+    return check_launch(ctx, "k_cg");
+  }
+};
+
+template <typename T>
 int solve_typed(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats) {
   phfem_mesh m = sys->mesh;
   phfem_ctx ctx = m->ctx;
-  cudaStream_t s = ctx->stream;
   const int nE = m->info.nE;
-  const int g = grid_for(ctx, nE);
-  T* ri = (T*)sys->ri;
-  T* pi = (T*)sys->pi;
-  T* qi = (T*)sys->qi;
-  const T* lval = (const T*)sys->lval;
-  const T* rdiag = (const T*)sys->rdiag;
-  const T* dinv = (const T*)sys->dinv;
-  const double rtol2 = o.rtol * o.rtol, irtol2 = o.inner_rtol * o.inner_rtol;
+  const Launch<T> L{sys, ctx->stream, grid_for(ctx, nE), nE, o.rtol * o.rtol, o.inner_rtol * o.inner_rtol};
   static const bool verbose = getenv("PHFEM_VERBOSE") != nullptr;
-  auto residual = [&](int mode) -> int {
-    prof_start(ctx, kProfResidual);
-    k_residual<T><<<g, kBlock, 0, s>>>(nE, m->nbr, sys->val, sys->b, sys->x, m->eclass, dinv, ri, pi,
-                                       sys->partials, sys->st, rtol2, irtol2, mode);
-    prof_stop(ctx, kProfResidual);
-    return check_launch(ctx, "k_residual");
-  };
   // ||b|| of the free-edge system (with the Dirichlet lifting), then the start
-  PH_TRY(residual(0));
-  PH_TRY(residual(1));
-  int iters = 0, updates = 1, converged = 0, status = PHFEM_OK, stagnant = 0, restarts = 0;
-  double rel = 0.0, best = 1e300;
+  PH_TRY(L.residual(0));
+  PH_TRY(L.residual(1));
   PH_TRY(read_state(sys));
+  int status = PHFEM_OK, stagnant = 0, last_updates = 0;
+  double best = 1e300;
   for (;;) {
     const SolveState& h = *sys->st_host;
+    if (h.updates != last_updates) {  // a new true residual: progress bookkeeping
+      last_updates = h.updates;
+      const double rel = h.bb > 0 ? std::sqrt(h.rr64 / h.bb) : 0.0;
+      if (verbose)
+        fprintf(stderr, "phfem: update %d  iterations %d  relative residual %.3e  fp64 floor %.3e  restart %d\n",
+                h.updates, h.it, rel, h.bb > 0 ? std::sqrt(h.floor2 / h.bb) : 0.0, h.restart);
+      stagnant = (rel > 0.5 * best) ? stagnant + 1 : 0;
+      best = rel < best ? rel : best;
+    }
     if (h.done == 3) {
       status = h.status;
       break;
     }
-    rel = h.bb > 0 ? std::sqrt(h.rr64 / h.bb) : 0.0;
-    const double floor_rel = h.bb > 0 ? std::sqrt(h.floor2 / h.bb) : 0.0;
-    if (verbose)
-      fprintf(stderr, "phfem: update %d  iterations %d  relative residual %.3e  fp64 floor %.3e  restarts %d\n",
-              updates, iters, rel, floor_rel, restarts);
-    if (h.rr64 <= rtol2 * h.bb || h.rr64 == 0.0) {
-      converged = 1;
-      break;
-    }
-    // at the level where rounding x to FP64 dominates, further work cannot help
-    if (rel <= 2.0 * floor_rel) {
-      converged = 2;
-      break;
-    }
-    stagnant = (rel > 0.5 * best) ? stagnant + 1 : 0;
-    best = rel < best ? rel : best;
-    if (iters >= o.max_iter || updates > o.max_refine || stagnant >= 8) {
+    if (h.done == 2) break;
+    if (h.it >= o.max_iter || h.updates > o.max_refine || stagnant >= 8) {
       status = PHFEM_ENOCONV;
       break;
     }
-    // iterate until the recursive residual fell by inner_rtol (or the limits)
-    int run = sys->st_host->it;
-    for (;;) {
-      int chunk = o.check_every;
-      if (iters + chunk > o.max_iter) chunk = o.max_iter - iters;
-      if (chunk <= 0) break;
-      for (int k = 0; k < chunk; ++k) {
-        prof_start(ctx, kProfSpmv);
-        k_cg_spmv<T><<<g, kBlock, 0, s>>>(nE, m->nbr, lval, rdiag, pi, qi, sys->partials, sys->st);
-        prof_stop(ctx, kProfSpmv);
-        prof_start(ctx, kProfUpdate);
-        k_cg_update<T><<<g, kBlock, 0, s>>>(nE, sys->x, pi, ri, qi, dinv, sys->partials, sys->st);
-        prof_stop(ctx, kProfUpdate);
-        prof_start(ctx, kProfDir);
-        k_cg_dir<T><<<g, kBlock, 0, s>>>(nE, ri, dinv, pi, sys->st);
-        prof_stop(ctx, kProfDir);
-        ctx->launches += 2;
-        PH_TRY(check_launch(ctx, "k_cg"));
-      }
+    if (h.done == 1) {  // reliable update requested by the iteration
+      PH_TRY(L.residual(2));
       PH_TRY(read_state(sys));
-      const int done_it = sys->st_host->it - run;
-      run = sys->st_host->it;
-      iters += done_it;
-      if (sys->st_host->done || iters >= o.max_iter) break;
+      continue;
     }
-    if (sys->st_host->done == 3) {
-      status = sys->st_host->status;
-      break;
-    }
-    // reliable update: the true residual of the FP64 x replaces the recursive one
-    const double rz_recursive = sys->st_host->rz;
-    PH_TRY(residual(2));
-    ++updates;
+    int chunk = o.check_every;
+    if (h.it + chunk > o.max_iter) chunk = o.max_iter - h.it;
+    for (int k = 0; k < chunk; ++k) PH_TRY(L.iteration());
     PH_TRY(read_state(sys));
-    if (sys->st_host->done == 0 && (sys->st_host->rz > 4.0 * rz_recursive || !(sys->st_host->rp > 0.0))) {
-      k_cg_restart<T><<<g, kBlock, 0, s>>>(nE, ri, dinv, pi, sys->st);
-      PH_TRY(check_launch(ctx, "k_cg_restart"));
-      ++restarts;
-    }
   }
+  const SolveState& h = *sys->st_host;
+  const double rel = h.bb > 0 ? std::sqrt(h.rr64 / h.bb) : 0.0;
   if (stats) {
-    stats->iterations += iters;
-    stats->refinements += updates;
-    stats->converged = converged;
+    stats->iterations += h.it;
+    stats->refinements += h.updates;
+    stats->converged = h.done == 2 ? h.conv : 0;
     stats->rel_residual = rel;
-    const SolveState& h = *sys->st_host;
     stats->fp64_floor = h.bb > 0 ? std::sqrt(h.floor2 / h.bb) : 0.0;
   }
   if (status != PHFEM_OK) {
     char buf[200];
     snprintf(buf, sizeof(buf), "solve: %s after %d iterations, %d residual updates, relative residual %.3e",
-             phfem_status_str(status), iters, updates, rel);
+             phfem_status_str(status), h.it, h.updates, rel);
     return fail(status, buf);
   }
   return PHFEM_OK;
 }
 
+// The start kernels, then a WHILE node whose body runs `per_body` iterations,
+// the conditional reliable update and the loop control.
+template <typename T>
+int capture_typed(phfem_sys sys, const phfem_solve_opts& o, cudaStream_t cs, int per_body) {
+  phfem_ctx ctx = sys->mesh->ctx;
+  const int nE = sys->mesh->info.nE;
+  const Launch<T> L{sys, cs, grid_for(ctx, nE), nE, o.rtol * o.rtol, o.inner_rtol * o.inner_rtol};
+  PH_TRY(L.residual(0));
+  PH_TRY(L.residual(1));
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t graph;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  PH_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, &deps, nullptr, &ndeps));
+  if (cst != cudaStreamCaptureStatusActive) return fail(PHFEM_ECUDA, "capture_solve: stream is not capturing");
+  cudaGraphConditionalHandle handle;
+  PH_CUDA(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  PH_CUDA(cudaGraphAddNode(&cnode, graph, deps, nullptr, ndeps, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  PH_CUDA(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  // the body is captured on a second private stream
+  cudaStream_t bs;
+  PH_CUDA(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+  int st = PHFEM_OK;
+  cudaError_t e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamBeginCaptureToGraph", __FILE__, __LINE__);
+  if (st == PHFEM_OK) {
+    const Launch<T> B{sys, bs, L.g, nE, L.rtol2, L.irtol2};
+    for (int k = 0; k < per_body && st == PHFEM_OK; ++k) st = B.iteration();
+    if (st == PHFEM_OK) st = B.residual(3);
+    if (st == PHFEM_OK) {
+      const int max_bodies = o.max_iter / (per_body > 0 ? per_body : 1) + o.max_refine + 16;
+      k_loop_control<<<1, 1, 0, bs>>>(sys->st, handle, o.max_iter, max_bodies);
+      st = check_launch(ctx, "k_loop_control");
+    }
+    cudaGraph_t out;
+    e = cudaStreamEndCapture(bs, &out);
+    if (e != cudaSuccess && st == PHFEM_OK) st = cuda_fail(e, "cudaStreamEndCapture(body)", __FILE__, __LINE__);
+  }
+  cudaStreamDestroy(bs);
+  return st;
+}
+
+}  // namespace
+
+void fill_opts(phfem_sys sys, phfem_solve_opts& o) {
+  if (o.rtol <= 0) o.rtol = 1e-10;
+  if (o.inner_rtol <= 0) o.inner_rtol = sys->fp32 ? 0.1 : 0.01;
+  if (o.max_iter <= 0) o.max_iter = 200000;
+  if (o.max_refine <= 0) o.max_refine = 1000;
+  if (o.check_every <= 0) o.check_every = 64;
+}
+
+int capture_solve(phfem_sys sys, const phfem_solve_opts* opts, cudaStream_t capture, int iters_per_body) {
+  phfem_solve_opts o{};
+  if (opts) o = *opts;
+  fill_opts(sys, o);
+  return sys->fp32 ? capture_typed<float>(sys, o, capture, iters_per_body)
+                   : capture_typed<double>(sys, o, capture, iters_per_body);
+}
+
+namespace {
 }  // namespace
 
 int sys_init_x(phfem_sys sys, const double* w0) {
@@ -396,11 +492,7 @@ int sys_init_x(phfem_sys sys, const double* w0) {
 int solve_system(phfem_sys sys, const phfem_solve_opts* opts, phfem_stats* stats, bool /*warm*/) {
   phfem_solve_opts o{};
   if (opts) o = *opts;
-  if (o.rtol <= 0) o.rtol = 1e-10;
-  if (o.inner_rtol <= 0) o.inner_rtol = sys->fp32 ? 0.1 : 0.01;
-  if (o.max_iter <= 0) o.max_iter = 200000;
-  if (o.max_refine <= 0) o.max_refine = 1000;
-  if (o.check_every <= 0) o.check_every = 64;
+  fill_opts(sys, o);
   return sys->fp32 ? solve_typed<float>(sys, o, stats) : solve_typed<double>(sys, o, stats);
 }
 

@@ -90,6 +90,7 @@ def lib() -> C.CDLL:
             "phfem_solve": (C.c_int, [_H, C.POINTER(SolveOpts), _P, _P, _P, _P, C.POINTER(Stats)]),
             "phfem_cn_create": (C.c_int, [_H, C.POINTER(Source), _P, _P, C.POINTER(_H)]),
             "phfem_cn_step": (C.c_int, [_H, C.c_int32, C.POINTER(SolveOpts), C.POINTER(Stats)]),
+            "phfem_cn_step_graph": (C.c_int, [_H, C.c_int32, C.POINTER(SolveOpts), C.POINTER(Stats)]),
             "phfem_cn_read": (C.c_int, [_H, _P, _P, _P, _P, C.POINTER(C.c_int32)]),
             "phfem_cn_destroy": (C.c_int, [_H]),
             "phfem_batch_create": (C.c_int, [_H, C.c_int32, C.POINTER(_H), C.POINTER(_H)]),
@@ -262,6 +263,13 @@ def phfem_cn_step(cn, nsteps, opts=None) -> dict:
     st = Stats()
     o = opts if opts is not None else solve_opts()
     _check(lib().phfem_cn_step(cn, int(nsteps), C.byref(o), C.byref(st)), "phfem_cn_step")
+    return st.as_dict()
+
+
+def phfem_cn_step_graph(cn, nsteps, opts=None) -> dict:
+    st = Stats()
+    o = opts if opts is not None else solve_opts()
+    _check(lib().phfem_cn_step_graph(cn, int(nsteps), C.byref(o), C.byref(st)), "phfem_cn_step_graph")
     return st.as_dict()
 
 

@@ -18,7 +18,8 @@ def ctx():
     P.phfem_ctx_destroy(c)
 
 
-def _run_gpu(ctx, mesh, terms, phi_fn, dt, nsteps, u0, delta, aT=None, precision=0, rtol=1e-13, Lambda0=None):
+def _run_gpu(ctx, mesh, terms, phi_fn, dt, nsteps, u0, delta, aT=None, precision=0, rtol=1e-13, Lambda0=None,
+             graph=False):
     """terms: list of (f_q, g_q, uD_q) spatial functions; phi_fn(t) -> [Q]."""
     from paper_2401_15557_gb300 import phfem as P
     from phfem_gpu import GpuMesh, dev
@@ -35,7 +36,12 @@ def _run_gpu(ctx, mesh, terms, phi_fn, dt, nsteps, u0, delta, aT=None, precision
                             dt=dt, precision=precision)
     w0, _ = gm.edge_data(u0)
     cn = P.phfem_cn_create(sysh, F, B, phi, w0, Lambda0=None if Lambda0 is None else dev(Lambda0, torch.float64))
-    st = P.phfem_cn_step(cn, nsteps, P.solve_opts(rtol=rtol))
+    if graph:  # two launches of the captured step sequence
+        st = P.phfem_cn_step_graph(cn, nsteps // 2, P.solve_opts(rtol=rtol))
+        st2 = P.phfem_cn_step_graph(cn, nsteps - nsteps // 2, P.solve_opts(rtol=rtol))
+        st["iterations"] += st2["iterations"]
+    else:
+        st = P.phfem_cn_step(cn, nsteps, P.solve_opts(rtol=rtol))
     I_ = gm.info
     U = torch.empty(3 * I_["nT"], dtype=torch.float64, device="cuda")
     Ln = torch.empty(I_["nL"], dtype=torch.float64, device="cuda")
@@ -91,3 +97,23 @@ def test_two_term_source_reaction_variable_coefficient(ctx):
     assert np.max(np.abs(out["U"] - ref["U"])) <= 1e-10 * np.max(np.abs(ref["U"]))
     assert np.max(np.abs(out["Lambda_half"] - ref["Lambda_half"])) <= 1e-8 * np.max(np.abs(ref["Lambda_half"]))
     assert np.max(np.abs(out["Lambda"] - ref["Lambda"])) <= 1e-7 * np.max(np.abs(ref["Lambda"]))
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32ir"])
+def test_graph_steps_equal_host_steps(ctx, precision):
+    """Steps replayed from the captured graph (device-controlled solve loop)
+    give bitwise the results of the host-driven steps."""
+    pi = np.pi
+    s = lambda x, y: np.sin(pi * x) * np.sin(pi * y)
+    mesh = I.lshape_mesh(n=6, seed=I.seed_for(1, 81), levels=1)
+    aT = I.element_mean_at_midpoints(mesh.xy, mesh.tri, I.coeff_lshape)
+    terms = [(lambda x, y: (2 * pi * pi - 1.0) * s(x, y),
+              lambda x, y, nx, ny: pi * (np.cos(pi * x) * np.sin(pi * y) * nx + np.sin(pi * x) * np.cos(pi * y) * ny),
+              lambda x, y: 0 * x)]
+    kw = dict(aT=aT, precision=precision, rtol=1e-10)
+    a = _run_gpu(ctx, mesh, terms, lambda t: [np.exp(-t)], 1.0 / 24, 12, s, 0.3, **kw)
+    b = _run_gpu(ctx, mesh, terms, lambda t: [np.exp(-t)], 1.0 / 24, 12, s, 0.3, graph=True, **kw)
+    assert b["step"] == 12
+    assert np.array_equal(a["U"], b["U"]) and np.array_equal(a["Lambda"], b["Lambda"])
+    assert np.array_equal(a["Lambda_half"], b["Lambda_half"])
+    assert a["stats"]["iterations"] == b["stats"]["iterations"]
