@@ -59,10 +59,13 @@ def parse():
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu", action="store_true")
-    ap.add_argument("--workload", default="lshape", choices=["lshape", "batched", "heat"],
+    ap.add_argument("--workload", default="lshape", choices=["lshape", "batched", "heat", "serve"],
                     help="lshape: the L-shaped 6.3M-triangle solve (default); batched: 4096 meshes in one "
                          "launch; heat: Crank-Nicolson on 512 x 512 squares, 512 steps")
     ap.add_argument("--heat-n", type=int, default=512)
+    ap.add_argument("--requests", type=int, default=120, help="serve: measured requests")
+    ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (requests/s)")
+    ap.add_argument("--slots", type=int, default=8, help="serve: worker slots")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--no-clocks", action="store_true",
                     help="do not sample nvidia-smi clocks (profiling runs under ncu)")
@@ -346,6 +349,80 @@ def run_heat(args):
     return 0
 
 
+def run_serve(args):
+    """Poisson arrivals (seeded; mean rate 200/s) of 70 % elliptic and 30 %
+    Crank-Nicolson requests (16..128 steps, dt = 1/n), meshes with triangle
+    counts log-uniform in [1e3, 4e6] (n x n unit squares, n = round(sqrt(nT/2))),
+    a = exp(0.5 z) and delta ~ U[0, 2] as in the batched workload, f = 1,
+    homogeneous boundary data, FP32 + FP64 refinement; the server admits by a
+    120 GB HBM budget.  Inputs are uploaded before the arrival clock starts;
+    latency = finish - submit."""
+    import numpy as np
+    import torch
+    import __graft_entry__
+    from paper_2401_15557_gb300 import inputs as I
+    from paper_2401_15557_gb300 import phfem as P
+    __graft_entry__.build()
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    R = args.requests + args.warmup
+    seed = I.seed_for(4, 0)
+    u = I.uniform(seed ^ 0x5E5E, 4 * R)
+    nT_target = np.exp(np.log(1e3) + u[0::4] * (np.log(4e6) - np.log(1e3)))
+    sides = np.maximum(2, np.rint(np.sqrt(nT_target / 2))).astype(int)
+    kinds = (u[1::4] < 0.3).astype(int)
+    steps = 16 + np.floor(u[2::4] * 113).astype(int)
+    arrivals = I.poisson_arrivals(R, args.rate, seed)
+    d = lambda a, t: torch.as_tensor(np.ascontiguousarray(a), dtype=t, device=dev)
+    reqs, keep = [], []
+    t0 = time.perf_counter()
+    for i in range(R):
+        m, aT, delta = I.batch_member(i, int(sides[i]), workload=4)
+        t = dict(xy=d(m.xy, torch.float64), tri=d(m.tri, torch.int32), dd=d(m.dirichlet, torch.int32),
+                 nn=d(m.neumann, torch.int32), aT=d(aT, torch.float64),
+                 U=torch.empty(3 * m.nT, dtype=torch.float64, device=dev))
+        rq = P.make_request(t["xy"], t["tri"], t["dd"], t["nn"], kind=int(kinds[i]), a_T=t["aT"], delta=delta,
+                            f=1.0, dt=1.0 / sides[i], steps=int(steps[i]), precision=P.PHFEM_FP32_IR, U_out=t["U"])
+        reqs.append((rq, m.nT))
+        keep.append(t)
+    torch.cuda.synchronize()
+    t_setup = time.perf_counter() - t0
+    srv = P.phfem_server_create(args.slots, 120e9, P.solve_opts(rtol=1e-10))
+    clocks = ClockSampler(0) if not args.no_clocks else None
+    if clocks:
+        clocks.start()
+    start = time.perf_counter()
+    ids = []
+    for (rq, _), ta in zip(reqs, arrivals):
+        delay = ta - (time.perf_counter() - start)
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(P.phfem_server_submit(srv, rq))
+    P.phfem_server_drain(srv)
+    clk = clocks.stop() if clocks else None
+    res = [P.phfem_server_poll(srv, i, wait=False) for i in ids]
+    P.phfem_server_destroy(srv)
+    meas = res[args.warmup:]
+    lat = np.array([r["t_finish"] - r["t_submit"] for r in meas]) * 1e3
+    wait = np.array([r["t_admit"] - r["t_submit"] for r in meas]) * 1e3
+    span = max(r["t_finish"] for r in meas) - min(r["t_submit"] for r in meas)
+    tri = sum(nt for (_, nt) in reqs[args.warmup:])
+    ok = sum(1 for r in meas if r["status"] == 0)
+    p50, p99 = float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
+    line = {"metric": METRIC, "value": ok / span, "unit": "solves/s", "n_gpus": 1, "steps": len(meas),
+            "warmup": args.warmup, "ms_per_step": 1e3 * span / len(meas), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "serve-poisson", "rate_per_s": args.rate, "requests": len(meas),
+                       "slots": args.slots, "hbm_budget_gb": 120, "mix": "70% elliptic / 30% CN 16-128 steps",
+                       "triangles": "log-uniform 1e3..4e6"},
+            "p50_ms": p50, "p99_ms": p99, "mean_queue_wait_ms": float(wait.mean()),
+            "triangles_per_s": tri / span, "ok": ok, "failed": len(meas) - ok,
+            "offered_triangles_per_s": tri / (arrivals[-1] - arrivals[args.warmup]) if len(meas) > 1 else None,
+            "setup_s": t_setup, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -354,6 +431,8 @@ def main():
         return run_batched(args)
     if args.workload == "heat":
         return run_heat(args)
+    if args.workload == "serve":
+        return run_serve(args)
 
     import numpy as np
     import torch

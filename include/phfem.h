@@ -307,6 +307,59 @@ PHFEM_API int phfem_batch_tune(phfem_batch batch, const double* a_T, const doubl
 PHFEM_API int phfem_batch_destroy(phfem_batch batch);
 
 /* ------------------------------------------------------------------------ */
+/* Request server with continuous batching                                   */
+/* ------------------------------------------------------------------------ */
+
+typedef struct phfem_server_s* phfem_server;
+
+/* One request: an elliptic solve (kind 0) or a Crank-Nicolson run (kind 1)
+ * with constant data f, u_D, g (and u0 for kind 1).  Every pointer is device
+ * memory owned by the caller and must stay valid until the request is done. */
+typedef struct {
+  int32_t kind;            /* 0 elliptic, 1 Crank-Nicolson                               */
+  int32_t nV, nT, nD, nN;
+  const double* xy;        /* [nV][2]                                                      */
+  const int32_t* tri;      /* [nT][3] counter-clockwise                                    */
+  const int32_t* dirichlet;/* [nD][2]                                                      */
+  const int32_t* neumann;  /* [nN][2]                                                      */
+  const double* a_T;       /* [nT] or NULL (a = 1)                                         */
+  double delta, f, uD, g;  /* reaction, source, Dirichlet value, Neumann flux (constants)  */
+  double dt, u0;           /* kind 1: time step and initial value                          */
+  int32_t steps;           /* kind 1: number of time steps                                  */
+  int32_t precision;       /* PHFEM_FP64 or PHFEM_FP32_IR                                   */
+  double* U_out;           /* [3 nT] or NULL: u_h at the vertices (final time for kind 1)  */
+  double* Lambda_out;      /* [nE] or NULL (room for nE, the first nL written)             */
+} phfem_request;
+
+typedef struct {
+  int64_t id;
+  int32_t status;          /* phfem_status of the request once done                      */
+  int32_t done;            /* 1 when finished                                              */
+  int32_t iterations;      /* conjugate-gradient iterations (all steps)                    */
+  int32_t slot;            /* worker slot that ran it (-1 while queued)                    */
+  int32_t nE, nL;
+  double rel_residual;
+  double t_submit, t_admit, t_finish;  /* seconds since the server was created          */
+} phfem_result;
+
+/* Creates a server on the current device with `slots` workers, each a host
+ * thread with its own context and CUDA stream, so admitted requests overlap on
+ * the GPU.  A request is admitted (first in, first out) when a slot is free
+ * and its device-memory estimate (400 bytes per triangle + 1 MB) fits in
+ * hbm_budget_bytes minus what admitted requests hold; a request larger than
+ * the whole budget runs alone.  opts apply to every solve. */
+PHFEM_API int phfem_server_create(int32_t slots, double hbm_budget_bytes, const phfem_solve_opts* opts,
+                                  phfem_server* out);
+/* Queues a request (copied) and returns its id; never blocks on the GPU. */
+PHFEM_API int phfem_server_submit(phfem_server server, const phfem_request* req, int64_t* id);
+/* Reads a request's record; wait != 0 blocks until it is done. */
+PHFEM_API int phfem_server_poll(phfem_server server, int64_t id, int32_t wait, phfem_result* out);
+/* Blocks until every submitted request is done. */
+PHFEM_API int phfem_server_drain(phfem_server server);
+/* Finishes the queued requests, then stops the workers and frees the server. */
+PHFEM_API int phfem_server_destroy(phfem_server server);
+
+/* ------------------------------------------------------------------------ */
 /* Solve without device allocation                                           */
 /* ------------------------------------------------------------------------ */
 

@@ -1,0 +1,256 @@
+// Continuous-batching request server.
+//
+// Requests (elliptic solves and Crank-Nicolson runs on meshes of any size)
+// are queued in arrival order.  Worker slots -- each a host thread owning a
+// context on its own CUDA stream -- take the head of the queue as soon as they
+// are free and the request's device-memory estimate fits in what remains of
+// the HBM budget, so requests that arrive while others run are admitted as
+// slots and memory free up and their kernels overlap on the GPU.  Mesh
+// tables, the condensed system, the Jacobi preconditioner and the time-stepping
+// state live on the device for the lifetime of a request.  Every request
+// records its submit, admit and finish times (seconds since the server started).
+#include <chrono>
+#include <condition_variable>
+#include <deque>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace phfem {
+namespace {
+
+// f at every edge, u_D on Dirichlet edges and g on Neumann edges (constants).
+__global__ void k_fill_edge_data(int nE, const uint8_t* __restrict__ eclass, double f, double uD, double g,
+                                 double* __restrict__ f_mid, double* __restrict__ bc_mid, double u0,
+                                 double* __restrict__ w0) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    const uint8_t c = eclass[e];
+    f_mid[e] = f;
+    bc_mid[e] = c == PHFEM_EDGE_DIRICHLET ? uD : (c == PHFEM_EDGE_NEUMANN ? g : 0.0);
+    if (w0) w0[e] = c == PHFEM_EDGE_DIRICHLET ? uD : u0;
+  }
+}
+
+double now_since(std::chrono::steady_clock::time_point t0) {
+  return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+}  // namespace
+}  // namespace phfem
+
+using namespace phfem;
+
+struct phfem_server_s {
+  int device;
+  double budget;
+  double reserved = 0.0;
+  phfem_solve_opts opts;
+  std::chrono::steady_clock::time_point t0;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  std::deque<std::pair<int64_t, phfem_request>> queue;
+  std::map<int64_t, phfem_result> results;
+  int64_t next_id = 1;
+  bool stop = false;
+  std::vector<std::thread> workers;
+  std::vector<phfem_ctx> ctxs;
+  std::vector<cudaStream_t> streams;
+  int64_t completed = 0;
+};
+
+namespace phfem {
+namespace {
+
+double estimate_bytes(const phfem_request& r) {
+  // tables (~100 B/triangle), system (~150 B/edge at 1.5 edges/triangle),
+  // solver vectors and CN state: 400 B per triangle covers both kinds
+  return 400.0 * (double)r.nT + (double)(1 << 20);
+}
+
+int run_request(phfem_ctx ctx, const phfem_request& r, const phfem_solve_opts& opts, phfem_result& out) {
+  cudaStream_t s = ctx->stream;
+  phfem_mesh m = nullptr;
+  PH_TRY(phfem_mesh_build(ctx, r.nV, r.xy, r.nT, r.tri, r.nD, r.dirichlet, r.nN, r.neumann, &m));
+  const phfem_mesh_info I = m->info;
+  out.nL = I.nL;
+  out.nE = I.nE;
+  double *f = nullptr, *bc = nullptr, *w0 = nullptr;
+  int st = dalloc_n(ctx, &f, I.nE);
+  if (st == PHFEM_OK) st = dalloc_n(ctx, &bc, I.nE);
+  if (st == PHFEM_OK && r.kind == 1) st = dalloc_n(ctx, &w0, I.nE);
+  if (st == PHFEM_OK) {
+    k_fill_edge_data<<<grid_for(ctx, I.nE), kBlock, 0, s>>>(I.nE, m->eclass, r.f, r.uD, r.g, f, bc, r.u0, w0);
+    st = check_launch(ctx, "k_fill_edge_data");
+  }
+  phfem_sys sys = nullptr;
+  if (st == PHFEM_OK) {
+    phfem_coeffs c{r.a_T, 1.0, r.delta, r.kind == 1 ? r.dt : 0.0, r.precision, 0};
+    st = phfem_assemble(m, &c, r.kind == 1 ? nullptr : f, r.kind == 1 ? nullptr : bc, &sys);
+  }
+  if (st == PHFEM_OK && r.kind == 0) {
+    phfem_stats stats{};
+    st = phfem_solve(sys, &opts, nullptr, nullptr, r.U_out, r.Lambda_out, &stats);
+    out.iterations = stats.iterations;
+    out.rel_residual = stats.rel_residual;
+  } else if (st == PHFEM_OK) {
+    std::vector<double> phi((size_t)r.steps + 1, 1.0);  // constant-in-time data
+    phfem_source src{1, r.steps + 1, f, bc, phi.data()};
+    phfem_cn cn = nullptr;
+    st = phfem_cn_create(sys, &src, w0, nullptr, &cn);
+    if (st == PHFEM_OK) {
+      phfem_stats stats{};
+      st = phfem_cn_step_graph(cn, r.steps, &opts, &stats);
+      out.iterations = stats.iterations;
+      out.rel_residual = stats.rel_residual;
+      if (st == PHFEM_OK) st = phfem_cn_read(cn, nullptr, r.U_out, r.Lambda_out, nullptr, nullptr);
+      phfem_cn_destroy(cn);
+    }
+  }
+  if (sys) phfem_sys_destroy(sys);
+  dfree(ctx, f);
+  dfree(ctx, bc);
+  dfree(ctx, w0);
+  phfem_mesh_destroy(m);
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (st == PHFEM_OK && e != cudaSuccess) st = cuda_fail(e, "server request", __FILE__, __LINE__);
+  return st;
+}
+
+void worker(phfem_server S, int slot) {
+  cudaSetDevice(S->device);
+  phfem_ctx ctx = S->ctxs[slot];
+  for (;;) {
+    std::pair<int64_t, phfem_request> job;
+    double est = 0.0;
+    {
+      std::unique_lock<std::mutex> lock(S->mu);
+      // FIFO admission: the head waits until its memory estimate fits
+      S->cv_work.wait(lock, [&] {
+        if (S->stop) return true;
+        if (S->queue.empty()) return false;
+        const double e = estimate_bytes(S->queue.front().second);
+        return S->reserved + e <= S->budget || S->reserved == 0.0;
+      });
+      if (S->stop && S->queue.empty()) return;
+      job = S->queue.front();
+      S->queue.pop_front();
+      est = estimate_bytes(job.second);
+      S->reserved += est;
+      S->results[job.first].t_admit = now_since(S->t0);
+      S->results[job.first].slot = slot;
+    }
+    phfem_result res{};
+    const int st = run_request(ctx, job.second, S->opts, res);
+    {
+      std::lock_guard<std::mutex> lock(S->mu);
+      S->reserved -= est;
+      phfem_result& R = S->results[job.first];
+      R.status = st;
+      R.done = 1;
+      R.iterations = res.iterations;
+      R.rel_residual = res.rel_residual;
+      R.nL = res.nL;
+      R.nE = res.nE;
+      R.t_finish = now_since(S->t0);
+      S->completed++;
+    }
+    S->cv_done.notify_all();
+    S->cv_work.notify_all();
+  }
+}
+
+}  // namespace
+}  // namespace phfem
+
+extern "C" {
+
+PHFEM_API int phfem_server_create(int32_t slots, double hbm_budget_bytes, const phfem_solve_opts* opts,
+                                  phfem_server* out) {
+  if (!out) return fail(PHFEM_EINVAL, "phfem_server_create: out is NULL");
+  *out = nullptr;
+  if (slots < 1 || slots > 64 || !(hbm_budget_bytes > 0))
+    return fail(PHFEM_EINVAL, "phfem_server_create: 1..64 slots and a positive budget");
+  phfem_server S = new phfem_server_s();
+  PH_CUDA(cudaGetDevice(&S->device));
+  S->budget = hbm_budget_bytes;
+  S->opts = opts ? *opts : phfem_solve_opts{};
+  S->t0 = std::chrono::steady_clock::now();
+  for (int i = 0; i < slots; ++i) {
+    cudaStream_t s;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    phfem_ctx c = nullptr;
+    if (e != cudaSuccess || phfem_ctx_create(s, &c) != PHFEM_OK) {
+      for (size_t j = 0; j < S->ctxs.size(); ++j) {
+        phfem_ctx_destroy(S->ctxs[j]);
+        cudaStreamDestroy(S->streams[j]);
+      }
+      delete S;
+      return fail(PHFEM_ECUDA, "phfem_server_create: stream or context creation failed");
+    }
+    S->streams.push_back(s);
+    S->ctxs.push_back(c);
+  }
+  for (int i = 0; i < slots; ++i) S->workers.emplace_back(worker, S, i);
+  *out = S;
+  return PHFEM_OK;
+}
+
+PHFEM_API int phfem_server_submit(phfem_server S, const phfem_request* req, int64_t* id) {
+  if (!S || !req) return fail(PHFEM_EINVAL, "phfem_server_submit: NULL argument");
+  if (req->kind != 0 && req->kind != 1) return fail(PHFEM_EINVAL, "phfem_server_submit: kind must be 0 or 1");
+  if (req->kind == 1 && (!(req->dt > 0) || req->steps < 1))
+    return fail(PHFEM_EINVAL, "phfem_server_submit: a Crank-Nicolson request needs dt > 0 and steps >= 1");
+  int64_t my;
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    if (S->stop) return fail(PHFEM_EINVAL, "phfem_server_submit: server is stopping");
+    my = S->next_id++;
+    phfem_result r{};
+    r.id = my;
+    r.t_submit = now_since(S->t0);
+    r.slot = -1;
+    S->results[my] = r;
+    S->queue.emplace_back(my, *req);
+  }
+  S->cv_work.notify_all();
+  if (id) *id = my;
+  return PHFEM_OK;
+}
+
+PHFEM_API int phfem_server_poll(phfem_server S, int64_t id, int32_t wait, phfem_result* out) {
+  if (!S || !out) return fail(PHFEM_EINVAL, "phfem_server_poll: NULL argument");
+  std::unique_lock<std::mutex> lock(S->mu);
+  auto it = S->results.find(id);
+  if (it == S->results.end()) return fail(PHFEM_EINVAL, "phfem_server_poll: unknown request id");
+  if (wait) S->cv_done.wait(lock, [&] { return S->results[id].done != 0; });
+  *out = S->results[id];
+  return PHFEM_OK;
+}
+
+PHFEM_API int phfem_server_drain(phfem_server S) {
+  if (!S) return fail(PHFEM_EINVAL, "phfem_server_drain: NULL server");
+  std::unique_lock<std::mutex> lock(S->mu);
+  S->cv_done.wait(lock, [&] { return S->queue.empty() && S->completed == S->next_id - 1; });
+  return PHFEM_OK;
+}
+
+PHFEM_API int phfem_server_destroy(phfem_server S) {
+  if (!S) return fail(PHFEM_EINVAL, "phfem_server_destroy: NULL server");
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  for (auto& t : S->workers) t.join();
+  for (size_t j = 0; j < S->ctxs.size(); ++j) {
+    phfem_ctx_destroy(S->ctxs[j]);
+    cudaStreamDestroy(S->streams[j]);
+  }
+  delete S;
+  return PHFEM_OK;
+}
+
+}  // extern "C"

@@ -56,6 +56,23 @@ class Source(C.Structure):
                 ("phi", C.c_void_p)]
 
 
+class Request(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("nV", C.c_int32), ("nT", C.c_int32), ("nD", C.c_int32), ("nN", C.c_int32),
+                ("xy", C.c_void_p), ("tri", C.c_void_p), ("dirichlet", C.c_void_p), ("neumann", C.c_void_p),
+                ("a_T", C.c_void_p), ("delta", C.c_double), ("f", C.c_double), ("uD", C.c_double),
+                ("g", C.c_double), ("dt", C.c_double), ("u0", C.c_double), ("steps", C.c_int32),
+                ("precision", C.c_int32), ("U_out", C.c_void_p), ("Lambda_out", C.c_void_p)]
+
+
+class Result(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int32), ("done", C.c_int32), ("iterations", C.c_int32),
+                ("slot", C.c_int32), ("nE", C.c_int32), ("nL", C.c_int32), ("rel_residual", C.c_double),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_finish", C.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 _lib = None
 _H = C.c_void_p
 _P = C.c_void_p
@@ -100,6 +117,11 @@ def lib() -> C.CDLL:
             "phfem_batch_tune": (C.c_int, [_H, _P, _P, _P, _P, C.c_int32, C.POINTER(SolveOpts), C.POINTER(C.c_int32),
                                            _P]),
             "phfem_batch_destroy": (C.c_int, [_H]),
+            "phfem_server_create": (C.c_int, [C.c_int32, C.c_double, C.POINTER(SolveOpts), C.POINTER(_H)]),
+            "phfem_server_submit": (C.c_int, [_H, C.POINTER(Request), C.POINTER(C.c_int64)]),
+            "phfem_server_poll": (C.c_int, [_H, C.c_int64, C.c_int32, C.POINTER(Result)]),
+            "phfem_server_drain": (C.c_int, [_H]),
+            "phfem_server_destroy": (C.c_int, [_H]),
             "phfem_csr_pcg_noalloc": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, C.c_double, C.c_int32,
                                                 C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
         }
@@ -338,6 +360,46 @@ def phfem_batch_tune(batch, delta, a_T=None, f_mid=None, bc_mid=None, precision=
 
 def phfem_batch_destroy(batch):
     _check(lib().phfem_batch_destroy(batch), "phfem_batch_destroy")
+
+
+# --- request server --------------------------------------------------------------
+
+def phfem_server_create(slots, hbm_budget_bytes, opts=None):
+    h = _H()
+    o = opts if opts is not None else solve_opts()
+    _check(lib().phfem_server_create(int(slots), float(hbm_budget_bytes), C.byref(o), C.byref(h)),
+           "phfem_server_create")
+    return h
+
+
+def make_request(xy, tri, dirichlet, neumann, kind=0, a_T=None, delta=0.0, f=1.0, uD=0.0, g=0.0, dt=0.0, u0=0.0,
+                 steps=0, precision=PHFEM_FP32_IR, U_out=None, Lambda_out=None) -> Request:
+    return Request(int(kind), xy.shape[0], tri.shape[0], dirichlet.shape[0] if dirichlet is not None else 0,
+                   neumann.shape[0] if neumann is not None else 0, _ptr(xy, torch.float64), _ptr(tri, torch.int32),
+                   _ptr(dirichlet, torch.int32) if dirichlet is not None and dirichlet.numel() else None,
+                   _ptr(neumann, torch.int32) if neumann is not None and neumann.numel() else None,
+                   _ptr(a_T, torch.float64), float(delta), float(f), float(uD), float(g), float(dt), float(u0),
+                   int(steps), int(precision), _ptr(U_out, torch.float64), _ptr(Lambda_out, torch.float64))
+
+
+def phfem_server_submit(server, req: Request) -> int:
+    rid = C.c_int64()
+    _check(lib().phfem_server_submit(server, C.byref(req), C.byref(rid)), "phfem_server_submit")
+    return int(rid.value)
+
+
+def phfem_server_poll(server, rid, wait=True) -> dict:
+    r = Result()
+    _check(lib().phfem_server_poll(server, int(rid), int(bool(wait)), C.byref(r)), "phfem_server_poll")
+    return r.as_dict()
+
+
+def phfem_server_drain(server):
+    _check(lib().phfem_server_drain(server), "phfem_server_drain")
+
+
+def phfem_server_destroy(server):
+    _check(lib().phfem_server_destroy(server), "phfem_server_destroy")
 
 
 # --- solve without device allocation -------------------------------------------

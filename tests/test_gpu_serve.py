@@ -1,0 +1,102 @@
+"""Request server: results are the same alone and in the mix; admission obeys
+the HBM budget in arrival order."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import phfem_oracle as O
+from paper_2401_15557_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests():
+    """Uneven elliptic and Crank-Nicolson requests with their device inputs."""
+    from paper_2401_15557_gb300 import phfem as P
+    dev = lambda a, t: torch.as_tensor(np.ascontiguousarray(a), dtype=t, device="cuda")
+    specs = []
+    sizes = [6, 40, 12, 60, 9, 25, 16, 33]
+    for i, n in enumerate(sizes):
+        m = I.square_mesh(n)
+        fld = I.fourier_field(I.seed_for(4, 200 + i))
+        aT = I.element_mean_at_midpoints(m.xy, m.tri, fld.a)
+        kind = 1 if i % 3 == 2 else 0
+        specs.append(dict(mesh=m, aT=aT, kind=kind, delta=0.25 * (i % 4), steps=16 + 4 * (i % 3),
+                          dt=1.0 / n, precision=i % 2))
+    lsh = I.lshape_mesh(n=8, seed=I.seed_for(1, 91), levels=1)
+    specs.append(dict(mesh=lsh, aT=I.element_mean_at_midpoints(lsh.xy, lsh.tri, I.coeff_lshape), kind=0, delta=1.0,
+                      steps=0, dt=0.0, precision=1))
+    out = []
+    for sp in specs:
+        m = sp["mesh"]
+        nE = m.nV + m.nT - 1
+        t = dict(xy=dev(m.xy, torch.float64), tri=dev(m.tri, torch.int32),
+                 d=dev(m.dirichlet, torch.int32), nn=dev(m.neumann, torch.int32), aT=dev(sp["aT"], torch.float64))
+        t["U"] = torch.full((3 * m.nT,), np.nan, dtype=torch.float64, device="cuda")
+        t["L"] = torch.full((nE,), np.nan, dtype=torch.float64, device="cuda")
+        req = P.make_request(t["xy"], t["tri"], t["d"], t["nn"], kind=sp["kind"], a_T=t["aT"], delta=sp["delta"],
+                             f=1.0, uD=0.2, g=0.1, dt=sp["dt"], u0=0.0, steps=sp["steps"],
+                             precision=sp["precision"], U_out=t["U"], Lambda_out=t["L"])
+        out.append((sp, t, req))
+    return out
+
+
+def _collect(reqs, results):
+    return [(t["U"].cpu().numpy().copy(), t["L"].cpu().numpy()[:r["nL"]].copy(), r) for (_, t, _), r in
+            zip(reqs, results)]
+
+
+def test_same_result_alone_and_in_the_mix():
+    from paper_2401_15557_gb300 import phfem as P
+    reqs = _requests()
+    # alone: one slot, one request at a time
+    srv = P.phfem_server_create(1, 64e9, P.solve_opts(rtol=1e-10))
+    alone = []
+    for _, _, rq in reqs:
+        rid = P.phfem_server_submit(srv, rq)
+        alone.append(P.phfem_server_poll(srv, rid, wait=True))
+    P.phfem_server_destroy(srv)
+    A = _collect(reqs, alone)
+    for _, t, _ in reqs:
+        t["U"].fill_(np.nan)
+        t["L"].fill_(np.nan)
+    # in the mix: four slots, everything submitted at once
+    srv = P.phfem_server_create(4, 64e9, P.solve_opts(rtol=1e-10))
+    ids = [P.phfem_server_submit(srv, rq) for _, _, rq in reqs]
+    P.phfem_server_drain(srv)
+    mixed = [P.phfem_server_poll(srv, i, wait=False) for i in ids]
+    P.phfem_server_destroy(srv)
+    B = _collect(reqs, mixed)
+    slots = {r["slot"] for r in mixed}
+    assert len(slots) > 1  # the work was spread over several slots
+    overlap = any(mixed[i]["t_admit"] < mixed[j]["t_finish"] and mixed[j]["t_admit"] < mixed[i]["t_finish"]
+                  for i in range(len(mixed)) for j in range(i + 1, len(mixed)))
+    assert overlap  # admitted while others were running
+    for (Ua, La, ra), (Ub, Lb, rb) in zip(A, B):
+        assert ra["status"] == 0 and rb["status"] == 0
+        assert ra["rel_residual"] <= 1e-10 and rb["rel_residual"] <= 1e-10
+        # deterministic kernels: bitwise the same alone and in the mix
+        assert np.array_equal(Ua, Ub) and np.array_equal(La, Lb)
+        assert ra["iterations"] == rb["iterations"]
+    # an elliptic request against the oracle's saddle-point solve
+    sp, t, _ = reqs[1]
+    m = sp["mesh"]
+    pb = I.Problem(f=lambda x, y: 1.0 + 0 * x, g=lambda x, y, nx, ny: 0.1 + 0 * x, uD=lambda x, y: 0.2 + 0 * x,
+                   delta=sp["delta"])
+    ref = O.solve_saddle(m, pb, aT=sp["aT"])
+    assert np.max(np.abs(B[1][0] - ref["U"])) <= 1e-7 * np.max(np.abs(ref["U"]))
+    assert np.max(np.abs(B[1][1] - ref["Lambda"])) <= 1e-6 * np.max(np.abs(ref["Lambda"]))
+
+
+def test_budget_admission_in_arrival_order():
+    from paper_2401_15557_gb300 import phfem as P
+    reqs = _requests()[:5]
+    srv = P.phfem_server_create(4, 1.0, P.solve_opts(rtol=1e-10))  # every request exceeds the budget
+    ids = [P.phfem_server_submit(srv, rq) for _, _, rq in reqs]
+    P.phfem_server_drain(srv)
+    res = [P.phfem_server_poll(srv, i, wait=False) for i in ids]
+    P.phfem_server_destroy(srv)
+    for a, b in zip(res, res[1:]):
+        assert b["t_admit"] >= a["t_finish"] - 1e-9  # one at a time, first in first out
+        assert b["t_admit"] >= a["t_admit"]
+    assert all(r["status"] == 0 for r in res)
