@@ -146,8 +146,11 @@ typedef struct {
   double delta;       /* reaction coefficient delta >= 0 (Eq. eq1)                */
   double dt;          /* 0: elliptic; > 0: Crank-Nicolson matrix M + dt/2 K (Sec. 4) */
   int32_t precision;  /* PHFEM_FP64 or PHFEM_FP32_IR (FP32 inner solve + FP64 refinement) */
-  int32_t reserved;
+  int32_t form;       /* PHFEM_FORM_TRACE (edge-midpoint values, default) or
+                         PHFEM_FORM_FLUX (multipliers; elliptic with delta > 0)     */
 } phfem_coeffs;
+
+enum { PHFEM_FORM_TRACE = 0, PHFEM_FORM_FLUX = 1 };
 
 /* Assembles, per triangle, the stiffness/reaction blocks of Definition 3.1
  * condensed to the edge midpoints, K^CR_T = R^-T (a_T B_T + delta M_T) R^-1
@@ -160,6 +163,13 @@ typedef struct {
  *                       flux) on Neumann edges, ignored elsewhere
  * For dt > 0 the matrix is M^CR + dt/2 K^CR (M^CR = |T|/3 I per triangle) and
  * f_mid/bc_mid may be NULL (the source comes with phfem_cn_create).
+ * PHFEM_FORM_FLUX eliminates the element unknowns in favour of the multipliers
+ * instead (Sec. 3.5 with U_T = K_T^-1 (F_T + C_T' Lambda_T)): the SPD system
+ * S Lambda = -b_D - sum_T C_T K_T^-1 F_T over the non-Neumann edges, with
+ * S_T = C_T K_T^-1 C_T' = diag(sigma|E|) (K^CR_T)^-1 diag(sigma|E|) per
+ * triangle (Neumann edges become identity rows with Lambda = 0).  It needs an
+ * invertible K_T (delta > 0) and is elliptic only (dt = 0); phfem_sys_csr is
+ * not available for it (its rows are the multiplier edges).
  * Returns PHFEM_EINVAL for delta < 0, dt < 0 or a nonpositive a; PHFEM_ENAN
  * when a coefficient is not finite. */
 PHFEM_API int phfem_assemble(phfem_mesh mesh, const phfem_coeffs* coeffs, const double* f_mid,
@@ -205,7 +215,9 @@ typedef struct {
  * not, and below that level no FP64 vector w satisfies the system better.
  *   w0     [nE] double  initial midpoint values (NULL = zero); Dirichlet
  *                       entries are ignored (u_D is imposed)
- *   w      [nE] double  out: midpoint values of u_h on every edge (or NULL)
+ *   w      [nE] double  out: midpoint values of u_h on every edge (or NULL);
+ *                       with PHFEM_FORM_FLUX: the multiplier of every edge
+ *                       (0 on Neumann edges)
  *   U      [3 nT] double out: u_h at the vertices, element-major (3t + k;
  *                       Wvec(1:N) of Main.m) (or NULL)
  *   Lambda [nL] double  out: multipliers in Redges order (Wvec(N+1:N+L)) (or NULL)

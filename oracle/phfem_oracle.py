@@ -21,6 +21,8 @@ What it computes, in the paper's order and notation:
     element unknowns with u_T = R^{-1} w_T (the equivalence stated in the
     introduction; the multiplier constraint forces midpoint continuity), its
     recovery of U and Lambda, and a plain Jacobi-PCG for large meshes;
+  * the multiplier ("flux") Schur complement C K^{-1} C' of the same saddle
+    system (reaction delta > 0) and its recovery of U;
   * error norms: L2, broken H1 seminorm, and a mesh M-norm of kappa - kappa_h.
 
 Readings of passages that are ambiguous (all listed in the design notes):
@@ -432,6 +434,40 @@ def solve_condensed(mesh, problem, aT=None, A=None, method="direct", rtol=1e-13,
     rec = recover(cs["st"], cs["cl"], w)
     rec.update(w=w, wf=wf, info=info, cs=cs)
     return rec
+
+
+def flux_system(mesh, problem, aT=None, A=None):
+    """Multiplier ("flux") Schur complement of the saddle system of Section 3.5:
+    the element rows K U - C' Lambda = F give U = K^{-1} (F + C' Lambda), and the
+    constraint rows -C U = b_D then read
+        (C K^{-1} C') Lambda = -b_D - C K^{-1} F.
+    K = B + D + M is block diagonal over the elements; each 3x3 block is
+    inverted on its own (it is invertible only when the reaction delta > 0).
+    Rows and columns are the multipliers in Redges order (interior and
+    Dirichlet edges)."""
+    st = setup(mesh, problem, aT=aT, A=A)
+    glob = global_blocks(st["tri"], st["topo"], st["bsets"], st["geo"], st["loc"])
+    lv = load_vectors(st["xy"], st["tri"], st["topo"], st["bsets"], st["geo"],
+                      problem.f, problem.g, problem.uD)
+    loc = st["loc"]
+    KT = loc["B"] + loc["D"] + loc["M"]
+    nT = KT.shape[0]
+    Kinv_T = np.linalg.inv(KT)                    # raises on a singular block
+    r = (3 * np.arange(nT))[:, None, None] + np.arange(3)[None, :, None]
+    c = (3 * np.arange(nT))[:, None, None] + np.arange(3)[None, None, :]
+    Kinv = sp.csr_matrix((Kinv_T.ravel(), (np.broadcast_to(r, (nT, 3, 3)).ravel(),
+                                           np.broadcast_to(c, (nT, 3, 3)).ravel())),
+                         shape=(3 * nT, 3 * nT))
+    C = glob["C"].tocsr()
+    F = lv["b"] + lv["LN"]
+    S = (C @ Kinv @ C.T).tocsr()
+    rhs = -lv["bD"] - C @ (Kinv @ F)
+    return dict(S=S, rhs=rhs, Kinv=Kinv, C=C, F=F, st=st)
+
+
+def flux_recover(fs, Lambda):
+    """U = K^{-1} (F + C' Lambda) (the element rows of Section 3.5)."""
+    return fs["Kinv"] @ (fs["F"] + fs["C"].T @ Lambda)
 
 
 def relative_residual(S, b, x) -> float:

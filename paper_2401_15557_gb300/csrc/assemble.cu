@@ -75,6 +75,98 @@ __global__ void k_asm_rows(int nE, int nT, const int32_t* __restrict__ ed2el, co
   }
 }
 
+// Flux form, per triangle: S_T = D (K^CR_T)^-1 D with D = diag(sigma_k |E_k|)
+// and the load term g_T = -D (K^CR_T)^-1 F^CR_T, F^CR_T[k] = |T|/3 f(m_k)
+// + [edge k Neumann] |E_k| g(m_k) (C_T K_T^-1 C_T' and C_T K_T^-1 F_T written
+// with C_T = D R and R K_T^-1 R' = (K^CR_T)^-1).  The inverse of the symmetric
+// 3x3 block is its cofactor matrix over the determinant.
+__global__ void k_asm_flux_tri(int nT, const int32_t* __restrict__ t2e, const int8_t* __restrict__ sigma,
+                               const uint8_t* __restrict__ eclass, const double* __restrict__ elen,
+                               const double* __restrict__ Kt, const double* __restrict__ f_mid,
+                               const double* __restrict__ bc_mid, double* __restrict__ St) {
+  const size_t n = (size_t)nT;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nT; t += gridDim.x * blockDim.x) {
+    const double a = Kt[t], b = Kt[n + t], c = Kt[2 * n + t];
+    const double d = Kt[3 * n + t], e = Kt[4 * n + t], f = Kt[5 * n + t], mT = Kt[6 * n + t];
+    const double C00 = b * c - e * e, C11 = a * c - f * f, C22 = a * b - d * d;
+    const double C01 = e * f - d * c, C12 = d * f - a * e, C20 = d * e - b * f;
+    const double inv = 1.0 / (a * C00 + d * C01 + f * C20);
+    const double I00 = C00 * inv, I11 = C11 * inv, I22 = C22 * inv, I01 = C01 * inv, I12 = C12 * inv,
+                 I20 = C20 * inv;
+    double D[3], F[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int ek = t2e[3 * t + k];
+      D[k] = sigma[3 * t + k] * elen[ek];
+      F[k] = (f_mid ? mT * f_mid[ek] : 0.0) +
+             ((bc_mid && eclass[ek] == PHFEM_EDGE_NEUMANN) ? elen[ek] * bc_mid[ek] : 0.0);
+    }
+    St[0 * n + t] = D[0] * I00 * D[0];
+    St[1 * n + t] = D[1] * I11 * D[1];
+    St[2 * n + t] = D[2] * I22 * D[2];
+    St[3 * n + t] = D[0] * I01 * D[1];
+    St[4 * n + t] = D[1] * I12 * D[2];
+    St[5 * n + t] = D[2] * I20 * D[0];
+    const double y0 = I00 * F[0] + I01 * F[1] + I20 * F[2];
+    const double y1 = I01 * F[0] + I11 * F[1] + I12 * F[2];
+    const double y2 = I20 * F[0] + I12 * F[1] + I22 * F[2];
+    St[6 * n + t] = -D[0] * y0;
+    St[7 * n + t] = -D[1] * y1;
+    St[8 * n + t] = -D[2] * y2;
+  }
+}
+
+// Flux-form rows: the rows of S_{T+} and S_{T-} at the edge, rhs = sum of the
+// load terms + |E| u_D on Dirichlet edges (-b_D of Eq. DirichletEqn);
+// Neumann edges are identity rows with Lambda = 0.
+template <typename T>
+__global__ void k_asm_rows_flux(int nE, int nT, const int32_t* __restrict__ ed2el, const uint8_t* __restrict__ lk,
+                                const uint8_t* __restrict__ eclass, const double* __restrict__ St,
+                                const double* __restrict__ bc_mid, const double* __restrict__ elen,
+                                double* __restrict__ val, double* __restrict__ b, T* __restrict__ lval,
+                                T* __restrict__ rdiag, T* __restrict__ dinv) {
+  const size_t n = (size_t)nT, m = (size_t)nE;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    const int4 q = reinterpret_cast<const int4*>(ed2el)[e];
+    const int kk = lk[e];
+    const uint8_t cls = eclass[e];
+    double diag, v[4] = {0.0, 0.0, 0.0, 0.0}, rhs;
+    if (cls == PHFEM_EDGE_NEUMANN) {
+      diag = 1.0;
+      rhs = 0.0;
+    } else {
+      double d, o1, o2, unused;
+      int k = kk & 3;
+      tri_row(St, n, q.z, k, d, o1, o2, unused);
+      diag = d;
+      v[0] = o1;
+      v[1] = o2;
+      rhs = __ldg(St + (size_t)(6 + k) * n + q.z);
+      if (q.w >= 0) {
+        k = (kk >> 2) & 3;
+        tri_row(St, n, q.w, k, d, o1, o2, unused);
+        diag += d;
+        v[2] = o1;
+        v[3] = o2;
+        rhs += __ldg(St + (size_t)(6 + k) * n + q.w);
+      }
+      if (cls == PHFEM_EDGE_DIRICHLET && bc_mid) rhs += elen[e] * bc_mid[e];
+    }
+    double rpart = diag;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) rpart += v[s];  // diag = rpart + sum of l, l = -off
+    val[e] = rpart;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      val[(s + 1) * m + e] = -v[s];
+      lval[s * m + e] = (T)(-v[s]);
+    }
+    b[e] = rhs;
+    rdiag[e] = (T)rpart;
+    dinv[e] = (T)(1.0 / diag);
+  }
+}
+
 // CSR export of the free-edge system: the row of free edge e lists (column,
 // value) for e and its free neighbours, sorted by column; rhs subtracts the
 // Dirichlet couplings times u_D (the lifting).
@@ -136,6 +228,8 @@ void sys_free(phfem_sys s) {
   dfree(c, s->rdiag);
   dfree(c, s->dinv);
   dfree(c, s->f);
+  dfree(c, s->bc);
+  dfree(c, s->St);
   dfree(c, s->x);
   dfree(c, s->r64);
   dfree(c, s->ri);
@@ -161,6 +255,24 @@ int assemble_into(phfem_sys sys, const double* f_mid, const double* bc_mid, int*
                                                  c.delta, sys->Kt, d_bad);
   prof_stop(ctx, kProfAsmTri);
   PH_TRY(check_launch(ctx, "k_asm_tri"));
+  if (sys->form == PHFEM_FORM_FLUX) {
+    k_asm_flux_tri<<<grid_for(ctx, nT), kBlock, 0, s>>>(nT, m->t2e, m->sigma, m->eclass, m->elen, sys->Kt, f_mid,
+                                                        bc_mid, sys->St);
+    PH_TRY(check_launch(ctx, "k_asm_flux_tri"));
+    prof_start(ctx, kProfAsmRows);
+    if (sys->fp32)
+      k_asm_rows_flux<float><<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, nT, m->ed2el, m->lk, m->eclass, sys->St,
+                                                                  bc_mid, m->elen, sys->val, sys->b,
+                                                                  (float*)sys->lval, (float*)sys->rdiag,
+                                                                  (float*)sys->dinv);
+    else
+      k_asm_rows_flux<double><<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, nT, m->ed2el, m->lk, m->eclass, sys->St,
+                                                                   bc_mid, m->elen, sys->val, sys->b,
+                                                                   (double*)sys->lval, (double*)sys->rdiag,
+                                                                   (double*)sys->dinv);
+    prof_stop(ctx, kProfAsmRows);
+    return check_launch(ctx, "k_asm_rows_flux");
+  }
   const double sK = c.dt > 0 ? 0.5 * c.dt : 1.0, sM = c.dt > 0 ? 1.0 : 0.0;
   prof_start(ctx, kProfAsmRows);
   if (sys->fp32)
@@ -195,6 +307,12 @@ PHFEM_API int phfem_assemble(phfem_mesh mesh, const phfem_coeffs* coeffs, const 
     return fail(PHFEM_EINVAL, "phfem_assemble: unknown precision");
   if (c.delta == 0.0 && c.dt == 0.0 && mesh->info.nD == 0)
     return fail(PHFEM_EINVAL, "phfem_assemble: no Dirichlet edge and no reaction term (singular system)");
+  if (c.form != PHFEM_FORM_TRACE && c.form != PHFEM_FORM_FLUX)
+    return fail(PHFEM_EINVAL, "phfem_assemble: unknown form");
+  if (c.form == PHFEM_FORM_FLUX && !(c.delta > 0.0))
+    return fail(PHFEM_EINVAL, "phfem_assemble: the flux form needs delta > 0 (an invertible element block)");
+  if (c.form == PHFEM_FORM_FLUX && c.dt != 0.0)
+    return fail(PHFEM_EINVAL, "phfem_assemble: the flux form is elliptic only (dt = 0)");
   if (!std::isfinite(c.delta) || !std::isfinite(c.dt) || (!c.a_T && !std::isfinite(c.a)))
     return fail(PHFEM_ENAN, "phfem_assemble: non-finite coefficient");
   phfem_ctx ctx = mesh->ctx;
@@ -205,6 +323,8 @@ PHFEM_API int phfem_assemble(phfem_mesh mesh, const phfem_coeffs* coeffs, const 
   sys->c = c;
   sys->c.a_T = nullptr;  // the pointer is only valid during this call
   sys->fp32 = c.precision == PHFEM_FP32_IR;
+  sys->form = c.form;
+  sys->ident_class = c.form == PHFEM_FORM_FLUX ? PHFEM_EDGE_NEUMANN : PHFEM_EDGE_DIRICHLET;
   const size_t isz = sys->fp32 ? sizeof(float) : sizeof(double);
   int st = PHFEM_OK;
   int* d_bad = nullptr;
@@ -219,6 +339,8 @@ PHFEM_API int phfem_assemble(phfem_mesh mesh, const phfem_coeffs* coeffs, const 
   chk(dalloc(ctx, &sys->rdiag, nE * isz));
   chk(dalloc(ctx, &sys->dinv, nE * isz));
   chk(dalloc_n(ctx, &sys->f, nE));
+  chk(dalloc_n(ctx, &sys->bc, nE));
+  if (c.form == PHFEM_FORM_FLUX) chk(dalloc_n(ctx, &sys->St, 9 * nT));
   chk(dalloc_n(ctx, &sys->x, nE));
   chk(dalloc_n(ctx, &sys->r64, nE));
   chk(dalloc(ctx, &sys->ri, nE * isz));
@@ -237,6 +359,8 @@ PHFEM_API int phfem_assemble(phfem_mesh mesh, const phfem_coeffs* coeffs, const 
     cudaMemsetAsync(d_bad, 0, sizeof(int), s);
     if (f_mid) cudaMemcpyAsync(sys->f, f_mid, nE * sizeof(double), cudaMemcpyDeviceToDevice, s);
     else cudaMemsetAsync(sys->f, 0, nE * sizeof(double), s);
+    if (bc_mid) cudaMemcpyAsync(sys->bc, bc_mid, nE * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    else cudaMemsetAsync(sys->bc, 0, nE * sizeof(double), s);
     sys->c.a_T = c.a_T;
     st = assemble_into(sys, f_mid, bc_mid, d_bad);
     sys->c.a_T = nullptr;
@@ -261,6 +385,7 @@ PHFEM_API int phfem_assemble(phfem_mesh mesh, const phfem_coeffs* coeffs, const 
 
 PHFEM_API int phfem_sys_csr(phfem_sys sys, double* val, double* rhs) {
   if (!sys) return fail(PHFEM_EINVAL, "phfem_sys_csr: NULL system");
+  if (sys->form != PHFEM_FORM_TRACE) return fail(PHFEM_EINVAL, "phfem_sys_csr: only the trace form has a CSR export");
   phfem_mesh m = sys->mesh;
   phfem_ctx ctx = m->ctx;
   const int nE = m->info.nE;

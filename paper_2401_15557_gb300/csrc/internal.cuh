@@ -108,6 +108,10 @@ struct phfem_sys_s {
   phfem_mesh mesh;
   phfem_coeffs c;
   bool fp32;
+  int form;              // PHFEM_FORM_TRACE or PHFEM_FORM_FLUX
+  uint8_t ident_class;   // class of the identity rows: Dirichlet (trace) or Neumann (flux)
+  double* St;            // [9][nT] flux form: S_T (00, 11, 22, 01, 12, 20) and the load terms g_T
+  double* bc;            // [nE] copy of the boundary data (flux-form recovery)
   double* Kt;            // [7][nT]: K^CR_T entries (00, 11, 22, 01, 12, 20) and |T|/3
   double* val;           // [5][nE]: FP64 row in difference form: slot 0 = r_e (reaction/mass
                          //          part of the diagonal), slots 1..4 = l_es = -S_{e,nbr_s}

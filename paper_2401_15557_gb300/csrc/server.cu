@@ -87,7 +87,7 @@ int run_request(phfem_ctx ctx, const phfem_request& r, const phfem_solve_opts& o
   }
   phfem_sys sys = nullptr;
   if (st == PHFEM_OK) {
-    phfem_coeffs c{r.a_T, 1.0, r.delta, r.kind == 1 ? r.dt : 0.0, r.precision, 0};
+    phfem_coeffs c{r.a_T, 1.0, r.delta, r.kind == 1 ? r.dt : 0.0, r.precision, PHFEM_FORM_TRACE};
     st = phfem_assemble(m, &c, r.kind == 1 ? nullptr : f, r.kind == 1 ? nullptr : bc, &sys);
   }
   if (st == PHFEM_OK && r.kind == 0) {

@@ -51,7 +51,7 @@ namespace {
 template <typename T>
 __global__ void k_residual(int nE, const int32_t* __restrict__ nbr, const double* __restrict__ val,
                            const double* __restrict__ b, const double* __restrict__ x,
-                           const uint8_t* __restrict__ eclass, const T* __restrict__ dinv,
+                           const uint8_t* __restrict__ eclass, uint8_t ident, const T* __restrict__ dinv,
                            T* __restrict__ ri, T* __restrict__ pi, double* partials,
                            SolveState* st, double rtol2, double inner_rtol2, int mode) {
   if (mode == 3) {
@@ -64,14 +64,14 @@ __global__ void k_residual(int nE, const int32_t* __restrict__ nbr, const double
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
     double r;
     if (mode == 0) {
-      if (eclass[e] == PHFEM_EDGE_DIRICHLET) {
+      if (eclass[e] == ident) {  // identity rows hold their fixed value
         r = 0.0;
       } else {
         r = b[e];
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
           const int c = nbr[s * m + e];
-          if (c != e && eclass[c] == PHFEM_EDGE_DIRICHLET) r += val[(s + 1) * m + e] * b[c];
+          if (c != e && eclass[c] == ident) r += val[(s + 1) * m + e] * b[c];
         }
       }
       acc_r += r * r;
@@ -255,10 +255,47 @@ __global__ void k_loop_control(SolveState* st, cudaGraphConditionalHandle handle
   cudaGraphSetConditional(handle, more ? 1u : 0u);
 }
 
-__global__ void k_init_x(int nE, const uint8_t* __restrict__ eclass, const double* __restrict__ b,
+__global__ void k_init_x(int nE, const uint8_t* __restrict__ eclass, uint8_t ident, const double* __restrict__ b,
                          const double* __restrict__ w0, double* __restrict__ x) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x)
-    x[e] = (eclass[e] == PHFEM_EDGE_DIRICHLET) ? b[e] : (w0 ? w0[e] : 0.0);
+    x[e] = (eclass[e] == ident) ? b[e] : (w0 ? w0[e] : 0.0);
+}
+
+// Flux form: w_T = (K^CR_T)^-1 (F^CR_T + diag(sigma |E|) Lambda_T), U = R^-1 w_T.
+__global__ void k_recover_flux(int nT, const int32_t* __restrict__ t2e, const int8_t* __restrict__ sigma,
+                               const uint8_t* __restrict__ eclass, const double* __restrict__ elen,
+                               const double* __restrict__ Kt, const double* __restrict__ f,
+                               const double* __restrict__ bc, const double* __restrict__ lam, double* __restrict__ U) {
+  const size_t n = (size_t)nT;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nT; t += gridDim.x * blockDim.x) {
+    const double a = Kt[t], b = Kt[n + t], c = Kt[2 * n + t];
+    const double d = Kt[3 * n + t], e = Kt[4 * n + t], g = Kt[5 * n + t], mT = Kt[6 * n + t];
+    const double C00 = b * c - e * e, C11 = a * c - g * g, C22 = a * b - d * d;
+    const double C01 = e * g - d * c, C12 = d * g - a * e, C20 = d * e - b * g;
+    const double inv = 1.0 / (a * C00 + d * C01 + g * C20);
+    double rhs[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      const int ek = t2e[3 * t + k];
+      const double L = elen[ek];
+      rhs[k] = mT * f[ek] + (eclass[ek] == PHFEM_EDGE_NEUMANN ? L * bc[ek] : 0.0) + sigma[3 * t + k] * L * lam[ek];
+    }
+    const double w0 = (C00 * rhs[0] + C01 * rhs[1] + C20 * rhs[2]) * inv;
+    const double w1 = (C01 * rhs[0] + C11 * rhs[1] + C12 * rhs[2]) * inv;
+    const double w2 = (C20 * rhs[0] + C12 * rhs[1] + C22 * rhs[2]) * inv;
+    const double sw = w0 + w1 + w2;
+    U[3 * t] = sw - 2.0 * w0;
+    U[3 * t + 1] = sw - 2.0 * w1;
+    U[3 * t + 2] = sw - 2.0 * w2;
+  }
+}
+
+__global__ void k_copy_lambda(int nE, const int32_t* __restrict__ lam_id, const double* __restrict__ x,
+                              double* __restrict__ Lambda) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    const int li = lam_id[e];
+    if (li >= 0) Lambda[li] = x[e];
+  }
 }
 
 // U = R^-1 w per triangle (u at the vertices); with Lambda: the element row
@@ -323,8 +360,8 @@ struct Launch {
     phfem_ctx ctx = sys->mesh->ctx;
     prof_start(ctx, kProfResidual);
     k_residual<T><<<g, kBlock, 0, s>>>(nE, sys->mesh->nbr, sys->val, sys->b, sys->x, sys->mesh->eclass,
-                                       (const T*)sys->dinv, (T*)sys->ri, (T*)sys->pi, sys->partials, sys->st, rtol2,
-                                       irtol2, mode);
+                                       sys->ident_class, (const T*)sys->dinv, (T*)sys->ri, (T*)sys->pi,
+                                       sys->partials, sys->st, rtol2, irtol2, mode);
     prof_stop(ctx, kProfResidual);
     return check_launch(ctx, "k_residual");
   }
@@ -485,7 +522,7 @@ int sys_init_x(phfem_sys sys, const double* w0) {
   phfem_mesh m = sys->mesh;
   phfem_ctx ctx = m->ctx;
   const int nE = m->info.nE;
-  k_init_x<<<grid_for(ctx, nE), kBlock, 0, ctx->stream>>>(nE, m->eclass, sys->b, w0, sys->x);
+  k_init_x<<<grid_for(ctx, nE), kBlock, 0, ctx->stream>>>(nE, m->eclass, sys->ident_class, sys->b, w0, sys->x);
   return check_launch(ctx, "k_init_x");
 }
 
@@ -526,7 +563,20 @@ PHFEM_API int phfem_solve(phfem_sys sys, const phfem_solve_opts* opts, const dou
     phfem_mesh m = sys->mesh;
     cudaStream_t s = m->ctx->stream;
     if (w) PH_CUDA(cudaMemcpyAsync(w, sys->x, sizeof(double) * m->info.nE, cudaMemcpyDeviceToDevice, s));
-    PH_TRY(recover(sys, sys->x, nullptr, sys->f, 0.0, 1.0, U, Lambda));
+    if (sys->form == PHFEM_FORM_FLUX) {
+      phfem_ctx ctx = m->ctx;
+      if (U) {
+        k_recover_flux<<<grid_for(ctx, m->info.nT), kBlock, 0, s>>>(m->info.nT, m->t2e, m->sigma, m->eclass, m->elen,
+                                                                    sys->Kt, sys->f, sys->bc, sys->x, U);
+        PH_TRY(check_launch(ctx, "k_recover_flux"));
+      }
+      if (Lambda) {
+        k_copy_lambda<<<grid_for(ctx, m->info.nE), kBlock, 0, s>>>(m->info.nE, m->lam_id, sys->x, Lambda);
+        PH_TRY(check_launch(ctx, "k_copy_lambda"));
+      }
+    } else {
+      PH_TRY(recover(sys, sys->x, nullptr, sys->f, 0.0, 1.0, U, Lambda));
+    }
     PH_CUDA(cudaStreamSynchronize(s));
   }
   st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();

@@ -15,7 +15,10 @@ import torch
 from . import build as _build
 
 PHFEM_FP64, PHFEM_FP32_IR = 0, 1
+PHFEM_FORM_TRACE, PHFEM_FORM_FLUX = 0, 1
 EDGE_INTERIOR, EDGE_DIRICHLET, EDGE_NEUMANN = 0, 1, 2
+PHFEM_OK, PHFEM_EINVAL, PHFEM_EMESH, PHFEM_ENOMEM = 0, -1, -2, -3
+PHFEM_ENOCONV, PHFEM_EBREAKDOWN, PHFEM_ENAN, PHFEM_ECUDA = -4, -5, -6, -7
 MAX_TERMS = 4
 
 
@@ -34,7 +37,7 @@ class MeshInfo(C.Structure):
 
 class Coeffs(C.Structure):
     _fields_ = [("a_T", C.c_void_p), ("a", C.c_double), ("delta", C.c_double), ("dt", C.c_double),
-                ("precision", C.c_int32), ("reserved", C.c_int32)]
+                ("precision", C.c_int32), ("form", C.c_int32)]
 
 
 class SolveOpts(C.Structure):
@@ -231,9 +234,10 @@ def phfem_mesh_destroy(mesh):
 
 # --- assembly ----------------------------------------------------------------
 
-def phfem_assemble(mesh, f_mid=None, bc_mid=None, a_T=None, a=1.0, delta=0.0, dt=0.0, precision=PHFEM_FP64):
+def phfem_assemble(mesh, f_mid=None, bc_mid=None, a_T=None, a=1.0, delta=0.0, dt=0.0, precision=PHFEM_FP64,
+                   form=PHFEM_FORM_TRACE):
     I = phfem_mesh_info_get(mesh)
-    c = Coeffs(_ptr(a_T, torch.float64, I["nT"]), float(a), float(delta), float(dt), int(precision), 0)
+    c = Coeffs(_ptr(a_T, torch.float64, I["nT"]), float(a), float(delta), float(dt), int(precision), int(form))
     h = _H()
     _check(lib().phfem_assemble(mesh, C.byref(c), _ptr(f_mid, torch.float64, I["nE"]),
                                 _ptr(bc_mid, torch.float64, I["nE"]), C.byref(h)), "phfem_assemble")

@@ -243,3 +243,49 @@ def test_relative_residual_against_exact_rationals():
         r2 += acc * acc
     exact_p = float(np.sqrt(float(r2))) / np.linalg.norm(b)
     assert abs(O.relative_residual(S, b, xp) - exact_p) <= 1e-3 * exact_p
+
+
+@pytest.mark.parametrize("mk", ["lshape", "square", "crisscross"])
+def test_flux_schur_patch_test(mk):
+    """The multiplier Schur route reproduces a linear solution and its exact
+    normal flux A grad u . nu (a closed form, independent of any solve)."""
+    mesh = {"lshape": lambda: I.lshape_mesh(n=4, seed=I.seed_for(1, 3)),
+            "square": lambda: I.square_mesh(6),
+            "crisscross": lambda: I.criss_cross(2)}[mk]()
+    pb = _patch_problem(A_SPD, 0.7)
+    fs = O.flux_system(mesh, pb)
+    lam = spla.spsolve(fs["S"].tocsc(), fs["rhs"])
+    st = fs["st"]
+    kappa = O.exact_flux(st, pb.grad, A=A_SPD)
+    assert np.max(np.abs(lam - kappa)) < 1e-11
+    P = st["geo"]["P"]
+    u_vert = pb.u(P[..., 0], P[..., 1]).reshape(-1)
+    assert np.max(np.abs(O.flux_recover(fs, lam) - u_vert)) < 1e-12
+
+
+@pytest.mark.parametrize("var", [False, True])
+def test_flux_schur_equals_saddle(var):
+    """C K^-1 C' is symmetric positive definite for delta > 0 and its solution
+    is the multiplier of the saddle-point solve."""
+    mesh = I.lshape_mesh(n=6, seed=I.seed_for(1, 5), levels=1)
+    pb = I.problem_sine_exp()
+    pb.delta = 0.9
+    aT = I.element_mean_at_midpoints(mesh.xy, mesh.tri, I.coeff_lshape) if var else None
+    fs = O.flux_system(mesh, pb, aT=aT)
+    S = fs["S"].toarray()
+    assert np.allclose(S, S.T, rtol=0, atol=1e-13 * np.abs(S).max())
+    assert np.linalg.eigvalsh(S).min() > 0
+    lam = np.linalg.solve(S, fs["rhs"])
+    ref = O.solve_saddle(mesh, pb, aT=aT)
+    assert np.max(np.abs(lam - ref["Lambda"])) <= 1e-10 * np.max(np.abs(ref["Lambda"]))
+    U = O.flux_recover(fs, lam)
+    assert np.max(np.abs(U - ref["U"])) <= 1e-10 * np.max(np.abs(ref["U"]))
+
+
+def test_flux_schur_needs_reaction():
+    """Without the reaction term every element block has the constants in its
+    kernel, so the multiplier Schur complement does not exist."""
+    pb = I.problem_sine_exp()
+    pb.delta = 0.0
+    with pytest.raises(np.linalg.LinAlgError):
+        O.flux_system(I.square_mesh(3), pb)
