@@ -372,6 +372,47 @@ PHFEM_API int phfem_server_drain(phfem_server server);
 PHFEM_API int phfem_server_destroy(phfem_server server);
 
 /* ------------------------------------------------------------------------ */
+/* Error report (Section 5: L2 error, broken H1 error, mesh norm of kappa)   */
+/* ------------------------------------------------------------------------ */
+
+/* Quadrature of the report.  Triangles: a Duffy-collapsed nq x nq
+ * Gauss-Legendre rule, point q = i nq + j at barycentric coordinates
+ * (1 - s - t, s, t), s = x_i, t = x_j (1 - x_i), weight w_i w_j (1 - x_i)
+ * times 2|T|, with (x_i, w_i) the nq-point Gauss-Legendre rule on [0, 1].
+ * Multiplier edges (interior and Dirichlet, in multiplier order): the nq
+ * Gauss-Legendre points from the initial to the end vertex of the edge. */
+typedef struct {
+  double L2;      /* ||u - u_h||_{L2}                                            */
+  double H1semi;  /* broken ||grad_h (u - u_h)||_{L2}                             */
+  double H1;      /* sqrt(L2^2 + H1semi^2)                                        */
+  double M;       /* sqrt(sum_E |E| int_E (kappa - Lambda_E)^2) over the multiplier
+                     edges: the mesh norm of the multiplier error; 0 without kappa */
+} phfem_errors;
+
+/* Writes the physical quadrature points where the caller evaluates the exact
+ * solution (device buffers, each may be NULL):
+ *   tri_xy  [nT][nq*nq][2] double   triangle points (x, y)
+ *   edge_xy [nL][nq][2]    double   edge points
+ *   edge_nu [nL][2]        double   unit normal of the edge pointing out of T+
+ *                                   (the direction of Lambda)
+ * 1 <= nq <= 16 (else PHFEM_EINVAL).  Asynchronous on the context's stream. */
+PHFEM_API int phfem_error_points(phfem_mesh mesh, int32_t nq, double* tri_xy, double* edge_xy,
+                                 double* edge_nu);
+
+/* Integrates the errors of a solution (all device buffers):
+ *   U [3nT]              element values at the vertices (phfem_solve's U)
+ *   u_q [nT][nq*nq]      exact u at tri_xy
+ *   grad_q [nT][nq*nq][2]  exact grad u at tri_xy
+ *   Lambda [nL]          multipliers (phfem_solve's Lambda)
+ *   kappa_q [nL][nq]     exact normal flux (A grad u) . nu at edge_xy
+ * U, u_q and grad_q come together (or are all NULL: L2 = H1semi = H1 = 0);
+ * so do Lambda and kappa_q (or M = 0).  Sums are FP64 in a fixed order.
+ * Blocks the host until *out (host) is written. */
+PHFEM_API int phfem_error_norms(phfem_mesh mesh, int32_t nq, const double* U, const double* u_q,
+                                const double* grad_q, const double* Lambda, const double* kappa_q,
+                                phfem_errors* out);
+
+/* ------------------------------------------------------------------------ */
 /* Solve without device allocation                                           */
 /* ------------------------------------------------------------------------ */
 

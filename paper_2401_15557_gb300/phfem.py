@@ -76,6 +76,13 @@ class Result(C.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class Errors(C.Structure):
+    _fields_ = [("L2", C.c_double), ("H1semi", C.c_double), ("H1", C.c_double), ("M", C.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
 _lib = None
 _H = C.c_void_p
 _P = C.c_void_p
@@ -125,6 +132,8 @@ def lib() -> C.CDLL:
             "phfem_server_poll": (C.c_int, [_H, C.c_int64, C.c_int32, C.POINTER(Result)]),
             "phfem_server_drain": (C.c_int, [_H]),
             "phfem_server_destroy": (C.c_int, [_H]),
+            "phfem_error_points": (C.c_int, [_H, C.c_int32, _P, _P, _P]),
+            "phfem_error_norms": (C.c_int, [_H, C.c_int32, _P, _P, _P, _P, _P, C.POINTER(Errors)]),
             "phfem_csr_pcg_noalloc": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, C.c_double, C.c_int32,
                                                 C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
         }
@@ -404,6 +413,30 @@ def phfem_server_drain(server):
 
 def phfem_server_destroy(server):
     _check(lib().phfem_server_destroy(server), "phfem_server_destroy")
+
+
+# --- error report -----------------------------------------------------------------
+
+def phfem_error_points(mesh, nq, tri_xy=None, edge_xy=None, edge_nu=None):
+    """Quadrature points of the error report: tri_xy (nT, nq*nq, 2), edge_xy
+    (nL, nq, 2) and edge_nu (nL, 2), float64 CUDA tensors (each optional)."""
+    I = phfem_mesh_info_get(mesh)
+    Q = nq * nq
+    _check(lib().phfem_error_points(mesh, int(nq), _ptr(tri_xy, torch.float64, 2 * Q * I["nT"]),
+                                    _ptr(edge_xy, torch.float64, 2 * nq * I["nL"]),
+                                    _ptr(edge_nu, torch.float64, 2 * I["nL"])), "phfem_error_points")
+
+
+def phfem_error_norms(mesh, nq, U=None, u_q=None, grad_q=None, Lambda=None, kappa_q=None) -> dict:
+    """L2, broken H1 and multiplier mesh-norm errors (host floats)."""
+    I = phfem_mesh_info_get(mesh)
+    Q = nq * nq
+    out = Errors()
+    _check(lib().phfem_error_norms(mesh, int(nq), _ptr(U, torch.float64, 3 * I["nT"]),
+                                   _ptr(u_q, torch.float64, Q * I["nT"]), _ptr(grad_q, torch.float64, 2 * Q * I["nT"]),
+                                   _ptr(Lambda, torch.float64, I["nL"]), _ptr(kappa_q, torch.float64, nq * I["nL"]),
+                                   C.byref(out)), "phfem_error_norms")
+    return out.as_dict()
 
 
 # --- solve without device allocation -------------------------------------------
