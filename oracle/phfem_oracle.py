@@ -9,6 +9,7 @@ imports nothing from the product.  It shares no code with the CUDA path: the
 two only consume the same seeded inputs.
 
 What it computes, in the paper's order and notation:
+  * uniform red refinement (Section 2.3, redrefine_vec);
   * topology (Section 2.2, Eqs. n2el/n2ed/ed2el, Listings 1-3): nodes2element,
     nodes2edge (edges numbered by the column-major order of triu(B)),
     edge2element = [initial, end, T+, T-] with T+ the first element (element-major
@@ -168,6 +169,42 @@ def boundary_sets(topo: dict, dirichlet: np.ndarray, neumann: np.ndarray) -> dic
     eclass[isN] = 2
     return dict(Dbed=Dbed, Nbed=Nbed, Redges=Redges, free=free, lam_id=lam_id,
                 free_id=free_id, isD=isD, isN=isN, eclass=eclass)
+
+
+def redrefine(xy: np.ndarray, tri: np.ndarray, dirichlet: np.ndarray, neumann: np.ndarray):
+    """Uniform red refinement of Section 2.3 (redrefine_vec): the midpoint of
+    edge e (the edge numbering of Eq. n2ed) becomes vertex nV + e at
+    (initial + end) / 2; element t becomes its middle child [M1 M2 M3] (Mk the
+    new vertex on the edge opposite Pk) at position t, and its corner children
+    [P1 M3 M2], [P2 M1 M3], [P3 M2 M1] are appended at nT + 3t, nT + 3t + 1,
+    nT + 3t + 2.  A listed boundary pair (a, b) with new vertex m becomes
+    (a, m) at its own position and (m, b) at position (list length + its own)."""
+    xy = np.asarray(xy, dtype=np.float64)
+    tri = np.asarray(tri, dtype=np.int64)
+    nV, nT = xy.shape[0], tri.shape[0]
+    topo = edge_tables(tri, nV)
+    ed2el, t2e, n2ed = topo["ed2el"], topo["t2e"], topo["n2ed"]
+    marker = nV + np.arange(topo["nE"])
+    new_xy = np.concatenate([xy, (xy[ed2el[:, 0]] + xy[ed2el[:, 1]]) / 2], axis=0)
+    M1, M2, M3 = marker[t2e[:, 0]], marker[t2e[:, 1]], marker[t2e[:, 2]]
+    P1, P2, P3 = tri[:, 0], tri[:, 1], tri[:, 2]
+    out = np.empty((4 * nT, 3), dtype=np.int64)
+    out[:nT] = np.stack([M1, M2, M3], axis=1)
+    out[nT::3] = np.stack([P1, M3, M2], axis=1)
+    out[nT + 1::3] = np.stack([P2, M1, M3], axis=1)
+    out[nT + 2::3] = np.stack([P3, M2, M1], axis=1)
+
+    def refine_edges(pairs):
+        pairs = np.asarray(pairs, dtype=np.int64).reshape(-1, 2)
+        if pairs.shape[0] == 0:
+            return pairs
+        base = _lookup(n2ed, pairs[:, 0], pairs[:, 1]) - 1
+        if (base < 0).any():
+            raise ValueError("a listed boundary pair is not an edge")
+        m = marker[base]
+        return np.concatenate([np.stack([pairs[:, 0], m], axis=1), np.stack([m, pairs[:, 1]], axis=1)], axis=0)
+
+    return new_xy, out, refine_edges(dirichlet), refine_edges(neumann)
 
 
 # ---------------------------------------------------------------------------
