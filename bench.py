@@ -58,6 +58,7 @@ def parse():
     ap.add_argument("--levels", type=int, default=LEVELS)
     ap.add_argument("--fp64-steps", type=int, default=2)
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--refine-steps", type=int, default=3, help="timed device refinements of the mesh (0: skip)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="lshape", choices=["lshape", "batched", "heat", "serve"],
                     help="lshape: the L-shaped 6.3M-triangle solve (default); batched: 4096 meshes in one "
@@ -585,6 +586,26 @@ def main():
         e2e = {"value": world * nT * 1e3 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
 
+    # ---- device red refinement of the level-L mesh (Section 2.3) --------------
+    refine = None
+    if args.refine_steps > 0:
+        mL = P.phfem_mesh_build(ctx, xy, tri, dd, nn)
+        fine = P.phfem_mesh_refine(mL)  # warm-up (allocations)
+        P.phfem_mesh_destroy(fine)
+        torch.cuda.synchronize()
+        r0, r1 = ev(), ev()
+        r0.record(stream)
+        for _ in range(args.refine_steps):
+            fine = P.phfem_mesh_refine(mL)
+            P.phfem_mesh_destroy(fine)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        ms_ref = r0.elapsed_time(r1) / args.refine_steps
+        refine = {"from_triangles": nT, "to_triangles": 4 * nT, "ms": ms_ref,
+                  "refined_triangles_per_s": 4 * nT * 1e3 / ms_ref,
+                  "step": "refine kernels + phfem_mesh_build of the refined mesh"}
+        P.phfem_mesh_destroy(mL)
+
     # ---- roofline of the dominant kernel (cg_spmv) ----------------------------
     spmv_ms, spmv_n = ktimes["cg_spmv"]
     peaks = {}
@@ -630,7 +651,7 @@ def main():
             "assembly_triangles_per_s": nT * 1e3 / med(ph["assemble"]) if ph["assemble"] else None,
             "mesh_build_triangles_per_s": nT * 1e3 / med(ph["mesh_build"]) if ph["mesh_build"] else None,
             "solve": {"iterations": med(iters), "refinements": med(refs), "rel_residual_max": max(rel) if rel else None},
-            "fp64": fp64, "e2e": e2e, "roofline": roof, "kernels": kernel_share,
+            "fp64": fp64, "e2e": e2e, "refine": refine, "roofline": roof, "kernels": kernel_share,
             "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
         }
         print(json.dumps(line), flush=True)

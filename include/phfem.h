@@ -136,6 +136,24 @@ PHFEM_API int phfem_mesh_tables(phfem_mesh mesh, int32_t* ed2el, int32_t* t2e, i
                                 int32_t* row_ptr, int32_t* col);
 PHFEM_API int phfem_mesh_destroy(phfem_mesh mesh);
 
+/* Uniform red refinement (Section 2.3, redrefine_vec) of a built mesh:
+ *   - the midpoint of edge e (the mesh's edge numbering) becomes vertex nV + e,
+ *     at (initial + end) / 2;
+ *   - triangle t becomes its middle child [M1 M2 M3] at position t (Mk = the new
+ *     vertex on the edge opposite Pk), and its corner children [P1 M3 M2],
+ *     [P2 M1 M3], [P3 M2 M1] go to positions nT + 3t, nT + 3t + 1, nT + 3t + 2;
+ *   - each listed boundary pair (a, b), in the order it was given to
+ *     phfem_mesh_build, becomes (a, m) at its own position and (m, b) at
+ *     position (list length + its own).
+ * Outputs (caller device buffers; each may be NULL, then a temporary is used):
+ *   xy [nV + nE][2] double, tri [4 nT][3] int32, dirichlet [2 nD][2] int32,
+ *   neumann [2 nN][2] int32.
+ * If fine != NULL, the refined mesh is also built (phfem_mesh_build on those
+ * arrays) and returned; with fine == NULL, xy and tri must be given.
+ * PHFEM_EINVAL when a refined count exceeds the int32 range. */
+PHFEM_API int phfem_mesh_refine(phfem_mesh coarse, double* xy, int32_t* tri, int32_t* dirichlet,
+                                int32_t* neumann, phfem_mesh* fine);
+
 /* ------------------------------------------------------------------------ */
 /* Assembly (Definition 3.1; Eqs. right_b, right_g, DirichletEqn; Sec. 3.5)  */
 /* ------------------------------------------------------------------------ */

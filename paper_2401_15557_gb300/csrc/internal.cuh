@@ -102,6 +102,8 @@ struct phfem_mesh_s {
   double* elen;          // [nE] edge lengths
   int32_t* row_ptr;      // [nF + 1]
   int32_t* col;          // [nnz]
+  int32_t* bpairs;       // [nD + nN][2] copies of the listed Dirichlet then Neumann pairs
+  int32_t* bedge;        // [nD + nN] edge id of each listed pair
 };
 
 struct phfem_sys_s {

@@ -149,7 +149,7 @@ __global__ void k_edges(int nV, const int32_t* __restrict__ tri, const int32_t* 
 __global__ void k_bclass(int nB, const int32_t* __restrict__ pairs, int code, int nV,
                          const int32_t* __restrict__ bstart, const unsigned long long* __restrict__ buf,
                          const int32_t* __restrict__ pos_edge, const int32_t* __restrict__ ed2el,
-                         int32_t* __restrict__ ecode, DevStatus* err) {
+                         int32_t* __restrict__ ecode, int32_t* __restrict__ bedge, DevStatus* err) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nB; i += gridDim.x * blockDim.x) {
     int a = pairs[2 * i], b = pairs[2 * i + 1];
     if (a < 0 || b < 0 || a >= nV || b >= nV || a == b) {
@@ -168,6 +168,7 @@ __global__ void k_bclass(int nB, const int32_t* __restrict__ pairs, int code, in
       continue;
     }
     int e = pos_edge[found];
+    bedge[i] = e;
     if (ed2el[4 * e + 3] >= 0) {
       record(err, PHFEM_EMESH, i, kInteriorListed);
       continue;
@@ -317,6 +318,8 @@ void mesh_free(phfem_mesh m) {
   dfree(c, m->elen);
   dfree(c, m->row_ptr);
   dfree(c, m->col);
+  dfree(c, m->bpairs);
+  dfree(c, m->bedge);
   delete m;
 }
 
@@ -378,12 +381,19 @@ int build(phfem_ctx ctx, int nV, const double* xy, int nT, const int32_t* tri, i
   PH_TRY(tmp.get(&isfree, (size_t)nE + 1));
   PH_TRY(tmp.get(&islam, (size_t)nE + 1));
   PH_CUDA(cudaMemsetAsync(ecode, 0, sizeof(int32_t) * nE, s));
+  PH_TRY(dalloc_n(ctx, &m->bpairs, 2 * ((size_t)nD + nN)));
+  PH_TRY(dalloc_n(ctx, &m->bedge, (size_t)nD + nN));
   if (nD > 0) {
-    k_bclass<<<grid_for(ctx, nD), kBlock, 0, s>>>(nD, dir, 1, nV, bstart, buf, pos_edge, m->ed2el, ecode, err);
+    PH_CUDA(cudaMemcpyAsync(m->bpairs, dir, sizeof(int32_t) * 2 * (size_t)nD, cudaMemcpyDeviceToDevice, s));
+    k_bclass<<<grid_for(ctx, nD), kBlock, 0, s>>>(nD, dir, 1, nV, bstart, buf, pos_edge, m->ed2el, ecode, m->bedge,
+                                                  err);
     PH_TRY(check_launch(ctx, "k_bclass"));
   }
   if (nN > 0) {
-    k_bclass<<<grid_for(ctx, nN), kBlock, 0, s>>>(nN, neu, 16, nV, bstart, buf, pos_edge, m->ed2el, ecode, err);
+    PH_CUDA(cudaMemcpyAsync(m->bpairs + 2 * (size_t)nD, neu, sizeof(int32_t) * 2 * (size_t)nN,
+                            cudaMemcpyDeviceToDevice, s));
+    k_bclass<<<grid_for(ctx, nN), kBlock, 0, s>>>(nN, neu, 16, nV, bstart, buf, pos_edge, m->ed2el, ecode,
+                                                  m->bedge + nD, err);
     PH_TRY(check_launch(ctx, "k_bclass"));
   }
   PH_TRY(dalloc_n(ctx, &m->eclass, (size_t)nE));

@@ -111,6 +111,7 @@ def lib() -> C.CDLL:
             "phfem_mesh_info_get": (C.c_int, [_H, C.POINTER(MeshInfo)]),
             "phfem_mesh_tables": (C.c_int, [_H, _P, _P, _P, _P, _P, _P, _P, _P]),
             "phfem_mesh_destroy": (C.c_int, [_H]),
+            "phfem_mesh_refine": (C.c_int, [_H, _P, _P, _P, _P, C.POINTER(_H)]),
             "phfem_assemble": (C.c_int, [_H, C.POINTER(Coeffs), _P, _P, C.POINTER(_H)]),
             "phfem_sys_csr": (C.c_int, [_H, _P, _P]),
             "phfem_sys_destroy": (C.c_int, [_H]),
@@ -211,6 +212,27 @@ def phfem_mesh_build(ctx, xy, tri, dirichlet, neumann):
                                   nN, _ptr(neumann, torch.int32) if nN else None, C.byref(h)),
            "phfem_mesh_build")
     return h
+
+
+def phfem_mesh_refine(mesh, build=True, arrays=False):
+    """Red refinement on the device.  Returns the refined mesh handle (build),
+    and with arrays=True also the refined xy, tri, dirichlet, neumann tensors."""
+    I = phfem_mesh_info_get(mesh)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    out = None
+    if arrays:
+        out = dict(xy=torch.empty((I["nV"] + I["nE"], 2), dtype=torch.float64, device=dev),
+                   tri=torch.empty((4 * I["nT"], 3), dtype=torch.int32, device=dev),
+                   dirichlet=torch.empty((2 * I["nD"], 2), dtype=torch.int32, device=dev),
+                   neumann=torch.empty((2 * I["nN"], 2), dtype=torch.int32, device=dev))
+    h = _H()
+    _check(lib().phfem_mesh_refine(mesh, _ptr(out["xy"]) if out else None, _ptr(out["tri"]) if out else None,
+                                   _ptr(out["dirichlet"]) if out and I["nD"] else None,
+                                   _ptr(out["neumann"]) if out and I["nN"] else None,
+                                   C.byref(h) if build else None), "phfem_mesh_refine")
+    if build and arrays:
+        return h, out
+    return h if build else out
 
 
 def phfem_mesh_info_get(mesh) -> dict:
