@@ -9,7 +9,9 @@ imports nothing from the product.  It shares no code with the CUDA path: the
 two only consume the same seeded inputs.
 
 What it computes, in the paper's order and notation:
-  * uniform red refinement (Section 2.3, redrefine_vec);
+  * uniform red refinement (Section 2.3, redrefine_vec) and the prolongation
+    of Crouzeix-Raviart functions from a mesh to its refinement (the coarse
+    piecewise-linear function evaluated at the fine edge midpoints);
   * topology (Section 2.2, Eqs. n2el/n2ed/ed2el, Listings 1-3): nodes2element,
     nodes2edge (edges numbered by the column-major order of triu(B)),
     edge2element = [initial, end, T+, T-] with T+ the first element (element-major
@@ -205,6 +207,49 @@ def redrefine(xy: np.ndarray, tri: np.ndarray, dirichlet: np.ndarray, neumann: n
         return np.concatenate([np.stack([pairs[:, 0], m], axis=1), np.stack([m, pairs[:, 1]], axis=1)], axis=0)
 
     return new_xy, out, refine_edges(dirichlet), refine_edges(neumann)
+
+
+def cr_prolongation(xy_c, tri_c, xy_f, tri_f) -> sp.csr_matrix:
+    """Prolongation of Crouzeix-Raviart functions (values at edge midpoints)
+    from a mesh to its red refinement (redrefine): the coarse function
+    v = sum_k v_{E_k} (1 - 2 lambda_k) on each coarse triangle, evaluated at
+    every fine edge midpoint, and averaged over the (one or two) coarse
+    triangles whose closure holds that midpoint.  Fine vertex nV_c + E is the
+    midpoint of coarse edge E.  Returns the (nE_f x nE_c) matrix."""
+    xy_c = np.asarray(xy_c, dtype=np.float64)
+    xy_f = np.asarray(xy_f, dtype=np.float64)
+    tri_c = np.asarray(tri_c, dtype=np.int64)
+    nVc = xy_c.shape[0]
+    tc = edge_tables(tri_c, nVc)
+    tf = edge_tables(np.asarray(tri_f, dtype=np.int64), xy_f.shape[0])
+    t2e_c, ed2el_c = tc["t2e"], tc["ed2el"]
+    # coarse triangle holding each pair of its edges
+    owner = {}
+    for t in range(tri_c.shape[0]):
+        for k in range(3):
+            a, b = t2e_c[t, (k + 1) % 3], t2e_c[t, (k + 2) % 3]
+            owner[(min(a, b), max(a, b))] = t
+    rows, cols, vals = [], [], []
+    for f in range(tf["nE"]):
+        a, b = tf["ed2el"][f, 0], tf["ed2el"][f, 1]
+        x = 0.5 * (xy_f[a] + xy_f[b])
+        if a >= nVc and b >= nVc:       # inside one coarse triangle
+            e1, e2 = a - nVc, b - nVc
+            tris = [owner[(min(e1, e2), max(e1, e2))]]
+        else:                           # half of a coarse edge
+            E = max(a, b) - nVc
+            tris = [t for t in ed2el_c[E, 2:4] if t >= 0]
+        for t in tris:
+            P = xy_c[tri_c[t]]
+            # barycentric coordinates of x in t
+            Tm = np.array([[P[1, 0] - P[0, 0], P[2, 0] - P[0, 0]], [P[1, 1] - P[0, 1], P[2, 1] - P[0, 1]]])
+            l12 = np.linalg.solve(Tm, x - P[0])
+            lam = np.array([1.0 - l12[0] - l12[1], l12[0], l12[1]])
+            for k in range(3):
+                rows.append(f)
+                cols.append(t2e_c[t, k])
+                vals.append((1.0 - 2.0 * lam[k]) / len(tris))
+    return sp.coo_matrix((vals, (rows, cols)), shape=(tf["nE"], tc["nE"])).tocsr()
 
 
 # ---------------------------------------------------------------------------

@@ -90,3 +90,59 @@ def test_same_geometry_as_the_generator(levels):
     assert tris(xy, tri) == tris(g.xy, g.tri)
     assert segs(xy, d) == segs(g.xy, g.dirichlet)
     assert segs(xy, n) == segs(g.xy, g.neumann)
+
+
+def _refined(m):
+    xy, tri, d, n = O.redrefine(m.xy, m.tri, m.dirichlet, m.neumann)
+    return xy, tri
+
+
+@pytest.mark.parametrize("mk", ["lshape", "crisscross"])
+def test_prolongation_reproduces_affine_functions(mk):
+    """An affine function sampled at the coarse midpoints is prolongated to the
+    same function at the fine midpoints (a closed form)."""
+    m = {"lshape": lambda: I.lshape_mesh(n=3, seed=I.seed_for(1, 12)), "crisscross": lambda: I.criss_cross(1)}[mk]()
+    xy, tri = _refined(m)
+    P = O.cr_prolongation(m.xy, m.tri, xy, tri)
+    g = lambda X: 0.3 - 1.7 * X[:, 0] + 0.9 * X[:, 1]
+    ec = O.edge_tables(m.tri, m.nV)["ed2el"]
+    ef = O.edge_tables(tri, xy.shape[0])["ed2el"]
+    mc = 0.5 * (m.xy[ec[:, 0]] + m.xy[ec[:, 1]])
+    mf = 0.5 * (xy[ef[:, 0]] + xy[ef[:, 1]])
+    assert np.max(np.abs(P @ g(mc) - g(mf))) < 1e-13
+    # constants: every row sums to one
+    assert np.allclose(np.asarray(P.sum(axis=1)).ravel(), 1.0, rtol=0, atol=1e-14)
+
+
+def test_prolongation_of_a_basis_function_by_hand():
+    """Two triangles of the unit square, split by the diagonal (0,0)-(1,1):
+    the basis function of the diagonal is 1 at its midpoint and 0 at the
+    other midpoints; on each triangle it is 1 - 2 lambda of the opposite
+    vertex.  At the fine midpoints: 1 on the diagonal's halves, 1/2 on the
+    four interior edges that touch its midpoint, 0 on the two interior edges
+    that do not, and +1/2 / -1/2 on the halves of the outer edges near a
+    vertex on / off the diagonal (at the quarter point next to the vertex P
+    off the diagonal, lambda_P = 3/4)."""
+    m = I.square_mesh(1)
+    xy, tri = _refined(m)
+    P = O.cr_prolongation(m.xy, m.tri, xy, tri).toarray()
+    ec = O.edge_tables(m.tri, m.nV)["ed2el"]
+    diag = [e for e in range(ec.shape[0]) if {tuple(m.xy[ec[e, 0]]), tuple(m.xy[ec[e, 1]])} == {(0.0, 0.0), (1.0, 1.0)}]
+    assert len(diag) == 1
+    col = P[:, diag[0]]
+    ef = O.edge_tables(tri, xy.shape[0])["ed2el"]
+    mid = 0.5 * (xy[ef[:, 0]] + xy[ef[:, 1]])
+    for f in range(ef.shape[0]):
+        x, y = mid[f]
+        on_diag = abs(x - y) < 1e-15
+        a, b = xy[ef[f, 0]], xy[ef[f, 1]]
+        outer = any(abs(c) < 1e-15 or abs(c - 1) < 1e-15 for c in (x, y)) and not on_diag
+        if on_diag and (abs(x - 0.25) < 1e-15 or abs(x - 0.75) < 1e-15) and (0.5 in (a[0], b[0])):
+            assert col[f] == 1.0            # halves of the diagonal
+        elif outer:
+            # half of an outer edge near a diagonal vertex (0,0) or (1,1): +1/2, else -1/2
+            near_diag_vertex = max(x, y) < 0.5 or min(x, y) > 0.5
+            assert col[f] == (0.5 if near_diag_vertex else -0.5), (x, y, col[f])
+        else:
+            touches = any(np.allclose(v, (0.5, 0.5)) for v in (a, b))
+            assert col[f] == (0.5 if touches else 0.0), (x, y, col[f])
