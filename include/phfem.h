@@ -79,8 +79,9 @@ PHFEM_API const char* phfem_last_error(void);
 /* Number of kernels the library launched on this context so far. */
 PHFEM_API int64_t phfem_ctx_launches(phfem_ctx ctx);
 /* Instrumentation (not part of the method): when enabled, launches of the
- * kernels "cg_spmv", "cg_update", "cg_dir", "residual", "asm_tri", "asm_rows"
- * and "recover" are bracketed by CUDA events on the context
+ * kernels "cg_spmv", "cg_update", "cg_dir", "residual", "asm_tri", "asm_rows",
+ * "recover" and of whole multigrid V-cycles ("mg_vcycle") are bracketed by
+ * CUDA events on the context
  * stream.  phfem_ctx_kernel_time synchronises on the last event and returns
  * the summed device time (ms) and the number of timed launches of one kernel;
  * reset != 0 starts a new accumulation. */
@@ -206,10 +207,12 @@ typedef struct {
   double rtol;          /* stop when ||b - S w||_2 <= rtol ||b||_2 (FP64 S, free rows); 0 -> 1e-10 */
   double inner_rtol;    /* reliable-update factor: the true FP64 residual replaces the
                            recursive one whenever the latter fell by this factor;
-                           0 -> 0.1 (FP32_IR) or 0.01 (FP64)                       */
+                           0 -> 0.1 (FP32_IR) or 0.01 (FP64); with a multigrid
+                           preconditioner 0 -> 1e-3 (FP32_IR) or 1e-4 (FP64)       */
   int32_t max_iter;     /* total inner iterations; 0 -> 200000                        */
-  int32_t max_refine;   /* outer refinement steps; 0 -> 40                            */
-  int32_t check_every;  /* inner iterations between host convergence checks; 0 -> 64  */
+  int32_t max_refine;   /* reliable updates (FP64 residual evaluations); 0 -> 1000    */
+  int32_t check_every;  /* inner iterations between host convergence checks; 0 -> 64
+                           (2 with a multigrid preconditioner)                     */
   int32_t reserved;
 } phfem_solve_opts;
 
@@ -245,6 +248,58 @@ typedef struct {
  * still written), PHFEM_EBREAKDOWN or PHFEM_ENAN on numerical failure. */
 PHFEM_API int phfem_solve(phfem_sys sys, const phfem_solve_opts* opts, const double* w0,
                           double* w, double* U, double* Lambda, phfem_stats* stats);
+
+/* ------------------------------------------------------------------------ */
+/* Multigrid preconditioner over a red-refinement hierarchy (Section 2.3)     */
+/* ------------------------------------------------------------------------ */
+
+/* The paper solves with a direct solver; this preconditioner replaces the
+ * Jacobi one in phfem_solve (and phfem_cn_step / phfem_cn_step_graph) when
+ * the mesh comes from uniform red refinements.  Level l + 1 must be the
+ * phfem_mesh_refine of level l; the finest level is the system's mesh.
+ * Transfer between levels is that of Crouzeix-Raviart functions (the coarse
+ * piecewise-linear function evaluated at the fine edge midpoints, averaged
+ * over the two coarse triangles on coarse edges) and its transpose; coarse
+ * operators are assembled like the fine one with a_T averaged over the four
+ * children.  Smoothing: a Chebyshev polynomial of degree nu in D^-1 A on
+ * [b / smooth_ratio, b], b the Gershgorin bound, before and after the coarse
+ * correction (a symmetric V-cycle); the coarsest level: a Chebyshev
+ * polynomial on the interval of its extreme Ritz values (Lanczos), of the
+ * degree that reduces the error by coarse_eps.  The preconditioner is a fixed
+ * linear SPD operator, so the conjugate-gradient iteration is unchanged. */
+typedef struct phfem_mg_s* phfem_mg;
+typedef struct {
+  int32_t nu;            /* smoothing degree before and after; 0 -> 2 (1..16)        */
+  double smooth_ratio;   /* smoothing interval [b / ratio, b]; 0 -> 6                */
+  double coarse_eps;     /* coarsest-level error reduction; 0 -> 0.3                 */
+  int32_t coarse_degree; /* > 0: fixed coarsest degree instead (<= 2000)            */
+  int32_t reserved;
+} phfem_mg_opts;
+typedef struct {
+  int32_t levels, nu, coarse_degree, reserved;
+  double coarse_a, coarse_b, smooth_ratio;
+} phfem_mg_info_t;
+
+/* Builds the hierarchy for `sys` (assembled on meshes[nlevels-1]):
+ *   meshes [nlevels]  coarsest first; each the phfem_mesh_refine of the one
+ *                     before (checked; PHFEM_EINVAL otherwise); the caller keeps
+ *                     them alive while the multigrid exists
+ *   a_T [nT_finest]   the fine coefficient given to phfem_assemble (device), or
+ *                     NULL for the scalar a of the system's coefficients
+ * Trace form only.  Blocks the host (it reads level bounds back). */
+PHFEM_API int phfem_mg_create(phfem_sys sys, int32_t nlevels, const phfem_mesh* meshes,
+                              const double* a_T, const phfem_mg_opts* opts, phfem_mg* out);
+PHFEM_API int phfem_mg_info(phfem_mg mg, phfem_mg_info_t* out);
+/* Attaches the multigrid to its system (NULL: back to Jacobi). */
+PHFEM_API int phfem_sys_set_mg(phfem_sys sys, phfem_mg mg);
+/* The transfer operators in FP64 (device buffers), for level l and l + 1:
+ *   direction 0: out [nE_{l+1}] = P in [nE_l]   (zero on Dirichlet edges of l + 1;
+ *                in must vanish on the Dirichlet edges of l, as corrections do)
+ *   direction 1: out [nE_l] = P' in [nE_{l+1}]  (zero on Dirichlet edges of l) */
+PHFEM_API int phfem_mg_transfer(phfem_mg mg, int32_t level, int32_t direction, const double* in,
+                                double* out);
+/* Detaches the multigrid from its system and frees it (before the system). */
+PHFEM_API int phfem_mg_destroy(phfem_mg mg);
 
 /* ------------------------------------------------------------------------ */
 /* Crank-Nicolson (Section 4, Eq. MatrixformParabolic)                       */

@@ -198,7 +198,7 @@ int build_step_graph(phfem_cn cn, const phfem_solve_opts& o) {
   cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamBeginCapture", __FILE__, __LINE__);
   if (st == PHFEM_OK) st = enqueue_pre(cn);
-  if (st == PHFEM_OK) st = capture_solve(cn->sys, &o, cs, 8);
+  if (st == PHFEM_OK) st = capture_solve(cn->sys, &o, cs, cn->sys->mg ? 2 : 8);
   if (st == PHFEM_OK) st = enqueue_post(cn);
   cudaGraph_t graph = nullptr;
   e = cudaStreamEndCapture(cs, &graph);

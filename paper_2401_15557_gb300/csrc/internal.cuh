@@ -50,6 +50,7 @@ struct SolveState {
   double bb;       // ||b||^2 of the free-edge system (with lifting)
   double floor2;   // squared estimate of the residual that rounding x to FP64 alone leaves
   double rp;       // r.p right after a reliable update (p kept)
+  double rr_pending, ff_pending;  // ||r||^2 and floor of a true residual awaiting the preconditioner
   int use_rp;      // 1: the next step is a line search alpha = r.p / p.Ap
   int restart;     // 1: the next SpMV restarts the direction, p = D^-1 r
   int conv;        // 1: rtol met, 2: stopped at the FP64 floor
@@ -68,7 +69,7 @@ struct SolveState {
 namespace phfem {
 // Kernels whose launches can be timed with CUDA events (phfem_ctx_profile).
 enum ProfKernel { kProfSpmv = 0, kProfUpdate, kProfDir, kProfResidual, kProfAsmTri, kProfAsmRows,
-                  kProfRecover, kNumProf };
+                  kProfRecover, kProfMg, kNumProf };
 struct ProfSlot {
   std::vector<cudaEvent_t> ev;  // start/stop pairs
   size_t used = 0;
@@ -134,6 +135,7 @@ struct phfem_sys_s {
   double* partials;      // [4][kMaxGrid]
   phfem::SolveState* st;       // device
   phfem::SolveState* st_host;  // pinned host mirror
+  phfem_mg mg;                 // multigrid preconditioner (not owned), or NULL: Jacobi
 };
 
 namespace phfem {
@@ -165,6 +167,10 @@ int sys_init_x(phfem_sys sys, const double* w0);
 void fill_opts(phfem_sys sys, phfem_solve_opts& o);
 int recover(phfem_sys sys, const double* x_new, const double* x_old, const double* f_eff,
             double inv_dt, double theta, double* U, double* Lambda);
+// z = V-cycle(r) on the multigrid's finest level (into mg_fine_z(mg)); with
+// st != NULL every kernel runs only while st->done == want.
+int mg_apply(phfem_mg mg, cudaStream_t s, const void* r, const SolveState* st, int want);
+void* mg_fine_z(phfem_mg mg);
 
 // Device helpers ---------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {

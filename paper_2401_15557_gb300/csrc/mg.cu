@@ -1,0 +1,644 @@
+// Geometric multigrid preconditioner for the condensed edge system over a
+// hierarchy of uniform red refinements (Section 2.3).
+//
+// Level l + 1 is the red refinement of level l, so every fine edge is either
+// half of a coarse edge or one of the three edges of the middle child of a
+// coarse triangle.  Unknowns are values at edge midpoints (the trace form), so
+// the transfer between levels is that of Crouzeix-Raviart functions:
+//   prolongation  the coarse function v = sum_k v_k (1 - 2 lambda_k) on each
+//                 coarse triangle, evaluated at the fine midpoints: (v_a + v_b)/2
+//                 on the middle child's edge joining the midpoints of coarse
+//                 edges a and b; on the half of coarse edge E_k next to vertex
+//                 P_i (other end P_j) v_k - v_i/2 + v_j/2 (v_i on the edge
+//                 opposite P_i), averaged over the two coarse triangles of E_k;
+//   restriction   its transpose.
+// Identity rows (Dirichlet edges) carry zero corrections on every level.
+// Coarse operators are rediscretisations (the same assembly, a_T averaged
+// over the four children).  Smoothing is a Chebyshev polynomial in D^-1 A on
+// [b/ratio, b] with b the Gershgorin bound of D^-1 A, the same polynomial
+// before and after the coarse correction, so the V-cycle is a symmetric
+// positive definite preconditioner; the coarsest level is solved
+// approximately by a fixed Chebyshev polynomial on an interval estimated by
+// Lanczos, which keeps the whole preconditioner linear.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "kernels.cuh"
+
+struct phfem_mg_s {
+  struct Level {
+    phfem_mesh mesh = nullptr;
+    phfem_sys sys = nullptr;
+    bool owned = false;
+    int nE = 0, nT = 0;
+    void* rhs = nullptr;  // restricted right-hand side (coarse levels)
+    void* z = nullptr;
+    void* zb = nullptr;
+    void* d = nullptr;
+    void* res = nullptr;
+    int32_t* ct = nullptr;  // [nT][9] fine edges of each triangle (levels below the finest)
+    double b = 0.0;         // Gershgorin bound of D^-1 A
+  };
+  phfem_sys fine = nullptr;
+  bool fp32 = false;
+  std::vector<Level> L;
+  int nu = 2;
+  double ratio = 6.0;
+  double coarse_a = 0.0, coarse_b = 0.0;
+  int coarse_deg = 0;
+};
+
+namespace phfem {
+namespace {
+
+__device__ __forceinline__ bool skip(const SolveState* st, int want) { return st && st->done != want; }
+
+// Chebyshev step in D^-1 A (difference form):
+//   mode 0: d = cr D^-1 rhs, zout = d                       (from zero)
+//   mode 1: d = cr D^-1 (rhs - A zin), zout = zin + d        (from zin)
+//   mode 2: d = cd d + cr D^-1 (rhs - A zin), zout = zin + d
+template <typename T>
+__global__ void k_mg_cheb(int nE, const int32_t* __restrict__ nbr, const T* __restrict__ lval,
+                          const T* __restrict__ rdiag, const T* __restrict__ dinv, const T* __restrict__ rhs,
+                          const T* __restrict__ zin, T* __restrict__ zout, T* __restrict__ d, T cd, T cr, int mode,
+                          const SolveState* st, int want) {
+  if (skip(st, want)) return;
+  const size_t m = (size_t)nE;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    if (mode == 0) {
+      const T de = cr * (dinv[e] * rhs[e]);
+      d[e] = de;
+      zout[e] = de;
+    } else {
+      const T res = rhs[e] - spmv_row(nbr, lval, rdiag, zin, m, e);
+      const T de = (mode == 1 ? (T)0 : cd * d[e]) + cr * (dinv[e] * res);
+      d[e] = de;
+      zout[e] = zin[e] + de;
+    }
+  }
+}
+
+template <typename T>
+__global__ void k_mg_residual(int nE, const int32_t* __restrict__ nbr, const T* __restrict__ lval,
+                              const T* __restrict__ rdiag, const T* __restrict__ rhs, const T* __restrict__ z,
+                              T* __restrict__ res, const SolveState* st, int want) {
+  if (skip(st, want)) return;
+  const size_t m = (size_t)nE;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x)
+    res[e] = rhs[e] - spmv_row(nbr, lval, rdiag, z, m, e);
+}
+
+// zf += P zc.  Threads [0, nTc) own the middle-child edges of a coarse
+// triangle, threads [nTc, nTc + nEc) the two halves of a coarse edge.
+template <typename T>
+__global__ void k_mg_prolong(int nTc, int nEc, const int32_t* __restrict__ t2e, const int32_t* __restrict__ ed2el,
+                             const uint8_t* __restrict__ lk, const int32_t* __restrict__ ct,
+                             const uint8_t* __restrict__ eclass_f, uint8_t ident, const T* __restrict__ zc,
+                             T* __restrict__ zf, const SolveState* st, int want) {
+  if (skip(st, want)) return;
+  const int n = nTc + nEc;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (i < nTc) {
+      const int t = i;
+      const T v0 = zc[t2e[3 * t]], v1 = zc[t2e[3 * t + 1]], v2 = zc[t2e[3 * t + 2]];
+      const int32_t* c = ct + 9 * (size_t)t;
+      zf[c[0]] += (T)0.5 * (v1 + v2);  // joins the midpoints of edges 1 and 2
+      zf[c[1]] += (T)0.5 * (v2 + v0);
+      zf[c[2]] += (T)0.5 * (v0 + v1);
+    } else {
+      const int E = i - nTc;
+      const int tp = ed2el[4 * E + 2], tm = ed2el[4 * E + 3];
+      const int kp = lk[E] & 3, km = (lk[E] >> 2) & 3;
+      const T v = zc[E];
+      const T p1 = zc[t2e[3 * tp + (kp + 1) % 3]], p2 = zc[t2e[3 * tp + (kp + 2) % 3]];
+      // halves next to P_{kp+1} (A) and P_{kp+2} (B) of T+
+      T vA = v - (T)0.5 * p1 + (T)0.5 * p2;
+      T vB = v - (T)0.5 * p2 + (T)0.5 * p1;
+      if (tm >= 0) {  // in T- the edge runs the other way: its P_{km+1} is P_{kp+2} of T+
+        const T m1 = zc[t2e[3 * tm + (km + 1) % 3]], m2 = zc[t2e[3 * tm + (km + 2) % 3]];
+        vB = (T)0.5 * (vB + (v - (T)0.5 * m1 + (T)0.5 * m2));
+        vA = (T)0.5 * (vA + (v - (T)0.5 * m2 + (T)0.5 * m1));
+      }
+      const int hA = ct[9 * (size_t)tp + 3 + 2 * kp], hB = ct[9 * (size_t)tp + 4 + 2 * kp];
+      if (eclass_f[hA] != ident) zf[hA] += vA;
+      if (eclass_f[hB] != ident) zf[hB] += vB;
+    }
+  }
+}
+
+// rc = P' rf, one coarse edge per thread (zero on identity rows).
+template <typename T>
+__global__ void k_mg_restrict(int nEc, const int32_t* __restrict__ t2e, const int32_t* __restrict__ ed2el,
+                              const uint8_t* __restrict__ lk, const uint8_t* __restrict__ eclass_c, uint8_t ident,
+                              const int32_t* __restrict__ ct, const T* __restrict__ rf, T* __restrict__ rc,
+                              const SolveState* st, int want) {
+  if (skip(st, want)) return;
+  for (int E = blockIdx.x * blockDim.x + threadIdx.x; E < nEc; E += gridDim.x * blockDim.x) {
+    if (eclass_c[E] == ident) {
+      rc[E] = (T)0;
+      continue;
+    }
+    const int tp = ed2el[4 * E + 2], tm = ed2el[4 * E + 3];
+    const int kp = lk[E] & 3, km = (lk[E] >> 2) & 3;
+    // its own halves (weight 1)
+    T acc = rf[ct[9 * (size_t)tp + 3 + 2 * kp]] + rf[ct[9 * (size_t)tp + 4 + 2 * kp]];
+    for (int side = 0; side < 2; ++side) {
+      const int t = side == 0 ? tp : tm;
+      if (t < 0) break;
+      const int mloc = side == 0 ? kp : km;
+      const int32_t* c = ct + 9 * (size_t)t;
+      const int k1 = (mloc + 1) % 3, k2 = (mloc + 2) % 3;
+      // middle-child edges touching the midpoint of E (weight 1/2 each)
+      acc += (T)0.5 * (rf[c[k1]] + rf[c[k2]]);
+      // halves of the other two edges, averaged over their triangles
+      const T w1 = ed2el[4 * t2e[3 * t + k1] + 3] >= 0 ? (T)0.25 : (T)0.5;
+      const T w2 = ed2el[4 * t2e[3 * t + k2] + 3] >= 0 ? (T)0.25 : (T)0.5;
+      acc += w1 * (rf[c[3 + 2 * k1]] - rf[c[4 + 2 * k1]]);  // E is edge k1 + 2 of t
+      acc += w2 * (rf[c[4 + 2 * k2]] - rf[c[3 + 2 * k2]]);  // E is edge k2 + 1 of t
+    }
+    rc[E] = acc;
+  }
+}
+
+// Fine edges of every coarse triangle from the refined mesh's t2e: the middle
+// child t holds (opposite its vertex M_k) the edge joining the other two
+// midpoints; corner child nT + 3t + j = [P_j, M_{j+2}, M_{j+1}] holds the half
+// of edge j + 2 next to P_j as its edge 2 and the half of edge j + 1 next to
+// P_j as its edge 1.  ct[t] = {g0, g1, g2, h00, h01, h10, h11, h20, h21} with
+// hk0 / hk1 the half of edge k next to P_{k+1} / P_{k+2}.  Also checks that the
+// fine mesh is the red refinement of the coarse one.
+__global__ void k_mg_ct(int nTc, int nVc, const int32_t* __restrict__ tri_c, const int32_t* __restrict__ t2e_c,
+                        const int32_t* __restrict__ tri_f, const int32_t* __restrict__ t2e_f, int32_t* __restrict__ ct,
+                        int* __restrict__ bad) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nTc; t += gridDim.x * blockDim.x) {
+    bool ok = true;
+    for (int k = 0; k < 3; ++k) {
+      ok = ok && tri_f[3 * t + k] == nVc + t2e_c[3 * t + k];
+      ok = ok && tri_f[3 * ((size_t)nTc + 3 * t + k)] == tri_c[3 * t + k];
+    }
+    if (!ok) atomicOr(bad, 1);
+    int32_t* c = ct + 9 * (size_t)t;
+    for (int k = 0; k < 3; ++k) {
+      c[k] = t2e_f[3 * t + k];
+      c[3 + 2 * k] = t2e_f[3 * ((size_t)nTc + 3 * t + (k + 1) % 3) + 2];
+      c[4 + 2 * k] = t2e_f[3 * ((size_t)nTc + 3 * t + (k + 2) % 3) + 1];
+    }
+  }
+}
+
+__global__ void k_mg_coarsen_a(int nTc, const double* __restrict__ af, double* __restrict__ ac) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nTc; t += gridDim.x * blockDim.x) {
+    const size_t c = (size_t)nTc + 3 * (size_t)t;
+    ac[t] = 0.25 * (af[t] + af[c] + af[c + 1] + af[c + 2]);
+  }
+}
+
+// max over rows of (A_ee + sum |A_es|) / A_ee from the FP64 difference-form rows.
+__global__ void k_mg_gershgorin(int nE, const int32_t* __restrict__ nbr, const double* __restrict__ val,
+                                unsigned int* __restrict__ out) {
+  const size_t m = (size_t)nE;
+  float best = 0.0f;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    double diag = val[e], off = 0.0;
+    for (int s = 0; s < 4; ++s) {
+      const double l = val[(s + 1) * m + e];
+      if (nbr[s * m + e] != e) {
+        diag += l;
+        off += fabs(l);
+      }
+    }
+    best = fmaxf(best, (float)((diag + off) / diag) * 1.0001f);
+  }
+  // positive floats order like their bit patterns
+  atomicMax(out, __float_as_uint(best));
+}
+
+// Largest and smallest eigenvalue of a symmetric tridiagonal matrix by
+// bisection on Sturm sequence counts.
+double tridiag_eig(const std::vector<double>& a, const std::vector<double>& b, int which_smallest) {
+  const int n = (int)a.size();
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < n; ++i) {
+    const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < n ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  auto count_below = [&](double x) {  // eigenvalues < x
+    int c = 0;
+    double q = a[0] - x;
+    if (q < 0) ++c;
+    for (int i = 1; i < n; ++i) {
+      const double qq = q == 0.0 ? 1e-300 : q;
+      q = a[i] - x - b[i - 1] * b[i - 1] / qq;
+      if (q < 0) ++c;
+    }
+    return c;
+  };
+  const int target = which_smallest ? 1 : n;  // the target-th eigenvalue
+  for (int it = 0; it < 200; ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (count_below(mid) >= target) hi = mid;
+    else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// Lanczos on D^-1/2 A D^-1/2 restricted to the rows that are not identity rows
+// (FP64, on the host): extreme Ritz values after k steps.
+void lanczos_bounds(int nE, const std::vector<int32_t>& nbr, const std::vector<double>& val,
+                    const std::vector<uint8_t>& eclass, uint8_t ident, int k, double& lmin, double& lmax) {
+  const size_t m = (size_t)nE;
+  std::vector<double> diag(nE), sq(nE);
+  for (int e = 0; e < nE; ++e) {
+    double d = val[e];
+    for (int s = 0; s < 4; ++s)
+      if (nbr[s * m + e] != e) d += val[(s + 1) * m + e];
+    diag[e] = d;
+    sq[e] = eclass[e] == ident ? 0.0 : 1.0 / std::sqrt(d);
+  }
+  auto apply = [&](const std::vector<double>& v, std::vector<double>& w) {
+    for (int e = 0; e < nE; ++e) {
+      if (sq[e] == 0.0) {
+        w[e] = 0.0;
+        continue;
+      }
+      const double ve = v[e] * sq[e];
+      double s = val[e] * ve;
+      for (int j = 0; j < 4; ++j) {
+        const int c = nbr[j * m + e];
+        if (c != e) s += val[(j + 1) * m + e] * (ve - v[c] * sq[c]);
+      }
+      w[e] = s * sq[e];
+    }
+  };
+  std::vector<double> v(nE), vp(nE, 0.0), w(nE);
+  uint64_t state = 0x9E3779B97F4A7C15ull;  // deterministic start vector (xorshift)
+  double nrm = 0.0;
+  for (int e = 0; e < nE; ++e) {
+    state ^= state << 13;
+    state ^= state >> 7;
+    state ^= state << 17;
+    v[e] = sq[e] == 0.0 ? 0.0 : (double)(state >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+    nrm += v[e] * v[e];
+  }
+  nrm = std::sqrt(nrm);
+  for (double& x : v) x /= nrm;
+  std::vector<double> al, be;
+  double beta = 0.0;
+  for (int j = 0; j < k; ++j) {
+    apply(v, w);
+    double a = 0.0;
+    for (int e = 0; e < nE; ++e) {
+      w[e] -= beta * vp[e];
+      a += w[e] * v[e];
+    }
+    double bn = 0.0;
+    for (int e = 0; e < nE; ++e) {
+      w[e] -= a * v[e];
+      bn += w[e] * w[e];
+    }
+    bn = std::sqrt(bn);
+    al.push_back(a);
+    if (bn < 1e-300 || j + 1 == k) break;
+    be.push_back(bn);
+    for (int e = 0; e < nE; ++e) {
+      vp[e] = v[e];
+      v[e] = w[e] / bn;
+    }
+    beta = bn;
+  }
+  be.resize(al.size() > 0 ? al.size() - 1 : 0);
+  lmin = tridiag_eig(al, be, 1);
+  lmax = tridiag_eig(al, be, 0);
+}
+
+// Chebyshev coefficients (cd_k, cr_k) of degree `deg` on [a, b].
+void cheb_coeffs(double a, double b, int deg, std::vector<double>& cd, std::vector<double>& cr) {
+  const double th = 0.5 * (b + a), de = 0.5 * (b - a), sig = th / de;
+  cd.assign(deg, 0.0);
+  cr.assign(deg, 0.0);
+  double rho = 1.0 / sig;
+  cr[0] = 1.0 / th;
+  for (int k = 1; k < deg; ++k) {
+    const double rn = 1.0 / (2.0 * sig - rho);
+    cd[k] = rn * rho;
+    cr[k] = 2.0 * rn / de;
+    rho = rn;
+  }
+}
+
+template <typename T>
+struct MgRun {
+  phfem_mg mg;
+  cudaStream_t s;
+  const SolveState* st;
+  int want;
+
+  phfem_ctx ctx(int l) const { return mg->L[l].mesh->ctx; }
+
+  int smooth(int l, const T* rhs, T* zin_out_first, T* zalt, bool from_zero, int deg, const double* cd,
+             const double* cr, T** result) {
+    // alternates between the two buffers; returns the buffer with the result
+    phfem_mg_s::Level& Lv = mg->L[l];
+    phfem_sys sy = Lv.sys;
+    const int g = grid_for(ctx(l), Lv.nE);
+    T* cur = zin_out_first;
+    T* other = zalt;
+    for (int k = 0; k < deg; ++k) {
+      const int mode = k == 0 ? (from_zero ? 0 : 1) : 2;
+      T* out = (k == 0 && from_zero) ? cur : other;
+      k_mg_cheb<T><<<g, kBlock, 0, s>>>(Lv.nE, Lv.mesh->nbr, (const T*)sy->lval, (const T*)sy->rdiag,
+                                        (const T*)sy->dinv, rhs, cur, out, (T*)Lv.d, (T)cd[k], (T)cr[k], mode, st,
+                                        want);
+      PH_TRY(check_launch(ctx(l), "k_mg_cheb"));
+      if (out != cur) std::swap(cur, other);
+    }
+    *result = cur;
+    return PHFEM_OK;
+  }
+
+  // z_l = V(rhs_l); the result is written to `z_out`.
+  int vcycle(int l, const T* rhs, T* z_out) {
+    phfem_mg_s::Level& Lv = mg->L[l];
+    T* zb = (T*)Lv.zb;
+    T* res = nullptr;
+    if (l == 0) {
+      std::vector<double> cd, cr;
+      cheb_coeffs(mg->coarse_a, mg->coarse_b, mg->coarse_deg, cd, cr);
+      // writes alternate starting at the first buffer: start so that the last lands in z_out
+      T* first = (mg->coarse_deg % 2 == 1) ? z_out : zb;
+      T* second = first == z_out ? zb : z_out;
+      T* outp = nullptr;
+      PH_TRY(smooth(0, rhs, first, second, true, mg->coarse_deg, cd.data(), cr.data(), &outp));
+      if (outp != z_out) return fail(PHFEM_ECUDA, "multigrid: coarse buffer parity");
+      return PHFEM_OK;
+    }
+    std::vector<double> cd, cr;
+    cheb_coeffs(Lv.b / mg->ratio, Lv.b, mg->nu, cd, cr);
+    // pre-smoothing: nu writes starting in zb; the post-smoothing's nu writes
+    // then end in z_out (2 nu writes alternate zb, z_out, ...)
+    T* cur = nullptr;
+    PH_TRY(smooth(l, rhs, zb, z_out, true, mg->nu, cd.data(), cr.data(), &cur));
+    res = (T*)Lv.res;
+    const int g = grid_for(ctx(l), Lv.nE);
+    phfem_sys sy = Lv.sys;
+    k_mg_residual<T><<<g, kBlock, 0, s>>>(Lv.nE, Lv.mesh->nbr, (const T*)sy->lval, (const T*)sy->rdiag, rhs, cur,
+                                          res, st, want);
+    PH_TRY(check_launch(ctx(l), "k_mg_residual"));
+    phfem_mg_s::Level& C = mg->L[l - 1];
+    k_mg_restrict<T><<<grid_for(ctx(l), C.nE), kBlock, 0, s>>>(C.nE, C.mesh->t2e, C.mesh->ed2el, C.mesh->lk,
+                                                                C.mesh->eclass, C.sys->ident_class, C.ct, res,
+                                                                (T*)C.rhs, st, want);
+    PH_TRY(check_launch(ctx(l), "k_mg_restrict"));
+    PH_TRY(vcycle(l - 1, (const T*)C.rhs, (T*)C.z));
+    k_mg_prolong<T><<<grid_for(ctx(l), (int64_t)C.nT + C.nE), kBlock, 0, s>>>(
+        C.nT, C.nE, C.mesh->t2e, C.mesh->ed2el, C.mesh->lk, C.ct, Lv.mesh->eclass, Lv.sys->ident_class,
+        (const T*)C.z, cur, st, want);
+    PH_TRY(check_launch(ctx(l), "k_mg_prolong"));
+    T* alt = cur == zb ? z_out : zb;
+    T* outp = nullptr;
+    PH_TRY(smooth(l, rhs, cur, alt, false, mg->nu, cd.data(), cr.data(), &outp));
+    if (outp != z_out) return fail(PHFEM_ECUDA, "multigrid: buffer parity");
+    return PHFEM_OK;
+  }
+};
+
+void mg_free(phfem_mg mg) {
+  for (size_t l = 0; l < mg->L.size(); ++l) {
+    phfem_mg_s::Level& Lv = mg->L[l];
+    if (!Lv.mesh) continue;
+    phfem_ctx c = Lv.mesh->ctx;
+    dfree(c, Lv.rhs);
+    dfree(c, Lv.z);
+    dfree(c, Lv.zb);
+    dfree(c, Lv.d);
+    dfree(c, Lv.res);
+    dfree(c, Lv.ct);
+    if (Lv.owned && Lv.sys) phfem_sys_destroy(Lv.sys);
+  }
+  if (mg->fine && mg->fine->mg == mg) mg->fine->mg = nullptr;
+  delete mg;
+}
+
+}  // namespace
+
+int mg_apply(phfem_mg mg, cudaStream_t s, const void* r, const SolveState* st, int want) {
+  const int top = (int)mg->L.size() - 1;
+  if (mg->fp32) {
+    MgRun<float> R{mg, s, st, want};
+    return R.vcycle(top, (const float*)r, (float*)mg->L[top].z);
+  }
+  MgRun<double> R{mg, s, st, want};
+  return R.vcycle(top, (const double*)r, (double*)mg->L[top].z);
+}
+
+void* mg_fine_z(phfem_mg mg) { return mg->L.back().z; }
+
+}  // namespace phfem
+
+using namespace phfem;
+
+extern "C" {
+
+PHFEM_API int phfem_mg_create(phfem_sys sys, int32_t nlevels, const phfem_mesh* meshes, const double* a_T,
+                              const phfem_mg_opts* opts, phfem_mg* out) {
+  if (!out) return fail(PHFEM_EINVAL, "phfem_mg_create: out is NULL");
+  *out = nullptr;
+  if (!sys || !meshes || nlevels < 2) return fail(PHFEM_EINVAL, "phfem_mg_create: a system and >= 2 levels");
+  if (meshes[nlevels - 1] != sys->mesh)
+    return fail(PHFEM_EINVAL, "phfem_mg_create: the finest mesh must be the system's mesh");
+  if (sys->form != PHFEM_FORM_TRACE) return fail(PHFEM_EINVAL, "phfem_mg_create: the trace form only");
+  phfem_mg_opts o{};
+  if (opts) o = *opts;
+  if (o.nu <= 0) o.nu = 2;
+  if (!(o.smooth_ratio > 1.0)) o.smooth_ratio = 6.0;
+  if (!(o.coarse_eps > 0.0 && o.coarse_eps < 1.0)) o.coarse_eps = 0.3;
+  if (o.nu > 16 || o.coarse_degree < 0 || o.coarse_degree > 2000)
+    return fail(PHFEM_EINVAL, "phfem_mg_create: nu in 1..16, coarse_degree in 0..2000");
+  phfem_ctx ctx = sys->mesh->ctx;
+  cudaStream_t s = ctx->stream;
+  for (int l = 0; l < nlevels; ++l)
+    if (!meshes[l] || meshes[l]->ctx != ctx) return fail(PHFEM_EINVAL, "phfem_mg_create: NULL mesh or another context");
+  phfem_mg mg = new phfem_mg_s();
+  mg->fine = sys;
+  mg->fp32 = sys->fp32;
+  mg->nu = o.nu;
+  mg->ratio = o.smooth_ratio;
+  mg->L.resize(nlevels);
+  const size_t es = sys->fp32 ? sizeof(float) : sizeof(double);
+  int st = PHFEM_OK;
+  // coefficients of every level: the fine a_T averaged over children
+  std::vector<double*> aT(nlevels, nullptr);
+  int* bad = nullptr;
+  unsigned int* gb = nullptr;
+  st = dalloc_n(ctx, &bad, 1);
+  if (st == PHFEM_OK) st = dalloc_n(ctx, &gb, 1);
+  if (st == PHFEM_OK) {
+    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), s);
+    if (e != cudaSuccess) st = cuda_fail(e, "cudaMemsetAsync", __FILE__, __LINE__);
+  }
+  for (int l = 0; l < nlevels && st == PHFEM_OK; ++l) {
+    phfem_mg_s::Level& Lv = mg->L[l];
+    Lv.mesh = meshes[l];
+    Lv.nE = meshes[l]->info.nE;
+    Lv.nT = meshes[l]->info.nT;
+    if (l + 1 < nlevels) {
+      const phfem_mesh_info& F = meshes[l + 1]->info;
+      if (F.nT != 4 * (int64_t)Lv.nT || F.nV != meshes[l]->info.nV + Lv.nE) {
+        st = fail(PHFEM_EINVAL, "phfem_mg_create: level " + std::to_string(l + 1) +
+                                    " is not the red refinement of level " + std::to_string(l));
+        break;
+      }
+      st = dalloc_n(ctx, &Lv.ct, 9 * (size_t)Lv.nT);
+      if (st != PHFEM_OK) break;
+      k_mg_ct<<<grid_for(ctx, Lv.nT), kBlock, 0, s>>>(Lv.nT, meshes[l]->info.nV, meshes[l]->tri, meshes[l]->t2e,
+                                                      meshes[l + 1]->tri, meshes[l + 1]->t2e, Lv.ct, bad);
+      st = check_launch(ctx, "k_mg_ct");
+    }
+    if (st == PHFEM_OK) st = dalloc(ctx, &Lv.rhs, es * Lv.nE + 16);
+    if (st == PHFEM_OK) st = dalloc(ctx, &Lv.z, es * Lv.nE + 16);
+    if (st == PHFEM_OK) st = dalloc(ctx, &Lv.zb, es * Lv.nE + 16);
+    if (st == PHFEM_OK) st = dalloc(ctx, &Lv.d, es * Lv.nE + 16);
+    if (st == PHFEM_OK && l > 0) st = dalloc(ctx, &Lv.res, es * Lv.nE + 16);
+  }
+  if (st == PHFEM_OK) {
+    int h = 0;
+    cudaError_t e = cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) st = cuda_fail(e, "phfem_mg_create", __FILE__, __LINE__);
+    else if (h) st = fail(PHFEM_EINVAL, "phfem_mg_create: a level is not the red refinement of the one below");
+  }
+  // coefficients, then the coarse systems (rediscretisation)
+  if (st == PHFEM_OK && a_T) {
+    aT[nlevels - 1] = const_cast<double*>(a_T);
+    for (int l = nlevels - 2; l >= 0 && st == PHFEM_OK; --l) {
+      st = dalloc_n(ctx, &aT[l], (size_t)mg->L[l].nT);
+      if (st != PHFEM_OK) break;
+      k_mg_coarsen_a<<<grid_for(ctx, mg->L[l].nT), kBlock, 0, s>>>(mg->L[l].nT, aT[l + 1], aT[l]);
+      st = check_launch(ctx, "k_mg_coarsen_a");
+    }
+  }
+  for (int l = 0; l < nlevels && st == PHFEM_OK; ++l) {
+    phfem_mg_s::Level& Lv = mg->L[l];
+    if (l == nlevels - 1) {
+      Lv.sys = sys;
+      Lv.owned = false;
+    } else {
+      phfem_coeffs c = sys->c;
+      c.a_T = a_T ? aT[l] : nullptr;
+      c.form = PHFEM_FORM_TRACE;
+      st = phfem_assemble(meshes[l], &c, nullptr, nullptr, &Lv.sys);
+      Lv.owned = true;
+    }
+  }
+  for (int l = nlevels - 2; l >= 0; --l)
+    if (aT[l]) dfree(ctx, aT[l]);
+  // Gershgorin bounds of every level
+  for (int l = 0; l < nlevels && st == PHFEM_OK; ++l) {
+    phfem_mg_s::Level& Lv = mg->L[l];
+    unsigned int hb = 0;
+    cudaError_t e = cudaMemsetAsync(gb, 0, sizeof(unsigned int), s);
+    if (e == cudaSuccess) {
+      k_mg_gershgorin<<<grid_for(ctx, Lv.nE), kBlock, 0, s>>>(Lv.nE, Lv.mesh->nbr, Lv.sys->val, gb);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, gb, sizeof(hb), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "phfem_mg_create: Gershgorin bound", __FILE__, __LINE__);
+      break;
+    }
+    float fb;
+    std::memcpy(&fb, &hb, sizeof(fb));
+    Lv.b = fb > 1.0f ? (double)fb : 1.0;
+  }
+  // interval and degree of the coarsest polynomial: Lanczos on the host
+  if (st == PHFEM_OK) {
+    phfem_mg_s::Level& C = mg->L[0];
+    const int n = C.nE;
+    std::vector<int32_t> nbr(4 * (size_t)n);
+    std::vector<double> val(5 * (size_t)n);
+    std::vector<uint8_t> ec(n);
+    cudaError_t e = cudaMemcpyAsync(nbr.data(), C.mesh->nbr, sizeof(int32_t) * nbr.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(val.data(), C.sys->val, sizeof(double) * val.size(), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ec.data(), C.mesh->eclass, n, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      st = cuda_fail(e, "phfem_mg_create: coarse level read", __FILE__, __LINE__);
+    } else {
+      const int steps = n <= 200000 ? std::min(n, 300) : 60;
+      double lmin = 0.0, lmax = 0.0;
+      lanczos_bounds(n, nbr, val, ec, C.sys->ident_class, steps, lmin, lmax);
+      // Ritz values lie inside the spectrum: widen both ends
+      mg->coarse_b = std::min(1.02 * lmax, C.b);
+      mg->coarse_a = (n <= 200000 ? 0.9 : 0.25) * lmin;
+      if (!(mg->coarse_a > 0.0) || !(mg->coarse_a < mg->coarse_b)) mg->coarse_a = mg->coarse_b * 1e-4;
+      if (o.coarse_degree > 0) {
+        mg->coarse_deg = o.coarse_degree;
+      } else {
+        const double kap = mg->coarse_b / mg->coarse_a;
+        const double rho = (std::sqrt(kap) - 1.0) / (std::sqrt(kap) + 1.0);
+        int deg = (int)std::ceil(std::log(2.0 / o.coarse_eps) / std::log(1.0 / rho));
+        mg->coarse_deg = std::max(1, std::min(deg, 2000));
+      }
+    }
+  }
+  dfree(ctx, bad);
+  dfree(ctx, gb);
+  if (st != PHFEM_OK) {
+    mg_free(mg);
+    return st;
+  }
+  *out = mg;
+  return PHFEM_OK;
+}
+
+PHFEM_API int phfem_mg_info(phfem_mg mg, phfem_mg_info_t* out) {
+  if (!mg || !out) return fail(PHFEM_EINVAL, "phfem_mg_info: NULL argument");
+  out->levels = (int32_t)mg->L.size();
+  out->nu = mg->nu;
+  out->coarse_degree = mg->coarse_deg;
+  out->coarse_a = mg->coarse_a;
+  out->coarse_b = mg->coarse_b;
+  out->smooth_ratio = mg->ratio;
+  return PHFEM_OK;
+}
+
+PHFEM_API int phfem_sys_set_mg(phfem_sys sys, phfem_mg mg) {
+  if (!sys) return fail(PHFEM_EINVAL, "phfem_sys_set_mg: NULL system");
+  if (mg && mg->fine != sys) return fail(PHFEM_EINVAL, "phfem_sys_set_mg: the multigrid belongs to another system");
+  sys->mg = mg;
+  return PHFEM_OK;
+}
+
+PHFEM_API int phfem_mg_transfer(phfem_mg mg, int32_t level, int32_t direction, const double* in, double* out) {
+  if (!mg || !in || !out) return fail(PHFEM_EINVAL, "phfem_mg_transfer: NULL argument");
+  if (level < 0 || level + 1 >= (int)mg->L.size() || (direction != 0 && direction != 1))
+    return fail(PHFEM_EINVAL, "phfem_mg_transfer: level in 0..levels-2, direction 0 or 1");
+  phfem_mg_s::Level& C = mg->L[level];
+  phfem_mg_s::Level& F = mg->L[level + 1];
+  phfem_ctx ctx = C.mesh->ctx;
+  cudaStream_t s = ctx->stream;
+  if (direction == 0) {
+    PH_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * F.nE, s));
+    k_mg_prolong<double><<<grid_for(ctx, (int64_t)C.nT + C.nE), kBlock, 0, s>>>(
+        C.nT, C.nE, C.mesh->t2e, C.mesh->ed2el, C.mesh->lk, C.ct, F.mesh->eclass, F.sys->ident_class, in, out,
+        nullptr, 0);
+    return check_launch(ctx, "k_mg_prolong");
+  }
+  k_mg_restrict<double><<<grid_for(ctx, C.nE), kBlock, 0, s>>>(C.nE, C.mesh->t2e, C.mesh->ed2el, C.mesh->lk,
+                                                                C.mesh->eclass, C.sys->ident_class, C.ct, in, out,
+                                                                nullptr, 0);
+  return check_launch(ctx, "k_mg_restrict");
+}
+
+PHFEM_API int phfem_mg_destroy(phfem_mg mg) {
+  if (!mg) return fail(PHFEM_EINVAL, "phfem_mg_destroy: NULL multigrid");
+  mg_free(mg);
+  return PHFEM_OK;
+}
+
+}  // extern "C"

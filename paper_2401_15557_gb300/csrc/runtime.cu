@@ -45,7 +45,7 @@ int grid_for(phfem_ctx ctx, int64_t n) {
 }
 
 static const char* kProfNames[kNumProf] = {"cg_spmv", "cg_update", "cg_dir", "residual",
-                                           "asm_tri", "asm_rows", "recover"};
+                                           "asm_tri", "asm_rows", "recover", "mg_vcycle"};
 
 void prof_start(phfem_ctx ctx, int k) {
   if (!ctx->profile) return;

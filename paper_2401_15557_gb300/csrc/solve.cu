@@ -48,12 +48,56 @@ namespace {
 //   3  as 2, but only if the iteration asked for an update (done == 1).
 // The last block decides on the device: converged (rtol, or twice the FP64
 // floor), the line-search step, or a restart of the direction.
+// Decision after a true residual (last block, thread 0): the iteration's
+// state, convergence (rtol, or twice the FP64 floor), and for a reliable
+// update the line-search step or a restart of the direction.
+__device__ void decide(SolveState* st, double rr, double rz, double ff, double rp, int mode, double rtol2,
+                       double inner_rtol2) {
+  const double rz_recursive = st->rz;
+  st->rr64 = rr;
+  st->floor2 = ff;
+  st->rz = rz;
+  st->rp = rp;
+  st->tol2 = inner_rtol2 * rz;
+  st->status = 0;
+  if (mode == 1) {
+    st->rz0 = rz;
+    st->it = 0;
+    st->updates = 1;
+    st->bodies = 0;
+    st->use_rp = 0;
+    st->restart = 0;
+  } else {
+    st->updates += 1;
+    // line search along the kept direction, or restart it when it no longer
+    // fits the replaced residual
+    const int restart = (rz > 4.0 * rz_recursive) || !(rp > 0.0);
+    st->restart = restart;
+    st->use_rp = !restart;
+  }
+  st->conv = 0;
+  if (!isfinite(rr) || !isfinite(rz)) {
+    st->done = 3;
+    st->status = PHFEM_ENAN;
+  } else if (rr <= rtol2 * st->bb || rr == 0.0) {
+    st->done = 2;
+    st->conv = 1;
+  } else if (rr <= 4.0 * ff) {  // relative residual within twice the FP64 floor
+    st->done = 2;
+    st->conv = 2;
+  } else {
+    st->done = 0;
+  }
+}
+
+// With precond != 0 (multigrid) the kernel only forms r and the sums ||r||^2
+// and the floor; the preconditioner and k_mg_finish complete the step.
 template <typename T>
 __global__ void k_residual(int nE, const int32_t* __restrict__ nbr, const double* __restrict__ val,
                            const double* __restrict__ b, const double* __restrict__ x,
                            const uint8_t* __restrict__ eclass, uint8_t ident, const T* __restrict__ dinv,
                            T* __restrict__ ri, T* __restrict__ pi, double* partials,
-                           SolveState* st, double rtol2, double inner_rtol2, int mode) {
+                           SolveState* st, double rtol2, double inner_rtol2, int mode, int precond) {
   if (mode == 3) {
     if (st->done != 1) return;  // every block reads done before the last block rewrites it
     mode = 2;
@@ -82,11 +126,13 @@ __global__ void k_residual(int nE, const int32_t* __restrict__ nbr, const double
       fl *= 0x1p-53;
       acc_f += fl * fl;
       const T rs = (T)r;
-      const T zs = dinv[e] * rs;
       ri[e] = rs;
-      if (mode == 1) pi[e] = zs;
-      else acc_p += (double)rs * (double)pi[e];
-      acc_z += (double)rs * (double)zs;
+      if (!precond) {
+        const T zs = dinv[e] * rs;
+        if (mode == 1) pi[e] = zs;
+        else acc_p += (double)rs * (double)pi[e];
+        acc_z += (double)rs * (double)zs;
+      }
     }
   }
   acc_r = block_sum(acc_r, smem);
@@ -110,53 +156,59 @@ __global__ void k_residual(int nE, const int32_t* __restrict__ nbr, const double
       st->bb = rr;
       return;
     }
-    const double rz_recursive = st->rz;
-    st->rr64 = rr;
-    st->floor2 = ff;
-    st->rz = rz;
-    st->rp = rp;
-    st->tol2 = inner_rtol2 * rz;
-    st->status = 0;
-    if (mode == 1) {
-      st->rz0 = rz;
-      st->it = 0;
-      st->updates = 1;
-      st->bodies = 0;
-      st->use_rp = 0;
-      st->restart = 0;
-    } else {
-      st->updates += 1;
-      // line search along the kept direction, or restart it when it no longer
-      // fits the replaced residual
-      const int restart = (rz > 4.0 * rz_recursive) || !(rp > 0.0);
-      st->restart = restart;
-      st->use_rp = !restart;
+    if (precond) {  // completed by k_mg_finish
+      st->rr_pending = rr;
+      st->ff_pending = ff;
+      return;
     }
-    st->conv = 0;
-    if (!isfinite(rr) || !isfinite(rz)) {
-      st->done = 3;
-      st->status = PHFEM_ENAN;
-    } else if (rr <= rtol2 * st->bb || rr == 0.0) {
-      st->done = 2;
-      st->conv = 1;
-    } else if (rr <= 4.0 * ff) {  // relative residual within twice the FP64 floor
-      st->done = 2;
-      st->conv = 2;
-    } else {
-      st->done = 0;
-    }
+    decide(st, rr, rz, ff, rp, mode, rtol2, inner_rtol2);
+  }
+}
+
+// Completes a true residual under the multigrid preconditioner: z = M^-1 r is
+// in zi; rz = r.z, and p = z at the start (mode 1) or r.p for the line search
+// (mode 2; mode 3 = mode 2 when the iteration asked for it).
+template <typename T>
+__global__ void k_mg_finish(int nE, const T* __restrict__ ri, const T* __restrict__ zi, T* __restrict__ pi,
+                            double* partials, SolveState* st, double rtol2, double inner_rtol2, int mode) {
+  if (mode == 3) {
+    if (st->done != 1) return;
+    mode = 2;
+  }
+  __shared__ double smem[kBlock / 32];
+  T acc_z = (T)0, acc_p = (T)0;  // this thread's few rows in T; across threads and blocks in FP64
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    const T r = ri[e], z = zi[e];
+    acc_z += r * z;
+    if (mode == 1) pi[e] = z;
+    else acc_p += r * pi[e];
+  }
+  const double sz = block_sum((double)acc_z, smem);
+  const double sp = block_sum((double)acc_p, smem);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = sz;
+    partials[kMaxGrid + blockIdx.x] = sp;
+  }
+  if (!arrive_last(&st->counter[3])) return;
+  const double rz = sum_partials(partials, smem);
+  const double rp = sum_partials(partials + kMaxGrid, smem);
+  if (threadIdx.x == 0) {
+    st->counter[3] = 0;
+    decide(st, st->rr_pending, rz, st->ff_pending, rp, mode, rtol2, inner_rtol2);
   }
 }
 
 // q = S p in difference form, p.q -> alpha = rz / p.q (or r.p / p.q right
 // after a reliable update).  In restart mode the direction is first set to
-// p = D^-1 r (each block writes its own rows and computes neighbours' values
-// from r and D^-1, so no block reads p being written).
+// p = D^-1 r, or to the stored z = M^-1 r (zsrc) under multigrid (each block
+// writes its own rows and takes neighbours' values from r and D^-1 or from z,
+// so no block reads p being written).
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cg_spmv(int nE, const int32_t* __restrict__ nbr,
                                                     const T* __restrict__ lval, const T* __restrict__ rdiag,
                                                     T* __restrict__ p, T* __restrict__ q, const T* __restrict__ r,
-                                                    const T* __restrict__ dinv, double* partials, SolveState* st) {
+                                                    const T* __restrict__ dinv, const T* __restrict__ zsrc,
+                                                    double* partials, SolveState* st) {
   if (blockIdx.x == 0 && threadIdx.x == 0) st->dir_pending = 0;  // no block of this kernel reads it
   if (st->done) return;
   __shared__ double smem[kBlock / 32];
@@ -164,12 +216,12 @@ __global__ void __launch_bounds__(kBlock) k_cg_spmv(int nE, const int32_t* __res
   T acc = (T)0;  // this thread's few rows in T; across threads and blocks in FP64
   if (st->restart) {
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
-      const T pe = dinv[e] * r[e];
+      const T pe = zsrc ? zsrc[e] : dinv[e] * r[e];
       T s = rdiag[e] * pe;
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int c = nbr[k * m + e];
-        s += lval[k * m + e] * (pe - dinv[c] * r[c]);
+        s += lval[k * m + e] * (pe - (zsrc ? zsrc[c] : dinv[c] * r[c]));
       }
       p[e] = pe;
       q[e] = s;
@@ -231,6 +283,55 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(int nE, double* __restrict
       st->status = PHFEM_ENAN;
     }
   }
+}
+
+// Multigrid iteration: x += alpha p, r -= alpha q (the preconditioner then
+// forms z), r.z -> beta, p = z + beta p.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cg_update_x(int nE, double* __restrict__ x, const T* __restrict__ p,
+                                                        T* __restrict__ r, const T* __restrict__ q,
+                                                        const SolveState* st) {
+  if (st->done) return;
+  const double alpha64 = st->alpha;
+  const T alpha = (T)alpha64;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    x[e] += alpha64 * (double)p[e];
+    r[e] = r[e] - alpha * q[e];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cg_rz(int nE, const T* __restrict__ r, const T* __restrict__ z,
+                                                  double* partials, SolveState* st) {
+  if (st->done) return;
+  __shared__ double smem[kBlock / 32];
+  T acc = (T)0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) acc += r[e] * z[e];
+  const double accd = block_sum((double)acc, smem);
+  if (threadIdx.x == 0) partials[kMaxGrid + blockIdx.x] = accd;
+  if (!arrive_last(&st->counter[2])) return;
+  const double rz = sum_partials(partials + kMaxGrid, smem);
+  if (threadIdx.x == 0) {
+    st->counter[2] = 0;
+    st->beta = st->rz > 0.0 ? rz / st->rz : 0.0;
+    st->rz = rz;
+    st->it += 1;
+    st->dir_pending = 1;
+    if (!isfinite(rz)) {
+      st->done = 3;
+      st->status = PHFEM_ENAN;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_cg_dir_z(int nE, const T* __restrict__ z, T* __restrict__ p,
+                                                     SolveState* st) {
+  if (!st->dir_pending) return;
+  const T beta = (T)st->beta;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x)
+    p[e] = z[e] + beta * p[e];
+  if (blockIdx.x == 0 && threadIdx.x == 0 && st->done == 0 && st->rz <= st->tol2) st->done = 1;
 }
 
 // p = D^-1 r + beta p; then the test of the recursive residual, so that the
@@ -358,12 +459,21 @@ struct Launch {
   double rtol2, irtol2;
   int residual(int mode) const {
     phfem_ctx ctx = sys->mesh->ctx;
+    const int pre = (sys->mg && mode != 0) ? 1 : 0;
     prof_start(ctx, kProfResidual);
     k_residual<T><<<g, kBlock, 0, s>>>(nE, sys->mesh->nbr, sys->val, sys->b, sys->x, sys->mesh->eclass,
                                        sys->ident_class, (const T*)sys->dinv, (T*)sys->ri, (T*)sys->pi,
-                                       sys->partials, sys->st, rtol2, irtol2, mode);
+                                       sys->partials, sys->st, rtol2, irtol2, mode, pre);
     prof_stop(ctx, kProfResidual);
-    return check_launch(ctx, "k_residual");
+    PH_TRY(check_launch(ctx, "k_residual"));
+    if (!pre) return PHFEM_OK;
+    // z = M^-1 r, then r.z (and p = z or r.p) and the decision
+    prof_start(ctx, kProfMg);
+    PH_TRY(mg_apply(sys->mg, s, sys->ri, mode == 3 ? sys->st : nullptr, 1));
+    prof_stop(ctx, kProfMg);
+    k_mg_finish<T><<<g, kBlock, 0, s>>>(nE, (const T*)sys->ri, (const T*)mg_fine_z(sys->mg), (T*)sys->pi,
+                                        sys->partials, sys->st, rtol2, irtol2, mode);
+    return check_launch(ctx, "k_mg_finish");
   }
   int iteration() const {
     phfem_ctx ctx = sys->mesh->ctx;
@@ -373,9 +483,26 @@ struct Launch {
     T* ri = (T*)sys->ri;
     T* pi = (T*)sys->pi;
     T* qi = (T*)sys->qi;
+    const T* zmg = sys->mg ? (const T*)mg_fine_z(sys->mg) : nullptr;
     prof_start(ctx, kProfSpmv);
-    k_cg_spmv<T><<<g, kBlock, 0, s>>>(nE, sys->mesh->nbr, lval, rdiag, pi, qi, ri, dinv, sys->partials, sys->st);
+    k_cg_spmv<T><<<g, kBlock, 0, s>>>(nE, sys->mesh->nbr, lval, rdiag, pi, qi, ri, dinv, zmg, sys->partials,
+                                      sys->st);
     prof_stop(ctx, kProfSpmv);
+    if (sys->mg) {
+      prof_start(ctx, kProfUpdate);
+      k_cg_update_x<T><<<g, kBlock, 0, s>>>(nE, sys->x, pi, ri, qi, sys->st);
+      prof_stop(ctx, kProfUpdate);
+      PH_TRY(check_launch(ctx, "k_cg_update_x"));
+      prof_start(ctx, kProfMg);
+      PH_TRY(mg_apply(sys->mg, s, ri, sys->st, 0));
+      prof_stop(ctx, kProfMg);
+      prof_start(ctx, kProfDir);
+      k_cg_rz<T><<<g, kBlock, 0, s>>>(nE, ri, zmg, sys->partials, sys->st);
+      k_cg_dir_z<T><<<g, kBlock, 0, s>>>(nE, zmg, pi, sys->st);
+      prof_stop(ctx, kProfDir);
+      ctx->launches += 2;  // spmv and rz (update_x and dir_z counted by check_launch)
+      return check_launch(ctx, "k_cg");
+    }
     prof_start(ctx, kProfUpdate);
     k_cg_update<T><<<g, kBlock, 0, s>>>(nE, sys->x, pi, ri, qi, dinv, sys->partials, sys->st);
     prof_stop(ctx, kProfUpdate);
@@ -501,10 +628,10 @@ int capture_typed(phfem_sys sys, const phfem_solve_opts& o, cudaStream_t cs, int
 
 void fill_opts(phfem_sys sys, phfem_solve_opts& o) {
   if (o.rtol <= 0) o.rtol = 1e-10;
-  if (o.inner_rtol <= 0) o.inner_rtol = sys->fp32 ? 0.1 : 0.01;
+  if (o.inner_rtol <= 0) o.inner_rtol = sys->mg ? (sys->fp32 ? 1e-3 : 1e-4) : (sys->fp32 ? 0.1 : 0.01);
   if (o.max_iter <= 0) o.max_iter = 200000;
   if (o.max_refine <= 0) o.max_refine = 1000;
-  if (o.check_every <= 0) o.check_every = 64;
+  if (o.check_every <= 0) o.check_every = sys->mg ? 2 : 64;
 }
 
 int capture_solve(phfem_sys sys, const phfem_solve_opts* opts, cudaStream_t capture, int iters_per_body) {

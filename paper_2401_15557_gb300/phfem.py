@@ -76,6 +76,19 @@ class Result(C.Structure):
         return {n: getattr(self, n) for n, _ in self._fields_}
 
 
+class MgOpts(C.Structure):
+    _fields_ = [("nu", C.c_int32), ("smooth_ratio", C.c_double), ("coarse_eps", C.c_double),
+                ("coarse_degree", C.c_int32), ("reserved", C.c_int32)]
+
+
+class MgInfo(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("nu", C.c_int32), ("coarse_degree", C.c_int32), ("reserved", C.c_int32),
+                ("coarse_a", C.c_double), ("coarse_b", C.c_double), ("smooth_ratio", C.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_ if n != "reserved"}
+
+
 class Errors(C.Structure):
     _fields_ = [("L2", C.c_double), ("H1semi", C.c_double), ("H1", C.c_double), ("M", C.c_double)]
 
@@ -133,6 +146,11 @@ def lib() -> C.CDLL:
             "phfem_server_poll": (C.c_int, [_H, C.c_int64, C.c_int32, C.POINTER(Result)]),
             "phfem_server_drain": (C.c_int, [_H]),
             "phfem_server_destroy": (C.c_int, [_H]),
+            "phfem_mg_create": (C.c_int, [_H, C.c_int32, C.POINTER(_H), _P, C.POINTER(MgOpts), C.POINTER(_H)]),
+            "phfem_mg_info": (C.c_int, [_H, C.POINTER(MgInfo)]),
+            "phfem_sys_set_mg": (C.c_int, [_H, _H]),
+            "phfem_mg_transfer": (C.c_int, [_H, C.c_int32, C.c_int32, _P, _P]),
+            "phfem_mg_destroy": (C.c_int, [_H]),
             "phfem_error_points": (C.c_int, [_H, C.c_int32, _P, _P, _P]),
             "phfem_error_norms": (C.c_int, [_H, C.c_int32, _P, _P, _P, _P, _P, C.POINTER(Errors)]),
             "phfem_csr_pcg_noalloc": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, C.c_double, C.c_int32,
@@ -435,6 +453,39 @@ def phfem_server_drain(server):
 
 def phfem_server_destroy(server):
     _check(lib().phfem_server_destroy(server), "phfem_server_destroy")
+
+
+# --- multigrid preconditioner --------------------------------------------------------
+
+def phfem_mg_create(sys, meshes, a_T=None, nu=0, smooth_ratio=0.0, coarse_eps=0.0, coarse_degree=0):
+    """Multigrid over meshes (coarsest first, each the refinement of the one
+    before, the last the system's mesh)."""
+    arr = (_H * len(meshes))(*[m.value if isinstance(m, _H) else m for m in meshes])
+    I = phfem_mesh_info_get(meshes[-1])
+    o = MgOpts(int(nu), float(smooth_ratio), float(coarse_eps), int(coarse_degree), 0)
+    h = _H()
+    _check(lib().phfem_mg_create(sys, len(meshes), arr, _ptr(a_T, torch.float64, I["nT"]), C.byref(o), C.byref(h)),
+           "phfem_mg_create")
+    return h
+
+
+def phfem_mg_info(mg) -> dict:
+    out = MgInfo()
+    _check(lib().phfem_mg_info(mg, C.byref(out)), "phfem_mg_info")
+    return out.as_dict()
+
+
+def phfem_sys_set_mg(sys, mg):
+    _check(lib().phfem_sys_set_mg(sys, mg), "phfem_sys_set_mg")
+
+
+def phfem_mg_transfer(mg, level, direction, inp, out):
+    _check(lib().phfem_mg_transfer(mg, int(level), int(direction), _ptr(inp, torch.float64),
+                                   _ptr(out, torch.float64)), "phfem_mg_transfer")
+
+
+def phfem_mg_destroy(mg):
+    _check(lib().phfem_mg_destroy(mg), "phfem_mg_destroy")
 
 
 # --- error report -----------------------------------------------------------------
