@@ -40,8 +40,8 @@ SPMV_BYTES_PER_ROW = 4 * 4 + 4 * 4 + 4 + 4 + 4   # nbr, l (FP32), r, p, q
 # DRAM traffic of one cg_spmv launch at the full workload, from the ncu capture
 # summarised in profiles/cg_kernels_full_lshape_l5.md; valid only for the kernel
 # source whose hash is recorded with it.
-SPMV_TRAFFIC = 465.76e6
-SPMV_TRAFFIC_SRC_SHA = "15947392d944502d"
+SPMV_TRAFFIC = 465.73e6
+SPMV_TRAFFIC_SRC_SHA = "310db104b9112955"
 
 
 def _sha_solve_src():
@@ -60,6 +60,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--refine-steps", type=int, default=3, help="timed device refinements of the mesh (0: skip)")
     ap.add_argument("--mg-steps", type=int, default=3, help="timed steps of the multigrid variant (0: skip)")
+    ap.add_argument("--mg-fp64", type=int, default=1, help="also time the FP64 multigrid variant")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="lshape", choices=["lshape", "batched", "heat", "serve"],
                     help="lshape: the L-shaped 6.3M-triangle solve (default); batched: 4096 meshes in one "
@@ -598,6 +599,7 @@ def main():
         X0, T0 = d(m0.xy, torch.float64), d(m0.tri, torch.int32)
         D0, N0 = d(m0.dirichlet, torch.int32), d(m0.neumann, torch.int32)
         U_mg = torch.empty_like(U)
+        opts_mg = P.solve_opts(rtol=1e-10)
         Lam_mg = torch.empty_like(Lam)
 
         def mg_step(prec, phases=None):
@@ -611,7 +613,7 @@ def main():
             mg = P.phfem_mg_create(s_, hs, a_T=a)
             P.phfem_sys_set_mg(s_, mg)
             e2.record(stream)
-            st_ = P.phfem_solve(s_, opts, U=U_mg, Lambda=Lam_mg)
+            st_ = P.phfem_solve(s_, opts_mg, U=U_mg, Lambda=Lam_mg)
             e3.record(stream)
             info_mg = P.phfem_mg_info(mg)
             P.phfem_mg_destroy(mg)
@@ -633,7 +635,8 @@ def main():
             P.phfem_mesh_destroy(h)
         del arr
         mg_out = {}
-        for prec, name in ((P.PHFEM_FP32_IR, "fp32_refined"), (P.PHFEM_FP64, "fp64")):
+        precs = ((P.PHFEM_FP32_IR, "fp32_refined"), (P.PHFEM_FP64, "fp64"))[:2 if args.mg_fp64 else 1]
+        for prec, name in precs:
             for _ in range(args.warmup):
                 mg_step(prec)
             torch.cuda.synchronize()
