@@ -61,11 +61,15 @@ def parse():
     ap.add_argument("--refine-steps", type=int, default=3, help="timed device refinements of the mesh (0: skip)")
     ap.add_argument("--mg-steps", type=int, default=3, help="timed steps of the multigrid variant (0: skip)")
     ap.add_argument("--mg-fp64", type=int, default=1, help="also time the FP64 multigrid variant")
+    ap.add_argument("--mg-nu", type=int, default=0, help="multigrid smoothing degree (0: library default)")
+    ap.add_argument("--mg-ratio", type=float, default=0.0, help="multigrid smoothing interval ratio (0: default)")
+    ap.add_argument("--mg-eps", type=float, default=0.0, help="multigrid coarsest reduction (0: default)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--workload", default="lshape", choices=["lshape", "batched", "heat", "serve"],
                     help="lshape: the L-shaped 6.3M-triangle solve (default); batched: 4096 meshes in one "
                          "launch; heat: Crank-Nicolson on 512 x 512 squares, 512 steps")
     ap.add_argument("--heat-n", type=int, default=512)
+    ap.add_argument("--heat-mg", type=int, default=1, help="heat: also run under the multigrid preconditioner")
     ap.add_argument("--requests", type=int, default=120, help="serve: measured requests")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (requests/s)")
     ap.add_argument("--slots", type=int, default=8, help="serve: worker slots")
@@ -340,12 +344,59 @@ def run_heat(args):
         ue = np.exp(-1.0) * sfun(P_[..., 0], P_[..., 1]).ravel()
         out[f"{name}_graph"]["max_vertex_error_t1"] = float(np.max(np.abs(U.cpu().numpy() - ue)))
         P.phfem_sys_destroy(sysh)
+    # ---- the same run under the multigrid preconditioner: the n x n square is
+    # the k-fold device refinement of an (n / 2^k)-square mesh
+    k = 0
+    while n % (2 ** (k + 1)) == 0:
+        k += 1
+    mg_info = None
+    if args.heat_mg and k >= 1:
+        m0 = I.square_mesh(n >> k)
+        hs = [P.phfem_mesh_build(ctx, d(m0.xy, torch.float64), d(m0.tri, torch.int32),
+                                 d(m0.dirichlet, torch.int32), d(m0.neumann, torch.int32))]
+        for _ in range(k - 1):
+            hs.append(P.phfem_mesh_refine(hs[-1]))
+        hf, arr = P.phfem_mesh_refine(hs[-1], build=True, arrays=True)
+        hs.append(hf)
+        xyf, trif = arr["xy"].cpu().numpy(), arr["tri"].cpu().numpy()
+        Tf = {kk: v.cpu().numpy() for kk, v in P.phfem_mesh_tables(hf).items()}
+        f1, g1 = I.edge_data(xyf, Tf["ed2el"], Tf["eclass"], lambda x, y: (2 * pi * pi - 1.0) * sfun(x, y),
+                             lambda x, y, nx, ny: pi * (np.cos(pi * x) * np.sin(pi * y) * nx
+                                                        + np.sin(pi * x) * np.cos(pi * y) * ny),
+                             lambda x, y: 0 * x)
+        w1, _ = I.edge_data(xyf, Tf["ed2el"], Tf["eclass"], sfun)
+        F1, G1, W1 = d(f1[None], torch.float64), d(g1[None], torch.float64), d(w1, torch.float64)
+        for prec, name in ((P.PHFEM_FP32_IR, "fp32_refined"), (P.PHFEM_FP64, "fp64")):
+            sysh = P.phfem_assemble(hf, None, None, delta=0.0, dt=dt, precision=prec)
+            mg = P.phfem_mg_create(sysh, hs)
+            mg_info = P.phfem_mg_info(mg)
+            P.phfem_sys_set_mg(sysh, mg)
+            cn = P.phfem_cn_create(sysh, F1, G1, phi, W1)
+            P.phfem_cn_step_graph(cn, 2, P.solve_opts(rtol=1e-10))
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            st = P.phfem_cn_step_graph(cn, nsteps - 2, P.solve_opts(rtol=1e-10))
+            torch.cuda.synchronize()
+            el = time.perf_counter() - t0
+            P.phfem_cn_read(cn, U=U)
+            P.phfem_cn_destroy(cn)
+            P_ = xyf[trif]
+            ue = np.exp(-1.0) * sfun(P_[..., 0], P_[..., 1]).ravel()
+            out[f"mg_{name}_graph"] = {"steps_per_s": (nsteps - 2) / el, "ms_per_step": 1e3 * el / (nsteps - 2),
+                                       "iterations_per_step": st["iterations"] / max(1, nsteps - 2),
+                                       "converged": st["converged"], "rel_residual_max": st["rel_residual"],
+                                       "max_vertex_error_t1": float(np.max(np.abs(U.cpu().numpy() - ue))),
+                                       "levels": k + 1}
+            P.phfem_mg_destroy(mg)
+            P.phfem_sys_destroy(sysh)
+        for h in reversed(hs):
+            P.phfem_mesh_destroy(h)
     g = out["fp32_refined_graph"]
     line = {"metric": METRIC, "value": g["steps_per_s"] * mesh.nT, "unit": UNIT + " (per CN step)", "n_gpus": 1,
             "steps": nsteps - 2, "warmup": 2, "ms_per_step": g["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"heat-cn-{n}x{n}", "triangles": mesh.nT, "edges": info["nE"], "dt": dt,
-                       "steps": nsteps}, "cn": out}
+                       "steps": nsteps}, "cn": out, "multigrid": mg_info}
     print(json.dumps(line), flush=True)
     P.phfem_mesh_destroy(mh)
     P.phfem_ctx_destroy(ctx)
@@ -610,7 +661,7 @@ def main():
                 hs.append(P.phfem_mesh_refine(hs[-1]))
             e1.record(stream)
             s_ = P.phfem_assemble(hs[-1], f_mid, bc_mid, a_T=a, delta=1.0, precision=prec)
-            mg = P.phfem_mg_create(s_, hs, a_T=a)
+            mg = P.phfem_mg_create(s_, hs, a_T=a, nu=args.mg_nu, smooth_ratio=args.mg_ratio, coarse_eps=args.mg_eps)
             P.phfem_sys_set_mg(s_, mg)
             e2.record(stream)
             st_ = P.phfem_solve(s_, opts_mg, U=U_mg, Lambda=Lam_mg)

@@ -237,7 +237,6 @@ void sys_free(phfem_sys s) {
   dfree(c, s->qi);
   dfree(c, s->partials);
   dfree(c, s->st);
-  if (s->st_host) cudaFreeHost(s->st_host);
   delete s;
 }
 
@@ -300,7 +299,16 @@ PHFEM_API int phfem_assemble(phfem_mesh mesh, const phfem_coeffs* coeffs, const 
   if (!out) return fail(PHFEM_EINVAL, "phfem_assemble: out is NULL");
   *out = nullptr;
   if (!mesh || !coeffs) return fail(PHFEM_EINVAL, "phfem_assemble: NULL argument");
-  const phfem_coeffs& c = *coeffs;
+  return assemble_system(mesh, *coeffs, f_mid, bc_mid, out, true);
+}
+
+}  // extern "C"
+
+namespace phfem {
+
+int assemble_system(phfem_mesh mesh, const phfem_coeffs& c, const double* f_mid, const double* bc_mid,
+                    phfem_sys* out, bool check) {
+  *out = nullptr;
   if (!(c.delta >= 0.0) || !(c.dt >= 0.0)) return fail(PHFEM_EINVAL, "phfem_assemble: delta and dt must be >= 0");
   if (!c.a_T && !(c.a > 0.0)) return fail(PHFEM_EINVAL, "phfem_assemble: coefficient a must be > 0");
   if (c.precision != PHFEM_FP64 && c.precision != PHFEM_FP32_IR)
@@ -349,11 +357,7 @@ PHFEM_API int phfem_assemble(phfem_mesh mesh, const phfem_coeffs* coeffs, const 
   chk(dalloc_n(ctx, &sys->partials, 4 * (size_t)kMaxGrid));
   chk(dalloc_n(ctx, &sys->st, 1));
   chk(dalloc_n(ctx, &d_bad, 1));
-  if (st == PHFEM_OK && cudaMallocHost((void**)&sys->st_host, sizeof(SolveState)) != cudaSuccess) {
-    cudaGetLastError();
-    sys->st_host = nullptr;
-    st = fail(PHFEM_ENOMEM, "phfem_assemble: pinned host allocation failed");
-  }
+  sys->st_host = ctx->st_pinned;
   if (st == PHFEM_OK) {
     cudaMemsetAsync(sys->st, 0, sizeof(SolveState), s);
     cudaMemsetAsync(d_bad, 0, sizeof(int), s);
@@ -365,7 +369,7 @@ PHFEM_API int phfem_assemble(phfem_mesh mesh, const phfem_coeffs* coeffs, const 
     st = assemble_into(sys, f_mid, bc_mid, d_bad);
     sys->c.a_T = nullptr;
   }
-  if (st == PHFEM_OK) {
+  if (st == PHFEM_OK && check) {
     int bad = 0;
     cudaError_t e = cudaMemcpyAsync(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
@@ -382,6 +386,10 @@ PHFEM_API int phfem_assemble(phfem_mesh mesh, const phfem_coeffs* coeffs, const 
   *out = sys;
   return PHFEM_OK;
 }
+
+}  // namespace phfem
+
+extern "C" {
 
 PHFEM_API int phfem_sys_csr(phfem_sys sys, double* val, double* rhs) {
   if (!sys) return fail(PHFEM_EINVAL, "phfem_sys_csr: NULL system");

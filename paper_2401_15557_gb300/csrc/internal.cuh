@@ -85,6 +85,8 @@ struct phfem_ctx_s {
   int64_t launches;
   bool profile = false;
   phfem::ProfSlot prof[phfem::kNumProf];
+  phfem::SolveState* st_pinned = nullptr;  // pinned host mirror of a solver state, shared by the
+                                           // context's systems (read right after each copy)
 };
 
 struct phfem_mesh_s {
@@ -134,7 +136,7 @@ struct phfem_sys_s {
   void* qi;
   double* partials;      // [4][kMaxGrid]
   phfem::SolveState* st;       // device
-  phfem::SolveState* st_host;  // pinned host mirror
+  phfem::SolveState* st_host;  // pinned host mirror (the context's)
   phfem_mg mg;                 // multigrid preconditioner (not owned), or NULL: Jacobi
 };
 
@@ -165,6 +167,10 @@ int solve_system(phfem_sys sys, const phfem_solve_opts* opts, phfem_stats* stats
 int capture_solve(phfem_sys sys, const phfem_solve_opts* opts, cudaStream_t capture, int iters_per_body);
 int sys_init_x(phfem_sys sys, const double* w0);
 void fill_opts(phfem_sys sys, phfem_solve_opts& o);
+// phfem_assemble without the host synchronisation that checks a_T (for
+// coefficients the library derived itself).
+int assemble_system(phfem_mesh mesh, const phfem_coeffs& c, const double* f_mid, const double* bc_mid,
+                    phfem_sys* out, bool check);
 int recover(phfem_sys sys, const double* x_new, const double* x_old, const double* f_eff,
             double inv_dt, double theta, double* U, double* Lambda);
 // z = V-cycle(r) on the multigrid's finest level (into mg_fine_z(mg)); with

@@ -21,7 +21,10 @@
 // approximately by a fixed Chebyshev polynomial on an interval estimated by
 // Lanczos, which keeps the whole preconditioner linear.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -211,8 +214,16 @@ __global__ void k_mg_gershgorin(int nE, const int32_t* __restrict__ nbr, const d
     }
     best = fmaxf(best, (float)((diag + off) / diag) * 1.0001f);
   }
-  // positive floats order like their bit patterns
-  atomicMax(out, __float_as_uint(best));
+  // block maximum, then one atomic per block (positive floats order like their bit patterns)
+  for (int o = 16; o > 0; o >>= 1) best = fmaxf(best, __shfl_down_sync(0xffffffffu, best, o));
+  __shared__ float wmax[kBlock / 32];
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = best;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float b = 0.0f;
+    for (int w = 0; w < kBlock / 32; ++w) b = fmaxf(b, wmax[w]);
+    atomicMax(out, __float_as_uint(b));
+  }
 }
 
 // Largest and smallest eigenvalue of a symmetric tridiagonal matrix by
@@ -245,34 +256,29 @@ double tridiag_eig(const std::vector<double>& a, const std::vector<double>& b, i
   return 0.5 * (lo + hi);
 }
 
-// Lanczos on D^-1/2 A D^-1/2 restricted to the rows that are not identity rows
-// (FP64, on the host): extreme Ritz values after k steps.
+// Lanczos on B = D^-1/2 A D^-1/2 restricted to the rows that are not identity
+// rows (FP64, on the host): extreme Ritz values.  In difference form
+// B = I - W with W_es = l_es / sqrt(A_ee A_ss) on the neighbour slots.  Runs
+// until the smallest Ritz value changes by less than 3 % over 20 steps, or
+// `kmax` steps.
 void lanczos_bounds(int nE, const std::vector<int32_t>& nbr, const std::vector<double>& val,
-                    const std::vector<uint8_t>& eclass, uint8_t ident, int k, double& lmin, double& lmax) {
+                    const std::vector<uint8_t>& eclass, uint8_t ident, int kmax, double& lmin, double& lmax) {
   const size_t m = (size_t)nE;
-  std::vector<double> diag(nE), sq(nE);
+  std::vector<double> sq(nE);
   for (int e = 0; e < nE; ++e) {
     double d = val[e];
     for (int s = 0; s < 4; ++s)
       if (nbr[s * m + e] != e) d += val[(s + 1) * m + e];
-    diag[e] = d;
     sq[e] = eclass[e] == ident ? 0.0 : 1.0 / std::sqrt(d);
   }
-  auto apply = [&](const std::vector<double>& v, std::vector<double>& w) {
-    for (int e = 0; e < nE; ++e) {
-      if (sq[e] == 0.0) {
-        w[e] = 0.0;
-        continue;
-      }
-      const double ve = v[e] * sq[e];
-      double s = val[e] * ve;
-      for (int j = 0; j < 4; ++j) {
-        const int c = nbr[j * m + e];
-        if (c != e) s += val[(j + 1) * m + e] * (ve - v[c] * sq[c]);
-      }
-      w[e] = s * sq[e];
+  std::vector<double> W(4 * m, 0.0);
+  std::vector<int32_t> C(4 * m, 0);
+  for (int e = 0; e < nE; ++e)
+    for (int s = 0; s < 4; ++s) {
+      const int c = nbr[s * m + e];
+      C[s * m + e] = c;
+      if (c != e) W[s * m + e] = val[(s + 1) * m + e] * sq[e] * sq[c];
     }
-  };
   std::vector<double> v(nE), vp(nE, 0.0), w(nE);
   uint64_t state = 0x9E3779B97F4A7C15ull;  // deterministic start vector (xorshift)
   double nrm = 0.0;
@@ -286,13 +292,16 @@ void lanczos_bounds(int nE, const std::vector<int32_t>& nbr, const std::vector<d
   nrm = std::sqrt(nrm);
   for (double& x : v) x /= nrm;
   std::vector<double> al, be;
-  double beta = 0.0;
-  for (int j = 0; j < k; ++j) {
-    apply(v, w);
+  double beta = 0.0, prev_min = 0.0;
+  lmin = lmax = 1.0;
+  for (int j = 0; j < kmax; ++j) {
     double a = 0.0;
     for (int e = 0; e < nE; ++e) {
-      w[e] -= beta * vp[e];
-      a += w[e] * v[e];
+      double t = sq[e] == 0.0 ? 0.0 : v[e];
+      for (int s = 0; s < 4; ++s) t -= W[s * m + e] * v[C[s * m + e]];
+      t -= beta * vp[e];
+      w[e] = t;
+      a += t * v[e];
     }
     double bn = 0.0;
     for (int e = 0; e < nE; ++e) {
@@ -301,7 +310,15 @@ void lanczos_bounds(int nE, const std::vector<int32_t>& nbr, const std::vector<d
     }
     bn = std::sqrt(bn);
     al.push_back(a);
-    if (bn < 1e-300 || j + 1 == k) break;
+    const bool last = bn < 1e-300 || j + 1 == kmax;
+    if ((j + 1) % 20 == 0 || last) {
+      std::vector<double> bb(be.begin(), be.end());
+      lmin = tridiag_eig(al, bb, 1);
+      lmax = tridiag_eig(al, bb, 0);
+      if (j + 1 >= 40 && std::fabs(lmin - prev_min) < 0.03 * lmin) break;
+      prev_min = lmin;
+    }
+    if (last) break;
     be.push_back(bn);
     for (int e = 0; e < nE; ++e) {
       vp[e] = v[e];
@@ -309,9 +326,6 @@ void lanczos_bounds(int nE, const std::vector<int32_t>& nbr, const std::vector<d
     }
     beta = bn;
   }
-  be.resize(al.size() > 0 ? al.size() - 1 : 0);
-  lmin = tridiag_eig(al, be, 1);
-  lmax = tridiag_eig(al, be, 0);
 }
 
 // Chebyshev coefficients (cd_k, cr_k) of degree `deg` on [a, b].
@@ -461,6 +475,13 @@ PHFEM_API int phfem_mg_create(phfem_sys sys, int32_t nlevels, const phfem_mesh* 
   cudaStream_t s = ctx->stream;
   for (int l = 0; l < nlevels; ++l)
     if (!meshes[l] || meshes[l]->ctx != ctx) return fail(PHFEM_EINVAL, "phfem_mg_create: NULL mesh or another context");
+  for (int l = 0; l + 1 < nlevels; ++l) {
+    const phfem_mesh_info& C = meshes[l]->info;
+    const phfem_mesh_info& F = meshes[l + 1]->info;
+    if (F.nT != 4 * (int64_t)C.nT || F.nV != (int64_t)C.nV + C.nE)
+      return fail(PHFEM_EINVAL, "phfem_mg_create: level " + std::to_string(l + 1) +
+                                    " is not the red refinement of level " + std::to_string(l));
+  }
   phfem_mg mg = new phfem_mg_s();
   mg->fine = sys;
   mg->fp32 = sys->fp32;
@@ -469,55 +490,46 @@ PHFEM_API int phfem_mg_create(phfem_sys sys, int32_t nlevels, const phfem_mesh* 
   mg->L.resize(nlevels);
   const size_t es = sys->fp32 ? sizeof(float) : sizeof(double);
   int st = PHFEM_OK;
-  // coefficients of every level: the fine a_T averaged over children
-  std::vector<double*> aT(nlevels, nullptr);
-  int* bad = nullptr;
-  unsigned int* gb = nullptr;
-  st = dalloc_n(ctx, &bad, 1);
-  if (st == PHFEM_OK) st = dalloc_n(ctx, &gb, 1);
+  auto chk = [&](int r) {
+    if (st == PHFEM_OK) st = r;
+  };
+  // device scratch: [0] bad flag, [1 .. nlevels] Gershgorin bounds (float bits)
+  unsigned int* flags = nullptr;
+  chk(dalloc_n(ctx, &flags, (size_t)nlevels + 1));
   if (st == PHFEM_OK) {
-    cudaError_t e = cudaMemsetAsync(bad, 0, sizeof(int), s);
+    cudaError_t e = cudaMemsetAsync(flags, 0, sizeof(unsigned int) * (nlevels + 1), s);
     if (e != cudaSuccess) st = cuda_fail(e, "cudaMemsetAsync", __FILE__, __LINE__);
   }
+  // transfer tables (checking the refinement structure) and vectors
   for (int l = 0; l < nlevels && st == PHFEM_OK; ++l) {
     phfem_mg_s::Level& Lv = mg->L[l];
     Lv.mesh = meshes[l];
     Lv.nE = meshes[l]->info.nE;
     Lv.nT = meshes[l]->info.nT;
     if (l + 1 < nlevels) {
-      const phfem_mesh_info& F = meshes[l + 1]->info;
-      if (F.nT != 4 * (int64_t)Lv.nT || F.nV != meshes[l]->info.nV + Lv.nE) {
-        st = fail(PHFEM_EINVAL, "phfem_mg_create: level " + std::to_string(l + 1) +
-                                    " is not the red refinement of level " + std::to_string(l));
-        break;
-      }
-      st = dalloc_n(ctx, &Lv.ct, 9 * (size_t)Lv.nT);
+      chk(dalloc_n(ctx, &Lv.ct, 9 * (size_t)Lv.nT));
       if (st != PHFEM_OK) break;
       k_mg_ct<<<grid_for(ctx, Lv.nT), kBlock, 0, s>>>(Lv.nT, meshes[l]->info.nV, meshes[l]->tri, meshes[l]->t2e,
-                                                      meshes[l + 1]->tri, meshes[l + 1]->t2e, Lv.ct, bad);
-      st = check_launch(ctx, "k_mg_ct");
+                                                      meshes[l + 1]->tri, meshes[l + 1]->t2e, Lv.ct,
+                                                      reinterpret_cast<int*>(flags));
+      chk(check_launch(ctx, "k_mg_ct"));
     }
-    if (st == PHFEM_OK) st = dalloc(ctx, &Lv.rhs, es * Lv.nE + 16);
-    if (st == PHFEM_OK) st = dalloc(ctx, &Lv.z, es * Lv.nE + 16);
-    if (st == PHFEM_OK) st = dalloc(ctx, &Lv.zb, es * Lv.nE + 16);
-    if (st == PHFEM_OK) st = dalloc(ctx, &Lv.d, es * Lv.nE + 16);
-    if (st == PHFEM_OK && l > 0) st = dalloc(ctx, &Lv.res, es * Lv.nE + 16);
+    chk(dalloc(ctx, &Lv.rhs, es * Lv.nE + 16));
+    chk(dalloc(ctx, &Lv.z, es * Lv.nE + 16));
+    chk(dalloc(ctx, &Lv.zb, es * Lv.nE + 16));
+    chk(dalloc(ctx, &Lv.d, es * Lv.nE + 16));
+    if (l > 0) chk(dalloc(ctx, &Lv.res, es * Lv.nE + 16));
   }
-  if (st == PHFEM_OK) {
-    int h = 0;
-    cudaError_t e = cudaMemcpyAsync(&h, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) st = cuda_fail(e, "phfem_mg_create", __FILE__, __LINE__);
-    else if (h) st = fail(PHFEM_EINVAL, "phfem_mg_create: a level is not the red refinement of the one below");
-  }
-  // coefficients, then the coarse systems (rediscretisation)
+  // coefficients of every level (the fine a_T averaged over children), then
+  // the coarse systems (rediscretisation), with no host synchronisation
+  std::vector<double*> aT(nlevels, nullptr);
   if (st == PHFEM_OK && a_T) {
     aT[nlevels - 1] = const_cast<double*>(a_T);
     for (int l = nlevels - 2; l >= 0 && st == PHFEM_OK; --l) {
-      st = dalloc_n(ctx, &aT[l], (size_t)mg->L[l].nT);
+      chk(dalloc_n(ctx, &aT[l], (size_t)mg->L[l].nT));
       if (st != PHFEM_OK) break;
       k_mg_coarsen_a<<<grid_for(ctx, mg->L[l].nT), kBlock, 0, s>>>(mg->L[l].nT, aT[l + 1], aT[l]);
-      st = check_launch(ctx, "k_mg_coarsen_a");
+      chk(check_launch(ctx, "k_mg_coarsen_a"));
     }
   }
   for (int l = 0; l < nlevels && st == PHFEM_OK; ++l) {
@@ -529,66 +541,66 @@ PHFEM_API int phfem_mg_create(phfem_sys sys, int32_t nlevels, const phfem_mesh* 
       phfem_coeffs c = sys->c;
       c.a_T = a_T ? aT[l] : nullptr;
       c.form = PHFEM_FORM_TRACE;
-      st = phfem_assemble(meshes[l], &c, nullptr, nullptr, &Lv.sys);
+      chk(assemble_system(meshes[l], c, nullptr, nullptr, &Lv.sys, false));
       Lv.owned = true;
     }
   }
   for (int l = nlevels - 2; l >= 0; --l)
     if (aT[l]) dfree(ctx, aT[l]);
-  // Gershgorin bounds of every level
   for (int l = 0; l < nlevels && st == PHFEM_OK; ++l) {
     phfem_mg_s::Level& Lv = mg->L[l];
-    unsigned int hb = 0;
-    cudaError_t e = cudaMemsetAsync(gb, 0, sizeof(unsigned int), s);
-    if (e == cudaSuccess) {
-      k_mg_gershgorin<<<grid_for(ctx, Lv.nE), kBlock, 0, s>>>(Lv.nE, Lv.mesh->nbr, Lv.sys->val, gb);
-      e = cudaGetLastError();
-    }
-    if (e == cudaSuccess) e = cudaMemcpyAsync(&hb, gb, sizeof(hb), cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-      st = cuda_fail(e, "phfem_mg_create: Gershgorin bound", __FILE__, __LINE__);
-      break;
-    }
-    float fb;
-    std::memcpy(&fb, &hb, sizeof(fb));
-    Lv.b = fb > 1.0f ? (double)fb : 1.0;
+    k_mg_gershgorin<<<grid_for(ctx, Lv.nE), kBlock, 0, s>>>(Lv.nE, Lv.mesh->nbr, Lv.sys->val, flags + 1 + l);
+    chk(check_launch(ctx, "k_mg_gershgorin"));
   }
-  // interval and degree of the coarsest polynomial: Lanczos on the host
+  // one read-back: flags, bounds and the coarsest level for the Lanczos run
+  std::vector<unsigned int> hflags(nlevels + 1, 0);
+  phfem_mg_s::Level& C = mg->L[0];
+  const int n = C.nE;
+  std::vector<int32_t> nbr(4 * (size_t)n);
+  std::vector<double> val(5 * (size_t)n);
+  std::vector<uint8_t> ec(n);
   if (st == PHFEM_OK) {
-    phfem_mg_s::Level& C = mg->L[0];
-    const int n = C.nE;
-    std::vector<int32_t> nbr(4 * (size_t)n);
-    std::vector<double> val(5 * (size_t)n);
-    std::vector<uint8_t> ec(n);
-    cudaError_t e = cudaMemcpyAsync(nbr.data(), C.mesh->nbr, sizeof(int32_t) * nbr.size(), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaMemcpyAsync(hflags.data(), flags, sizeof(unsigned int) * hflags.size(),
+                                    cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(nbr.data(), C.mesh->nbr, sizeof(int32_t) * nbr.size(), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess)
       e = cudaMemcpyAsync(val.data(), C.sys->val, sizeof(double) * val.size(), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaMemcpyAsync(ec.data(), C.mesh->eclass, n, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) {
-      st = cuda_fail(e, "phfem_mg_create: coarse level read", __FILE__, __LINE__);
+    if (e != cudaSuccess) st = cuda_fail(e, "phfem_mg_create: read-back", __FILE__, __LINE__);
+    else if (hflags[0]) st = fail(PHFEM_EINVAL, "phfem_mg_create: a level is not the red refinement of the one below");
+  }
+  if (st == PHFEM_OK) {
+    for (int l = 0; l < nlevels; ++l) {
+      float fb;
+      std::memcpy(&fb, &hflags[1 + l], sizeof(fb));
+      mg->L[l].b = fb > 1.0f ? (double)fb : 1.0;
+    }
+    // interval and degree of the coarsest polynomial
+    const int steps = n <= 200000 ? std::min(n, 400) : 60;
+    double lmin = 0.0, lmax = 0.0;
+    const auto t0 = std::chrono::steady_clock::now();
+    lanczos_bounds(n, nbr, val, ec, C.sys->ident_class, steps, lmin, lmax);
+    if (getenv("PHFEM_VERBOSE"))
+      fprintf(stderr, "phfem: multigrid coarsest level %d rows, Ritz interval [%.4e, %.4e], %.2f ms\n", n, lmin,
+              lmax, std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count());
+    // Ritz values lie inside the spectrum: widen both ends
+    mg->coarse_b = std::min(1.02 * lmax, C.b);
+    mg->coarse_a = (n <= 200000 ? 0.85 : 0.25) * lmin;
+    if (!(mg->coarse_a > 0.0) || !(mg->coarse_a < mg->coarse_b)) mg->coarse_a = mg->coarse_b * 1e-4;
+    if (o.coarse_degree > 0) {
+      mg->coarse_deg = o.coarse_degree;
     } else {
-      const int steps = n <= 200000 ? std::min(n, 300) : 60;
-      double lmin = 0.0, lmax = 0.0;
-      lanczos_bounds(n, nbr, val, ec, C.sys->ident_class, steps, lmin, lmax);
-      // Ritz values lie inside the spectrum: widen both ends
-      mg->coarse_b = std::min(1.02 * lmax, C.b);
-      mg->coarse_a = (n <= 200000 ? 0.9 : 0.25) * lmin;
-      if (!(mg->coarse_a > 0.0) || !(mg->coarse_a < mg->coarse_b)) mg->coarse_a = mg->coarse_b * 1e-4;
-      if (o.coarse_degree > 0) {
-        mg->coarse_deg = o.coarse_degree;
-      } else {
-        const double kap = mg->coarse_b / mg->coarse_a;
-        const double rho = (std::sqrt(kap) - 1.0) / (std::sqrt(kap) + 1.0);
-        int deg = (int)std::ceil(std::log(2.0 / o.coarse_eps) / std::log(1.0 / rho));
-        mg->coarse_deg = std::max(1, std::min(deg, 2000));
-      }
+      const double kap = mg->coarse_b / mg->coarse_a;
+      const double rho = (std::sqrt(kap) - 1.0) / (std::sqrt(kap) + 1.0);
+      const int deg = rho > 0.0 ? (int)std::ceil(std::log(2.0 / o.coarse_eps) / std::log(1.0 / rho)) : 1;
+      mg->coarse_deg = std::max(1, std::min(deg, 2000));
     }
   }
-  dfree(ctx, bad);
-  dfree(ctx, gb);
+  dfree(ctx, flags);
   if (st != PHFEM_OK) {
+    cudaStreamSynchronize(s);
     mg_free(mg);
     return st;
   }

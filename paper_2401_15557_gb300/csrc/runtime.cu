@@ -207,7 +207,10 @@ PHFEM_API int phfem_ctx_create(void* cuda_stream, phfem_ctx* out) {
   PH_CUDA(cudaGetDevice(&dev));
   int sms = 0;
   PH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  phfem::SolveState* pinned = nullptr;
+  PH_CUDA(cudaMallocHost((void**)&pinned, sizeof(phfem::SolveState)));
   phfem_ctx c = new phfem_ctx_s();
+  c->st_pinned = pinned;
   c->stream = (cudaStream_t)cuda_stream;
   c->device = dev;
   c->num_sms = sms;
@@ -222,6 +225,7 @@ PHFEM_API int phfem_ctx_destroy(phfem_ctx ctx) {
   if (!ctx) return fail(PHFEM_EINVAL, "phfem_ctx_destroy: NULL context");
   for (auto& p : ctx->prof)
     for (cudaEvent_t e : p.ev) cudaEventDestroy(e);
+  if (ctx->st_pinned) cudaFreeHost(ctx->st_pinned);
   delete ctx;
   return PHFEM_OK;
 }
