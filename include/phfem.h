@@ -167,6 +167,12 @@ typedef struct {
   int32_t precision;  /* PHFEM_FP64 or PHFEM_FP32_IR (FP32 inner solve + FP64 refinement) */
   int32_t form;       /* PHFEM_FORM_TRACE (edge-midpoint values, default) or
                          PHFEM_FORM_FLUX (multipliers; elliptic with delta > 0)     */
+  double A[3];        /* constant SPD tensor (A11, A12, A22) of Eq. eq1, scaled per
+                         triangle by a_T (or a); all zero = identity               */
+  double p[2];        /* constant convection velocity (the D_T block of Definition
+                         3.1); nonzero makes the system nonsymmetric: phfem_solve
+                         then uses BiCGStab (trace form; not with multigrid or the
+                         graph-captured Crank-Nicolson step)                       */
 } phfem_coeffs;
 
 enum { PHFEM_FORM_TRACE = 0, PHFEM_FORM_FLUX = 1 };

@@ -31,18 +31,42 @@
 namespace phfem {
 namespace {
 
+// Kt rows 7..9 (with convection): the column values c_j of the convection block.
 __global__ void k_asm_tri(int nT, const int32_t* __restrict__ tri, const double2* __restrict__ xy,
-                          const double* __restrict__ aT, double a_const, double delta,
-                          double* __restrict__ Kt, int* __restrict__ bad) {
+                          const double* __restrict__ aT, double a_const, double delta, double A11, double A12,
+                          double A22, double px, double py, int conv, double* __restrict__ Kt,
+                          int* __restrict__ bad) {
   const size_t n = (size_t)nT;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nT; t += gridDim.x * blockDim.x) {
     const int v0 = tri[3 * t], v1 = tri[3 * t + 1], v2 = tri[3 * t + 2];
     const double a = aT ? aT[t] : a_const;
     if (!(a > 0.0) || !isfinite(a)) atomicOr(bad, isfinite(a) ? 1 : 2);
     double K[7];
-    tri_block(__ldg(xy + v0), __ldg(xy + v1), __ldg(xy + v2), a, delta, K);
+    const double2 p0 = __ldg(xy + v0), p1 = __ldg(xy + v1), p2 = __ldg(xy + v2);
+    tri_block(p0, p1, p2, a, delta, K, A11, A12, A22);
 #pragma unroll
     for (int j = 0; j < 7; ++j) Kt[j * n + t] = K[j];
+    if (conv) {
+      double c[3];
+      tri_conv(p0, p1, p2, px, py, c);
+#pragma unroll
+      for (int j = 0; j < 3; ++j) Kt[(7 + j) * n + t] = c[j];
+    }
+  }
+}
+
+// Adds the convection columns of T+ (tp, local kp) and T- to an edge row
+// (slots: T+ (k+1, k+2), T- (k+1, k+2)); the row sums do not change.
+__device__ __forceinline__ void add_conv(const double* Kt, size_t n, int tp, int kp, int tm, int km, double sK,
+                                         EdgeRow& R) {
+  const double* c = Kt + 7 * n;
+  R.diag += sK * c[(size_t)kp * n + tp];
+  R.l[0] -= sK * c[(size_t)((kp + 1) % 3) * n + tp];
+  R.l[1] -= sK * c[(size_t)((kp + 2) % 3) * n + tp];
+  if (tm >= 0) {
+    R.diag += sK * c[(size_t)km * n + tm];
+    R.l[2] -= sK * c[(size_t)((km + 1) % 3) * n + tm];
+    R.l[3] -= sK * c[(size_t)((km + 2) % 3) * n + tm];
   }
 }
 
@@ -51,7 +75,7 @@ template <typename T>
 __global__ void k_asm_rows(int nE, int nT, const int32_t* __restrict__ ed2el, const uint8_t* __restrict__ lk,
                            const uint8_t* __restrict__ eclass, const double* __restrict__ Kt,
                            const double* __restrict__ f_mid, const double* __restrict__ bc_mid,
-                           const double* __restrict__ elen, double sK, double sM, double delta,
+                           const double* __restrict__ elen, double sK, double sM, double delta, int conv,
                            double* __restrict__ val, double* __restrict__ b, double* __restrict__ me,
                            T* __restrict__ lval, T* __restrict__ rdiag, T* __restrict__ dinv) {
   const size_t n = (size_t)nT, m = (size_t)nE;
@@ -59,9 +83,10 @@ __global__ void k_asm_rows(int nE, int nT, const int32_t* __restrict__ ed2el, co
     const int4 q = reinterpret_cast<const int4*>(ed2el)[e];
     const int kk = lk[e];
     const uint8_t cls = eclass[e];
-    const EdgeRow R = edge_row(Kt, n, q.z, kk & 3, q.w, (kk >> 2) & 3, cls, f_mid ? f_mid[e] : 0.0,
-                               bc_mid ? bc_mid[e] : 0.0, cls == PHFEM_EDGE_NEUMANN ? elen[e] : 0.0, sK, sM,
-                               delta, f_mid != nullptr, bc_mid != nullptr);
+    EdgeRow R = edge_row(Kt, n, q.z, kk & 3, q.w, (kk >> 2) & 3, cls, f_mid ? f_mid[e] : 0.0,
+                         bc_mid ? bc_mid[e] : 0.0, cls == PHFEM_EDGE_NEUMANN ? elen[e] : 0.0, sK, sM, delta,
+                         f_mid != nullptr, bc_mid != nullptr);
+    if (conv && cls != PHFEM_EDGE_DIRICHLET) add_conv(Kt, n, q.z, kk & 3, q.w, (kk >> 2) & 3, sK, R);
     val[e] = R.rpart;
 #pragma unroll
     for (int s = 0; s < 4; ++s) {
@@ -230,6 +255,7 @@ void sys_free(phfem_sys s) {
   dfree(c, s->f);
   dfree(c, s->bc);
   dfree(c, s->St);
+  dfree(c, s->bw);
   dfree(c, s->x);
   dfree(c, s->r64);
   dfree(c, s->ri);
@@ -250,8 +276,11 @@ int assemble_into(phfem_sys sys, const double* f_mid, const double* bc_mid, int*
   const int nT = m->info.nT, nE = m->info.nE;
   const phfem_coeffs& c = sys->c;
   prof_start(ctx, kProfAsmTri);
+  const bool iso = c.A[0] == 0.0 && c.A[1] == 0.0 && c.A[2] == 0.0;
   k_asm_tri<<<grid_for(ctx, nT), kBlock, 0, s>>>(nT, m->tri, reinterpret_cast<const double2*>(m->xy), c.a_T, c.a,
-                                                 c.delta, sys->Kt, d_bad);
+                                                 c.delta, iso ? 1.0 : c.A[0], iso ? 0.0 : c.A[1],
+                                                 iso ? 1.0 : c.A[2], c.p[0], c.p[1], sys->conv ? 1 : 0, sys->Kt,
+                                                 d_bad);
   prof_stop(ctx, kProfAsmTri);
   PH_TRY(check_launch(ctx, "k_asm_tri"));
   if (sys->form == PHFEM_FORM_FLUX) {
@@ -276,14 +305,14 @@ int assemble_into(phfem_sys sys, const double* f_mid, const double* bc_mid, int*
   prof_start(ctx, kProfAsmRows);
   if (sys->fp32)
     k_asm_rows<float><<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, nT, m->ed2el, m->lk, m->eclass, sys->Kt, f_mid,
-                                                           bc_mid, m->elen, sK, sM, c.delta, sys->val, sys->b,
-                                                           sys->me, (float*)sys->lval, (float*)sys->rdiag,
-                                                           (float*)sys->dinv);
+                                                           bc_mid, m->elen, sK, sM, c.delta, sys->conv ? 1 : 0,
+                                                           sys->val, sys->b, sys->me, (float*)sys->lval,
+                                                           (float*)sys->rdiag, (float*)sys->dinv);
   else
     k_asm_rows<double><<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, nT, m->ed2el, m->lk, m->eclass, sys->Kt, f_mid,
-                                                            bc_mid, m->elen, sK, sM, c.delta, sys->val, sys->b,
-                                                            sys->me, (double*)sys->lval, (double*)sys->rdiag,
-                                                            (double*)sys->dinv);
+                                                            bc_mid, m->elen, sK, sM, c.delta, sys->conv ? 1 : 0,
+                                                            sys->val, sys->b, sys->me, (double*)sys->lval,
+                                                            (double*)sys->rdiag, (double*)sys->dinv);
   prof_stop(ctx, kProfAsmRows);
   return check_launch(ctx, "k_asm_rows");
 }
@@ -323,6 +352,13 @@ int assemble_system(phfem_mesh mesh, const phfem_coeffs& c, const double* f_mid,
     return fail(PHFEM_EINVAL, "phfem_assemble: the flux form is elliptic only (dt = 0)");
   if (!std::isfinite(c.delta) || !std::isfinite(c.dt) || (!c.a_T && !std::isfinite(c.a)))
     return fail(PHFEM_ENAN, "phfem_assemble: non-finite coefficient");
+  const bool iso = c.A[0] == 0.0 && c.A[1] == 0.0 && c.A[2] == 0.0;
+  if (!iso && !(c.A[0] > 0.0 && c.A[2] > 0.0 && c.A[0] * c.A[2] - c.A[1] * c.A[1] > 0.0))
+    return fail(PHFEM_EINVAL, "phfem_assemble: the tensor A must be symmetric positive definite");
+  const bool conv = c.p[0] != 0.0 || c.p[1] != 0.0;
+  if (!std::isfinite(c.p[0]) || !std::isfinite(c.p[1])) return fail(PHFEM_ENAN, "phfem_assemble: non-finite p");
+  if (conv && c.form != PHFEM_FORM_TRACE)
+    return fail(PHFEM_EINVAL, "phfem_assemble: convection needs the trace form");
   phfem_ctx ctx = mesh->ctx;
   cudaStream_t s = ctx->stream;
   const size_t nT = mesh->info.nT, nE = mesh->info.nE;
@@ -332,6 +368,7 @@ int assemble_system(phfem_mesh mesh, const phfem_coeffs& c, const double* f_mid,
   sys->c.a_T = nullptr;  // the pointer is only valid during this call
   sys->fp32 = c.precision == PHFEM_FP32_IR;
   sys->form = c.form;
+  sys->conv = conv;
   sys->ident_class = c.form == PHFEM_FORM_FLUX ? PHFEM_EDGE_NEUMANN : PHFEM_EDGE_DIRICHLET;
   const size_t isz = sys->fp32 ? sizeof(float) : sizeof(double);
   int st = PHFEM_OK;
@@ -339,7 +376,7 @@ int assemble_system(phfem_mesh mesh, const phfem_coeffs& c, const double* f_mid,
   auto chk = [&](int r) {
     if (st == PHFEM_OK) st = r;
   };
-  chk(dalloc_n(ctx, &sys->Kt, 7 * nT));
+  chk(dalloc_n(ctx, &sys->Kt, (conv ? 10 : 7) * nT));
   chk(dalloc_n(ctx, &sys->val, 5 * nE));
   chk(dalloc_n(ctx, &sys->b, nE));
   chk(dalloc_n(ctx, &sys->me, nE));

@@ -51,6 +51,7 @@ struct SolveState {
   double floor2;   // squared estimate of the residual that rounding x to FP64 alone leaves
   double rp;       // r.p right after a reliable update (p kept)
   double rr_pending, ff_pending;  // ||r||^2 and floor of a true residual awaiting the preconditioner
+  double rho, omega;               // BiCGStab: (r^, r) and the stabilisation step
   int use_rp;      // 1: the next step is a line search alpha = r.p / p.Ap
   int restart;     // 1: the next SpMV restarts the direction, p = D^-1 r
   int conv;        // 1: rtol met, 2: stopped at the FP64 floor
@@ -114,10 +115,13 @@ struct phfem_sys_s {
   phfem_coeffs c;
   bool fp32;
   int form;              // PHFEM_FORM_TRACE or PHFEM_FORM_FLUX
+  bool conv;             // convection: nonsymmetric rows, Kt rows 7..9 hold its columns, BiCGStab
+  void* bw;              // BiCGStab workspace [7][nE] in the inner precision (allocated on first use)
   uint8_t ident_class;   // class of the identity rows: Dirichlet (trace) or Neumann (flux)
   double* St;            // [9][nT] flux form: S_T (00, 11, 22, 01, 12, 20) and the load terms g_T
   double* bc;            // [nE] copy of the boundary data (flux-form recovery)
   double* Kt;            // [7][nT]: K^CR_T entries (00, 11, 22, 01, 12, 20) and |T|/3
+                         //          (+ [3][nT] convection columns c_j with convection)
   double* val;           // [5][nE]: FP64 row in difference form: slot 0 = r_e (reaction/mass
                          //          part of the diagonal), slots 1..4 = l_es = -S_{e,nbr_s}
   double* b;             // [nE]: right-hand side; u_D on Dirichlet rows
@@ -167,6 +171,8 @@ int solve_system(phfem_sys sys, const phfem_solve_opts* opts, phfem_stats* stats
 int capture_solve(phfem_sys sys, const phfem_solve_opts* opts, cudaStream_t capture, int iters_per_body);
 int sys_init_x(phfem_sys sys, const double* w0);
 void fill_opts(phfem_sys sys, phfem_solve_opts& o);
+// BiCGStab for systems with convection (same stopping rules and state).
+int solve_bicgstab(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats);
 // phfem_assemble without the host synchronisation that checks a_T (for
 // coefficients the library derived itself).
 int assemble_system(phfem_mesh mesh, const phfem_coeffs& c, const double* f_mid, const double* bc_mid,

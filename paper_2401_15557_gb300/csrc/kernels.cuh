@@ -19,11 +19,12 @@ __device__ __forceinline__ T ld(const T* ptr) {
   else return *ptr;
 }
 
-// K^CR_T = (a/|T|) e_k . e_j + delta |T|/3 I for the triangle (p0, p1, p2),
-// e_k = P_{k+2} - P_{k+1}: out[0..2] diagonal, out[3] (0,1), out[4] (1,2),
-// out[5] (2,0), out[6] = |T|/3.
+// K^CR_T = (a/|T|) e_k' A~ e_j + delta |T|/3 I for the triangle (p0, p1, p2),
+// e_k = P_{k+2} - P_{k+1}, A~ = [[A22, -A12], [-A12, A11]] (since |T| grad
+// lambda_k = the edge vector e_k turned by a right angle, over 2): out[0..2]
+// diagonal, out[3] (0,1), out[4] (1,2), out[5] (2,0), out[6] = |T|/3.
 __device__ __forceinline__ void tri_block(double2 p0, double2 p1, double2 p2, double a, double delta,
-                                          double out[7]) {
+                                          double out[7], double A11 = 1.0, double A12 = 0.0, double A22 = 1.0) {
   const double e0x = p2.x - p1.x, e0y = p2.y - p1.y;
   const double e1x = p0.x - p2.x, e1y = p0.y - p2.y;
   const double e2x = p1.x - p0.x, e2y = p1.y - p0.y;
@@ -31,13 +32,25 @@ __device__ __forceinline__ void tri_block(double2 p0, double2 p1, double2 p2, do
   const double mT = area2 * (1.0 / 6.0);       // |T|/3
   const double c = (a + a) / area2;            // a / |T|
   const double dm = delta * mT;
-  out[0] = c * (e0x * e0x + e0y * e0y) + dm;
-  out[1] = c * (e1x * e1x + e1y * e1y) + dm;
-  out[2] = c * (e2x * e2x + e2y * e2y) + dm;
-  out[3] = c * (e0x * e1x + e0y * e1y);
-  out[4] = c * (e1x * e2x + e1y * e2y);
-  out[5] = c * (e2x * e0x + e2y * e0y);
+  auto q = [&](double ux, double uy, double vx, double vy) {
+    return A22 * ux * vx - A12 * (ux * vy + uy * vx) + A11 * uy * vy;
+  };
+  out[0] = c * q(e0x, e0y, e0x, e0y) + dm;
+  out[1] = c * q(e1x, e1y, e1x, e1y) + dm;
+  out[2] = c * q(e2x, e2y, e2x, e2y) + dm;
+  out[3] = c * q(e0x, e0y, e1x, e1y);
+  out[4] = c * q(e1x, e1y, e2x, e2y);
+  out[5] = c * q(e2x, e2y, e0x, e0y);
   out[6] = mT;
+}
+
+// Convection in the trace form: R^-T D_T R^-1 with the column-constant
+// (D_T)_{rc} = |T|/3 p.grad(lambda_c) is column-constant as well,
+// -2|T|/3 p.grad(lambda_j) = (p_x e_jy - p_y e_jx) / 3 in column j (rows sum to 0).
+__device__ __forceinline__ void tri_conv(double2 p0, double2 p1, double2 p2, double px, double py, double out[3]) {
+  out[0] = (px * (p2.y - p1.y) - py * (p2.x - p1.x)) * (1.0 / 3.0);
+  out[1] = (px * (p0.y - p2.y) - py * (p0.x - p2.x)) * (1.0 / 3.0);
+  out[2] = (px * (p1.y - p0.y) - py * (p1.x - p0.x)) * (1.0 / 3.0);
 }
 
 // Entries of row k of K^CR_T stored slot-major with stride n: diagonal,

@@ -464,6 +464,7 @@ PHFEM_API int phfem_mg_create(phfem_sys sys, int32_t nlevels, const phfem_mesh* 
   if (meshes[nlevels - 1] != sys->mesh)
     return fail(PHFEM_EINVAL, "phfem_mg_create: the finest mesh must be the system's mesh");
   if (sys->form != PHFEM_FORM_TRACE) return fail(PHFEM_EINVAL, "phfem_mg_create: the trace form only");
+  if (sys->conv) return fail(PHFEM_EINVAL, "phfem_mg_create: symmetric systems only (no convection)");
   phfem_mg_opts o{};
   if (opts) o = *opts;
   if (o.nu <= 0) o.nu = 2;

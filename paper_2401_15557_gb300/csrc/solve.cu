@@ -406,7 +406,7 @@ __global__ void k_recover(int nT, const int32_t* __restrict__ t2e, const int8_t*
                           const int32_t* __restrict__ lam_id, const double* __restrict__ Kt,
                           const double* __restrict__ elen, const double* __restrict__ wa,
                           const double* __restrict__ wb, const double* __restrict__ f, double inv_dt,
-                          double theta, double* __restrict__ U, double* __restrict__ Lambda) {
+                          double theta, int conv, double* __restrict__ U, double* __restrict__ Lambda) {
   const size_t n = (size_t)nT;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nT; t += gridDim.x * blockDim.x) {
     const int e0 = t2e[3 * t], e1 = t2e[3 * t + 1], e2 = t2e[3 * t + 2];
@@ -429,8 +429,10 @@ __global__ void k_recover(int nT, const int32_t* __restrict__ t2e, const int8_t*
     const double m2 = theta * a2 + (1.0 - theta) * b2;
     const double K00 = Kt[t], K11 = Kt[n + t], K22 = Kt[2 * n + t];
     const double K01 = Kt[3 * n + t], K12 = Kt[4 * n + t], K20 = Kt[5 * n + t], mT = Kt[6 * n + t];
-    const double res[3] = {K00 * m0 + K01 * m1 + K20 * m2, K01 * m0 + K11 * m1 + K12 * m2,
-                           K20 * m0 + K12 * m1 + K22 * m2};
+    // convection adds the same sum_j c_j m_j to every row
+    const double cv = conv ? Kt[7 * n + t] * m0 + Kt[8 * n + t] * m1 + Kt[9 * n + t] * m2 : 0.0;
+    const double res[3] = {K00 * m0 + K01 * m1 + K20 * m2 + cv, K01 * m0 + K11 * m1 + K12 * m2 + cv,
+                           K20 * m0 + K12 * m1 + K22 * m2 + cv};
     const double dw[3] = {a0 - b0, a1 - b1, a2 - b2};
     const int ee[3] = {e0, e1, e2};
 #pragma unroll
@@ -442,6 +444,205 @@ __global__ void k_recover(int nT, const int32_t* __restrict__ t2e, const int8_t*
       Lambda[li] = r / elen[ee[k]];
     }
   }
+}
+
+// ---- BiCGStab (systems with convection) ------------------------------------
+// Jacobi-preconditioned (on the right) BiCGStab in the inner precision with the
+// solution accumulated in FP64 and the same reliable updates as the CG path:
+// when the recursive residual has fallen by inner_rtol (or on a breakdown) the
+// true FP64 residual replaces it and the iteration restarts with r^ = r.
+
+// After a true residual (k_residual with precond = 1): r^ = p = r, rho = r.r,
+// and the convergence decision.
+template <typename T>
+__global__ void k_bi_start(int nE, const T* __restrict__ r, T* __restrict__ rh, T* __restrict__ p, double* partials,
+                           SolveState* st, double rtol2, double inner_rtol2, int mode) {
+  if (mode == 3) {
+    if (st->done != 1) return;
+    mode = 2;
+  }
+  __shared__ double smem[kBlock / 32];
+  T acc = (T)0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    const T re = r[e];
+    rh[e] = re;
+    p[e] = re;
+    acc += re * re;
+  }
+  const double a = block_sum((double)acc, smem);
+  if (threadIdx.x == 0) partials[blockIdx.x] = a;
+  if (!arrive_last(&st->counter[3])) return;
+  const double rho = sum_partials(partials, smem);
+  if (threadIdx.x == 0) {
+    st->counter[3] = 0;
+    const double rr = st->rr_pending, ff = st->ff_pending;
+    st->rr64 = rr;
+    st->floor2 = ff;
+    st->rho = rho;
+    st->rz = rho;
+    st->tol2 = inner_rtol2 * rho;
+    st->status = 0;
+    if (mode == 1) {
+      st->it = 0;
+      st->updates = 1;
+      st->bodies = 0;
+    } else {
+      st->updates += 1;
+    }
+    st->conv = 0;
+    if (!isfinite(rr) || !isfinite(rho)) {
+      st->done = 3;
+      st->status = PHFEM_ENAN;
+    } else if (rr <= rtol2 * st->bb || rr == 0.0) {
+      st->done = 2;
+      st->conv = 1;
+    } else if (rr <= 4.0 * ff) {
+      st->done = 2;
+      st->conv = 2;
+    } else {
+      st->done = 0;
+    }
+  }
+}
+
+// ph = D^-1 p, v = A ph (neighbours' ph from p and D^-1), alpha = rho / (r^, v).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_bi_v(int nE, const int32_t* __restrict__ nbr,
+                                                 const T* __restrict__ lval, const T* __restrict__ rdiag,
+                                                 const T* __restrict__ dinv, const T* __restrict__ p,
+                                                 T* __restrict__ ph, T* __restrict__ v, const T* __restrict__ rh,
+                                                 double* partials, SolveState* st) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->dir_pending = 0;
+  if (st->done) return;
+  __shared__ double smem[kBlock / 32];
+  const size_t m = (size_t)nE;
+  T acc = (T)0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    const T pe = dinv[e] * p[e];
+    T s = rdiag[e] * pe;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int c = nbr[k * m + e];
+      s += lval[k * m + e] * (pe - dinv[c] * p[c]);
+    }
+    ph[e] = pe;
+    v[e] = s;
+    acc += rh[e] * s;
+  }
+  const double a = block_sum((double)acc, smem);
+  if (threadIdx.x == 0) partials[blockIdx.x] = a;
+  if (!arrive_last(&st->counter[1])) return;
+  const double rv = sum_partials(partials, smem);
+  if (threadIdx.x == 0) {
+    st->counter[1] = 0;
+    if (!isfinite(rv)) {
+      st->done = 3;
+      st->status = PHFEM_ENAN;
+    } else if (rv == 0.0 || st->rho == 0.0) {
+      st->done = 1;  // breakdown: restart from the true residual
+    } else {
+      st->alpha = st->rho / rv;
+    }
+  }
+}
+
+// s = r - alpha v, sh = D^-1 s.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_bi_s(int nE, const T* __restrict__ r, const T* __restrict__ v,
+                                                 const T* __restrict__ dinv, T* __restrict__ s, T* __restrict__ sh,
+                                                 const SolveState* st) {
+  if (st->done) return;
+  const T alpha = (T)st->alpha;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    const T se = r[e] - alpha * v[e];
+    s[e] = se;
+    sh[e] = dinv[e] * se;
+  }
+}
+
+// t = A sh, omega = (t, s) / (t, t).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_bi_t(int nE, const int32_t* __restrict__ nbr,
+                                                 const T* __restrict__ lval, const T* __restrict__ rdiag,
+                                                 const T* __restrict__ sh, const T* __restrict__ s, T* __restrict__ t,
+                                                 double* partials, SolveState* st) {
+  if (st->done) return;
+  __shared__ double smem[kBlock / 32];
+  const size_t m = (size_t)nE;
+  T ats = (T)0, att = (T)0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    const T te = spmv_row(nbr, lval, rdiag, sh, m, e);
+    t[e] = te;
+    ats += te * s[e];
+    att += te * te;
+  }
+  const double a = block_sum((double)ats, smem);
+  const double b = block_sum((double)att, smem);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = a;
+    partials[kMaxGrid + blockIdx.x] = b;
+  }
+  if (!arrive_last(&st->counter[2])) return;
+  const double ts = sum_partials(partials, smem);
+  const double tt = sum_partials(partials + kMaxGrid, smem);
+  if (threadIdx.x == 0) {
+    st->counter[2] = 0;
+    st->omega = tt > 0.0 ? ts / tt : 0.0;
+  }
+}
+
+// x += alpha ph + omega sh (FP64), r = s - omega t, rho' = (r^, r), ||r||^2.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_bi_x(int nE, double* __restrict__ x, const T* __restrict__ ph,
+                                                 const T* __restrict__ sh, const T* __restrict__ s,
+                                                 const T* __restrict__ t, T* __restrict__ r, const T* __restrict__ rh,
+                                                 double* partials, SolveState* st) {
+  if (st->done) return;
+  __shared__ double smem[kBlock / 32];
+  const double alpha64 = st->alpha, omega64 = st->omega;
+  const T omega = (T)omega64;
+  T arr = (T)0, arh = (T)0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    x[e] += alpha64 * (double)ph[e] + omega64 * (double)sh[e];
+    const T re = s[e] - omega * t[e];
+    r[e] = re;
+    arr += re * re;
+    arh += rh[e] * re;
+  }
+  const double a = block_sum((double)arr, smem);
+  const double b = block_sum((double)arh, smem);
+  if (threadIdx.x == 0) {
+    partials[2 * kMaxGrid + blockIdx.x] = a;
+    partials[3 * kMaxGrid + blockIdx.x] = b;
+  }
+  if (!arrive_last(&st->counter[0])) return;
+  const double rr = sum_partials(partials + 2 * kMaxGrid, smem);
+  const double rho = sum_partials(partials + 3 * kMaxGrid, smem);
+  if (threadIdx.x == 0) {
+    st->counter[0] = 0;
+    st->beta = (st->rho != 0.0 && omega64 != 0.0) ? (rho / st->rho) * (st->alpha / omega64) : 0.0;
+    st->rho = rho;
+    st->rz = rr;
+    st->it += 1;
+    st->dir_pending = 1;
+    if (!isfinite(rr)) {
+      st->done = 3;
+      st->status = PHFEM_ENAN;
+    } else if (omega64 == 0.0 || rho == 0.0) {
+      st->done = 1;  // stagnation or breakdown: restart from the true residual
+    }
+  }
+}
+
+// p = r + beta (p - omega v); then the test of the recursive residual.
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_bi_p(int nE, const T* __restrict__ r, const T* __restrict__ v,
+                                                 T* __restrict__ p, SolveState* st) {
+  if (!st->dir_pending) return;
+  const T beta = (T)st->beta, omega = (T)st->omega;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x)
+    p[e] = r[e] + beta * (p[e] - omega * v[e]);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && st->done == 0 && st->rz <= st->tol2) st->done = 1;
 }
 
 int read_state(phfem_sys sys) {
@@ -575,6 +776,95 @@ int solve_typed(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats) {
   return PHFEM_OK;
 }
 
+template <typename T>
+int bicgstab_typed(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats) {
+  phfem_mesh m = sys->mesh;
+  phfem_ctx ctx = m->ctx;
+  cudaStream_t s = ctx->stream;
+  const int nE = m->info.nE;
+  const size_t mm = (size_t)nE;
+  if (!sys->bw) PH_TRY(dalloc(ctx, &sys->bw, 7 * mm * sizeof(T) + 16));
+  T* W = (T*)sys->bw;
+  T *rh = W, *p = W + mm, *v = W + 2 * mm, *sv = W + 3 * mm, *tv = W + 4 * mm, *ph = W + 5 * mm, *sh = W + 6 * mm;
+  T* r = (T*)sys->ri;
+  const T* lval = (const T*)sys->lval;
+  const T* rdiag = (const T*)sys->rdiag;
+  const T* dinv = (const T*)sys->dinv;
+  const int g = grid_for(ctx, nE);
+  const double rtol2 = o.rtol * o.rtol, irtol2 = o.inner_rtol * o.inner_rtol;
+  auto residual = [&](int mode) -> int {
+    prof_start(ctx, kProfResidual);
+    k_residual<T><<<g, kBlock, 0, s>>>(nE, m->nbr, sys->val, sys->b, sys->x, m->eclass, sys->ident_class, dinv, r,
+                                       (T*)sys->pi, sys->partials, sys->st, rtol2, irtol2, mode, mode == 0 ? 0 : 1);
+    prof_stop(ctx, kProfResidual);
+    PH_TRY(check_launch(ctx, "k_residual"));
+    if (mode == 0) return PHFEM_OK;
+    k_bi_start<T><<<g, kBlock, 0, s>>>(nE, r, rh, p, sys->partials, sys->st, rtol2, irtol2, mode);
+    return check_launch(ctx, "k_bi_start");
+  };
+  auto iteration = [&]() -> int {
+    prof_start(ctx, kProfSpmv);
+    k_bi_v<T><<<g, kBlock, 0, s>>>(nE, m->nbr, lval, rdiag, dinv, p, ph, v, rh, sys->partials, sys->st);
+    k_bi_s<T><<<g, kBlock, 0, s>>>(nE, r, v, dinv, sv, sh, sys->st);
+    k_bi_t<T><<<g, kBlock, 0, s>>>(nE, m->nbr, lval, rdiag, sh, sv, tv, sys->partials, sys->st);
+    prof_stop(ctx, kProfSpmv);
+    prof_start(ctx, kProfUpdate);
+    k_bi_x<T><<<g, kBlock, 0, s>>>(nE, sys->x, ph, sh, sv, tv, r, rh, sys->partials, sys->st);
+    k_bi_p<T><<<g, kBlock, 0, s>>>(nE, r, v, p, sys->st);
+    prof_stop(ctx, kProfUpdate);
+    ctx->launches += 4;
+    return check_launch(ctx, "k_bi");
+  };
+  PH_TRY(residual(0));
+  PH_TRY(residual(1));
+  PH_TRY(read_state(sys));
+  int status = PHFEM_OK, stagnant = 0, last_updates = 0;
+  double best = 1e300;
+  for (;;) {
+    const SolveState& h = *sys->st_host;
+    if (h.updates != last_updates) {
+      last_updates = h.updates;
+      const double rel = h.bb > 0 ? std::sqrt(h.rr64 / h.bb) : 0.0;
+      stagnant = (rel > 0.5 * best) ? stagnant + 1 : 0;
+      best = rel < best ? rel : best;
+    }
+    if (h.done == 3) {
+      status = h.status;
+      break;
+    }
+    if (h.done == 2) break;
+    if (h.it >= o.max_iter || h.updates > o.max_refine || stagnant >= 8) {
+      status = PHFEM_ENOCONV;
+      break;
+    }
+    if (h.done == 1) {
+      PH_TRY(residual(2));
+      PH_TRY(read_state(sys));
+      continue;
+    }
+    int chunk = o.check_every;
+    if (h.it + chunk > o.max_iter) chunk = o.max_iter - h.it;
+    for (int k = 0; k < chunk; ++k) PH_TRY(iteration());
+    PH_TRY(read_state(sys));
+  }
+  const SolveState& h = *sys->st_host;
+  const double rel = h.bb > 0 ? std::sqrt(h.rr64 / h.bb) : 0.0;
+  if (stats) {
+    stats->iterations += h.it;
+    stats->refinements += h.updates;
+    stats->converged = h.done == 2 ? h.conv : 0;
+    stats->rel_residual = rel;
+    stats->fp64_floor = h.bb > 0 ? std::sqrt(h.floor2 / h.bb) : 0.0;
+  }
+  if (status != PHFEM_OK) {
+    char buf[200];
+    snprintf(buf, sizeof(buf), "BiCGStab: %s after %d iterations, %d residual updates, relative residual %.3e",
+             phfem_status_str(status), h.it, h.updates, rel);
+    return fail(status, buf);
+  }
+  return PHFEM_OK;
+}
+
 // The start kernels, then a WHILE node whose body runs `per_body` iterations,
 // the conditional reliable update and the loop control.
 template <typename T>
@@ -628,13 +918,20 @@ int capture_typed(phfem_sys sys, const phfem_solve_opts& o, cudaStream_t cs, int
 
 void fill_opts(phfem_sys sys, phfem_solve_opts& o) {
   if (o.rtol <= 0) o.rtol = 1e-10;
-  if (o.inner_rtol <= 0) o.inner_rtol = sys->mg ? (sys->fp32 ? 1e-3 : 1e-4) : (sys->fp32 ? 0.1 : 0.01);
+  if (o.inner_rtol <= 0)
+    o.inner_rtol = sys->conv ? (sys->fp32 ? 1e-2 : 1e-6)
+                             : sys->mg ? (sys->fp32 ? 1e-3 : 1e-4) : (sys->fp32 ? 0.1 : 0.01);
   if (o.max_iter <= 0) o.max_iter = 200000;
   if (o.max_refine <= 0) o.max_refine = 1000;
-  if (o.check_every <= 0) o.check_every = sys->mg ? 2 : 64;
+  if (o.check_every <= 0) o.check_every = sys->mg ? 2 : (sys->conv ? 16 : 64);
+}
+
+int solve_bicgstab(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats) {
+  return sys->fp32 ? bicgstab_typed<float>(sys, o, stats) : bicgstab_typed<double>(sys, o, stats);
 }
 
 int capture_solve(phfem_sys sys, const phfem_solve_opts* opts, cudaStream_t capture, int iters_per_body) {
+  if (sys->conv) return fail(PHFEM_EINVAL, "graph-captured steps: not with convection (use phfem_cn_step)");
   phfem_solve_opts o{};
   if (opts) o = *opts;
   fill_opts(sys, o);
@@ -657,6 +954,7 @@ int solve_system(phfem_sys sys, const phfem_solve_opts* opts, phfem_stats* stats
   phfem_solve_opts o{};
   if (opts) o = *opts;
   fill_opts(sys, o);
+  if (sys->conv) return solve_bicgstab(sys, o, stats);
   return sys->fp32 ? solve_typed<float>(sys, o, stats) : solve_typed<double>(sys, o, stats);
 }
 
@@ -668,7 +966,8 @@ int recover(phfem_sys sys, const double* x_new, const double* x_old, const doubl
   if (!U && !Lambda) return PHFEM_OK;
   prof_start(ctx, kProfRecover);
   k_recover<<<grid_for(ctx, nT), kBlock, 0, ctx->stream>>>(nT, m->t2e, m->sigma, m->lam_id, sys->Kt, m->elen,
-                                                           x_new, x_old, f_eff, inv_dt, theta, U, Lambda);
+                                                           x_new, x_old, f_eff, inv_dt, theta, sys->conv ? 1 : 0,
+                                                           U, Lambda);
   prof_stop(ctx, kProfRecover);
   return check_launch(ctx, "k_recover");
 }

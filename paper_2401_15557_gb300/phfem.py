@@ -37,7 +37,7 @@ class MeshInfo(C.Structure):
 
 class Coeffs(C.Structure):
     _fields_ = [("a_T", C.c_void_p), ("a", C.c_double), ("delta", C.c_double), ("dt", C.c_double),
-                ("precision", C.c_int32), ("form", C.c_int32)]
+                ("precision", C.c_int32), ("form", C.c_int32), ("A", C.c_double * 3), ("p", C.c_double * 2)]
 
 
 class SolveOpts(C.Structure):
@@ -284,9 +284,18 @@ def phfem_mesh_destroy(mesh):
 # --- assembly ----------------------------------------------------------------
 
 def phfem_assemble(mesh, f_mid=None, bc_mid=None, a_T=None, a=1.0, delta=0.0, dt=0.0, precision=PHFEM_FP64,
-                   form=PHFEM_FORM_TRACE):
+                   form=PHFEM_FORM_TRACE, A=None, p=None):
+    """A: constant SPD tensor as (A11, A12, A22) or a 2x2 array (None: identity);
+    p: constant convection velocity (px, py) (None: no convection)."""
     I = phfem_mesh_info_get(mesh)
     c = Coeffs(_ptr(a_T, torch.float64, I["nT"]), float(a), float(delta), float(dt), int(precision), int(form))
+    if A is not None:
+        import numpy as np
+        Aa = np.asarray(A, dtype=np.float64)
+        vals = (Aa[0, 0], Aa[0, 1], Aa[1, 1]) if Aa.shape == (2, 2) else tuple(Aa.ravel())
+        c.A = (C.c_double * 3)(*[float(v) for v in vals])
+    if p is not None:
+        c.p = (C.c_double * 2)(float(p[0]), float(p[1]))
     h = _H()
     _check(lib().phfem_assemble(mesh, C.byref(c), _ptr(f_mid, torch.float64, I["nE"]),
                                 _ptr(bc_mid, torch.float64, I["nE"]), C.byref(h)), "phfem_assemble")
