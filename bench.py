@@ -39,14 +39,27 @@ CPU_SAMPLE_LEVEL = 2
 SPMV_BYTES_PER_ROW = 4 * 4 + 4 * 4 + 4 + 4 + 4   # nbr, l (FP32), r, p, q
 # DRAM traffic of one cg_spmv launch at the full workload, from the ncu capture
 # summarised in profiles/cg_kernels_full_lshape_l5.md; valid only for the kernel
-# source whose hash is recorded with it.
+# source (k_cg_spmv and spmv_row) whose hash is recorded with it.
 SPMV_TRAFFIC = 465.73e6
-SPMV_TRAFFIC_SRC_SHA = "310db104b9112955"
+SPMV_TRAFFIC_SRC_SHA = "9f3f3644e1604c59"
 
 
-def _sha_solve_src():
-    p = os.path.join(ROOT, "paper_2401_15557_gb300", "csrc", "solve.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+def _function_src(path, signature):
+    """Source text of one function: from its signature to the closing brace at
+    column 0."""
+    src = open(path).read()
+    i = src.index(signature)
+    j = src.index("\n}\n", i)
+    return src[i:j + 3]
+
+
+def _sha_spmv_src():
+    """Hash of the SpMV kernel's own source (k_cg_spmv and spmv_row), so that
+    the captured traffic stays valid while unrelated code changes."""
+    csrc = os.path.join(ROOT, "paper_2401_15557_gb300", "csrc")
+    text = (_function_src(os.path.join(csrc, "solve.cu"), "__global__ void __launch_bounds__(kBlock) k_cg_spmv(")
+            + _function_src(os.path.join(csrc, "kernels.cuh"), "__device__ __forceinline__ T spmv_row("))
+    return hashlib.sha256(text.encode()).hexdigest()[:16]
 
 
 def parse():
@@ -60,6 +73,7 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--refine-steps", type=int, default=3, help="timed device refinements of the mesh (0: skip)")
     ap.add_argument("--mg-steps", type=int, default=3, help="timed steps of the multigrid variant (0: skip)")
+    ap.add_argument("--asm-runs", type=int, default=20, help="event-timed assembly runs (0: skip)")
     ap.add_argument("--mg-fp64", type=int, default=1, help="also time the FP64 multigrid variant")
     ap.add_argument("--mg-nu", type=int, default=0, help="multigrid smoothing degree (0: library default)")
     ap.add_argument("--mg-ratio", type=float, default=0.0, help="multigrid smoothing interval ratio (0: default)")
@@ -97,11 +111,14 @@ def problem():
 # CPU oracle (reported baseline, and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_step(mesh, aT):
+def oracle_step(mesh, aT, keep=None):
     from oracle import phfem_oracle as O
     t = time.perf_counter()
-    O.solve_saddle(mesh, problem(), aT=aT)
-    return time.perf_counter() - t
+    r = O.solve_saddle(mesh, problem(), aT=aT)
+    el = time.perf_counter() - t
+    if keep is not None:
+        keep["U"], keep["Lambda"] = r["U"], r["Lambda"]
+    return el
 
 
 def cpu_sample():
@@ -123,7 +140,10 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": f"lshape-jitter-level{CPU_SAMPLE_LEVEL}", "triangles": mesh.nT},
+            "data": "synthetic",
+            "config": {"workload": f"lshape-jitter-level{args.levels}", "sampled_level": CPU_SAMPLE_LEVEL,
+                       "sampled_triangles": mesh.nT, "rtol": 1e-10,
+                       "step": "oracle topology + saddle-point assembly + direct solve"},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -639,6 +659,29 @@ def main():
         e2e = {"value": world * nT * 1e3 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
 
+    # ---- assembly alone: median of 20 event-timed runs after warm-up ------------
+    asm20 = None
+    if args.asm_runs > 0:
+        mA = P.phfem_mesh_build(ctx, xy, tri, dd, nn)
+        res = {}
+        for prec, name in ((P.PHFEM_FP32_IR, "fp32_refined"), (P.PHFEM_FP64, "fp64")):
+            for _ in range(3):
+                P.phfem_sys_destroy(P.phfem_assemble(mA, f_mid, bc_mid, a_T=a, delta=1.0, precision=prec))
+            times = []
+            for _ in range(args.asm_runs):
+                e0, e1 = ev(), ev()
+                e0.record(stream)
+                sA = P.phfem_assemble(mA, f_mid, bc_mid, a_T=a, delta=1.0, precision=prec)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                times.append(e0.elapsed_time(e1))
+                P.phfem_sys_destroy(sA)
+            mt = statistics.median(times)
+            res[name] = {"ms": mt, "triangles_per_s": nT * 1e3 / mt}
+        P.phfem_mesh_destroy(mA)
+        asm20 = {"runs": args.asm_runs, **res,
+                 "note": "phfem_assemble alone (allocation, a3-a6 kernels, coefficient check)"}
+
     # ---- multigrid-preconditioned variant of the same step ----------------------
     # The level-0 mesh is refined on the device (the paper's refinement gives
     # the generator's triangles in the same order, so a_T carries over); the
@@ -749,7 +792,7 @@ def main():
     if spmv_n:
         avg = spmv_ms / spmv_n * 1e-3
         achieved = SPMV_BYTES_PER_ROW * nE / avg / 1e9
-        traffic = SPMV_TRAFFIC if SPMV_TRAFFIC_SRC_SHA == _sha_solve_src() else None
+        traffic = SPMV_TRAFFIC if SPMV_TRAFFIC_SRC_SHA == _sha_spmv_src() else None
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "k_cg_spmv<float>", "peak_source": peak_src,
                 "algorithmic_bytes_per_launch": SPMV_BYTES_PER_ROW * nE, "avg_launch_ms": avg * 1e3}
@@ -760,10 +803,35 @@ def main():
 
     # ---- CPU oracle on a bounded sample ---------------------------------------
     cpu = None
+    parity = None
     if rank == 0 and not args.no_cpu:
         cm, caT, sample = cpu_sample()
-        ts = [oracle_step(cm, caT) for _ in range(2)]
+        ref = {}
+        ts = [oracle_step(cm, caT, keep=ref) for _ in range(2)]
         cpu = {"value": cm.nT * len(ts) / sum(ts), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        # the same sample through the CUDA path: forward errors against the oracle's
+        # solution and the CSR pattern against the oracle's condensed system
+        from oracle import phfem_oracle as O
+        cs = O.condensed_system(cm, problem(), aT=caT)
+        mh = P.phfem_mesh_build(ctx, d(cm.xy, torch.float64), d(cm.tri, torch.int32),
+                                d(cm.dirichlet, torch.int32), d(cm.neumann, torch.int32))
+        ci = P.phfem_mesh_info_get(mh)
+        tabs = P.phfem_mesh_tables(mh)
+        pattern = bool(np.array_equal(tabs["row_ptr"].cpu().numpy(), cs["S"].indptr)
+                       and np.array_equal(tabs["col"].cpu().numpy(), cs["S"].indices))
+        parity = {"sample": f"level {CPU_SAMPLE_LEVEL} ({cm.nT} triangles)", "csr_pattern_bit_exact": pattern}
+        for prec, name in ((P.PHFEM_FP32_IR, "fp32_refined"), (P.PHFEM_FP64, "fp64")):
+            sh = P.phfem_assemble(mh, torch.ones(ci["nE"], dtype=torch.float64, device=dev),
+                                  torch.zeros(ci["nE"], dtype=torch.float64, device=dev),
+                                  a_T=d(caT, torch.float64), delta=1.0, precision=prec)
+            Uc = torch.empty(3 * ci["nT"], dtype=torch.float64, device=dev)
+            Lc = torch.empty(ci["nL"], dtype=torch.float64, device=dev)
+            stc = P.phfem_solve(sh, P.solve_opts(rtol=1e-10), U=Uc, Lambda=Lc)
+            P.phfem_sys_destroy(sh)
+            eu = float(np.max(np.abs(Uc.cpu().numpy() - ref["U"])) / np.max(np.abs(ref["U"])))
+            el = float(np.max(np.abs(Lc.cpu().numpy() - ref["Lambda"])) / np.max(np.abs(ref["Lambda"])))
+            parity[name] = {"U_max_rel_error": eu, "Lambda_max_rel_error": el, "rel_residual": stc["rel_residual"]}
+        P.phfem_mesh_destroy(mh)
 
     if rank == 0:
         med = lambda v: statistics.median(v) if v else None
@@ -782,7 +850,8 @@ def main():
             "solve": {"iterations": med(iters), "refinements": med(refs), "rel_residual_max": max(rel) if rel else None},
             "fp64": fp64, "e2e": e2e, "multigrid": mgres, "refine": refine, "roofline": roof,
             "kernels": kernel_share,
-            "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu,
+            "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu, "oracle_parity": parity,
+            "assembly_median_of_20": asm20,
         }
         print(json.dumps(line), flush=True)
     P.phfem_ctx_destroy(ctx)
