@@ -430,7 +430,10 @@ def run_serve(args):
     a = exp(0.5 z) and delta ~ U[0, 2] as in the batched workload, f = 1,
     homogeneous boundary data, FP32 + FP64 refinement; the server admits by a
     120 GB HBM budget.  Inputs are uploaded before the arrival clock starts;
-    latency = finish - submit."""
+    latency = finish - submit.  The same arrival stream is served twice: with
+    the meshes as given (Jacobi-PCG), and as refinement requests (the side n
+    realised as n0 2^k, n0 in [4, 8), the coarse n0-square refined k times by
+    the server, which then solves with the multigrid preconditioner)."""
     import numpy as np
     import torch
     import __graft_entry__
@@ -443,56 +446,117 @@ def run_serve(args):
     seed = I.seed_for(4, 0)
     u = I.uniform(seed ^ 0x5E5E, 4 * R)
     nT_target = np.exp(np.log(1e3) + u[0::4] * (np.log(4e6) - np.log(1e3)))
-    sides = np.maximum(2, np.rint(np.sqrt(nT_target / 2))).astype(int)
+    n_target = np.sqrt(nT_target / 2)
+    sides = np.maximum(2, np.rint(n_target)).astype(int)
     kinds = (u[1::4] < 0.3).astype(int)
     steps = 16 + np.floor(u[2::4] * 113).astype(int)
     arrivals = I.poisson_arrivals(R, args.rate, seed)
     d = lambda a, t: torch.as_tensor(np.ascontiguousarray(a), dtype=t, device=dev)
-    reqs, keep = [], []
-    t0 = time.perf_counter()
-    for i in range(R):
-        m, aT, delta = I.batch_member(i, int(sides[i]), workload=4)
-        t = dict(xy=d(m.xy, torch.float64), tri=d(m.tri, torch.int32), dd=d(m.dirichlet, torch.int32),
-                 nn=d(m.neumann, torch.int32), aT=d(aT, torch.float64),
-                 U=torch.empty(3 * m.nT, dtype=torch.float64, device=dev))
-        rq = P.make_request(t["xy"], t["tri"], t["dd"], t["nn"], kind=int(kinds[i]), a_T=t["aT"], delta=delta,
-                            f=1.0, dt=1.0 / sides[i], steps=int(steps[i]), precision=P.PHFEM_FP32_IR, U_out=t["U"])
-        reqs.append((rq, m.nT))
-        keep.append(t)
-    torch.cuda.synchronize()
-    t_setup = time.perf_counter() - t0
-    srv = P.phfem_server_create(args.slots, 120e9, P.solve_opts(rtol=1e-10))
-    clocks = ClockSampler(0) if not args.no_clocks else None
-    if clocks:
-        clocks.start()
-    start = time.perf_counter()
-    ids = []
-    for (rq, _), ta in zip(reqs, arrivals):
-        delay = ta - (time.perf_counter() - start)
-        if delay > 0:
-            time.sleep(delay)
-        ids.append(P.phfem_server_submit(srv, rq))
-    P.phfem_server_drain(srv)
-    clk = clocks.stop() if clocks else None
-    res = [P.phfem_server_poll(srv, i, wait=False) for i in ids]
-    P.phfem_server_destroy(srv)
-    meas = res[args.warmup:]
-    lat = np.array([r["t_finish"] - r["t_submit"] for r in meas]) * 1e3
-    wait = np.array([r["t_admit"] - r["t_submit"] for r in meas]) * 1e3
-    span = max(r["t_finish"] for r in meas) - min(r["t_submit"] for r in meas)
-    tri = sum(nt for (_, nt) in reqs[args.warmup:])
-    ok = sum(1 for r in meas if r["status"] == 0)
-    p50, p99 = float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
-    line = {"metric": METRIC, "value": ok / span, "unit": "solves/s", "n_gpus": 1, "steps": len(meas),
-            "warmup": args.warmup, "ms_per_step": 1e3 * span / len(meas), "higher_is_better": True,
+    ctx = P.phfem_ctx_create(torch.cuda.current_stream())
+
+    def member(i):
+        s_ = I.seed_for(4, i + 1)
+        return I.fourier_field(s_), 2.0 * float(I.uniform(s_ ^ 0xDE17A, 1)[0])
+
+    def a_T_device(fld, xy, tri):
+        """a_T = mean of a = exp(0.5 z) at the three edge midpoints, on the device."""
+        P_ = xy[tri.long()]
+        mids = [0.5 * (P_[:, 1] + P_[:, 2]), 0.5 * (P_[:, 0] + P_[:, 2]), 0.5 * (P_[:, 0] + P_[:, 1])]
+        acc = torch.zeros(tri.shape[0], dtype=torch.float64, device=dev)
+        for mxy in mids:
+            z = torch.zeros_like(acc)
+            for al, (kx, ky), ph in zip(fld.alpha, fld.k, fld.phi):
+                z += float(al) * torch.cos(2 * np.pi * (float(kx) * mxy[:, 0] + float(ky) * mxy[:, 1]) + float(ph))
+            acc += torch.exp(0.5 * z)
+        return acc / 3.0
+
+    def build(mode):
+        reqs, keep = [], []
+        for i in range(R):
+            fld, delta = member(i)
+            if mode == "jacobi":
+                m = I.square_mesh(int(sides[i]))
+                levels, n_real = 0, int(sides[i])
+            else:
+                k = max(0, int(np.floor(np.log2(n_target[i] / 4.0)))) if n_target[i] >= 8 else 0
+                n0 = max(2, int(np.rint(n_target[i] / 2 ** k)))
+                m = I.square_mesh(n0)
+                levels, n_real = k, n0 * 2 ** k
+            t = dict(xy=d(m.xy, torch.float64), tri=d(m.tri, torch.int32), dd=d(m.dirichlet, torch.int32),
+                     nn=d(m.neumann, torch.int32))
+            if levels == 0:
+                t["aT"] = d(I.element_mean_at_midpoints(m.xy, m.tri, fld.a), torch.float64)
+                nT_fine = m.nT
+            else:  # the coefficient on the refined mesh (the server refines the same way)
+                h = P.phfem_mesh_build(ctx, t["xy"], t["tri"], t["dd"], t["nn"])
+                hs = [h]
+                for _ in range(levels - 1):
+                    hs.append(P.phfem_mesh_refine(hs[-1]))
+                arr = P.phfem_mesh_refine(hs[-1], build=False, arrays=True)
+                for hh in reversed(hs):
+                    P.phfem_mesh_destroy(hh)
+                t["aT"] = a_T_device(fld, arr["xy"], arr["tri"])
+                nT_fine = arr["tri"].shape[0]
+                del arr
+            t["U"] = torch.empty(3 * nT_fine, dtype=torch.float64, device=dev)
+            rq = P.make_request(t["xy"], t["tri"], t["dd"], t["nn"], kind=int(kinds[i]), a_T=t["aT"], delta=delta,
+                                f=1.0, dt=1.0 / n_real, steps=int(steps[i]), precision=P.PHFEM_FP32_IR,
+                                U_out=t["U"], levels=levels)
+            reqs.append((rq, nT_fine))
+            keep.append(t)
+        torch.cuda.synchronize()
+        return reqs, keep
+
+    def serve(reqs):
+        srv = P.phfem_server_create(args.slots, 120e9, P.solve_opts(rtol=1e-10))
+        clocks = ClockSampler(0) if not args.no_clocks else None
+        if clocks:
+            clocks.start()
+        start = time.perf_counter()
+        ids = []
+        for (rq, _), ta in zip(reqs, arrivals):
+            delay = ta - (time.perf_counter() - start)
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(P.phfem_server_submit(srv, rq))
+        P.phfem_server_drain(srv)
+        clk = clocks.stop() if clocks else None
+        res = [P.phfem_server_poll(srv, i, wait=False) for i in ids]
+        P.phfem_server_destroy(srv)
+        meas = res[args.warmup:]
+        lat = np.array([r["t_finish"] - r["t_submit"] for r in meas]) * 1e3
+        wait = np.array([r["t_admit"] - r["t_submit"] for r in meas]) * 1e3
+        span = max(r["t_finish"] for r in meas) - min(r["t_submit"] for r in meas)
+        tri = sum(nt for (_, nt) in reqs[args.warmup:])
+        ok = sum(1 for r in meas if r["status"] == 0)
+        return {"solves_per_s": ok / span, "span_s": span, "p50_ms": float(np.percentile(lat, 50)),
+                "p99_ms": float(np.percentile(lat, 99)), "mean_queue_wait_ms": float(wait.mean()),
+                "triangles_per_s": tri / span, "ok": ok, "failed": len(meas) - ok,
+                "offered_triangles_per_s": tri / (arrivals[-1] - arrivals[args.warmup]) if len(meas) > 1 else None,
+                "iterations_median": float(np.median([r["iterations"] for r in meas])), "clocks": clk}
+
+    out = {}
+    for mode in ("jacobi", "multigrid"):
+        t0 = time.perf_counter()
+        reqs, keep = build(mode)
+        t_setup = time.perf_counter() - t0
+        out[mode] = serve(reqs)
+        out[mode]["setup_s"] = t_setup
+        del keep
+        torch.cuda.empty_cache()
+    P.phfem_ctx_destroy(ctx)
+    j = out["jacobi"]
+    nmeas = args.requests
+    line = {"metric": METRIC, "value": j["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": nmeas,
+            "warmup": args.warmup, "ms_per_step": 1e3 * j["span_s"] / nmeas, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": "serve-poisson", "rate_per_s": args.rate, "requests": len(meas),
+            "config": {"workload": "serve-poisson", "rate_per_s": args.rate, "requests": nmeas,
                        "slots": args.slots, "hbm_budget_gb": 120, "mix": "70% elliptic / 30% CN 16-128 steps",
                        "triangles": "log-uniform 1e3..4e6"},
-            "p50_ms": p50, "p99_ms": p99, "mean_queue_wait_ms": float(wait.mean()),
-            "triangles_per_s": tri / span, "ok": ok, "failed": len(meas) - ok,
-            "offered_triangles_per_s": tri / (arrivals[-1] - arrivals[args.warmup]) if len(meas) > 1 else None,
-            "setup_s": t_setup, "clocks": clk}
+            "p50_ms": j["p50_ms"], "p99_ms": j["p99_ms"], "mean_queue_wait_ms": j["mean_queue_wait_ms"],
+            "triangles_per_s": j["triangles_per_s"], "ok": j["ok"], "failed": j["failed"],
+            "offered_triangles_per_s": j["offered_triangles_per_s"], "setup_s": j["setup_s"], "clocks": j["clocks"],
+            "multigrid": out["multigrid"]}
     print(json.dumps(line), flush=True)
     return 0
 

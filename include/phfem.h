@@ -405,7 +405,11 @@ typedef struct phfem_server_s* phfem_server;
 
 /* One request: an elliptic solve (kind 0) or a Crank-Nicolson run (kind 1)
  * with constant data f, u_D, g (and u0 for kind 1).  Every pointer is device
- * memory owned by the caller and must stay valid until the request is done. */
+ * memory owned by the caller and must stay valid until the request is done.
+ * With levels > 0 the mesh is a coarse mesh that the server refines `levels`
+ * times (phfem_mesh_refine) and solves on the finest mesh with the multigrid
+ * preconditioner; a_T, U_out and Lambda_out then refer to the finest mesh
+ * (nT 4^levels triangles, in the refinement's order). */
 typedef struct {
   int32_t kind;            /* 0 elliptic, 1 Crank-Nicolson                               */
   int32_t nV, nT, nD, nN;
@@ -420,6 +424,8 @@ typedef struct {
   int32_t precision;       /* PHFEM_FP64 or PHFEM_FP32_IR                                   */
   double* U_out;           /* [3 nT] or NULL: u_h at the vertices (final time for kind 1)  */
   double* Lambda_out;      /* [nE] or NULL (room for nE, the first nL written)             */
+  int32_t levels;          /* 0: solve on the given mesh (Jacobi-PCG); > 0: see above      */
+  int32_t reserved;
 } phfem_request;
 
 typedef struct {

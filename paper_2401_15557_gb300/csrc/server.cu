@@ -9,7 +9,9 @@
 // tables, the condensed system, the Jacobi preconditioner and the time-stepping
 // state live on the device for the lifetime of a request.  Every request
 // records its submit, admit and finish times (seconds since the server started).
+#include <algorithm>
 #include <chrono>
+#include <cmath>
 #include <condition_variable>
 #include <deque>
 #include <map>
@@ -66,19 +68,36 @@ namespace {
 
 double estimate_bytes(const phfem_request& r) {
   // tables (~100 B/triangle), system (~150 B/edge at 1.5 edges/triangle),
-  // solver vectors and CN state: 400 B per triangle covers both kinds
-  return 400.0 * (double)r.nT + (double)(1 << 20);
+  // solver vectors and CN state: 400 B per triangle covers both kinds; a
+  // refinement hierarchy adds a third and the multigrid vectors
+  const double fine = (double)r.nT * std::pow(4.0, (double)std::max(0, r.levels));
+  return (r.levels > 0 ? 600.0 : 400.0) * fine + (double)(1 << 20);
 }
 
 int run_request(phfem_ctx ctx, const phfem_request& r, const phfem_solve_opts& opts, phfem_result& out) {
   cudaStream_t s = ctx->stream;
-  phfem_mesh m = nullptr;
-  PH_TRY(phfem_mesh_build(ctx, r.nV, r.xy, r.nT, r.tri, r.nD, r.dirichlet, r.nN, r.neumann, &m));
+  std::vector<phfem_mesh> H;  // the hierarchy, coarsest first (one mesh without refinement)
+  {
+    phfem_mesh m0 = nullptr;
+    PH_TRY(phfem_mesh_build(ctx, r.nV, r.xy, r.nT, r.tri, r.nD, r.dirichlet, r.nN, r.neumann, &m0));
+    H.push_back(m0);
+  }
+  int st = PHFEM_OK;
+  for (int l = 0; l < r.levels && st == PHFEM_OK; ++l) {
+    phfem_mesh f = nullptr;
+    st = phfem_mesh_refine(H.back(), nullptr, nullptr, nullptr, nullptr, &f);
+    if (st == PHFEM_OK) H.push_back(f);
+  }
+  if (st != PHFEM_OK) {
+    for (auto it = H.rbegin(); it != H.rend(); ++it) phfem_mesh_destroy(*it);
+    return st;
+  }
+  phfem_mesh m = H.back();
   const phfem_mesh_info I = m->info;
   out.nL = I.nL;
   out.nE = I.nE;
   double *f = nullptr, *bc = nullptr, *w0 = nullptr;
-  int st = dalloc_n(ctx, &f, I.nE);
+  st = dalloc_n(ctx, &f, I.nE);
   if (st == PHFEM_OK) st = dalloc_n(ctx, &bc, I.nE);
   if (st == PHFEM_OK && r.kind == 1) st = dalloc_n(ctx, &w0, I.nE);
   if (st == PHFEM_OK) {
@@ -86,9 +105,14 @@ int run_request(phfem_ctx ctx, const phfem_request& r, const phfem_solve_opts& o
     st = check_launch(ctx, "k_fill_edge_data");
   }
   phfem_sys sys = nullptr;
+  phfem_mg mg = nullptr;
   if (st == PHFEM_OK) {
     phfem_coeffs c{r.a_T, 1.0, r.delta, r.kind == 1 ? r.dt : 0.0, r.precision, PHFEM_FORM_TRACE};
     st = phfem_assemble(m, &c, r.kind == 1 ? nullptr : f, r.kind == 1 ? nullptr : bc, &sys);
+  }
+  if (st == PHFEM_OK && H.size() > 1) {
+    st = phfem_mg_create(sys, (int32_t)H.size(), H.data(), r.a_T, nullptr, &mg);
+    if (st == PHFEM_OK) st = phfem_sys_set_mg(sys, mg);
   }
   if (st == PHFEM_OK && r.kind == 0) {
     phfem_stats stats{};
@@ -109,11 +133,12 @@ int run_request(phfem_ctx ctx, const phfem_request& r, const phfem_solve_opts& o
       phfem_cn_destroy(cn);
     }
   }
+  if (mg) phfem_mg_destroy(mg);
   if (sys) phfem_sys_destroy(sys);
   dfree(ctx, f);
   dfree(ctx, bc);
   dfree(ctx, w0);
-  phfem_mesh_destroy(m);
+  for (auto it = H.rbegin(); it != H.rend(); ++it) phfem_mesh_destroy(*it);
   cudaError_t e = cudaStreamSynchronize(s);
   if (st == PHFEM_OK && e != cudaSuccess) st = cuda_fail(e, "server request", __FILE__, __LINE__);
   return st;
@@ -203,6 +228,8 @@ PHFEM_API int phfem_server_submit(phfem_server S, const phfem_request* req, int6
   if (req->kind != 0 && req->kind != 1) return fail(PHFEM_EINVAL, "phfem_server_submit: kind must be 0 or 1");
   if (req->kind == 1 && (!(req->dt > 0) || req->steps < 1))
     return fail(PHFEM_EINVAL, "phfem_server_submit: a Crank-Nicolson request needs dt > 0 and steps >= 1");
+  if (req->levels < 0 || req->levels > 12 || (double)req->nT * std::pow(4.0, req->levels) > 5e8)
+    return fail(PHFEM_EINVAL, "phfem_server_submit: levels in 0..12 and at most 5e8 refined triangles");
   int64_t my;
   {
     std::lock_guard<std::mutex> lock(S->mu);

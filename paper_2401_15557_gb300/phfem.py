@@ -64,7 +64,8 @@ class Request(C.Structure):
                 ("xy", C.c_void_p), ("tri", C.c_void_p), ("dirichlet", C.c_void_p), ("neumann", C.c_void_p),
                 ("a_T", C.c_void_p), ("delta", C.c_double), ("f", C.c_double), ("uD", C.c_double),
                 ("g", C.c_double), ("dt", C.c_double), ("u0", C.c_double), ("steps", C.c_int32),
-                ("precision", C.c_int32), ("U_out", C.c_void_p), ("Lambda_out", C.c_void_p)]
+                ("precision", C.c_int32), ("U_out", C.c_void_p), ("Lambda_out", C.c_void_p),
+                ("levels", C.c_int32), ("reserved", C.c_int32)]
 
 
 class Result(C.Structure):
@@ -435,13 +436,14 @@ def phfem_server_create(slots, hbm_budget_bytes, opts=None):
 
 
 def make_request(xy, tri, dirichlet, neumann, kind=0, a_T=None, delta=0.0, f=1.0, uD=0.0, g=0.0, dt=0.0, u0=0.0,
-                 steps=0, precision=PHFEM_FP32_IR, U_out=None, Lambda_out=None) -> Request:
+                 steps=0, precision=PHFEM_FP32_IR, U_out=None, Lambda_out=None, levels=0) -> Request:
     return Request(int(kind), xy.shape[0], tri.shape[0], dirichlet.shape[0] if dirichlet is not None else 0,
                    neumann.shape[0] if neumann is not None else 0, _ptr(xy, torch.float64), _ptr(tri, torch.int32),
                    _ptr(dirichlet, torch.int32) if dirichlet is not None and dirichlet.numel() else None,
                    _ptr(neumann, torch.int32) if neumann is not None and neumann.numel() else None,
                    _ptr(a_T, torch.float64), float(delta), float(f), float(uD), float(g), float(dt), float(u0),
-                   int(steps), int(precision), _ptr(U_out, torch.float64), _ptr(Lambda_out, torch.float64))
+                   int(steps), int(precision), _ptr(U_out, torch.float64), _ptr(Lambda_out, torch.float64),
+                   int(levels), 0)
 
 
 def phfem_server_submit(server, req: Request) -> int:
