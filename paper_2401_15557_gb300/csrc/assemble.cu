@@ -40,7 +40,11 @@ __global__ void k_asm_tri(int nT, const int32_t* __restrict__ tri, const double2
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nT; t += gridDim.x * blockDim.x) {
     const int v0 = tri[3 * t], v1 = tri[3 * t + 1], v2 = tri[3 * t + 2];
     const double a = aT ? aT[t] : a_const;
-    if (!(a > 0.0) || !isfinite(a)) atomicOr(bad, isfinite(a) ? 1 : 2);
+    // a > 0 and finite, tested on the bits (integer pipe): positive as a signed
+    // integer and an exponent below the all-ones of Inf / NaN
+    const long long ab = __double_as_longlong(a);
+    const bool finite = ((ab >> 52) & 0x7FF) != 0x7FF;
+    if (!(ab > 0 && finite)) atomicOr(bad, finite ? 1 : 2);
     double K[7];
     const double2 p0 = __ldg(xy + v0), p1 = __ldg(xy + v1), p2 = __ldg(xy + v2);
     tri_block(p0, p1, p2, a, delta, K, A11, A12, A22);
@@ -71,7 +75,7 @@ __device__ __forceinline__ void add_conv(const double* Kt, size_t n, int tp, int
 }
 
 // sK scales K^CR and sM the mass |T|/3 (elliptic: 1, 0; Crank-Nicolson: dt/2, 1).
-template <typename T>
+template <typename T, bool ELLIPTIC>
 __global__ void k_asm_rows(int nE, int nT, const int32_t* __restrict__ ed2el, const uint8_t* __restrict__ lk,
                            const uint8_t* __restrict__ eclass, const double* __restrict__ Kt,
                            const double* __restrict__ f_mid, const double* __restrict__ bc_mid,
@@ -83,9 +87,9 @@ __global__ void k_asm_rows(int nE, int nT, const int32_t* __restrict__ ed2el, co
     const int4 q = reinterpret_cast<const int4*>(ed2el)[e];
     const int kk = lk[e];
     const uint8_t cls = eclass[e];
-    EdgeRow R = edge_row(Kt, n, q.z, kk & 3, q.w, (kk >> 2) & 3, cls, f_mid ? f_mid[e] : 0.0,
-                         bc_mid ? bc_mid[e] : 0.0, cls == PHFEM_EDGE_NEUMANN ? elen[e] : 0.0, sK, sM, delta,
-                         f_mid != nullptr, bc_mid != nullptr);
+    EdgeRow R = edge_row<true, ELLIPTIC>(Kt, n, q.z, kk & 3, q.w, (kk >> 2) & 3, cls, f_mid ? f_mid[e] : 0.0,
+                                         bc_mid ? bc_mid[e] : 0.0, cls == PHFEM_EDGE_NEUMANN ? elen[e] : 0.0, sK,
+                                         sM, delta, f_mid != nullptr, bc_mid != nullptr);
     if (conv && cls != PHFEM_EDGE_DIRICHLET) add_conv(Kt, n, q.z, kk & 3, q.w, (kk >> 2) & 3, sK, R);
     val[e] = R.rpart;
 #pragma unroll
@@ -96,7 +100,8 @@ __global__ void k_asm_rows(int nE, int nT, const int32_t* __restrict__ ed2el, co
     b[e] = R.rhs;
     me[e] = R.mass;
     rdiag[e] = (T)R.rpart;
-    dinv[e] = (T)(1.0 / R.diag);
+    if constexpr (sizeof(T) == sizeof(float)) dinv[e] = 1.0f / (float)R.diag;  // inner precision suffices
+    else dinv[e] = (T)(1.0 / R.diag);
   }
 }
 
@@ -303,13 +308,26 @@ int assemble_into(phfem_sys sys, const double* f_mid, const double* bc_mid, int*
   }
   const double sK = c.dt > 0 ? 0.5 * c.dt : 1.0, sM = c.dt > 0 ? 1.0 : 0.0;
   prof_start(ctx, kProfAsmRows);
-  if (sys->fp32)
-    k_asm_rows<float><<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, nT, m->ed2el, m->lk, m->eclass, sys->Kt, f_mid,
+  const bool ell = c.dt == 0.0;
+  if (sys->fp32 && ell)
+    k_asm_rows<float, true><<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, nT, m->ed2el, m->lk, m->eclass, sys->Kt, f_mid,
+                                                                 bc_mid, m->elen, sK, sM, c.delta,
+                                                                 sys->conv ? 1 : 0, sys->val, sys->b, sys->me,
+                                                                 (float*)sys->lval, (float*)sys->rdiag,
+                                                                 (float*)sys->dinv);
+  else if (!sys->fp32 && ell)
+    k_asm_rows<double, true><<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, nT, m->ed2el, m->lk, m->eclass, sys->Kt,
+                                                                  f_mid, bc_mid, m->elen, sK, sM, c.delta,
+                                                                  sys->conv ? 1 : 0, sys->val, sys->b, sys->me,
+                                                                  (double*)sys->lval, (double*)sys->rdiag,
+                                                                  (double*)sys->dinv);
+  else if (sys->fp32)
+    k_asm_rows<float, false><<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, nT, m->ed2el, m->lk, m->eclass, sys->Kt, f_mid,
                                                            bc_mid, m->elen, sK, sM, c.delta, sys->conv ? 1 : 0,
                                                            sys->val, sys->b, sys->me, (float*)sys->lval,
                                                            (float*)sys->rdiag, (float*)sys->dinv);
   else
-    k_asm_rows<double><<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, nT, m->ed2el, m->lk, m->eclass, sys->Kt, f_mid,
+    k_asm_rows<double, false><<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, nT, m->ed2el, m->lk, m->eclass, sys->Kt, f_mid,
                                                             bc_mid, m->elen, sK, sM, c.delta, sys->conv ? 1 : 0,
                                                             sys->val, sys->b, sys->me, (double*)sys->lval,
                                                             (double*)sys->rdiag, (double*)sys->dinv);

@@ -32,15 +32,24 @@ __device__ __forceinline__ void tri_block(double2 p0, double2 p1, double2 p2, do
   const double mT = area2 * (1.0 / 6.0);       // |T|/3
   const double c = (a + a) / area2;            // a / |T|
   const double dm = delta * mT;
-  auto q = [&](double ux, double uy, double vx, double vy) {
-    return A22 * ux * vx - A12 * (ux * vy + uy * vx) + A11 * uy * vy;
-  };
-  out[0] = c * q(e0x, e0y, e0x, e0y) + dm;
-  out[1] = c * q(e1x, e1y, e1x, e1y) + dm;
-  out[2] = c * q(e2x, e2y, e2x, e2y) + dm;
-  out[3] = c * q(e0x, e0y, e1x, e1y);
-  out[4] = c * q(e1x, e1y, e2x, e2y);
-  out[5] = c * q(e2x, e2y, e0x, e0y);
+  if (A11 == 1.0 && A12 == 0.0 && A22 == 1.0) {  // A = I (uniform across a launch)
+    out[0] = c * (e0x * e0x + e0y * e0y) + dm;
+    out[1] = c * (e1x * e1x + e1y * e1y) + dm;
+    out[2] = c * (e2x * e2x + e2y * e2y) + dm;
+    out[3] = c * (e0x * e1x + e0y * e1y);
+    out[4] = c * (e1x * e2x + e1y * e2y);
+    out[5] = c * (e2x * e0x + e2y * e0y);
+  } else {
+    auto q = [&](double ux, double uy, double vx, double vy) {
+      return A22 * ux * vx - A12 * (ux * vy + uy * vx) + A11 * uy * vy;
+    };
+    out[0] = c * q(e0x, e0y, e0x, e0y) + dm;
+    out[1] = c * q(e1x, e1y, e1x, e1y) + dm;
+    out[2] = c * q(e2x, e2y, e2x, e2y) + dm;
+    out[3] = c * q(e0x, e0y, e1x, e1y);
+    out[4] = c * q(e1x, e1y, e2x, e2y);
+    out[5] = c * q(e2x, e2y, e0x, e0y);
+  }
   out[6] = mT;
 }
 
@@ -76,19 +85,35 @@ struct EdgeRow {
 // Row of edge e from the element blocks of T+ (tp, local kp) and T- (tm, km;
 // tm < 0 on the boundary); sK scales K^CR and sM the mass (elliptic 1, 0;
 // Crank-Nicolson dt/2, 1).  Dirichlet rows are identity rows holding u_D.
-template <bool RO = true>
+// ELLIPTIC: sK = 1 and sM = 0 (no scaling products).
+template <bool RO = true, bool ELLIPTIC = false>
 __device__ __forceinline__ EdgeRow edge_row(const double* Kt, size_t n, int tp, int kp, int tm,
                                             int km, uint8_t cls, double f, double bc, double elen, double sK,
                                             double sM, double delta, bool have_f, bool have_bc) {
   EdgeRow R;
   double d, o1, o2, mT;
   tri_row<RO>(Kt, n, tp, kp, d, o1, o2, mT);
-  double diag = sK * d + sM * mT, v1 = sK * o1, v2 = sK * o2, v3 = 0.0, v4 = 0.0, mass = mT;
+  double diag, v1, v2, v3 = 0.0, v4 = 0.0, mass = mT;
+  if (ELLIPTIC) {
+    diag = d;
+    v1 = o1;
+    v2 = o2;
+  } else {
+    diag = sK * d + sM * mT;
+    v1 = sK * o1;
+    v2 = sK * o2;
+  }
   if (tm >= 0) {
     tri_row<RO>(Kt, n, tm, km, d, o1, o2, mT);
-    diag += sK * d + sM * mT;
-    v3 = sK * o1;
-    v4 = sK * o2;
+    if (ELLIPTIC) {
+      diag += d;
+      v3 = o1;
+      v4 = o2;
+    } else {
+      diag += sK * d + sM * mT;
+      v3 = sK * o1;
+      v4 = sK * o2;
+    }
     mass += mT;
   }
   double rhs, rpart;
@@ -100,7 +125,7 @@ __device__ __forceinline__ EdgeRow edge_row(const double* Kt, size_t n, int tp, 
   } else {
     rhs = have_f ? mass * f : 0.0;
     if (cls == PHFEM_EDGE_NEUMANN && have_bc) rhs += elen * bc;
-    rpart = (sK * delta + sM) * mass;
+    rpart = ELLIPTIC ? delta * mass : (sK * delta + sM) * mass;
   }
   R.rpart = rpart;
   R.l[0] = -v1;

@@ -42,6 +42,7 @@ struct phfem_mg_s {
     void* d = nullptr;
     void* res = nullptr;
     int32_t* ct = nullptr;  // [nT][9] fine edges of each triangle (levels below the finest)
+    int32_t* parent = nullptr;  // [nE] parent codes of this level's edges (levels above the coarsest)
     double b = 0.0;         // Gershgorin bound of D^-1 A
   };
   phfem_sys fine = nullptr;
@@ -93,41 +94,54 @@ __global__ void k_mg_residual(int nE, const int32_t* __restrict__ nbr, const T* 
     res[e] = rhs[e] - spmv_row(nbr, lval, rdiag, z, m, e);
 }
 
-// zf += P zc.  Threads [0, nTc) own the middle-child edges of a coarse
-// triangle, threads [nTc, nTc + nEc) the two halves of a coarse edge.
-template <typename T>
-__global__ void k_mg_prolong(int nTc, int nEc, const int32_t* __restrict__ t2e, const int32_t* __restrict__ ed2el,
-                             const uint8_t* __restrict__ lk, const int32_t* __restrict__ ct,
-                             const uint8_t* __restrict__ eclass_f, uint8_t ident, const T* __restrict__ zc,
-                             T* __restrict__ zf, const SolveState* st, int want) {
-  if (skip(st, want)) return;
+// Parent of every fine edge (for the prolongation, one fine edge per thread):
+// (3t + k) << 2 for the middle-child edge opposite M_k of coarse triangle t,
+// (E << 2) | 1 and (E << 2) | 2 for the halves of coarse edge E next to
+// P_{kp+1} and P_{kp+2} of its T+, and 3 for identity rows (no correction).
+__global__ void k_mg_parent(int nTc, int nEc, const int32_t* __restrict__ ed2el, const uint8_t* __restrict__ lk,
+                            const int32_t* __restrict__ ct, const uint8_t* __restrict__ eclass_f, uint8_t ident,
+                            int32_t* __restrict__ parent) {
   const int n = nTc + nEc;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     if (i < nTc) {
-      const int t = i;
-      const T v0 = zc[t2e[3 * t]], v1 = zc[t2e[3 * t + 1]], v2 = zc[t2e[3 * t + 2]];
-      const int32_t* c = ct + 9 * (size_t)t;
-      zf[c[0]] += (T)0.5 * (v1 + v2);  // joins the midpoints of edges 1 and 2
-      zf[c[1]] += (T)0.5 * (v2 + v0);
-      zf[c[2]] += (T)0.5 * (v0 + v1);
+      for (int k = 0; k < 3; ++k) parent[ct[9 * (size_t)i + k]] = (3 * i + k) << 2;
     } else {
       const int E = i - nTc;
+      const int tp = ed2el[4 * E + 2], kp = lk[E] & 3;
+      const int hA = ct[9 * (size_t)tp + 3 + 2 * kp], hB = ct[9 * (size_t)tp + 4 + 2 * kp];
+      parent[hA] = eclass_f[hA] == ident ? 3 : ((E << 2) | 1);
+      parent[hB] = eclass_f[hB] == ident ? 3 : ((E << 2) | 2);
+    }
+  }
+}
+
+// zf += P zc, one fine edge per thread (coalesced on the fine side).
+template <typename T>
+__global__ void k_mg_prolong_f(int nEf, const int32_t* __restrict__ parent, const int32_t* __restrict__ t2e,
+                               const int32_t* __restrict__ ed2el, const uint8_t* __restrict__ lk,
+                               const T* __restrict__ zc, T* __restrict__ zf, const SolveState* st, int want) {
+  if (skip(st, want)) return;
+  for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nEf; f += gridDim.x * blockDim.x) {
+    const int code = parent[f], type = code & 3, id = code >> 2;
+    if (type == 3) continue;
+    T val;
+    if (type == 0) {  // joins the midpoints of edges k + 1 and k + 2 of coarse triangle t
+      const int t = id / 3, k = id - 3 * t;
+      val = (T)0.5 * (zc[t2e[3 * t + (k + 1) % 3]] + zc[t2e[3 * t + (k + 2) % 3]]);
+    } else {
+      const int E = id;
       const int tp = ed2el[4 * E + 2], tm = ed2el[4 * E + 3];
       const int kp = lk[E] & 3, km = (lk[E] >> 2) & 3;
       const T v = zc[E];
       const T p1 = zc[t2e[3 * tp + (kp + 1) % 3]], p2 = zc[t2e[3 * tp + (kp + 2) % 3]];
-      // halves next to P_{kp+1} (A) and P_{kp+2} (B) of T+
-      T vA = v - (T)0.5 * p1 + (T)0.5 * p2;
-      T vB = v - (T)0.5 * p2 + (T)0.5 * p1;
-      if (tm >= 0) {  // in T- the edge runs the other way: its P_{km+1} is P_{kp+2} of T+
+      // A: next to P_{kp+1} of T+ (P_{km+2} of T-); B: next to P_{kp+2} (P_{km+1} of T-)
+      val = type == 1 ? v - (T)0.5 * p1 + (T)0.5 * p2 : v - (T)0.5 * p2 + (T)0.5 * p1;
+      if (tm >= 0) {
         const T m1 = zc[t2e[3 * tm + (km + 1) % 3]], m2 = zc[t2e[3 * tm + (km + 2) % 3]];
-        vB = (T)0.5 * (vB + (v - (T)0.5 * m1 + (T)0.5 * m2));
-        vA = (T)0.5 * (vA + (v - (T)0.5 * m2 + (T)0.5 * m1));
+        val = (T)0.5 * (val + (type == 1 ? v - (T)0.5 * m2 + (T)0.5 * m1 : v - (T)0.5 * m1 + (T)0.5 * m2));
       }
-      const int hA = ct[9 * (size_t)tp + 3 + 2 * kp], hB = ct[9 * (size_t)tp + 4 + 2 * kp];
-      if (eclass_f[hA] != ident) zf[hA] += vA;
-      if (eclass_f[hB] != ident) zf[hB] += vB;
     }
+    zf[f] += val;
   }
 }
 
@@ -407,10 +421,9 @@ struct MgRun {
                                                                 (T*)C.rhs, st, want);
     PH_TRY(check_launch(ctx(l), "k_mg_restrict"));
     PH_TRY(vcycle(l - 1, (const T*)C.rhs, (T*)C.z));
-    k_mg_prolong<T><<<grid_for(ctx(l), (int64_t)C.nT + C.nE), kBlock, 0, s>>>(
-        C.nT, C.nE, C.mesh->t2e, C.mesh->ed2el, C.mesh->lk, C.ct, Lv.mesh->eclass, Lv.sys->ident_class,
-        (const T*)C.z, cur, st, want);
-    PH_TRY(check_launch(ctx(l), "k_mg_prolong"));
+    k_mg_prolong_f<T><<<grid_for(ctx(l), Lv.nE), kBlock, 0, s>>>(Lv.nE, Lv.parent, C.mesh->t2e, C.mesh->ed2el,
+                                                                  C.mesh->lk, (const T*)C.z, cur, st, want);
+    PH_TRY(check_launch(ctx(l), "k_mg_prolong_f"));
     T* alt = cur == zb ? z_out : zb;
     T* outp = nullptr;
     PH_TRY(smooth(l, rhs, cur, alt, false, mg->nu, cd.data(), cr.data(), &outp));
@@ -430,6 +443,7 @@ void mg_free(phfem_mg mg) {
     dfree(c, Lv.d);
     dfree(c, Lv.res);
     dfree(c, Lv.ct);
+    dfree(c, Lv.parent);
     if (Lv.owned && Lv.sys) phfem_sys_destroy(Lv.sys);
   }
   if (mg->fine && mg->fine->mg == mg) mg->fine->mg = nullptr;
@@ -548,6 +562,16 @@ PHFEM_API int phfem_mg_create(phfem_sys sys, int32_t nlevels, const phfem_mesh* 
   }
   for (int l = nlevels - 2; l >= 0; --l)
     if (aT[l]) dfree(ctx, aT[l]);
+  for (int l = 1; l < nlevels && st == PHFEM_OK; ++l) {
+    phfem_mg_s::Level& F = mg->L[l];
+    phfem_mg_s::Level& Cl = mg->L[l - 1];
+    chk(dalloc_n(ctx, &F.parent, (size_t)F.nE));
+    if (st != PHFEM_OK) break;
+    k_mg_parent<<<grid_for(ctx, (int64_t)Cl.nT + Cl.nE), kBlock, 0, s>>>(Cl.nT, Cl.nE, Cl.mesh->ed2el, Cl.mesh->lk,
+                                                                         Cl.ct, F.mesh->eclass, F.sys->ident_class,
+                                                                         F.parent);
+    chk(check_launch(ctx, "k_mg_parent"));
+  }
   for (int l = 0; l < nlevels && st == PHFEM_OK; ++l) {
     phfem_mg_s::Level& Lv = mg->L[l];
     k_mg_gershgorin<<<grid_for(ctx, Lv.nE), kBlock, 0, s>>>(Lv.nE, Lv.mesh->nbr, Lv.sys->val, flags + 1 + l);
@@ -637,10 +661,9 @@ PHFEM_API int phfem_mg_transfer(phfem_mg mg, int32_t level, int32_t direction, c
   cudaStream_t s = ctx->stream;
   if (direction == 0) {
     PH_CUDA(cudaMemsetAsync(out, 0, sizeof(double) * F.nE, s));
-    k_mg_prolong<double><<<grid_for(ctx, (int64_t)C.nT + C.nE), kBlock, 0, s>>>(
-        C.nT, C.nE, C.mesh->t2e, C.mesh->ed2el, C.mesh->lk, C.ct, F.mesh->eclass, F.sys->ident_class, in, out,
-        nullptr, 0);
-    return check_launch(ctx, "k_mg_prolong");
+    k_mg_prolong_f<double><<<grid_for(ctx, F.nE), kBlock, 0, s>>>(F.nE, F.parent, C.mesh->t2e, C.mesh->ed2el,
+                                                                   C.mesh->lk, in, out, nullptr, 0);
+    return check_launch(ctx, "k_mg_prolong_f");
   }
   k_mg_restrict<double><<<grid_for(ctx, C.nE), kBlock, 0, s>>>(C.nE, C.mesh->t2e, C.mesh->ed2el, C.mesh->lk,
                                                                 C.mesh->eclass, C.sys->ident_class, C.ct, in, out,
