@@ -40,6 +40,10 @@ SPMV_BYTES_PER_ROW = 4 * 4 + 4 * 4 + 4 + 4 + 4   # nbr, l (FP32), r, p, q
 # DRAM traffic of one cg_spmv launch at the full workload, from the ncu capture
 # summarised in profiles/cg_kernels_full_lshape_l5.md; valid only for the kernel
 # source (k_cg_spmv and spmv_row) whose hash is recorded with it.
+# Kernel timing inside the timed region brackets every 16th launch of each
+# kernel with CUDA events (an event between two launches keeps the second from
+# overlapping the first's drain, so timing every launch would slow the step).
+PROFILE_EVERY = 16
 SPMV_TRAFFIC = 465.73e6
 SPMV_TRAFFIC_SRC_SHA = "9f3f3644e1604c59"
 
@@ -643,7 +647,7 @@ def main():
     torch.cuda.synchronize()
     for k in ("cg_spmv", "cg_update", "cg_dir", "residual", "asm_tri", "asm_rows", "recover"):
         P.phfem_ctx_kernel_time(ctx, k, reset=True)
-    P.phfem_ctx_profile(ctx, True)
+    P.phfem_ctx_profile(ctx, PROFILE_EVERY)
     launches0 = P.phfem_ctx_launches(ctx)
     clocks = ClockSampler(torch.cuda.current_device()) if not args.no_clocks else None
     phases = []
@@ -862,8 +866,9 @@ def main():
                 "algorithmic_bytes_per_launch": SPMV_BYTES_PER_ROW * nE, "avg_launch_ms": avg * 1e3}
 
     tot_k = sum(v[0] for v in ktimes.values())
-    kernel_share = {k: {"ms": v[0], "launches": v[1], "share": v[0] / tot_k if tot_k else None}
+    kernel_share = {k: {"ms_timed": v[0], "timed_launches": v[1], "share": v[0] / tot_k if tot_k else None}
                     for k, v in ktimes.items()}
+    kernel_share["timed"] = f"every {PROFILE_EVERY}th launch of each kernel"
 
     # ---- CPU oracle on a bounded sample ---------------------------------------
     cpu = None

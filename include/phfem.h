@@ -82,8 +82,10 @@ PHFEM_API int64_t phfem_ctx_launches(phfem_ctx ctx);
  * kernels "cg_spmv", "cg_update", "cg_dir", "residual", "asm_tri", "asm_rows",
  * "recover" and of whole multigrid V-cycles ("mg_vcycle") are bracketed by
  * CUDA events on the context
- * stream.  phfem_ctx_kernel_time synchronises on the last event and returns
- * the summed device time (ms) and the number of timed launches of one kernel;
+ * stream; enable = n > 1 times only every n-th launch of each kernel (events
+ * between two launches keep the second from overlapping the first's drain).
+ * phfem_ctx_kernel_time synchronises on the last event and returns the summed
+ * device time (ms) and the number of timed launches of one kernel;
  * reset != 0 starts a new accumulation. */
 PHFEM_API int phfem_ctx_profile(phfem_ctx ctx, int enable);
 PHFEM_API int phfem_ctx_kernel_time(phfem_ctx ctx, const char* kernel, double* total_ms,

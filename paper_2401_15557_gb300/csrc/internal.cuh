@@ -74,6 +74,8 @@ enum ProfKernel { kProfSpmv = 0, kProfUpdate, kProfDir, kProfResidual, kProfAsmT
 struct ProfSlot {
   std::vector<cudaEvent_t> ev;  // start/stop pairs
   size_t used = 0;
+  int64_t calls = 0;            // launches seen since the last reset
+  bool armed = false;           // the current launch is being timed
 };
 }  // namespace phfem
 
@@ -85,6 +87,7 @@ struct phfem_ctx_s {
   int grid;              // blocks of the grid-stride kernels
   int64_t launches;
   bool profile = false;
+  int profile_every = 1;   // time every n-th launch of each kernel
   phfem::ProfSlot prof[phfem::kNumProf];
   phfem::SolveState* st_pinned = nullptr;  // pinned host mirror of a solver state, shared by the
                                            // context's systems (read right after each copy)

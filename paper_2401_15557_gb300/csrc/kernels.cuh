@@ -19,6 +19,30 @@ __device__ __forceinline__ T ld(const T* ptr) {
   else return *ptr;
 }
 
+// Programmatic dependent launch: iteration kernels are launched so that their
+// blocks may be scheduled while the previous kernel drains; each waits for the
+// previous grid to complete (and its writes to be visible) before it reads
+// anything, and lets the next kernel be scheduled at once.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, cudaStream_t s, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(kBlock);
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // K^CR_T = (a/|T|) e_k' A~ e_j + delta |T|/3 I for the triangle (p0, p1, p2),
 // e_k = P_{k+2} - P_{k+1}, A~ = [[A22, -A12], [-A12, A11]] (since |T| grad
 // lambda_k = the edge vector e_k turned by a right angle, over 2): out[0..2]

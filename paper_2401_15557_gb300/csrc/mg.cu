@@ -68,6 +68,7 @@ __global__ void k_mg_cheb(int nE, const int32_t* __restrict__ nbr, const T* __re
                           const T* __restrict__ rdiag, const T* __restrict__ dinv, const T* __restrict__ rhs,
                           const T* __restrict__ zin, T* __restrict__ zout, T* __restrict__ d, T cd, T cr, int mode,
                           const SolveState* st, int want) {
+  pdl_enter();
   if (skip(st, want)) return;
   const size_t m = (size_t)nE;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
@@ -88,6 +89,7 @@ template <typename T>
 __global__ void k_mg_residual(int nE, const int32_t* __restrict__ nbr, const T* __restrict__ lval,
                               const T* __restrict__ rdiag, const T* __restrict__ rhs, const T* __restrict__ z,
                               T* __restrict__ res, const SolveState* st, int want) {
+  pdl_enter();
   if (skip(st, want)) return;
   const size_t m = (size_t)nE;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x)
@@ -120,6 +122,7 @@ template <typename T>
 __global__ void k_mg_prolong_f(int nEf, const int32_t* __restrict__ parent, const int32_t* __restrict__ t2e,
                                const int32_t* __restrict__ ed2el, const uint8_t* __restrict__ lk,
                                const T* __restrict__ zc, T* __restrict__ zf, const SolveState* st, int want) {
+  pdl_enter();
   if (skip(st, want)) return;
   for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < nEf; f += gridDim.x * blockDim.x) {
     const int code = parent[f], type = code & 3, id = code >> 2;
@@ -151,6 +154,7 @@ __global__ void k_mg_restrict(int nEc, const int32_t* __restrict__ t2e, const in
                               const uint8_t* __restrict__ lk, const uint8_t* __restrict__ eclass_c, uint8_t ident,
                               const int32_t* __restrict__ ct, const T* __restrict__ rf, T* __restrict__ rc,
                               const SolveState* st, int want) {
+  pdl_enter();
   if (skip(st, want)) return;
   for (int E = blockIdx.x * blockDim.x + threadIdx.x; E < nEc; E += gridDim.x * blockDim.x) {
     if (eclass_c[E] == ident) {
@@ -377,9 +381,8 @@ struct MgRun {
     for (int k = 0; k < deg; ++k) {
       const int mode = k == 0 ? (from_zero ? 0 : 1) : 2;
       T* out = (k == 0 && from_zero) ? cur : other;
-      k_mg_cheb<T><<<g, kBlock, 0, s>>>(Lv.nE, Lv.mesh->nbr, (const T*)sy->lval, (const T*)sy->rdiag,
-                                        (const T*)sy->dinv, rhs, cur, out, (T*)Lv.d, (T)cd[k], (T)cr[k], mode, st,
-                                        want);
+      PH_CUDA(launch_pdl(k_mg_cheb<T>, g, s, Lv.nE, Lv.mesh->nbr, (const T*)sy->lval, (const T*)sy->rdiag,
+                         (const T*)sy->dinv, rhs, (const T*)cur, out, (T*)Lv.d, (T)cd[k], (T)cr[k], mode, st, want));
       PH_TRY(check_launch(ctx(l), "k_mg_cheb"));
       if (out != cur) std::swap(cur, other);
     }
@@ -412,17 +415,16 @@ struct MgRun {
     res = (T*)Lv.res;
     const int g = grid_for(ctx(l), Lv.nE);
     phfem_sys sy = Lv.sys;
-    k_mg_residual<T><<<g, kBlock, 0, s>>>(Lv.nE, Lv.mesh->nbr, (const T*)sy->lval, (const T*)sy->rdiag, rhs, cur,
-                                          res, st, want);
+    PH_CUDA(launch_pdl(k_mg_residual<T>, g, s, Lv.nE, Lv.mesh->nbr, (const T*)sy->lval, (const T*)sy->rdiag, rhs,
+                       (const T*)cur, res, st, want));
     PH_TRY(check_launch(ctx(l), "k_mg_residual"));
     phfem_mg_s::Level& C = mg->L[l - 1];
-    k_mg_restrict<T><<<grid_for(ctx(l), C.nE), kBlock, 0, s>>>(C.nE, C.mesh->t2e, C.mesh->ed2el, C.mesh->lk,
-                                                                C.mesh->eclass, C.sys->ident_class, C.ct, res,
-                                                                (T*)C.rhs, st, want);
+    PH_CUDA(launch_pdl(k_mg_restrict<T>, grid_for(ctx(l), C.nE), s, C.nE, C.mesh->t2e, C.mesh->ed2el, C.mesh->lk,
+                       C.mesh->eclass, C.sys->ident_class, C.ct, (const T*)res, (T*)C.rhs, st, want));
     PH_TRY(check_launch(ctx(l), "k_mg_restrict"));
     PH_TRY(vcycle(l - 1, (const T*)C.rhs, (T*)C.z));
-    k_mg_prolong_f<T><<<grid_for(ctx(l), Lv.nE), kBlock, 0, s>>>(Lv.nE, Lv.parent, C.mesh->t2e, C.mesh->ed2el,
-                                                                  C.mesh->lk, (const T*)C.z, cur, st, want);
+    PH_CUDA(launch_pdl(k_mg_prolong_f<T>, grid_for(ctx(l), Lv.nE), s, Lv.nE, Lv.parent, C.mesh->t2e,
+                       C.mesh->ed2el, C.mesh->lk, (const T*)C.z, cur, st, want));
     PH_TRY(check_launch(ctx(l), "k_mg_prolong_f"));
     T* alt = cur == zb ? z_out : zb;
     T* outp = nullptr;

@@ -50,6 +50,8 @@ static const char* kProfNames[kNumProf] = {"cg_spmv", "cg_update", "cg_dir", "re
 void prof_start(phfem_ctx ctx, int k) {
   if (!ctx->profile) return;
   ProfSlot& p = ctx->prof[k];
+  p.armed = (p.calls++ % ctx->profile_every) == 0;
+  if (!p.armed) return;
   if (p.used + 2 > p.ev.size()) {
     for (int i = 0; i < 2; ++i) {
       cudaEvent_t e;
@@ -63,7 +65,8 @@ void prof_start(phfem_ctx ctx, int k) {
 void prof_stop(phfem_ctx ctx, int k) {
   if (!ctx->profile) return;
   ProfSlot& p = ctx->prof[k];
-  if (p.used + 2 > p.ev.size()) return;
+  if (!p.armed || p.used + 2 > p.ev.size()) return;
+  p.armed = false;
   cudaEventRecord(p.ev[p.used + 1], ctx->stream);
   p.used += 2;
 }
@@ -235,6 +238,7 @@ PHFEM_API int64_t phfem_ctx_launches(phfem_ctx ctx) { return ctx ? ctx->launches
 PHFEM_API int phfem_ctx_profile(phfem_ctx ctx, int enable) {
   if (!ctx) return fail(PHFEM_EINVAL, "phfem_ctx_profile: NULL context");
   ctx->profile = enable != 0;
+  ctx->profile_every = enable > 1 ? enable : 1;
   return PHFEM_OK;
 }
 
@@ -255,7 +259,10 @@ PHFEM_API int phfem_ctx_kernel_time(phfem_ctx ctx, const char* kernel, double* t
   }
   if (total_ms) *total_ms = tot;
   if (launches) *launches = (int64_t)(p.used / 2);
-  if (reset) p.used = 0;
+  if (reset) {
+    p.used = 0;
+    p.calls = 0;
+  }
   return PHFEM_OK;
 }
 

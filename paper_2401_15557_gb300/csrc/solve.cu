@@ -171,6 +171,7 @@ __global__ void k_residual(int nE, const int32_t* __restrict__ nbr, const double
 template <typename T>
 __global__ void k_mg_finish(int nE, const T* __restrict__ ri, const T* __restrict__ zi, T* __restrict__ pi,
                             double* partials, SolveState* st, double rtol2, double inner_rtol2, int mode) {
+  pdl_enter();
   if (mode == 3) {
     if (st->done != 1) return;
     mode = 2;
@@ -209,6 +210,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_spmv(int nE, const int32_t* __res
                                                     T* __restrict__ p, T* __restrict__ q, const T* __restrict__ r,
                                                     const T* __restrict__ dinv, const T* __restrict__ zsrc,
                                                     double* partials, SolveState* st) {
+  pdl_enter();
   if (blockIdx.x == 0 && threadIdx.x == 0) st->dir_pending = 0;  // no block of this kernel reads it
   if (st->done) return;
   __shared__ double smem[kBlock / 32];
@@ -257,6 +259,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_update(int nE, double* __restrict
                                                       T* __restrict__ r, const T* __restrict__ q,
                                                       const T* __restrict__ dinv, double* partials,
                                                       SolveState* st) {
+  pdl_enter();
   if (st->done) return;
   __shared__ double smem[kBlock / 32];
   const double alpha64 = st->alpha;
@@ -291,6 +294,7 @@ template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cg_update_x(int nE, double* __restrict__ x, const T* __restrict__ p,
                                                         T* __restrict__ r, const T* __restrict__ q,
                                                         const SolveState* st) {
+  pdl_enter();
   if (st->done) return;
   const double alpha64 = st->alpha;
   const T alpha = (T)alpha64;
@@ -303,6 +307,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_update_x(int nE, double* __restri
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cg_rz(int nE, const T* __restrict__ r, const T* __restrict__ z,
                                                   double* partials, SolveState* st) {
+  pdl_enter();
   if (st->done) return;
   __shared__ double smem[kBlock / 32];
   T acc = (T)0;
@@ -327,6 +332,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_rz(int nE, const T* __restrict__ 
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cg_dir_z(int nE, const T* __restrict__ z, T* __restrict__ p,
                                                      SolveState* st) {
+  pdl_enter();
   if (!st->dir_pending) return;
   const T beta = (T)st->beta;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x)
@@ -341,6 +347,7 @@ __global__ void __launch_bounds__(kBlock) k_cg_dir_z(int nE, const T* __restrict
 template <typename T>
 __global__ void __launch_bounds__(kBlock) k_cg_dir(int nE, const T* __restrict__ r, const T* __restrict__ dinv,
                                                    T* __restrict__ p, SolveState* st) {
+  pdl_enter();
   if (!st->dir_pending) return;
   const T beta = (T)st->beta;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x)
@@ -672,8 +679,8 @@ struct Launch {
     prof_start(ctx, kProfMg);
     PH_TRY(mg_apply(sys->mg, s, sys->ri, mode == 3 ? sys->st : nullptr, 1));
     prof_stop(ctx, kProfMg);
-    k_mg_finish<T><<<g, kBlock, 0, s>>>(nE, (const T*)sys->ri, (const T*)mg_fine_z(sys->mg), (T*)sys->pi,
-                                        sys->partials, sys->st, rtol2, irtol2, mode);
+    PH_CUDA(launch_pdl(k_mg_finish<T>, g, s, nE, (const T*)sys->ri, (const T*)mg_fine_z(sys->mg), (T*)sys->pi,
+                       sys->partials, sys->st, rtol2, irtol2, mode));
     return check_launch(ctx, "k_mg_finish");
   }
   int iteration() const {
@@ -686,29 +693,31 @@ struct Launch {
     T* qi = (T*)sys->qi;
     const T* zmg = sys->mg ? (const T*)mg_fine_z(sys->mg) : nullptr;
     prof_start(ctx, kProfSpmv);
-    k_cg_spmv<T><<<g, kBlock, 0, s>>>(nE, sys->mesh->nbr, lval, rdiag, pi, qi, ri, dinv, zmg, sys->partials,
-                                      sys->st);
+    PH_CUDA(launch_pdl(k_cg_spmv<T>, g, s, nE, sys->mesh->nbr, lval, rdiag, pi, qi, ri, dinv, zmg, sys->partials,
+                       sys->st));
     prof_stop(ctx, kProfSpmv);
     if (sys->mg) {
       prof_start(ctx, kProfUpdate);
-      k_cg_update_x<T><<<g, kBlock, 0, s>>>(nE, sys->x, pi, ri, qi, sys->st);
+      PH_CUDA(launch_pdl(k_cg_update_x<T>, g, s, nE, sys->x, (const T*)pi, ri, (const T*)qi,
+                         (const SolveState*)sys->st));
       prof_stop(ctx, kProfUpdate);
       PH_TRY(check_launch(ctx, "k_cg_update_x"));
       prof_start(ctx, kProfMg);
       PH_TRY(mg_apply(sys->mg, s, ri, sys->st, 0));
       prof_stop(ctx, kProfMg);
       prof_start(ctx, kProfDir);
-      k_cg_rz<T><<<g, kBlock, 0, s>>>(nE, ri, zmg, sys->partials, sys->st);
-      k_cg_dir_z<T><<<g, kBlock, 0, s>>>(nE, zmg, pi, sys->st);
+      PH_CUDA(launch_pdl(k_cg_rz<T>, g, s, nE, (const T*)ri, zmg, sys->partials, sys->st));
+      PH_CUDA(launch_pdl(k_cg_dir_z<T>, g, s, nE, zmg, pi, sys->st));
       prof_stop(ctx, kProfDir);
       ctx->launches += 2;  // spmv and rz (update_x and dir_z counted by check_launch)
       return check_launch(ctx, "k_cg");
     }
     prof_start(ctx, kProfUpdate);
-    k_cg_update<T><<<g, kBlock, 0, s>>>(nE, sys->x, pi, ri, qi, dinv, sys->partials, sys->st);
+    PH_CUDA(launch_pdl(k_cg_update<T>, g, s, nE, sys->x, (const T*)pi, ri, (const T*)qi, dinv, sys->partials,
+                       sys->st));
     prof_stop(ctx, kProfUpdate);
     prof_start(ctx, kProfDir);
-    k_cg_dir<T><<<g, kBlock, 0, s>>>(nE, ri, dinv, pi, sys->st);
+    PH_CUDA(launch_pdl(k_cg_dir<T>, g, s, nE, (const T*)ri, dinv, pi, sys->st));
     prof_stop(ctx, kProfDir);
     ctx->launches += 2;
     return check_launch(ctx, "k_cg");

@@ -207,8 +207,10 @@ def phfem_ctx_launches(ctx) -> int:
     return int(lib().phfem_ctx_launches(ctx))
 
 
-def phfem_ctx_profile(ctx, enable: bool):
-    _check(lib().phfem_ctx_profile(ctx, int(bool(enable))), "phfem_ctx_profile")
+def phfem_ctx_profile(ctx, enable):
+    """enable: False/True, or n > 1 to time every n-th launch of each kernel."""
+    n = int(enable) if not isinstance(enable, bool) else int(enable)
+    _check(lib().phfem_ctx_profile(ctx, n), "phfem_ctx_profile")
 
 
 def phfem_ctx_kernel_time(ctx, kernel: str, reset: bool = True):
