@@ -843,7 +843,7 @@ def main():
         ms_ref = r0.elapsed_time(r1) / args.refine_steps
         refine = {"from_triangles": nT, "to_triangles": 4 * nT, "ms": ms_ref,
                   "refined_triangles_per_s": 4 * nT * 1e3 / ms_ref,
-                  "step": "refine kernels + phfem_mesh_build of the refined mesh"}
+                  "step": "phfem_mesh_refine: refined arrays and their tables in closed form"}
         P.phfem_mesh_destroy(mL)
 
     # ---- roofline of the dominant kernel (cg_spmv) ----------------------------

@@ -78,6 +78,8 @@ PHFEM_API const char* phfem_status_str(int status);
 PHFEM_API const char* phfem_last_error(void);
 /* Number of kernels the library launched on this context so far. */
 PHFEM_API int64_t phfem_ctx_launches(phfem_ctx ctx);
+/* A context, and everything built on it, is used by one host thread at a time
+ * (its systems share one pinned host mirror of the solver state). */
 /* Instrumentation (not part of the method): when enabled, launches of the
  * kernels "cg_spmv", "cg_update", "cg_dir", "residual", "asm_tri", "asm_rows",
  * "recover" and of whole multigrid V-cycles ("mg_vcycle") are bracketed by
@@ -151,8 +153,10 @@ PHFEM_API int phfem_mesh_destroy(phfem_mesh mesh);
  * Outputs (caller device buffers; each may be NULL, then a temporary is used):
  *   xy [nV + nE][2] double, tri [4 nT][3] int32, dirichlet [2 nD][2] int32,
  *   neumann [2 nN][2] int32.
- * If fine != NULL, the refined mesh is also built (phfem_mesh_build on those
- * arrays) and returned; with fine == NULL, xy and tri must be given.
+ * If fine != NULL, the refined mesh is also returned: its tables follow from the
+ * coarse ones in closed form (one scan, no sort) and equal those that
+ * phfem_mesh_build makes from the refined arrays; with fine == NULL, xy and
+ * tri must be given.
  * PHFEM_EINVAL when a refined count exceeds the int32 range. */
 PHFEM_API int phfem_mesh_refine(phfem_mesh coarse, double* xy, int32_t* tri, int32_t* dirichlet,
                                 int32_t* neumann, phfem_mesh* fine);
@@ -306,7 +310,9 @@ PHFEM_API int phfem_sys_set_mg(phfem_sys sys, phfem_mg mg);
  *   direction 1: out [nE_l] = P' in [nE_{l+1}]  (zero on Dirichlet edges of l) */
 PHFEM_API int phfem_mg_transfer(phfem_mg mg, int32_t level, int32_t direction, const double* in,
                                 double* out);
-/* Detaches the multigrid from its system and frees it (before the system). */
+/* Detaches the multigrid from its system and frees it.  Destroying the system
+ * first is allowed once the multigrid is attached (the multigrid then only
+ * frees its own levels). */
 PHFEM_API int phfem_mg_destroy(phfem_mg mg);
 
 /* ------------------------------------------------------------------------ */

@@ -261,6 +261,7 @@ void sys_free(phfem_sys s) {
   dfree(c, s->bc);
   dfree(c, s->St);
   dfree(c, s->bw);
+  if (s->mg) mg_forget_system(s->mg);
   dfree(c, s->x);
   dfree(c, s->r64);
   dfree(c, s->ri);

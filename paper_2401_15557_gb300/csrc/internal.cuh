@@ -174,6 +174,9 @@ int solve_system(phfem_sys sys, const phfem_solve_opts* opts, phfem_stats* stats
 int capture_solve(phfem_sys sys, const phfem_solve_opts* opts, cudaStream_t capture, int iters_per_body);
 int sys_init_x(phfem_sys sys, const double* w0);
 void fill_opts(phfem_sys sys, phfem_solve_opts& o);
+// Numbering of free edges and multipliers, neighbour slots, edge lengths and
+// the CSR pattern of a mesh whose xy, ed2el, lk, t2e and eclass are set.
+int mesh_finish(phfem_mesh m);
 // BiCGStab for systems with convection (same stopping rules and state).
 int solve_bicgstab(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats);
 // phfem_assemble without the host synchronisation that checks a_T (for
@@ -186,6 +189,9 @@ int recover(phfem_sys sys, const double* x_new, const double* x_old, const doubl
 // st != NULL every kernel runs only while st->done == want.
 int mg_apply(phfem_mg mg, cudaStream_t s, const void* r, const SolveState* st, int want);
 void* mg_fine_z(phfem_mg mg);
+// Called when the multigrid's system is destroyed first: the multigrid no
+// longer refers to it.
+void mg_forget_system(phfem_mg mg);
 
 // Device helpers ---------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {

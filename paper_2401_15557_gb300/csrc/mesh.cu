@@ -194,6 +194,15 @@ __global__ void k_class(int nE, const int32_t* __restrict__ ed2el, const int32_t
   }
 }
 
+__global__ void k_flags(int nE, const uint8_t* __restrict__ eclass, int32_t* __restrict__ isfree,
+                        int32_t* __restrict__ islam) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    const uint8_t c = eclass[e];
+    isfree[e] = c != PHFEM_EDGE_DIRICHLET;
+    islam[e] = c != PHFEM_EDGE_NEUMANN;
+  }
+}
+
 __global__ void k_ids(int nE, const int32_t* __restrict__ flag_free, const int32_t* __restrict__ flag_lam,
                       int32_t* __restrict__ free_id, int32_t* __restrict__ lam_id, const uint8_t* __restrict__ eclass) {
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
@@ -401,6 +410,23 @@ int build(phfem_ctx ctx, int nV, const double* xy, int nT, const int32_t* tri, i
   PH_TRY(check_launch(ctx, "k_class"));
   PH_TRY(check_status(ctx, err, "phfem_mesh_build"));
 
+  return mesh_finish(m);
+}
+
+}  // namespace
+
+// Free and multiplier numbering, neighbour slots, edge lengths and the CSR
+// pattern, from ed2el, lk, t2e, eclass and xy.
+int mesh_finish(phfem_mesh m) {
+  phfem_ctx ctx = m->ctx;
+  cudaStream_t s = ctx->stream;
+  const int nE = m->info.nE;
+  Temps tmp{ctx, {}};
+  int32_t *isfree, *islam;
+  PH_TRY(tmp.get(&isfree, (size_t)nE + 1));
+  PH_TRY(tmp.get(&islam, (size_t)nE + 1));
+  k_flags<<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, m->eclass, isfree, islam);
+  PH_TRY(check_launch(ctx, "k_flags"));
   PH_TRY(dalloc_n(ctx, &m->free_id, (size_t)nE));
   PH_TRY(dalloc_n(ctx, &m->lam_id, (size_t)nE));
   int32_t* totals;
@@ -437,7 +463,6 @@ int build(phfem_ctx ctx, int nV, const double* xy, int nT, const int32_t* tri, i
   return PHFEM_OK;
 }
 
-}  // namespace
 }  // namespace phfem
 
 using namespace phfem;

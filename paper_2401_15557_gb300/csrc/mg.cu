@@ -466,6 +466,11 @@ int mg_apply(phfem_mg mg, cudaStream_t s, const void* r, const SolveState* st, i
 
 void* mg_fine_z(phfem_mg mg) { return mg->L.back().z; }
 
+void mg_forget_system(phfem_mg mg) {
+  mg->fine = nullptr;
+  if (!mg->L.empty()) mg->L.back().sys = nullptr;
+}
+
 }  // namespace phfem
 
 using namespace phfem;
@@ -659,6 +664,7 @@ PHFEM_API int phfem_mg_transfer(phfem_mg mg, int32_t level, int32_t direction, c
     return fail(PHFEM_EINVAL, "phfem_mg_transfer: level in 0..levels-2, direction 0 or 1");
   phfem_mg_s::Level& C = mg->L[level];
   phfem_mg_s::Level& F = mg->L[level + 1];
+  if (!F.sys) return fail(PHFEM_EINVAL, "phfem_mg_transfer: the multigrid's system was destroyed");
   phfem_ctx ctx = C.mesh->ctx;
   cudaStream_t s = ctx->stream;
   if (direction == 0) {

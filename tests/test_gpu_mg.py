@@ -230,3 +230,72 @@ def test_rejections(ctx):
     other.close()
     shuffled.close()
     H.close()
+
+
+def test_system_destroyed_before_its_multigrid(ctx):
+    from phfem_gpu import dev
+    H = Hierarchy(ctx, I.square_mesh(3), 2)
+    P = H.P
+    pb = I.problem_sine_exp()
+    pb.delta = 1.0
+    aT = np.ones(H.meshes[-1].nT)
+    sysh = _system(H, pb, aT, P.PHFEM_FP64)
+    mg = P.phfem_mg_create(sysh, H.handles, a_T=dev(aT, torch.float64))
+    P.phfem_sys_set_mg(sysh, mg)
+    P.phfem_sys_destroy(sysh)
+    out = torch.empty(H.tables[1]["eclass"].size, dtype=torch.float64, device="cuda")
+    inp = torch.zeros(H.tables[0]["eclass"].size, dtype=torch.float64, device="cuda")
+    P.phfem_mg_transfer(mg, 0, 0, inp, out)  # level 1 is not the finest: still valid
+    with pytest.raises(P.PhfemError):
+        P.phfem_mg_transfer(mg, 1, 0, torch.zeros_like(out), torch.empty(H.tables[2]["eclass"].size,
+                                                                        dtype=torch.float64, device="cuda"))
+    P.phfem_mg_destroy(mg)
+    H.close()
+
+
+def test_full_size_lshape_multigrid(ctx):
+    """The benchmark's multigrid step at full size (level 0 refined five times on
+    the device, 6.3M triangles): the FP64 residual of the exported CSR system
+    meets the target, the iteration count stays small, and U equals the
+    element-major U of the Jacobi solve on the generator's level-5 mesh (the
+    same triangles in the same order)."""
+    import scipy.sparse as sp
+    from phfem_gpu import GpuMesh, dev, solve
+    from paper_2401_15557_gb300 import phfem as P
+    m0 = I.lshape_mesh(n=32, seed=I.seed_for(1, 0), levels=0)
+    h0 = P.phfem_mesh_build(ctx, dev(m0.xy, torch.float64), dev(m0.tri, torch.int32),
+                            dev(m0.dirichlet, torch.int32), dev(m0.neumann, torch.int32))
+    hs = [h0]
+    for _ in range(5):
+        hs.append(P.phfem_mesh_refine(hs[-1]))
+    fine = I.lshape_mesh(n=32, seed=I.seed_for(1, 0), levels=5)
+    aT = I.element_mean_at_midpoints(fine.xy, fine.tri, I.coeff_lshape)
+    info = P.phfem_mesh_info_get(hs[-1])
+    ones = torch.ones(info["nE"], dtype=torch.float64, device="cuda")
+    sysh = P.phfem_assemble(hs[-1], ones, torch.zeros_like(ones), a_T=dev(aT, torch.float64), delta=1.0,
+                            precision=P.PHFEM_FP32_IR)
+    mg = P.phfem_mg_create(sysh, hs, a_T=dev(aT, torch.float64))
+    P.phfem_sys_set_mg(sysh, mg)
+    U = torch.empty(3 * info["nT"], dtype=torch.float64, device="cuda")
+    w = torch.empty(info["nE"], dtype=torch.float64, device="cuda")
+    st = P.phfem_solve(sysh, P.solve_opts(rtol=1e-10), w=w, U=U)
+    assert st["converged"] in (1, 2) and st["iterations"] <= 60, st
+    target = max(1e-10, 2.0 * st["fp64_floor"])
+    assert st["rel_residual"] <= target, st
+    T = {k: v.cpu().numpy() for k, v in P.phfem_mesh_tables(hs[-1]).items()}
+    val = torch.empty(info["nnz"], dtype=torch.float64, device="cuda")
+    rhs = torch.empty(info["nF"], dtype=torch.float64, device="cuda")
+    P.phfem_sys_csr(sysh, val, rhs)
+    S = sp.csr_matrix((val.cpu().numpy(), T["col"], T["row_ptr"]), shape=(info["nF"], info["nF"]))
+    assert O.relative_residual(S, rhs.cpu().numpy(), w.cpu().numpy()[T["free_id"] >= 0]) <= 1.2 * target
+    # the same solution as Jacobi-PCG on the generator's numbering of the mesh
+    pb = I.Problem(f=lambda x, y: 1.0 + 0 * x, g=lambda x, y, nx, ny: 0 * x, uD=lambda x, y: 0 * x, delta=1.0)
+    gm = GpuMesh(fine, ctx)
+    out = solve(gm, pb, aT=aT, precision=1, rtol=1e-10)
+    Uj = out["U"]
+    assert np.max(np.abs(U.cpu().numpy() - Uj)) <= 1e-8 * np.max(np.abs(Uj))
+    gm.close()
+    P.phfem_mg_destroy(mg)
+    P.phfem_sys_destroy(sysh)
+    for h in reversed(hs):
+        P.phfem_mesh_destroy(h)

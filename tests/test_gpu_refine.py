@@ -92,3 +92,28 @@ def test_arrays_only_and_rejections(ctx):
         P.phfem_mesh_refine(gm.h, build=False, arrays=False)  # nothing to write to
     assert ei.value.status == P.PHFEM_EINVAL
     gm.close()
+
+
+@pytest.mark.parametrize("name", list(MESHES))
+def test_closed_form_tables_equal_the_sorted_build(ctx, name):
+    """The refined mesh's tables derived from the coarse ones equal, array by
+    array, those of phfem_mesh_build on the refined arrays (three levels)."""
+    from phfem_gpu import GpuMesh
+    from paper_2401_15557_gb300 import phfem as P
+    gm = GpuMesh(MESHES[name](), ctx)
+    h = gm.h
+    for level in range(3):
+        fine, arr = P.phfem_mesh_refine(h, build=True, arrays=True)
+        ref = P.phfem_mesh_build(ctx, arr["xy"], arr["tri"], arr["dirichlet"] if arr["dirichlet"].numel() else None,
+                                 arr["neumann"] if arr["neumann"].numel() else None)
+        a = {k: v.cpu().numpy() for k, v in P.phfem_mesh_tables(fine).items()}
+        b = {k: v.cpu().numpy() for k, v in P.phfem_mesh_tables(ref).items()}
+        assert P.phfem_mesh_info_get(fine) == P.phfem_mesh_info_get(ref)
+        for k in b:
+            assert np.array_equal(a[k], b[k]), (name, level, k)
+        P.phfem_mesh_destroy(ref)
+        if h is not gm.h:
+            P.phfem_mesh_destroy(h)
+        h = fine
+    P.phfem_mesh_destroy(h)
+    gm.close()

@@ -186,3 +186,24 @@ def test_full_size_lshape_fp32ir(ctx):
         ref = np.array([row[c] for c in cols])
         assert np.max(np.abs(out["val"][r0:r0 + len(row)] - ref)) <= 1e-12 * np.max(np.abs(ref))
     gm.close()
+
+
+def test_sampled_kernel_timing(ctx):
+    """phfem_ctx_profile(n) times every n-th launch of each kernel."""
+    from phfem_gpu import GpuMesh
+    from paper_2401_15557_gb300 import phfem as P
+    gm = GpuMesh(I.square_mesh(24), ctx)
+    pb = I.problem_sine_exp()
+    fm, bc = gm.edge_data(pb.f, pb.g, pb.uD)
+    sysh = P.phfem_assemble(gm.h, fm, bc, delta=0.0)
+    for k in ("cg_spmv", "cg_update", "cg_dir"):
+        P.phfem_ctx_kernel_time(ctx, k, reset=True)
+    P.phfem_ctx_profile(ctx, 8)
+    st = P.phfem_solve(sysh, P.solve_opts(rtol=1e-10, check_every=4))
+    P.phfem_ctx_profile(ctx, False)
+    ms, n = P.phfem_ctx_kernel_time(ctx, "cg_spmv", reset=True)
+    launches = st["iterations"]  # one spmv per iteration (the last chunk may add skipped launches)
+    assert n >= launches // 8 and n <= (launches + 8) // 8 + 2, (n, launches)
+    assert ms > 0.0
+    P.phfem_sys_destroy(sysh)
+    gm.close()
