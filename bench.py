@@ -565,6 +565,48 @@ def run_serve(args):
     return 0
 
 
+class Ranks:
+    """The processes of one launch: one per GPU under torchrun (RANK, WORLD_SIZE,
+    LOCAL_RANK, MASTER_ADDR/PORT from the environment), or a single process.
+    Replicas run the same workload with no collective on the data path; the
+    launch only synchronises and takes the slowest rank's time."""
+
+    def __init__(self, backend="nccl"):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.backend = backend
+        self.dist = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group(backend)
+            self.dist = dist
+
+    def barrier(self):
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, v, device=None):
+        """The largest v over the ranks (every rank gets it)."""
+        if self.dist is None:
+            return v
+        import torch
+        t = torch.tensor([float(v)], dtype=torch.float64, device=device if self.backend == "nccl" else "cpu")
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.dist is not None:
+            self.dist.destroy_process_group()
+            self.dist = None
+
+
+def weak_throughput(world, units_per_rank, ms_slowest):
+    """Whole-job throughput of `world` replicas that each processed
+    units_per_rank units, over the slowest rank's time."""
+    return world * units_per_rank * 1e3 / ms_slowest
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -579,16 +621,9 @@ def main():
     import numpy as np
     import torch
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        import torch.distributed as dist
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
-    else:
-        dist = None
-        torch.cuda.set_device(0)
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    ranks = Ranks("nccl")
+    world, rank = ranks.world, ranks.rank
 
     import __graft_entry__
     __graft_entry__.build()
@@ -630,16 +665,10 @@ def main():
             phases.append((e0, e1, e2, e3, st))
         return st
 
-    def barrier():
-        if dist is not None:
-            dist.barrier()
+    barrier = ranks.barrier
 
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return ranks.max(v, device=dev)
 
     # ---- main timed region: FP32 inner + FP64 refinement ------------------
     for _ in range(args.warmup):
@@ -678,7 +707,7 @@ def main():
         iters.append(st["iterations"])
         refs.append(st["refinements"])
         rel.append(st["rel_residual"])
-    value = world * nT * 1e3 / ms_step
+    value = weak_throughput(world, nT, ms_step)
 
     # ---- FP64 path ----------------------------------------------------------
     fp64 = None
@@ -693,7 +722,7 @@ def main():
         a1.record(stream)
         torch.cuda.synchronize()
         ms64 = max_over_ranks(a0.elapsed_time(a1)) / args.fp64_steps
-        fp64 = {"value": world * nT * 1e3 / ms64, "unit": UNIT, "ms_per_step": ms64,
+        fp64 = {"value": weak_throughput(world, nT, ms64), "unit": UNIT, "ms_per_step": ms64,
                 "solves_per_s": world * 1e3 / ms64, "iterations": ph64[-1][4]["iterations"],
                 "rel_residual": ph64[-1][4]["rel_residual"]}
 
@@ -724,7 +753,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
         ms_e2e = max_over_ranks(1e3 * (time.perf_counter() - t0)) / args.e2e_steps
-        e2e = {"value": world * nT * 1e3 / ms_e2e, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": weak_throughput(world, nT, ms_e2e), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "ms_per_step": ms_e2e}
 
     # ---- assembly alone: median of 20 event-timed runs after warm-up ------------
@@ -812,7 +841,7 @@ def main():
             msm = max_over_ranks(g0.elapsed_time(g1)) / args.mg_steps
             last = phm[-1]
             mg_out[name] = {
-                "value": world * nT * 1e3 / msm, "unit": UNIT, "ms_per_step": msm, "solves_per_s": world * 1e3 / msm,
+                "value": weak_throughput(world, nT, msm), "unit": UNIT, "ms_per_step": msm, "solves_per_s": world * 1e3 / msm,
                 "iterations": last[4]["iterations"], "refinements": last[4]["refinements"],
                 "rel_residual": last[4]["rel_residual"], "converged": last[4]["converged"],
                 "phases_ms_median": {
@@ -924,8 +953,7 @@ def main():
         }
         print(json.dumps(line), flush=True)
     P.phfem_ctx_destroy(ctx)
-    if dist is not None:
-        dist.destroy_process_group()
+    ranks.close()
     return 0
 
 
