@@ -73,6 +73,17 @@ typedef struct phfem_cn_s* phfem_cn;
  * (a cudaStream_t; NULL = the legacy default stream).  All work of handles
  * made from this context is ordered on that stream. */
 PHFEM_API int phfem_ctx_create(void* cuda_stream, phfem_ctx* out);
+/* Device memory of the context's handles normally comes from the stream-ordered
+ * allocator (cudaMallocAsync on the context stream).  With these callbacks it
+ * comes from the caller's allocator instead (for instance a framework's caching
+ * allocator, so that one pool owns all device memory): alloc returns `bytes` of
+ * device memory usable on `stream` (NULL on failure -> PHFEM_ENOMEM), free
+ * releases a pointer alloc returned, ordered on `stream`.  Both are called from
+ * the thread that calls the library. */
+typedef void* (*phfem_alloc_fn)(size_t bytes, void* stream, void* user);
+typedef void (*phfem_free_fn)(void* ptr, void* stream, void* user);
+PHFEM_API int phfem_ctx_create_with_allocator(void* cuda_stream, phfem_alloc_fn alloc, phfem_free_fn free_fn,
+                                              void* user, phfem_ctx* out);
 PHFEM_API int phfem_ctx_destroy(phfem_ctx ctx);
 PHFEM_API const char* phfem_status_str(int status);
 PHFEM_API const char* phfem_last_error(void);

@@ -89,6 +89,9 @@ struct phfem_ctx_s {
   bool profile = false;
   int profile_every = 1;   // time every n-th launch of each kernel
   phfem::ProfSlot prof[phfem::kNumProf];
+  phfem_alloc_fn alloc = nullptr;          // caller's allocator (NULL: cudaMallocAsync)
+  phfem_free_fn free_fn = nullptr;
+  void* alloc_user = nullptr;
   phfem::SolveState* st_pinned = nullptr;  // pinned host mirror of a solver state, shared by the
                                            // context's systems (read right after each copy)
 };

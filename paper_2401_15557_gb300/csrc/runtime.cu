@@ -24,6 +24,12 @@ int cuda_fail(cudaError_t err, const char* what, const char* file, int line) {
 
 int dalloc(phfem_ctx ctx, void** p, size_t bytes) {
   *p = nullptr;
+  if (ctx->alloc) {
+    *p = ctx->alloc(bytes, (void*)ctx->stream, ctx->alloc_user);
+    if (!*p) return fail(PHFEM_ENOMEM, std::string("device allocation of ") + std::to_string(bytes) +
+                                           " bytes failed (caller's allocator)");
+    return PHFEM_OK;
+  }
   cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -35,7 +41,9 @@ int dalloc(phfem_ctx ctx, void** p, size_t bytes) {
 }
 
 void dfree(phfem_ctx ctx, void* p) {
-  if (p) cudaFreeAsync(p, ctx->stream);
+  if (!p) return;
+  if (ctx->free_fn) ctx->free_fn(p, (void*)ctx->stream, ctx->alloc_user);
+  else cudaFreeAsync(p, ctx->stream);
 }
 
 int grid_for(phfem_ctx ctx, int64_t n) {
@@ -221,6 +229,18 @@ PHFEM_API int phfem_ctx_create(void* cuda_stream, phfem_ctx* out) {
   if (c->grid > kMaxGrid) c->grid = kMaxGrid;
   c->launches = 0;
   *out = c;
+  return PHFEM_OK;
+}
+
+PHFEM_API int phfem_ctx_create_with_allocator(void* cuda_stream, phfem_alloc_fn alloc, phfem_free_fn free_fn,
+                                              void* user, phfem_ctx* out) {
+  if (!out) return fail(PHFEM_EINVAL, "phfem_ctx_create_with_allocator: out is NULL");
+  *out = nullptr;
+  if (!alloc || !free_fn) return fail(PHFEM_EINVAL, "phfem_ctx_create_with_allocator: NULL callback");
+  PH_TRY(phfem_ctx_create(cuda_stream, out));
+  (*out)->alloc = alloc;
+  (*out)->free_fn = free_fn;
+  (*out)->alloc_user = user;
   return PHFEM_OK;
 }
 

@@ -100,6 +100,9 @@ class Errors(C.Structure):
 _lib = None
 _H = C.c_void_p
 _P = C.c_void_p
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+_allocators = {}  # context handle -> the callback objects (kept alive while the context exists)
 
 
 def lib() -> C.CDLL:
@@ -113,6 +116,7 @@ def lib() -> C.CDLL:
         L = C.CDLL(path)
         sig = {
             "phfem_ctx_create": (C.c_int, [_P, C.POINTER(_H)]),
+            "phfem_ctx_create_with_allocator": (C.c_int, [_P, _ALLOC_FN, _FREE_FN, _P, C.POINTER(_H)]),
             "phfem_ctx_destroy": (C.c_int, [_H]),
             "phfem_status_str": (C.c_char_p, [C.c_int]),
             "phfem_last_error": (C.c_char_p, []),
@@ -193,14 +197,39 @@ def _stream_ptr(stream=None):
 
 # --- context -----------------------------------------------------------------
 
-def phfem_ctx_create(stream=None):
+def phfem_ctx_create(stream=None, torch_allocator=False):
+    """A context on `stream`; with torch_allocator=True the library's device
+    memory comes from PyTorch's caching allocator (phfem_ctx_create_with_allocator)."""
     h = _H()
-    _check(lib().phfem_ctx_create(_stream_ptr(stream), C.byref(h)), "phfem_ctx_create")
+    if not torch_allocator:
+        _check(lib().phfem_ctx_create(_stream_ptr(stream), C.byref(h)), "phfem_ctx_create")
+        return h
+    device = torch.cuda.current_device()
+
+    def alloc(nbytes, strm, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device=device, stream=int(strm or 0))
+        except Exception:  # reported to the library as an allocation failure
+            return None
+
+    def free(ptr, strm, user):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    fa, ff = _ALLOC_FN(alloc), _FREE_FN(free)
+    _check(lib().phfem_ctx_create_with_allocator(_stream_ptr(stream), fa, ff, None, C.byref(h)),
+           "phfem_ctx_create_with_allocator")
+    _allocators[h.value] = (fa, ff)
     return h
+
+
+def phfem_ctx_create_with_allocator(stream=None):
+    """The context of phfem_ctx_create(stream, torch_allocator=True)."""
+    return phfem_ctx_create(stream, torch_allocator=True)
 
 
 def phfem_ctx_destroy(ctx):
     _check(lib().phfem_ctx_destroy(ctx), "phfem_ctx_destroy")
+    _allocators.pop(ctx.value if isinstance(ctx, _H) else ctx, None)
 
 
 def phfem_ctx_launches(ctx) -> int:

@@ -207,3 +207,44 @@ def test_sampled_kernel_timing(ctx):
     assert ms > 0.0
     P.phfem_sys_destroy(sysh)
     gm.close()
+
+
+def test_torch_caching_allocator_context():
+    """With the caller's allocator, the library's device memory is PyTorch's:
+    it shows in torch.cuda.memory_allocated while handles live and returns
+    after they are destroyed; results equal those of the default allocator."""
+    import torch
+    from phfem_gpu import dev
+    from paper_2401_15557_gb300 import phfem as P
+    mesh = I.lshape_mesh(n=8, seed=I.seed_for(1, 61), levels=1)
+    pb = I.problem_sine_exp()
+    pb.delta = 1.0
+    xy, tri = dev(mesh.xy, torch.float64), dev(mesh.tri, torch.int32)
+    dd, nn = dev(mesh.dirichlet, torch.int32), dev(mesh.neumann, torch.int32)
+    outs, deltas = [], []
+    for use_torch in (False, True):
+        c = P.phfem_ctx_create(torch.cuda.current_stream(), torch_allocator=use_torch)
+        torch.cuda.synchronize()
+        base = torch.cuda.memory_allocated()
+        m = P.phfem_mesh_build(c, xy, tri, dd, nn)
+        info = P.phfem_mesh_info_get(m)
+        tabs = {k: v.cpu().numpy() for k, v in P.phfem_mesh_tables(m).items()}
+        fm, bc = I.edge_data(mesh.xy, tabs["ed2el"], tabs["eclass"], pb.f, pb.g, pb.uD)
+        fm, bc = dev(fm, torch.float64), dev(bc, torch.float64)
+        s_ = P.phfem_assemble(m, fm, bc, delta=pb.delta, precision=1)
+        U = torch.empty(3 * info["nT"], dtype=torch.float64, device="cuda")
+        P.phfem_solve(s_, P.solve_opts(rtol=1e-10), U=U)
+        torch.cuda.synchronize()
+        during = torch.cuda.memory_allocated()
+        outs.append(U.cpu().numpy())
+        del U, fm, bc
+        P.phfem_sys_destroy(s_)
+        P.phfem_mesh_destroy(m)
+        torch.cuda.synchronize()
+        after = torch.cuda.memory_allocated()
+        P.phfem_ctx_destroy(c)
+        deltas.append(during - base)
+        if use_torch:
+            assert after == base, (base, after)
+    assert deltas[1] > deltas[0] + 200_000, deltas  # the library's buffers came from PyTorch
+    assert np.array_equal(outs[0], outs[1])
