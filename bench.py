@@ -286,6 +286,23 @@ def run_batched(args):
         tri_sample += m.nT
     torch.cuda.synchronize()
     t_single = time.perf_counter() - t0
+    # the batch's FP32 + refinement U of the eight smallest meshes against the
+    # oracle's direct saddle-point solve (the CPU-baseline leg)
+    parity = None
+    if not args.no_cpu:
+        from oracle import phfem_oracle as O
+        P.phfem_batch_solve(batch, count, delta, a_T=aT, f_mid=f, precision=P.PHFEM_FP32_IR, opts=opts, U=U)
+        Uh = U.cpu().numpy()
+        worst = 0.0
+        picks = np.argsort(sides, kind="stable")[:8]
+        for i in picks:
+            m, a, dl = members[i]
+            pb = I.Problem(f=lambda x, y: 1.0 + 0 * x, g=lambda x, y, nx, ny: 0 * x, uD=lambda x, y: 0 * x,
+                           delta=dl)
+            ref = O.solve_saddle(m, pb, aT=a)
+            got = Uh[3 * int(toff[i]):3 * int(toff[i + 1])]
+            worst = max(worst, float(np.max(np.abs(got - ref["U"])) / np.max(np.abs(ref["U"]))))
+        parity = {"meshes": [int(i) for i in picks], "U_max_rel_error": worst}
     line = {
         "metric": METRIC, "value": nT * 1e3 / ms, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -301,7 +318,7 @@ def run_batched(args):
         "single_mesh_fp64_sample": {"meshes": sample, "triangles_per_s": tri_sample / t_single,
                                     "solves_per_s": sample / t_single},
         "tune_ms_per_block": tune_ms, "setup_s": {"host_generation": t_gen, "tables": t_tables},
-        "clocks": clk,
+        "clocks": clk, "oracle_parity": parity,
     }
     print(json.dumps(line), flush=True)
     for h in meshes[:128]:
