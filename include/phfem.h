@@ -476,7 +476,7 @@ PHFEM_API int phfem_server_drain(phfem_server server);
 PHFEM_API int phfem_server_destroy(phfem_server server);
 
 /* ------------------------------------------------------------------------ */
-/* Error report (Section 5: L2 error, broken H1 error, mesh norm of kappa)   */
+/* Error report (Sec. 3.6 tables: L2 error, broken H1 error, mesh norm)     */
 /* ------------------------------------------------------------------------ */
 
 /* Quadrature of the report.  Triangles: a Duffy-collapsed nq x nq

@@ -1,5 +1,6 @@
-// Error report of a computed solution against an exact one (Section 5: the L2
-// error, the broken H1 error and the mesh norm of the multiplier error).
+// Error report of a computed solution against an exact one (the error tables
+// of Section 3.6: the L2 error, the broken H1 error and the mesh norm of the
+// multiplier error).
 //
 // The library owns the quadrature: a Duffy-collapsed nq x nq Gauss-Legendre
 // rule on every triangle (s = x_i, t = x_j (1 - x_i), weight w_i w_j (1 - x_i),

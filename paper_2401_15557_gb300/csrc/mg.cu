@@ -503,6 +503,8 @@ PHFEM_API int phfem_mg_create(phfem_sys sys, int32_t nlevels, const phfem_mesh* 
     if (F.nT != 4 * (int64_t)C.nT || F.nV != (int64_t)C.nV + C.nE)
       return fail(PHFEM_EINVAL, "phfem_mg_create: level " + std::to_string(l + 1) +
                                     " is not the red refinement of level " + std::to_string(l));
+    if (12 * (int64_t)C.nT >= (int64_t)INT32_MAX || 4 * (int64_t)C.nE >= (int64_t)INT32_MAX)
+      return fail(PHFEM_EINVAL, "phfem_mg_create: a coarse level exceeds the transfer tables' index range");
   }
   phfem_mg mg = new phfem_mg_s();
   mg->fine = sys;
