@@ -85,6 +85,9 @@ struct phfem_ctx_s {
   int device;
   int num_sms;
   int grid;              // blocks of the grid-stride kernels
+  size_t l2_persist_max = 0;  // largest L2 set-aside for persisting accesses (0: none)
+  size_t l2_window_max = 0;   // largest access-policy window
+  bool l2_limit_set = false;  // the set-aside was reserved (cudaLimitPersistingL2CacheSize)
   int64_t launches;
   bool profile = false;
   int profile_every = 1;   // time every n-th launch of each kernel
@@ -141,7 +144,8 @@ struct phfem_sys_s {
   // solver workspace
   double* x;             // [nE] current midpoint values (FP64)
   double* r64;           // [nE]
-  void* ri;              // [nE] inner vectors (float or double)
+  size_t l2_window;      // bytes of the r, p allocation (ri .. pi)
+  void* ri;              // [nE] inner vectors (float or double); pi follows ri in one allocation
   void* pi;
   void* qi;
   double* partials;      // [4][kMaxGrid]

@@ -28,19 +28,42 @@ __device__ __forceinline__ void pdl_enter() {
   asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
+// An L2 access-policy window: accesses inside [base, base + bytes) persist in
+// the L2 set-aside (with probability hit_ratio), others stream.  bytes == 0: none.
+struct L2Window {
+  void* base = nullptr;
+  size_t bytes = 0;
+  float hit_ratio = 0.f;
+};
+
 template <typename... KArgs, typename... Args>
-cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, cudaStream_t s, Args... args) {
+cudaError_t launch_pdl_w(const L2Window& w, void (*kernel)(KArgs...), int grid, cudaStream_t s, Args... args) {
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(kBlock);
   cfg.dynamicSmemBytes = 0;
   cfg.stream = s;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
   attr[0].val.programmaticStreamSerializationAllowed = 1;
+  int na = 1;
+  if (w.bytes > 0) {
+    attr[1].id = cudaLaunchAttributeAccessPolicyWindow;
+    attr[1].val.accessPolicyWindow.base_ptr = w.base;
+    attr[1].val.accessPolicyWindow.num_bytes = w.bytes;
+    attr[1].val.accessPolicyWindow.hitRatio = w.hit_ratio;
+    attr[1].val.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+    attr[1].val.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+    na = 2;
+  }
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = na;
   return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, cudaStream_t s, Args... args) {
+  return launch_pdl_w(L2Window{}, kernel, grid, s, args...);
 }
 
 // K^CR_T = (a/|T|) e_k' A~ e_j + delta |T|/3 I for the triangle (p0, p1, p2),

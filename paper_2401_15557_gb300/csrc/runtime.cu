@@ -220,7 +220,13 @@ PHFEM_API int phfem_ctx_create(void* cuda_stream, phfem_ctx* out) {
   PH_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
   phfem::SolveState* pinned = nullptr;
   PH_CUDA(cudaMallocHost((void**)&pinned, sizeof(phfem::SolveState)));
+  int persist = 0, window = 0;
+  if (cudaDeviceGetAttribute(&persist, cudaDevAttrMaxPersistingL2CacheSize, dev) != cudaSuccess) persist = 0;
+  if (cudaDeviceGetAttribute(&window, cudaDevAttrMaxAccessPolicyWindowSize, dev) != cudaSuccess) window = 0;
+  cudaGetLastError();
   phfem_ctx c = new phfem_ctx_s();
+  c->l2_persist_max = persist > 0 ? (size_t)persist : 0;
+  c->l2_window_max = window > 0 ? (size_t)window : 0;
   c->st_pinned = pinned;
   c->stream = (cudaStream_t)cuda_stream;
   c->device = dev;

@@ -659,12 +659,35 @@ int read_state(phfem_sys sys) {
   return PHFEM_OK;
 }
 
+// The L2 window over the r and p vectors of the inner iteration (both read
+// and written by every CG kernel), after reserving the L2 set-aside once per
+// context.
+L2Window rp_window(phfem_sys sys) {
+  phfem_ctx ctx = sys->mesh->ctx;
+  L2Window w;
+  if (ctx->l2_persist_max == 0 || ctx->l2_window_max == 0 || sys->l2_window == 0) return w;
+  if (!ctx->l2_limit_set) {
+    if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, ctx->l2_persist_max) != cudaSuccess) {
+      cudaGetLastError();
+      ctx->l2_persist_max = 0;
+      return w;
+    }
+    ctx->l2_limit_set = true;
+  }
+  w.base = sys->ri;
+  w.bytes = sys->l2_window < ctx->l2_window_max ? sys->l2_window : ctx->l2_window_max;
+  const double ratio = (double)ctx->l2_persist_max / (double)w.bytes;
+  w.hit_ratio = ratio >= 1.0 ? 1.0f : (float)ratio;
+  return w;
+}
+
 template <typename T>
 struct Launch {
   phfem_sys sys;
   cudaStream_t s;
   int g, nE;
   double rtol2, irtol2;
+  L2Window win;
   int residual(int mode) const {
     phfem_ctx ctx = sys->mesh->ctx;
     const int pre = (sys->mg && mode != 0) ? 1 : 0;
@@ -693,8 +716,8 @@ struct Launch {
     T* qi = (T*)sys->qi;
     const T* zmg = sys->mg ? (const T*)mg_fine_z(sys->mg) : nullptr;
     prof_start(ctx, kProfSpmv);
-    PH_CUDA(launch_pdl(k_cg_spmv<T>, g, s, nE, sys->mesh->nbr, lval, rdiag, pi, qi, ri, dinv, zmg, sys->partials,
-                       sys->st));
+    PH_CUDA(launch_pdl_w(win, k_cg_spmv<T>, g, s, nE, sys->mesh->nbr, lval, rdiag, pi, qi, ri, dinv, zmg,
+                         sys->partials, sys->st));
     prof_stop(ctx, kProfSpmv);
     if (sys->mg) {
       prof_start(ctx, kProfUpdate);
@@ -713,11 +736,11 @@ struct Launch {
       return check_launch(ctx, "k_cg");
     }
     prof_start(ctx, kProfUpdate);
-    PH_CUDA(launch_pdl(k_cg_update<T>, g, s, nE, sys->x, (const T*)pi, ri, (const T*)qi, dinv, sys->partials,
-                       sys->st));
+    PH_CUDA(launch_pdl_w(win, k_cg_update<T>, g, s, nE, sys->x, (const T*)pi, ri, (const T*)qi, dinv,
+                         sys->partials, sys->st));
     prof_stop(ctx, kProfUpdate);
     prof_start(ctx, kProfDir);
-    PH_CUDA(launch_pdl(k_cg_dir<T>, g, s, nE, (const T*)ri, dinv, pi, sys->st));
+    PH_CUDA(launch_pdl_w(win, k_cg_dir<T>, g, s, nE, (const T*)ri, dinv, pi, sys->st));
     prof_stop(ctx, kProfDir);
     ctx->launches += 2;
     return check_launch(ctx, "k_cg");
@@ -729,7 +752,8 @@ int solve_typed(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats) {
   phfem_mesh m = sys->mesh;
   phfem_ctx ctx = m->ctx;
   const int nE = m->info.nE;
-  const Launch<T> L{sys, ctx->stream, grid_for(ctx, nE), nE, o.rtol * o.rtol, o.inner_rtol * o.inner_rtol};
+  const Launch<T> L{sys, ctx->stream, grid_for(ctx, nE), nE, o.rtol * o.rtol, o.inner_rtol * o.inner_rtol,
+                    rp_window(sys)};
   static const bool verbose = getenv("PHFEM_VERBOSE") != nullptr;
   // ||b|| of the free-edge system (with the Dirichlet lifting), then the start
   PH_TRY(L.residual(0));
@@ -766,6 +790,10 @@ int solve_typed(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats) {
     if (h.it + chunk > o.max_iter) chunk = o.max_iter - h.it;
     for (int k = 0; k < chunk; ++k) PH_TRY(L.iteration());
     PH_TRY(read_state(sys));
+  }
+  if (L.win.bytes > 0) {  // the window's lines go back to normal L2 use
+    cudaCtxResetPersistingL2Cache();
+    cudaGetLastError();
   }
   const SolveState& h = *sys->st_host;
   const double rel = h.bb > 0 ? std::sqrt(h.rr64 / h.bb) : 0.0;
@@ -880,7 +908,7 @@ template <typename T>
 int capture_typed(phfem_sys sys, const phfem_solve_opts& o, cudaStream_t cs, int per_body) {
   phfem_ctx ctx = sys->mesh->ctx;
   const int nE = sys->mesh->info.nE;
-  const Launch<T> L{sys, cs, grid_for(ctx, nE), nE, o.rtol * o.rtol, o.inner_rtol * o.inner_rtol};
+  const Launch<T> L{sys, cs, grid_for(ctx, nE), nE, o.rtol * o.rtol, o.inner_rtol * o.inner_rtol, rp_window(sys)};
   PH_TRY(L.residual(0));
   PH_TRY(L.residual(1));
   cudaStreamCaptureStatus cst;
@@ -907,7 +935,7 @@ int capture_typed(phfem_sys sys, const phfem_solve_opts& o, cudaStream_t cs, int
   cudaError_t e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamBeginCaptureToGraph", __FILE__, __LINE__);
   if (st == PHFEM_OK) {
-    const Launch<T> B{sys, bs, L.g, nE, L.rtol2, L.irtol2};
+    const Launch<T> B{sys, bs, L.g, nE, L.rtol2, L.irtol2, L.win};
     for (int k = 0; k < per_body && st == PHFEM_OK; ++k) st = B.iteration();
     if (st == PHFEM_OK) st = B.residual(3);
     if (st == PHFEM_OK) {
