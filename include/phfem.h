@@ -91,6 +91,13 @@ PHFEM_API const char* phfem_last_error(void);
 PHFEM_API int64_t phfem_ctx_launches(phfem_ctx ctx);
 /* A context, and everything built on it, is used by one host thread at a time
  * (its systems share one pinned host mirror of the solver state). */
+/* Solves keep the iteration's residual and direction resident in L2 with an
+ * access-policy window when both fit the device's largest persisting set-aside;
+ * the set-aside (cudaLimitPersistingL2CacheSize, a limit of the process's CUDA
+ * context, released with it) is sized to the window, and the window's lines are
+ * reset after each solve.  Contexts driven from several host threads at once
+ * (the request server's) should turn the window off: the limit is shared. */
+PHFEM_API int phfem_ctx_set_l2_window(phfem_ctx ctx, int enable);
 /* Instrumentation (not part of the method): when enabled, launches of the
  * kernels "cg_spmv", "cg_update", "cg_dir", "residual", "asm_tri", "asm_rows",
  * "recover" and of whole multigrid V-cycles ("mg_vcycle") are bracketed by

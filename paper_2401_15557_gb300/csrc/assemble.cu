@@ -264,8 +264,7 @@ void sys_free(phfem_sys s) {
   if (s->mg) mg_forget_system(s->mg);
   dfree(c, s->x);
   dfree(c, s->r64);
-  dfree(c, s->ri);  // p lives in the same allocation
-  dfree(c, s->qi);
+  dfree(c, s->ri);  // p and q live in the same allocation
   dfree(c, s->partials);
   dfree(c, s->st);
   delete s;
@@ -406,13 +405,13 @@ int assemble_system(phfem_mesh mesh, const phfem_coeffs& c, const double* f_mid,
   if (c.form == PHFEM_FORM_FLUX) chk(dalloc_n(ctx, &sys->St, 9 * nT));
   chk(dalloc_n(ctx, &sys->x, nE));
   chk(dalloc_n(ctx, &sys->r64, nE));
-  {  // r and p in one allocation: the iteration keeps them resident in L2 as one window
+  {  // r, p and q in one allocation: the iteration keeps them resident in L2 as one window
     const size_t vb = (nE * isz + 255) / 256 * 256;
-    chk(dalloc(ctx, &sys->ri, 2 * vb));
+    chk(dalloc(ctx, &sys->ri, 3 * vb));
     sys->pi = st == PHFEM_OK ? (void*)((char*)sys->ri + vb) : nullptr;
-    sys->l2_window = 2 * vb;
+    sys->qi = st == PHFEM_OK ? (void*)((char*)sys->ri + 2 * vb) : nullptr;
+    sys->l2_vec = vb;
   }
-  chk(dalloc(ctx, &sys->qi, nE * isz));
   chk(dalloc_n(ctx, &sys->partials, 4 * (size_t)kMaxGrid));
   chk(dalloc_n(ctx, &sys->st, 1));
   chk(dalloc_n(ctx, &d_bad, 1));

@@ -87,7 +87,8 @@ struct phfem_ctx_s {
   int grid;              // blocks of the grid-stride kernels
   size_t l2_persist_max = 0;  // largest L2 set-aside for persisting accesses (0: none)
   size_t l2_window_max = 0;   // largest access-policy window
-  bool l2_limit_set = false;  // the set-aside was reserved (cudaLimitPersistingL2CacheSize)
+  size_t l2_limit = 0;        // the set-aside reserved now (cudaLimitPersistingL2CacheSize)
+  bool l2_window = true;      // solves may use an L2 persistence window
   int64_t launches;
   bool profile = false;
   int profile_every = 1;   // time every n-th launch of each kernel
@@ -144,8 +145,8 @@ struct phfem_sys_s {
   // solver workspace
   double* x;             // [nE] current midpoint values (FP64)
   double* r64;           // [nE]
-  size_t l2_window;      // bytes of the r, p allocation (ri .. pi)
-  void* ri;              // [nE] inner vectors (float or double); pi follows ri in one allocation
+  size_t l2_vec;         // bytes of one inner vector slot (r, p, q are consecutive slots)
+  void* ri;              // [nE] inner vectors (float or double); pi and qi follow ri in one allocation
   void* pi;
   void* qi;
   double* partials;      // [4][kMaxGrid]

@@ -261,6 +261,12 @@ PHFEM_API int phfem_ctx_destroy(phfem_ctx ctx) {
 
 PHFEM_API int64_t phfem_ctx_launches(phfem_ctx ctx) { return ctx ? ctx->launches : -1; }
 
+PHFEM_API int phfem_ctx_set_l2_window(phfem_ctx ctx, int enable) {
+  if (!ctx) return fail(PHFEM_EINVAL, "phfem_ctx_set_l2_window: NULL context");
+  ctx->l2_window = enable != 0;
+  return PHFEM_OK;
+}
+
 PHFEM_API int phfem_ctx_profile(phfem_ctx ctx, int enable) {
   if (!ctx) return fail(PHFEM_EINVAL, "phfem_ctx_profile: NULL context");
   ctx->profile = enable != 0;

@@ -207,7 +207,7 @@ PHFEM_API int phfem_server_create(int32_t slots, double hbm_budget_bytes, const 
     cudaStream_t s;
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
     phfem_ctx c = nullptr;
-    if (e != cudaSuccess || phfem_ctx_create(s, &c) != PHFEM_OK) {
+    if (e != cudaSuccess || phfem_ctx_create(s, &c) != PHFEM_OK || phfem_ctx_set_l2_window(c, 0) != PHFEM_OK) {
       for (size_t j = 0; j < S->ctxs.size(); ++j) {
         phfem_ctx_destroy(S->ctxs[j]);
         cudaStreamDestroy(S->streams[j]);

@@ -659,25 +659,43 @@ int read_state(phfem_sys sys) {
   return PHFEM_OK;
 }
 
-// The L2 window over the r and p vectors of the inner iteration (both read
-// and written by every CG kernel), after reserving the L2 set-aside once per
-// context.
+// The L2 window over the inner iteration's r and p (each read and written by
+// the CG kernels every iteration), with the L2 set-aside sized to it.  Used only
+// when both fit the largest set-aside: measured on the level-5 system, a window
+// that covers more than the set-aside (r, p and q with a 0.75 hit ratio), or a
+// set-aside larger than its window (r alone), is slower than no window at all.
+// Sets the device's persisting set-aside (0 releases it); not under a capture.
+bool set_l2_limit(phfem_ctx ctx, size_t bytes) {
+  if (ctx->l2_limit == bytes) return true;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return false;
+  }
+  if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  ctx->l2_limit = bytes;
+  return true;
+}
+
 L2Window rp_window(phfem_sys sys) {
   phfem_ctx ctx = sys->mesh->ctx;
   L2Window w;
-  if (ctx->l2_persist_max == 0 || ctx->l2_window_max == 0 || sys->l2_window == 0) return w;
-  if (!ctx->l2_limit_set) {
-    if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, ctx->l2_persist_max) != cudaSuccess) {
-      cudaGetLastError();
-      ctx->l2_persist_max = 0;
-      return w;
-    }
-    ctx->l2_limit_set = true;
+  const size_t want = 2 * sys->l2_vec;
+  if (!ctx->l2_window || want == 0 || want > ctx->l2_persist_max || want > ctx->l2_window_max) {
+    // no window: a set-aside left from an earlier solve would only shrink L2
+    if (ctx->l2_window) set_l2_limit(ctx, 0);
+    return w;
   }
+  if (!set_l2_limit(ctx, want)) return w;
   w.base = sys->ri;
-  w.bytes = sys->l2_window < ctx->l2_window_max ? sys->l2_window : ctx->l2_window_max;
-  const double ratio = (double)ctx->l2_persist_max / (double)w.bytes;
-  w.hit_ratio = ratio >= 1.0 ? 1.0f : (float)ratio;
+  w.bytes = want;
+  w.hit_ratio = 1.0f;
+  static const bool verbose = getenv("PHFEM_VERBOSE") != nullptr;
+  if (verbose)
+    fprintf(stderr, "phfem: L2 window %.1f MB, set-aside max %.1f MB\n", w.bytes / 1e6, ctx->l2_persist_max / 1e6);
   return w;
 }
 
@@ -721,16 +739,16 @@ struct Launch {
     prof_stop(ctx, kProfSpmv);
     if (sys->mg) {
       prof_start(ctx, kProfUpdate);
-      PH_CUDA(launch_pdl(k_cg_update_x<T>, g, s, nE, sys->x, (const T*)pi, ri, (const T*)qi,
-                         (const SolveState*)sys->st));
+      PH_CUDA(launch_pdl_w(win, k_cg_update_x<T>, g, s, nE, sys->x, (const T*)pi, ri, (const T*)qi,
+                           (const SolveState*)sys->st));
       prof_stop(ctx, kProfUpdate);
       PH_TRY(check_launch(ctx, "k_cg_update_x"));
       prof_start(ctx, kProfMg);
       PH_TRY(mg_apply(sys->mg, s, ri, sys->st, 0));
       prof_stop(ctx, kProfMg);
       prof_start(ctx, kProfDir);
-      PH_CUDA(launch_pdl(k_cg_rz<T>, g, s, nE, (const T*)ri, zmg, sys->partials, sys->st));
-      PH_CUDA(launch_pdl(k_cg_dir_z<T>, g, s, nE, zmg, pi, sys->st));
+      PH_CUDA(launch_pdl_w(win, k_cg_rz<T>, g, s, nE, (const T*)ri, zmg, sys->partials, sys->st));
+      PH_CUDA(launch_pdl_w(win, k_cg_dir_z<T>, g, s, nE, zmg, pi, sys->st));
       prof_stop(ctx, kProfDir);
       ctx->launches += 2;  // spmv and rz (update_x and dir_z counted by check_launch)
       return check_launch(ctx, "k_cg");
@@ -791,9 +809,10 @@ int solve_typed(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats) {
     for (int k = 0; k < chunk; ++k) PH_TRY(L.iteration());
     PH_TRY(read_state(sys));
   }
-  if (L.win.bytes > 0) {  // the window's lines go back to normal L2 use
+  if (L.win.bytes > 0) {  // the window's lines and the set-aside go back to normal L2 use
     cudaCtxResetPersistingL2Cache();
     cudaGetLastError();
+    set_l2_limit(ctx, 0);
   }
   const SolveState& h = *sys->st_host;
   const double rel = h.bb > 0 ? std::sqrt(h.rr64 / h.bb) : 0.0;

@@ -116,6 +116,7 @@ def lib() -> C.CDLL:
         L = C.CDLL(path)
         sig = {
             "phfem_ctx_create": (C.c_int, [_P, C.POINTER(_H)]),
+            "phfem_ctx_set_l2_window": (C.c_int, [_H, C.c_int]),
             "phfem_ctx_create_with_allocator": (C.c_int, [_P, _ALLOC_FN, _FREE_FN, _P, C.POINTER(_H)]),
             "phfem_ctx_destroy": (C.c_int, [_H]),
             "phfem_status_str": (C.c_char_p, [C.c_int]),
@@ -225,6 +226,10 @@ def phfem_ctx_create(stream=None, torch_allocator=False):
 def phfem_ctx_create_with_allocator(stream=None):
     """The context of phfem_ctx_create(stream, torch_allocator=True)."""
     return phfem_ctx_create(stream, torch_allocator=True)
+
+
+def phfem_ctx_set_l2_window(ctx, enable=True):
+    _check(lib().phfem_ctx_set_l2_window(ctx, int(bool(enable))), "phfem_ctx_set_l2_window")
 
 
 def phfem_ctx_destroy(ctx):
