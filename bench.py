@@ -38,14 +38,14 @@ LEVELS = 5
 CPU_SAMPLE_LEVEL = 2
 SPMV_BYTES_PER_ROW = 4 * 4 + 4 * 4 + 4 + 4 + 4   # nbr, l (FP32), r, p, q
 # DRAM traffic of one cg_spmv launch at the full workload, from the ncu capture
-# summarised in profiles/cg_kernels_full_lshape_l5.md; valid only for the kernel
-# source (k_cg_spmv and spmv_row) whose hash is recorded with it.
+# summarised in profiles/cg_kernels_l2_window_lshape_l5.md; valid only for the
+# kernel source and launch policy whose hash is recorded with it.
 # Kernel timing inside the timed region brackets every 16th launch of each
 # kernel with CUDA events (an event between two launches keeps the second from
 # overlapping the first's drain, so timing every launch would slow the step).
 PROFILE_EVERY = 16
-SPMV_TRAFFIC = 465.73e6
-SPMV_TRAFFIC_SRC_SHA = "9f3f3644e1604c59"
+SPMV_TRAFFIC = 479.54e6
+SPMV_TRAFFIC_SRC_SHA = "fb37e05a778acb44"
 
 
 def _function_src(path, signature):
@@ -58,11 +58,13 @@ def _function_src(path, signature):
 
 
 def _sha_spmv_src():
-    """Hash of the SpMV kernel's own source (k_cg_spmv and spmv_row), so that
-    the captured traffic stays valid while unrelated code changes."""
+    """Hash of the SpMV kernel's own source (k_cg_spmv, spmv_row) and of the L2
+    window it is launched with (rp_window), so that the captured traffic stays
+    valid while unrelated code changes."""
     csrc = os.path.join(ROOT, "paper_2401_15557_gb300", "csrc")
     text = (_function_src(os.path.join(csrc, "solve.cu"), "__global__ void __launch_bounds__(kBlock) k_cg_spmv(")
-            + _function_src(os.path.join(csrc, "kernels.cuh"), "__device__ __forceinline__ T spmv_row("))
+            + _function_src(os.path.join(csrc, "kernels.cuh"), "__device__ __forceinline__ T spmv_row(")
+            + _function_src(os.path.join(csrc, "solve.cu"), "L2Window rp_window(phfem_sys sys) {"))
     return hashlib.sha256(text.encode()).hexdigest()[:16]
 
 
