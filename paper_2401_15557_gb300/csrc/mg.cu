@@ -39,6 +39,7 @@ struct phfem_mg_s {
     void* rhs = nullptr;  // restricted right-hand side (coarse levels)
     void* z = nullptr;
     void* zb = nullptr;
+    size_t zbytes = 0;  // bytes of the z, zb allocation
     void* d = nullptr;
     void* res = nullptr;
     int32_t* ct = nullptr;  // [nT][9] fine edges of each triangle (levels below the finest)
@@ -370,6 +371,21 @@ struct MgRun {
 
   phfem_ctx ctx(int l) const { return mg->L[l].mesh->ctx; }
 
+  // The finest level's z, zb stay in L2 when the set-aside reserved for the
+  // iteration's window (r, p: the same size) can hold them.
+  L2Window window(int l) const {
+    L2Window w;
+    const phfem_mg_s::Level& Lv = mg->L[l];
+    phfem_ctx c = ctx(l);
+    if (l + 1 != (int)mg->L.size() || !c->l2_window || Lv.zbytes == 0 || c->l2_limit < Lv.zbytes ||
+        Lv.zbytes > c->l2_window_max)
+      return w;
+    w.base = Lv.z;
+    w.bytes = Lv.zbytes;
+    w.hit_ratio = 1.0f;
+    return w;
+  }
+
   int smooth(int l, const T* rhs, T* zin_out_first, T* zalt, bool from_zero, int deg, const double* cd,
              const double* cr, T** result) {
     // alternates between the two buffers; returns the buffer with the result
@@ -381,7 +397,7 @@ struct MgRun {
     for (int k = 0; k < deg; ++k) {
       const int mode = k == 0 ? (from_zero ? 0 : 1) : 2;
       T* out = (k == 0 && from_zero) ? cur : other;
-      PH_CUDA(launch_pdl(k_mg_cheb<T>, g, s, Lv.nE, Lv.mesh->nbr, (const T*)sy->lval, (const T*)sy->rdiag,
+      PH_CUDA(launch_pdl_w(window(l), k_mg_cheb<T>, g, s, Lv.nE, Lv.mesh->nbr, (const T*)sy->lval, (const T*)sy->rdiag,
                          (const T*)sy->dinv, rhs, (const T*)cur, out, (T*)Lv.d, (T)cd[k], (T)cr[k], mode, st, want));
       PH_TRY(check_launch(ctx(l), "k_mg_cheb"));
       if (out != cur) std::swap(cur, other);
@@ -415,7 +431,8 @@ struct MgRun {
     res = (T*)Lv.res;
     const int g = grid_for(ctx(l), Lv.nE);
     phfem_sys sy = Lv.sys;
-    PH_CUDA(launch_pdl(k_mg_residual<T>, g, s, Lv.nE, Lv.mesh->nbr, (const T*)sy->lval, (const T*)sy->rdiag, rhs,
+    PH_CUDA(launch_pdl_w(window(l), k_mg_residual<T>, g, s, Lv.nE, Lv.mesh->nbr, (const T*)sy->lval,
+                         (const T*)sy->rdiag, rhs,
                        (const T*)cur, res, st, want));
     PH_TRY(check_launch(ctx(l), "k_mg_residual"));
     phfem_mg_s::Level& C = mg->L[l - 1];
@@ -423,7 +440,7 @@ struct MgRun {
                        C.mesh->eclass, C.sys->ident_class, C.ct, (const T*)res, (T*)C.rhs, st, want));
     PH_TRY(check_launch(ctx(l), "k_mg_restrict"));
     PH_TRY(vcycle(l - 1, (const T*)C.rhs, (T*)C.z));
-    PH_CUDA(launch_pdl(k_mg_prolong_f<T>, grid_for(ctx(l), Lv.nE), s, Lv.nE, Lv.parent, C.mesh->t2e,
+    PH_CUDA(launch_pdl_w(window(l), k_mg_prolong_f<T>, grid_for(ctx(l), Lv.nE), s, Lv.nE, Lv.parent, C.mesh->t2e,
                        C.mesh->ed2el, C.mesh->lk, (const T*)C.z, cur, st, want));
     PH_TRY(check_launch(ctx(l), "k_mg_prolong_f"));
     T* alt = cur == zb ? z_out : zb;
@@ -440,8 +457,7 @@ void mg_free(phfem_mg mg) {
     if (!Lv.mesh) continue;
     phfem_ctx c = Lv.mesh->ctx;
     dfree(c, Lv.rhs);
-    dfree(c, Lv.z);
-    dfree(c, Lv.zb);
+    dfree(c, Lv.z);  // zb lives in the same allocation
     dfree(c, Lv.d);
     dfree(c, Lv.res);
     dfree(c, Lv.ct);
@@ -539,8 +555,12 @@ PHFEM_API int phfem_mg_create(phfem_sys sys, int32_t nlevels, const phfem_mesh* 
       chk(check_launch(ctx, "k_mg_ct"));
     }
     chk(dalloc(ctx, &Lv.rhs, es * Lv.nE + 16));
-    chk(dalloc(ctx, &Lv.z, es * Lv.nE + 16));
-    chk(dalloc(ctx, &Lv.zb, es * Lv.nE + 16));
+    {  // z and zb in one allocation (one L2 window covers both on the finest level)
+      const size_t vb = (es * Lv.nE + 255) / 256 * 256;
+      chk(dalloc(ctx, &Lv.z, 2 * vb));
+      Lv.zb = st == PHFEM_OK ? (void*)((char*)Lv.z + vb) : nullptr;
+      Lv.zbytes = 2 * vb;
+    }
     chk(dalloc(ctx, &Lv.d, es * Lv.nE + 16));
     if (l > 0) chk(dalloc(ctx, &Lv.res, es * Lv.nE + 16));
   }
