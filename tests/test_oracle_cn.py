@@ -9,7 +9,7 @@ from paper_2401_15557_gb300 import inputs as I
 
 def test_example2_orders_against_printed_orders():
     """Convergence orders with h = k (the printed errors themselves include a
-    contribution of the unprinted driver; with a solution linear in t the
+    contribution of the paper's unprinted main program; with a solution linear in t the
     scheme as printed has no time error, so only the orders are compared)."""
     rows = read_golden_rows("paper_example2_orders.txt")
     pb = I.problem_paper_example2()
