@@ -683,14 +683,19 @@ bool set_l2_limit(phfem_ctx ctx, size_t bytes) {
 L2Window rp_window(phfem_sys sys) {
   phfem_ctx ctx = sys->mesh->ctx;
   L2Window w;
-  const size_t want = 2 * sys->l2_vec;
+  size_t want = 2 * sys->l2_vec;
+  void* base = sys->ri;
+  if (want > ctx->l2_persist_max || want > ctx->l2_window_max) {  // p alone (the gathered vector)
+    want = sys->l2_vec;
+    base = sys->pi;
+  }
   if (!ctx->l2_window || want == 0 || want > ctx->l2_persist_max || want > ctx->l2_window_max) {
     // no window: a set-aside left from an earlier solve would only shrink L2
     if (ctx->l2_window) set_l2_limit(ctx, 0);
     return w;
   }
   if (!set_l2_limit(ctx, want)) return w;
-  w.base = sys->ri;
+  w.base = base;
   w.bytes = want;
   w.hit_ratio = 1.0f;
   static const bool verbose = getenv("PHFEM_VERBOSE") != nullptr;
