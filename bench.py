@@ -44,8 +44,8 @@ SPMV_BYTES_PER_ROW = 4 * 4 + 4 * 4 + 4 + 4 + 4   # nbr, l (FP32), r, p, q
 # kernel with CUDA events (an event between two launches keeps the second from
 # overlapping the first's drain, so timing every launch would slow the step).
 PROFILE_EVERY = 16
-SPMV_TRAFFIC = 479.54e6
-SPMV_TRAFFIC_SRC_SHA = "fb37e05a778acb44"
+SPMV_TRAFFIC = 478.84e6
+SPMV_TRAFFIC_SRC_SHA = "c0c7c313896d081d"
 
 
 def _function_src(path, signature):
