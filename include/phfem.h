@@ -202,8 +202,10 @@ typedef struct {
 enum { PHFEM_FORM_TRACE = 0, PHFEM_FORM_FLUX = 1 };
 
 /* Assembles, per triangle, the stiffness/reaction blocks of Definition 3.1
- * condensed to the edge midpoints, K^CR_T = R^-T (a_T B_T + delta M_T) R^-1
- * = a_T |T|^-1 (e_k . e_j) + delta |T|/3 I (e_k the edge vectors), and the
+ * condensed to the edge midpoints, K^CR_T = R^-T (a_T B_T + D_T + delta M_T) R^-1
+ * = a_T |T|^-1 (e_k' A~ e_j) + delta |T|/3 I + the convection columns
+ * (p_x e_jy - p_y e_jx)/3 (e_k the edge vectors, A~ = [[A22, -A12], [-A12, A11]],
+ * A = I unless given), and the
  * edge right-hand side of the midpoint quadrature of Eqs. right_b/right_g:
  *   rhs_e = sum_{T owning e} |T|/3 f(m_e) + [e Neumann] |E| g(m_e).
  * Dirichlet values enter through the matrix (lifting) at solve time.
@@ -219,8 +221,9 @@ enum { PHFEM_FORM_TRACE = 0, PHFEM_FORM_FLUX = 1 };
  * triangle (Neumann edges become identity rows with Lambda = 0).  It needs an
  * invertible K_T (delta > 0) and is elliptic only (dt = 0); phfem_sys_csr is
  * not available for it (its rows are the multiplier edges).
- * Returns PHFEM_EINVAL for delta < 0, dt < 0 or a nonpositive a; PHFEM_ENAN
- * when a coefficient is not finite. */
+ * Returns PHFEM_EINVAL for delta < 0, dt < 0, a nonpositive a, a tensor A that
+ * is not positive definite, or convection with the flux form; PHFEM_ENAN when a
+ * coefficient is not finite. */
 PHFEM_API int phfem_assemble(phfem_mesh mesh, const phfem_coeffs* coeffs, const double* f_mid,
                              const double* bc_mid, phfem_sys* out);
 /* The assembled free-edge system in CSR form (pattern of phfem_mesh_tables):
@@ -238,11 +241,12 @@ typedef struct {
   double inner_rtol;    /* reliable-update factor: the true FP64 residual replaces the
                            recursive one whenever the latter fell by this factor;
                            0 -> 0.1 (FP32_IR) or 0.01 (FP64); with a multigrid
-                           preconditioner 0 -> 1e-3 (FP32_IR) or 1e-4 (FP64)       */
+                           preconditioner 0 -> 1e-3 (FP32_IR) or 1e-4 (FP64); with
+                           convection (BiCGStab) 0 -> 1e-2 (FP32_IR) or 1e-6 (FP64) */
   int32_t max_iter;     /* total inner iterations; 0 -> 200000                        */
   int32_t max_refine;   /* reliable updates (FP64 residual evaluations); 0 -> 1000    */
   int32_t check_every;  /* inner iterations between host convergence checks; 0 -> 64
-                           (2 with a multigrid preconditioner)                     */
+                           (2 with a multigrid preconditioner, 16 with convection)  */
   int32_t reserved;
 } phfem_solve_opts;
 
@@ -261,6 +265,9 @@ typedef struct {
  * (FP64, or FP32 iterations with FP64-accumulated dot products whose residual
  * is replaced by the true FP64 residual at every reliable update, the FP64
  * solution accumulating the corrections), then recovers the paper's unknowns.
+ * With a multigrid attached (phfem_sys_set_mg) the V-cycle replaces the Jacobi
+ * step; with convection the iteration is BiCGStab (Jacobi on the right) with
+ * the same reliable updates and stopping rules.
  * The solve stops when rtol is met, or when the residual reaches twice the
  * FP64 floor (converged = 2): on fine meshes b scales like h^2 while S does
  * not, and below that level no FP64 vector w satisfies the system better.
