@@ -248,3 +248,25 @@ def test_torch_caching_allocator_context():
             assert after == base, (base, after)
     assert deltas[1] > deltas[0] + 200_000, deltas  # the library's buffers came from PyTorch
     assert np.array_equal(outs[0], outs[1])
+
+
+def test_l2_window_changes_no_result(ctx):
+    """The L2 persistence window is a caching policy: solutions are bitwise the
+    same with it on and off (FP32 + refinement and FP64)."""
+    from phfem_gpu import GpuMesh, solve
+    from paper_2401_15557_gb300 import phfem as P
+    mesh = I.lshape_mesh(n=16, seed=I.seed_for(1, 71), levels=1)
+    aT = I.element_mean_at_midpoints(mesh.xy, mesh.tri, I.coeff_lshape)
+    pb = I.problem_sine_exp()
+    pb.delta = 1.0
+    gm = GpuMesh(mesh, ctx)
+    for precision in (1, 0):
+        outs = []
+        for on in (True, False, True):
+            P.phfem_ctx_set_l2_window(ctx, on)
+            out = solve(gm, pb, aT=aT, precision=precision)
+            outs.append((out["w"], out["stats"]["iterations"]))
+            P.phfem_sys_destroy(out["sys"])
+        assert all(np.array_equal(outs[0][0], o[0]) and outs[0][1] == o[1] for o in outs[1:])
+    P.phfem_ctx_set_l2_window(ctx, True)
+    gm.close()
