@@ -37,6 +37,32 @@ UNIT = "triangles/s"
 LEVELS = 5
 CPU_SAMPLE_LEVEL = 2
 SPMV_BYTES_PER_ROW = 4 * 4 + 4 * 4 + 4 + 4 + 4   # nbr, l (FP32), r, p, q
+
+
+def assembly_bytes(nT, nE, nV, nD, nN, fp32=True):
+    """Bytes the two assembly kernels must move, every array touched once
+    (elliptic trace form with a_T, f and the boundary data):
+      k_asm_tri:  tri 12 + a_T 8 per triangle, xy 16 per vertex; writes the
+                  32-byte record per triangle;
+      k_asm_rows: ed2el 16, lk 1, eclass 1, f 8 per edge, the boundary data
+                  8 on boundary edges and the length 8 on Neumann edges, each
+                  record once; writes the FP64 row (5 x 8), the inner row (4 l,
+                  r, 1/d in the inner precision) and the rhs 8 per edge."""
+    isz = 4 if fp32 else 8
+    tri = (12 + 8 + 32) * nT + 16 * nV
+    rows = (16 + 1 + 1 + 8 + 40 + 6 * isz + 8) * nE + 8 * (nD + nN) + 8 * nN + 32 * nT
+    return tri, rows
+
+
+def hbm_peak():
+    """(GB/s, source) of the measured copy bandwidth, else the fallback figure."""
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        if peaks.get("hbm_gbs"):
+            return float(peaks["hbm_gbs"]), "measured"
+    except Exception:
+        pass
+    return 6800.0, "fallback"
 # DRAM traffic of one cg_spmv launch at the full workload, from the ncu capture
 # summarised in profiles/cg_kernels_l2_window_lshape_l5.md; valid only for the
 # kernel source and launch policy whose hash is recorded with it.
@@ -793,10 +819,32 @@ def main():
                 times.append(e0.elapsed_time(e1))
                 P.phfem_sys_destroy(sA)
             mt = statistics.median(times)
-            res[name] = {"ms": mt, "triangles_per_s": nT * 1e3 / mt}
+            # the same runs again with every launch of the two kernels event-timed
+            for k in ("asm_tri", "asm_rows"):
+                P.phfem_ctx_kernel_time(ctx, k, reset=True)
+            P.phfem_ctx_profile(ctx, True)
+            for _ in range(args.asm_runs):
+                P.phfem_sys_destroy(P.phfem_assemble(mA, f_mid, bc_mid, a_T=a, delta=1.0, precision=prec))
+            torch.cuda.synchronize()
+            P.phfem_ctx_profile(ctx, False)
+            bt, br = assembly_bytes(nT, nE, xy.shape[0], info["nD"], info["nN"], fp32=prec == P.PHFEM_FP32_IR)
+            kern = {}
+            for k, nb in (("asm_tri", bt), ("asm_rows", br)):
+                kms, kn = P.phfem_ctx_kernel_time(ctx, k, reset=True)
+                avg = kms / max(kn, 1)
+                kern[k] = {"ms": avg, "bytes": nb, "achieved_gbs": nb / (avg * 1e-3) / 1e9}
+            t2 = kern["asm_tri"]["ms"] + kern["asm_rows"]["ms"]
+            pk, pk_src = hbm_peak()
+            ach = (bt + br) / (t2 * 1e-3) / 1e9
+            res[name] = {"ms": mt, "triangles_per_s": nT * 1e3 / mt, "kernels": kern,
+                         "roofline": {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s",
+                                      "frac": ach / pk, "peak_source": pk_src,
+                                      "algorithmic_bytes": bt + br, "kernels_ms": t2}}
         P.phfem_mesh_destroy(mA)
         asm20 = {"runs": args.asm_runs, **res,
-                 "note": "phfem_assemble alone (allocation, a3-a6 kernels, coefficient check)"}
+                 "note": "phfem_assemble alone (allocation, a3-a6 kernels, coefficient check); "
+                         "kernels: mean of event-timed launches; roofline: algorithmic bytes of the two "
+                         "kernels over their summed time"}
 
     # ---- multigrid-preconditioned variant of the same step ----------------------
     # The level-0 mesh is refined on the device (the paper's refinement gives
@@ -896,14 +944,7 @@ def main():
 
     # ---- roofline of the dominant kernel (cg_spmv) ----------------------------
     spmv_ms, spmv_n = ktimes["cg_spmv"]
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    peak = peaks.get("hbm_gbs")
-    peak_src = "measured" if peak else "fallback"
-    peak = peak or 6800.0
+    peak, peak_src = hbm_peak()
     roof = None
     if spmv_n:
         avg = spmv_ms / spmv_n * 1e-3

@@ -11,59 +11,70 @@
 // Eq. right_g becomes |E| g(m_E) on that edge.
 //
 // Two passes, none with atomics:
-//   k_asm_tri   one thread per triangle: geometry and the 6 distinct entries of
-//               K^CR_T (FP64), plus |T|/3;
+//   k_asm_tri   one thread per triangle: geometry and the record of K^CR_T
+//               (its off-diagonal entries, negated, and |T|/3: the stiffness
+//               rows sum to zero, e_0 + e_1 + e_2 = 0, so the diagonal
+//               follows), 32 bytes AoS per triangle in FP64; FP32 systems
+//               take compensated FP32 element arithmetic (c32.cuh), FP64
+//               past an aspect bound;
 //   k_asm_rows  one thread per edge: its row = the rows of K^CR_{T+} and
-//               K^CR_{T-} at the edge (diagonal summed T+ then T-), the rhs, and
-//               the operator, in FP64 and in the inner precision, in difference form
+//               K^CR_{T-} at the edge, the rhs, and the operator, in FP64 and
+//               in the inner precision, in difference form
 //                 (S p)_e = r_e p_e + sum_s l_es (p_e - p_s),  l_es = -S_es,
 //               with r_e the reaction/mass part of the diagonal.  The stiffness
-//               rows of K^CR sum to zero (e_0 + e_1 + e_2 = 0), so the diagonal
-//               is sum_s l_es + r_e exactly; storing l and r instead of S keeps
-//               constants in the kernel of the rounded operator, and rounding
-//               l and r to FP32 perturbs S by a relative 2^-24 in the energy
-//               norm whatever its condition number -- which is what lets the
-//               FP32 inner solve drive an FP64 refinement on fine meshes.
+//               rows of K^CR sum to zero, so the diagonal is sum_s l_es + r_e
+//               exactly; storing l and r instead of S keeps constants in the
+//               kernel of the rounded operator, and rounding l and r to FP32
+//               perturbs S by a relative 2^-24 in the energy norm whatever its
+//               condition number -- which is what lets the FP32 inner solve
+//               drive an FP64 refinement on fine meshes.
 #include <cmath>
+#include <type_traits>
 
 #include "kernels.cuh"
 
 namespace phfem {
 namespace {
 
-// Kt rows 7..9 (with convection): the column values c_j of the convection block.
+// rec: [nT][4] records (C32: compensated FP32 element arithmetic, for FP32
+// systems); conv: [3][nT] the column values c_j of the convection block, or NULL.
+template <bool C32>
 __global__ void k_asm_tri(int nT, const int32_t* __restrict__ tri, const double2* __restrict__ xy,
-                          const double* __restrict__ aT, double a_const, double delta, double A11, double A12,
-                          double A22, double px, double py, int conv, double* __restrict__ Kt,
+                          const double* __restrict__ aT, double a_const, double A11, double A12, double A22,
+                          double px, double py, double* __restrict__ rec, double* __restrict__ conv,
                           int* __restrict__ bad) {
   const size_t n = (size_t)nT;
+  const bool iso = A11 == 1.0 && A12 == 0.0 && A22 == 1.0;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nT; t += gridDim.x * blockDim.x) {
     const int v0 = tri[3 * t], v1 = tri[3 * t + 1], v2 = tri[3 * t + 2];
     const double a = aT ? aT[t] : a_const;
-    // a > 0 and finite, tested on the bits (integer pipe): positive as a signed
-    // integer and an exponent below the all-ones of Inf / NaN
-    const long long ab = __double_as_longlong(a);
-    const bool finite = ((ab >> 52) & 0x7FF) != 0x7FF;
-    if (!(ab > 0 && finite)) atomicOr(bad, finite ? 1 : 2);
-    double K[7];
+    // a > 0 and finite, tested on the 32-bit halves of its bits (integer
+    // pipe): sign clear, not zero, and an exponent below the all-ones of Inf / NaN
+    const int ahi = __double2hiint(a);
+    const bool finite = ((ahi >> 20) & 0x7FF) != 0x7FF;
+    if (!(ahi >= 0 && (ahi | __double2loint(a)) != 0 && finite)) atomicOr(bad, finite ? 1 : 2);
     const double2 p0 = __ldg(xy + v0), p1 = __ldg(xy + v1), p2 = __ldg(xy + v2);
-    tri_block(p0, p1, p2, a, delta, K, A11, A12, A22);
-#pragma unroll
-    for (int j = 0; j < 7; ++j) Kt[j * n + t] = K[j];
+    double* dst = rec + (size_t)kRec * t;
+    if constexpr (C32) {
+      tri_record32_store(p0, p1, p2, a, dst, iso, A11, A12, A22);
+    } else {
+      double R[4];
+      tri_record64(p0, p1, p2, a, R, A11, A12, A22);
+      store_record(dst, R);
+    }
     if (conv) {
       double c[3];
       tri_conv(p0, p1, p2, px, py, c);
 #pragma unroll
-      for (int j = 0; j < 3; ++j) Kt[(7 + j) * n + t] = c[j];
+      for (int j = 0; j < 3; ++j) conv[j * n + t] = c[j];
     }
   }
 }
 
 // Adds the convection columns of T+ (tp, local kp) and T- to an edge row
 // (slots: T+ (k+1, k+2), T- (k+1, k+2)); the row sums do not change.
-__device__ __forceinline__ void add_conv(const double* Kt, size_t n, int tp, int kp, int tm, int km, double sK,
+__device__ __forceinline__ void add_conv(const double* c, size_t n, int tp, int kp, int tm, int km, double sK,
                                          EdgeRow& R) {
-  const double* c = Kt + 7 * n;
   R.diag += sK * c[(size_t)kp * n + tp];
   R.l[0] -= sK * c[(size_t)((kp + 1) % 3) * n + tp];
   R.l[1] -= sK * c[(size_t)((kp + 2) % 3) * n + tp];
@@ -75,33 +86,32 @@ __device__ __forceinline__ void add_conv(const double* Kt, size_t n, int tp, int
 }
 
 // sK scales K^CR and sM the mass |T|/3 (elliptic: 1, 0; Crank-Nicolson: dt/2, 1).
+// The boundary data is read on boundary edges only; me (the mass diagonal,
+// read by the Crank-Nicolson right-hand side) may be NULL.
 template <typename T, bool ELLIPTIC>
 __global__ void k_asm_rows(int nE, int nT, const int32_t* __restrict__ ed2el, const uint8_t* __restrict__ lk,
-                           const uint8_t* __restrict__ eclass, const double* __restrict__ Kt,
-                           const double* __restrict__ f_mid, const double* __restrict__ bc_mid,
-                           const double* __restrict__ elen, double sK, double sM, double delta, int conv,
-                           double* __restrict__ val, double* __restrict__ b, double* __restrict__ me,
+                           const uint8_t* __restrict__ eclass, const double* __restrict__ rec,
+                           const double* __restrict__ conv, const double* __restrict__ f_mid,
+                           const double* __restrict__ bc_mid, const double* __restrict__ elen, double sK, double sM,
+                           double delta, double* __restrict__ val, double* __restrict__ b, double* __restrict__ me,
                            T* __restrict__ lval, T* __restrict__ rdiag, T* __restrict__ dinv) {
   const size_t n = (size_t)nT, m = (size_t)nE;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
     const int4 q = reinterpret_cast<const int4*>(ed2el)[e];
     const int kk = lk[e];
     const uint8_t cls = eclass[e];
-    EdgeRow R = edge_row<true, ELLIPTIC>(Kt, n, q.z, kk & 3, q.w, (kk >> 2) & 3, cls, f_mid ? f_mid[e] : 0.0,
-                                         bc_mid ? bc_mid[e] : 0.0, cls == PHFEM_EDGE_NEUMANN ? elen[e] : 0.0, sK,
-                                         sM, delta, f_mid != nullptr, bc_mid != nullptr);
-    if (conv && cls != PHFEM_EDGE_DIRICHLET) add_conv(Kt, n, q.z, kk & 3, q.w, (kk >> 2) & 3, sK, R);
+    const int kp = kk & 3, km = (kk >> 2) & 3;
+    const double bc = (bc_mid && cls != PHFEM_EDGE_INTERIOR) ? bc_mid[e] : 0.0;
+    EdgeRow R = edge_row<true, ELLIPTIC>(rec, q.z, kp, q.w, km, cls, f_mid ? f_mid[e] : 0.0, bc,
+                                         cls == PHFEM_EDGE_NEUMANN ? elen[e] : 0.0, sK, sM, delta,
+                                         f_mid != nullptr, bc_mid != nullptr);
+    if (conv && cls != PHFEM_EDGE_DIRICHLET) add_conv(conv, n, q.z, kp, q.w, km, sK, R);
     val[e] = R.rpart;
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
-      val[(s + 1) * m + e] = R.l[s];
-      lval[s * m + e] = (T)R.l[s];
-    }
+    for (int s = 0; s < 4; ++s) val[(s + 1) * m + e] = R.l[s];
     b[e] = R.rhs;
-    me[e] = R.mass;
-    rdiag[e] = (T)R.rpart;
-    if constexpr (sizeof(T) == sizeof(float)) dinv[e] = 1.0f / (float)R.diag;  // inner precision suffices
-    else dinv[e] = (T)(1.0 / R.diag);
+    if (me) me[e] = R.mass;
+    store_inner(R, m, e, lval, rdiag, dinv);
   }
 }
 
@@ -112,12 +122,14 @@ __global__ void k_asm_rows(int nE, int nT, const int32_t* __restrict__ ed2el, co
 // 3x3 block is its cofactor matrix over the determinant.
 __global__ void k_asm_flux_tri(int nT, const int32_t* __restrict__ t2e, const int8_t* __restrict__ sigma,
                                const uint8_t* __restrict__ eclass, const double* __restrict__ elen,
-                               const double* __restrict__ Kt, const double* __restrict__ f_mid,
+                               const double* __restrict__ rec, double delta, const double* __restrict__ f_mid,
                                const double* __restrict__ bc_mid, double* __restrict__ St) {
   const size_t n = (size_t)nT;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nT; t += gridDim.x * blockDim.x) {
-    const double a = Kt[t], b = Kt[n + t], c = Kt[2 * n + t];
-    const double d = Kt[3 * n + t], e = Kt[4 * n + t], f = Kt[5 * n + t], mT = Kt[6 * n + t];
+    double r[4], K[6];
+    load_record<true>(rec, t, r);
+    record_block(r, delta, K);
+    const double a = K[0], b = K[1], c = K[2], d = K[3], e = K[4], f = K[5], mT = r[3];
     const double C00 = b * c - e * e, C11 = a * c - f * f, C22 = a * b - d * d;
     const double C01 = e * f - d * c, C12 = d * f - a * e, C20 = d * e - b * f;
     const double inv = 1.0 / (a * C00 + d * C01 + f * C20);
@@ -146,6 +158,16 @@ __global__ void k_asm_flux_tri(int nT, const int32_t* __restrict__ t2e, const in
   }
 }
 
+// Row k of S_T stored slot-major with stride n (00, 11, 22, 01, 12, 20):
+// the diagonal, (k, k+1) and (k+2, k).
+__device__ __forceinline__ void st_row(const double* St, size_t n, int t, int k, double& d, double& o1,
+                                       double& o2) {
+  const int k2 = (k == 0) ? 2 : k - 1;  // k + 2 mod 3
+  d = __ldg(St + (size_t)k * n + t);
+  o1 = __ldg(St + (size_t)(3 + k) * n + t);
+  o2 = __ldg(St + (size_t)(3 + k2) * n + t);
+}
+
 // Flux-form rows: the rows of S_{T+} and S_{T-} at the edge, rhs = sum of the
 // load terms + |E| u_D on Dirichlet edges (-b_D of Eq. DirichletEqn);
 // Neumann edges are identity rows with Lambda = 0.
@@ -165,16 +187,16 @@ __global__ void k_asm_rows_flux(int nE, int nT, const int32_t* __restrict__ ed2e
       diag = 1.0;
       rhs = 0.0;
     } else {
-      double d, o1, o2, unused;
+      double d, o1, o2;
       int k = kk & 3;
-      tri_row(St, n, q.z, k, d, o1, o2, unused);
+      st_row(St, n, q.z, k, d, o1, o2);
       diag = d;
       v[0] = o1;
       v[1] = o2;
       rhs = __ldg(St + (size_t)(6 + k) * n + q.z);
       if (q.w >= 0) {
         k = (kk >> 2) & 3;
-        tri_row(St, n, q.w, k, d, o1, o2, unused);
+        st_row(St, n, q.w, k, d, o1, o2);
         diag += d;
         v[2] = o1;
         v[3] = o2;
@@ -281,15 +303,16 @@ int assemble_into(phfem_sys sys, const double* f_mid, const double* bc_mid, int*
   const phfem_coeffs& c = sys->c;
   prof_start(ctx, kProfAsmTri);
   const bool iso = c.A[0] == 0.0 && c.A[1] == 0.0 && c.A[2] == 0.0;
-  k_asm_tri<<<grid_for(ctx, nT), kBlock, 0, s>>>(nT, m->tri, reinterpret_cast<const double2*>(m->xy), c.a_T, c.a,
-                                                 c.delta, iso ? 1.0 : c.A[0], iso ? 0.0 : c.A[1],
-                                                 iso ? 1.0 : c.A[2], c.p[0], c.p[1], sys->conv ? 1 : 0, sys->Kt,
-                                                 d_bad);
+  double* conv = sys->conv ? sys->Kt + (size_t)kRec * nT : nullptr;
+  auto tri_pass = sys->fp32 ? k_asm_tri<true> : k_asm_tri<false>;
+  tri_pass<<<grid_for(ctx, nT), kBlock, 0, s>>>(nT, m->tri, reinterpret_cast<const double2*>(m->xy), c.a_T, c.a,
+                                                iso ? 1.0 : c.A[0], iso ? 0.0 : c.A[1], iso ? 1.0 : c.A[2], c.p[0],
+                                                c.p[1], sys->Kt, conv, d_bad);
   prof_stop(ctx, kProfAsmTri);
   PH_TRY(check_launch(ctx, "k_asm_tri"));
   if (sys->form == PHFEM_FORM_FLUX) {
-    k_asm_flux_tri<<<grid_for(ctx, nT), kBlock, 0, s>>>(nT, m->t2e, m->sigma, m->eclass, m->elen, sys->Kt, f_mid,
-                                                        bc_mid, sys->St);
+    k_asm_flux_tri<<<grid_for(ctx, nT), kBlock, 0, s>>>(nT, m->t2e, m->sigma, m->eclass, m->elen, sys->Kt,
+                                                        c.delta, f_mid, bc_mid, sys->St);
     PH_TRY(check_launch(ctx, "k_asm_flux_tri"));
     prof_start(ctx, kProfAsmRows);
     if (sys->fp32)
@@ -308,28 +331,16 @@ int assemble_into(phfem_sys sys, const double* f_mid, const double* bc_mid, int*
   const double sK = c.dt > 0 ? 0.5 * c.dt : 1.0, sM = c.dt > 0 ? 1.0 : 0.0;
   prof_start(ctx, kProfAsmRows);
   const bool ell = c.dt == 0.0;
-  if (sys->fp32 && ell)
-    k_asm_rows<float, true><<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, nT, m->ed2el, m->lk, m->eclass, sys->Kt, f_mid,
-                                                                 bc_mid, m->elen, sK, sM, c.delta,
-                                                                 sys->conv ? 1 : 0, sys->val, sys->b, sys->me,
-                                                                 (float*)sys->lval, (float*)sys->rdiag,
-                                                                 (float*)sys->dinv);
-  else if (!sys->fp32 && ell)
-    k_asm_rows<double, true><<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, nT, m->ed2el, m->lk, m->eclass, sys->Kt,
-                                                                  f_mid, bc_mid, m->elen, sK, sM, c.delta,
-                                                                  sys->conv ? 1 : 0, sys->val, sys->b, sys->me,
-                                                                  (double*)sys->lval, (double*)sys->rdiag,
-                                                                  (double*)sys->dinv);
-  else if (sys->fp32)
-    k_asm_rows<float, false><<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, nT, m->ed2el, m->lk, m->eclass, sys->Kt, f_mid,
-                                                           bc_mid, m->elen, sK, sM, c.delta, sys->conv ? 1 : 0,
-                                                           sys->val, sys->b, sys->me, (float*)sys->lval,
-                                                           (float*)sys->rdiag, (float*)sys->dinv);
-  else
-    k_asm_rows<double, false><<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, nT, m->ed2el, m->lk, m->eclass, sys->Kt, f_mid,
-                                                            bc_mid, m->elen, sK, sM, c.delta, sys->conv ? 1 : 0,
-                                                            sys->val, sys->b, sys->me, (double*)sys->lval,
-                                                            (double*)sys->rdiag, (double*)sys->dinv);
+  auto rows = [&](auto kernel, auto* inner) {
+    using T = std::remove_pointer_t<decltype(inner)>;
+    kernel<<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, nT, m->ed2el, m->lk, m->eclass, sys->Kt, conv, f_mid,
+                                                bc_mid, m->elen, sK, sM, c.delta, sys->val, sys->b, sys->me,
+                                                (T*)sys->lval, (T*)sys->rdiag, (T*)sys->dinv);
+  };
+  if (sys->fp32 && ell) rows(k_asm_rows<float, true>, (float*)nullptr);
+  else if (!sys->fp32 && ell) rows(k_asm_rows<double, true>, (double*)nullptr);
+  else if (sys->fp32) rows(k_asm_rows<float, false>, (float*)nullptr);
+  else rows(k_asm_rows<double, false>, (double*)nullptr);
   prof_stop(ctx, kProfAsmRows);
   return check_launch(ctx, "k_asm_rows");
 }
@@ -393,10 +404,10 @@ int assemble_system(phfem_mesh mesh, const phfem_coeffs& c, const double* f_mid,
   auto chk = [&](int r) {
     if (st == PHFEM_OK) st = r;
   };
-  chk(dalloc_n(ctx, &sys->Kt, (conv ? 10 : 7) * nT));
+  chk(dalloc_n(ctx, &sys->Kt, (kRec + (conv ? 3 : 0)) * nT));
   chk(dalloc_n(ctx, &sys->val, 5 * nE));
   chk(dalloc_n(ctx, &sys->b, nE));
-  chk(dalloc_n(ctx, &sys->me, nE));
+  if (c.dt > 0) chk(dalloc_n(ctx, &sys->me, nE));
   chk(dalloc(ctx, &sys->lval, 4 * nE * isz));
   chk(dalloc(ctx, &sys->rdiag, nE * isz));
   chk(dalloc(ctx, &sys->dinv, nE * isz));

@@ -68,7 +68,7 @@ struct BatchArrays {
   const double* delta;   // [count]
   const double* f_mid;   // [sum nE] or NULL
   const double* bc_mid;  // [sum nE] or NULL
-  double* Kt;            // [7 sum nT] slot-major per mesh
+  double* Kt;            // [sum nT][4] records (AoS)
   double* val;           // [5 sum nE]
   double* b;
   T* lval;               // [4 sum nE]
@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
     const int id = order[k];
     const MeshDesc D = desc[id];
     const int nT = D.nT, nE = D.nE;
-    const size_t n = (size_t)nT, m = (size_t)nE;
+    const size_t m = (size_t)nE;
     const double2* xy = A.xy + D.v0;
     const int32_t* tri = A.tri + 3 * D.t0;
     const int32_t* ed2el = A.ed2el + 4 * D.e0;
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
     const uint8_t* ecl = A.eclass + D.e0;
     const int32_t* nbr = A.nbr + 4 * D.e0;
     const double* elen = A.elen + D.e0;
-    double* Kt = A.Kt + 7 * D.t0;
+    double* Kt = A.Kt + (size_t)kRec * D.t0;
     double* val = A.val + 5 * D.e0;
     double* b = A.b + D.e0;
     T* lval = A.lval + 4 * D.e0;
@@ -123,10 +123,15 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
     // 1. triangle pass
     for (int t = threadIdx.x; t < nT; t += BS) {
       const double a = A.aT ? A.aT[D.t0 + t] : P.a_const;
-      double K[7];
-      tri_block(xy[tri[3 * t]], xy[tri[3 * t + 1]], xy[tri[3 * t + 2]], a, delta, K);
-#pragma unroll
-      for (int j = 0; j < 7; ++j) Kt[j * n + t] = K[j];
+      const double2 p0 = xy[tri[3 * t]], p1 = xy[tri[3 * t + 1]], p2 = xy[tri[3 * t + 2]];
+      double* dst = Kt + (size_t)kRec * t;
+      if constexpr (sizeof(T) == sizeof(float)) {
+        tri_record32_store(p0, p1, p2, a, dst, true);
+      } else {
+        double R[4];
+        tri_record64(p0, p1, p2, a, R);
+        store_record(dst, R);
+      }
     }
     __syncthreads();
     // 2. edge rows; x starts at 0 on free edges and u_D on Dirichlet edges
@@ -134,18 +139,14 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
       const int4 qd = reinterpret_cast<const int4*>(ed2el)[e];
       const int kk = lk[e];
       const uint8_t cls = ecl[e];
-      const EdgeRow R = edge_row<false>(Kt, n, qd.z, kk & 3, qd.w, (kk >> 2) & 3, cls, f ? f[e] : 0.0, bc ? bc[e] : 0.0,
-                                 cls == PHFEM_EDGE_NEUMANN ? elen[e] : 0.0, 1.0, 0.0, delta, f != nullptr,
-                                 bc != nullptr);
+      const EdgeRow R = edge_row<false, true>(Kt, qd.z, kk & 3, qd.w, (kk >> 2) & 3, cls, f ? f[e] : 0.0,
+                                              bc ? bc[e] : 0.0, cls == PHFEM_EDGE_NEUMANN ? elen[e] : 0.0, 1.0, 0.0,
+                                              delta, f != nullptr, bc != nullptr);
       val[e] = R.rpart;
 #pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        val[(s + 1) * m + e] = R.l[s];
-        lval[s * m + e] = (T)R.l[s];
-      }
+      for (int s = 0; s < 4; ++s) val[(s + 1) * m + e] = R.l[s];
       b[e] = R.rhs;
-      rdiag[e] = (T)R.rpart;
-      dinv[e] = (T)(1.0 / R.diag);
+      store_inner(R, m, e, lval, rdiag, dinv);
       x[e] = (cls == PHFEM_EDGE_DIRICHLET) ? R.rhs : 0.0;
     }
     __syncthreads();
@@ -278,10 +279,10 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
           U[3 * t + 2] = s - 2.0 * a2;
         }
         if (A.Lambda) {
-          const double K00 = Kt[t], K11 = Kt[n + t], K22 = Kt[2 * n + t];
-          const double K01 = Kt[3 * n + t], K12 = Kt[4 * n + t], K20 = Kt[5 * n + t], mT = Kt[6 * n + t];
-          const double res[3] = {K00 * a0 + K01 * a1 + K20 * a2, K01 * a0 + K11 * a1 + K12 * a2,
-                                 K20 * a0 + K12 * a1 + K22 * a2};
+          double r4[4], res[3];
+          load_record<false>(Kt, t, r4);
+          record_apply(r4, delta, a0, a1, a2, res);
+          const double mT = r4[3];
           const int ee[3] = {e0, e1, e2};
 #pragma unroll
           for (int kk = 0; kk < 3; ++kk) {
@@ -522,7 +523,7 @@ PHFEM_API int phfem_batch_solve(phfem_batch B, const double* a_T, const double* 
     auto chk = [&](int r) {
       if (st == PHFEM_OK) st = r;
     };
-    chk(dalloc_n(ctx, &B->Kt, 7 * sT));
+    chk(dalloc_n(ctx, &B->Kt, (size_t)kRec * sT));
     chk(dalloc_n(ctx, &B->val, 5 * sE));
     chk(dalloc_n(ctx, &B->b, sE));
     chk(dalloc_n(ctx, &B->x, sE));

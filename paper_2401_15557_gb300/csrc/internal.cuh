@@ -125,17 +125,18 @@ struct phfem_sys_s {
   phfem_coeffs c;
   bool fp32;
   int form;              // PHFEM_FORM_TRACE or PHFEM_FORM_FLUX
-  bool conv;             // convection: nonsymmetric rows, Kt rows 7..9 hold its columns, BiCGStab
+  bool conv;             // convection: nonsymmetric rows, its columns follow the records in Kt, BiCGStab
   void* bw;              // BiCGStab workspace [7][nE] in the inner precision (allocated on first use)
   uint8_t ident_class;   // class of the identity rows: Dirichlet (trace) or Neumann (flux)
   double* St;            // [9][nT] flux form: S_T (00, 11, 22, 01, 12, 20) and the load terms g_T
   double* bc;            // [nE] copy of the boundary data (flux-form recovery)
-  double* Kt;            // [7][nT]: K^CR_T entries (00, 11, 22, 01, 12, 20) and |T|/3
+  double* Kt;            // [nT][4]: records of K^CR_T, AoS: -K01, -K12, -K20, |T|/3 (the
+                         //          stiffness rows sum to zero, so the diagonal follows)
                          //          (+ [3][nT] convection columns c_j with convection)
   double* val;           // [5][nE]: FP64 row in difference form: slot 0 = r_e (reaction/mass
                          //          part of the diagonal), slots 1..4 = l_es = -S_{e,nbr_s}
   double* b;             // [nE]: right-hand side; u_D on Dirichlet rows
-  double* me;            // [nE]: mass diagonal sum_T |T|/3
+  double* me;            // [nE]: mass diagonal sum_T |T|/3 (dt > 0 only, else NULL)
   // inner operator in difference form (float or double):
   //   (S p)_e = rdiag_e p_e + sum_s lval[s][e] (p_e - p[nbr[s][e]])
   void* lval;            // [4][nE]: -S_{e, nbr_s}

@@ -3,6 +3,7 @@
 // values.  See assemble.cu for the derivation of the condensed blocks.
 #pragma once
 
+#include "c32.cuh"
 #include "internal.cuh"
 
 namespace phfem {
@@ -11,7 +12,7 @@ namespace phfem {
 // compiler choose non-coherent loads by itself); the grid kernels pass RO = true.
 // Loads through the read-only (non-coherent) path are only valid for data that
 // no thread writes during the kernel: the grid-wide kernels use them, the
-// persistent batch kernel (which writes Kt and p and reads them back after a
+// persistent batch kernel (which writes the records and p and reads them back after a
 // block barrier) must use coherent loads.
 template <bool RO, typename T>
 __device__ __forceinline__ T ld(const T* ptr) {
@@ -66,38 +67,97 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, cudaStream_t s, Args.
   return launch_pdl_w(L2Window{}, kernel, grid, s, args...);
 }
 
-// K^CR_T = (a/|T|) e_k' A~ e_j + delta |T|/3 I for the triangle (p0, p1, p2),
-// e_k = P_{k+2} - P_{k+1}, A~ = [[A22, -A12], [-A12, A11]] (since |T| grad
-// lambda_k = the edge vector e_k turned by a right angle, over 2): out[0..2]
-// diagonal, out[3] (0,1), out[4] (1,2), out[5] (2,0), out[6] = |T|/3.
-__device__ __forceinline__ void tri_block(double2 p0, double2 p1, double2 p2, double a, double delta,
-                                          double out[7], double A11 = 1.0, double A12 = 0.0, double A22 = 1.0) {
+// Per-triangle record of the trace-form block K^CR_T = (a/|T|) e_i' A~ e_j +
+// delta |T|/3 I, e_k = P_{k+2} - P_{k+1}, A~ = [[A22, -A12], [-A12, A11]]
+// (|T| grad lambda_k is the edge vector e_k turned by a right angle, over 2).
+// The stiffness rows sum to zero (e_0 + e_1 + e_2 = 0, for any A), so the
+// block is fixed by its off-diagonal entries and |T|/3; the record holds
+//   L01, L12, L20 = -K^CR_T off the diagonal, and |T|/3
+// as four doubles (32 bytes, one sector, AoS), so an edge row reads one
+// sector per owner triangle.  The diagonal is
+// K_kk = L_{k,k+1} + L_{k+2,k} + delta |T|/3.
+constexpr int kRec = 4;
+
+// FP64 record of the triangle (p0, p1, p2).
+__device__ __forceinline__ void tri_record64(double2 p0, double2 p1, double2 p2, double a, double out[4],
+                                             double A11 = 1.0, double A12 = 0.0, double A22 = 1.0) {
   const double e0x = p2.x - p1.x, e0y = p2.y - p1.y;
   const double e1x = p0.x - p2.x, e1y = p0.y - p2.y;
   const double e2x = p1.x - p0.x, e2y = p1.y - p0.y;
   const double area2 = e1x * e2y - e1y * e2x;  // 2|T| = cross(P1 - P0, P2 - P0)
-  const double mT = area2 * (1.0 / 6.0);       // |T|/3
-  const double c = (a + a) / area2;            // a / |T|
-  const double dm = delta * mT;
+  const double nc = -(a + a) / area2;          // -a / |T|
   if (A11 == 1.0 && A12 == 0.0 && A22 == 1.0) {  // A = I (uniform across a launch)
-    out[0] = c * (e0x * e0x + e0y * e0y) + dm;
-    out[1] = c * (e1x * e1x + e1y * e1y) + dm;
-    out[2] = c * (e2x * e2x + e2y * e2y) + dm;
-    out[3] = c * (e0x * e1x + e0y * e1y);
-    out[4] = c * (e1x * e2x + e1y * e2y);
-    out[5] = c * (e2x * e0x + e2y * e0y);
+    out[0] = nc * (e0x * e1x + e0y * e1y);
+    out[1] = nc * (e1x * e2x + e1y * e2y);
+    out[2] = nc * (e2x * e0x + e2y * e0y);
   } else {
     auto q = [&](double ux, double uy, double vx, double vy) {
       return A22 * ux * vx - A12 * (ux * vy + uy * vx) + A11 * uy * vy;
     };
-    out[0] = c * q(e0x, e0y, e0x, e0y) + dm;
-    out[1] = c * q(e1x, e1y, e1x, e1y) + dm;
-    out[2] = c * q(e2x, e2y, e2x, e2y) + dm;
-    out[3] = c * q(e0x, e0y, e1x, e1y);
-    out[4] = c * q(e1x, e1y, e2x, e2y);
-    out[5] = c * q(e2x, e2y, e0x, e0y);
+    out[0] = nc * q(e0x, e0y, e1x, e1y);
+    out[1] = nc * q(e1x, e1y, e2x, e2y);
+    out[2] = nc * q(e2x, e2y, e0x, e0y);
   }
-  out[6] = mT;
+  out[3] = area2 * (1.0 / 6.0);
+}
+
+// Stores a record (two 16-byte stores; records are 32-byte aligned).
+__device__ __forceinline__ void store_record(double* dst, const double R[4]) {
+  double2* p = reinterpret_cast<double2*>(dst);
+  p[0] = make_double2(R[0], R[1]);
+  p[1] = make_double2(R[2], R[3]);
+}
+
+// The FP64 record computed and stored out of line: inlined next to the
+// compensated path, the compiler evaluates part of it (the edge vectors are
+// shared) ahead of that path's outcome.
+static __device__ __noinline__ void tri_record64_store(double2 p0, double2 p1, double2 p2, double a, double* dst, double A11,
+                                                double A12, double A22) {
+  double R[4];
+  tri_record64(p0, p1, p2, a, R, A11, A12, A22);
+  store_record(dst, R);
+}
+
+// Record of an FP32 system, stored at dst: compensated FP32 for the isotropic
+// case (within a few 1e-14 of the row scale), FP64 for triangles outside its
+// range or shape bound and for a tensor A.
+__device__ __forceinline__ void tri_record32_store(double2 p0, double2 p1, double2 p2, double a, double* dst, bool iso,
+                                                   double A11 = 1.0, double A12 = 0.0, double A22 = 1.0) {
+  double R[4];
+  if (iso && c32::tri_record(p0.x, p0.y, p1.x, p1.y, p2.x, p2.y, a, R)) store_record(dst, R);
+  else tri_record64_store(p0, p1, p2, a, dst, A11, A12, A22);
+}
+
+template <bool RO>
+__device__ __forceinline__ void load_record(const double* rec, int t, double r[4]) {
+  const double2* p = reinterpret_cast<const double2*>(rec + (size_t)kRec * t);
+  const double2 a = ld<RO>(p), b = ld<RO>(p + 1);
+  r[0] = a.x;
+  r[1] = a.y;
+  r[2] = b.x;
+  r[3] = b.y;
+}
+
+// The full block of a record: K[0..2] diagonal, K[3] (0,1), K[4] (1,2),
+// K[5] (2,0).
+__device__ __forceinline__ void record_block(const double r[4], double delta, double K[6]) {
+  const double dm = delta * r[3];
+  K[0] = r[0] + r[2] + dm;
+  K[1] = r[0] + r[1] + dm;
+  K[2] = r[1] + r[2] + dm;
+  K[3] = -r[0];
+  K[4] = -r[1];
+  K[5] = -r[2];
+}
+
+// (K^CR_T w)_k - the stiffness part in difference form,
+// sum_{j != k} L_kj (w_k - w_j), plus delta |T|/3 w_k.
+__device__ __forceinline__ void record_apply(const double r[4], double delta, double w0, double w1, double w2,
+                                             double out[3]) {
+  const double dm = delta * r[3];
+  out[0] = r[0] * (w0 - w1) + r[2] * (w0 - w2) + dm * w0;
+  out[1] = r[0] * (w1 - w0) + r[1] * (w1 - w2) + dm * w1;
+  out[2] = r[1] * (w2 - w1) + r[2] * (w2 - w0) + dm * w2;
 }
 
 // Convection in the trace form: R^-T D_T R^-1 with the column-constant
@@ -109,16 +169,11 @@ __device__ __forceinline__ void tri_conv(double2 p0, double2 p1, double2 p2, dou
   out[2] = (px * (p1.y - p0.y) - py * (p1.x - p0.x)) * (1.0 / 3.0);
 }
 
-// Entries of row k of K^CR_T stored slot-major with stride n: diagonal,
-// (k, k+1), (k, k+2), and |T|/3.
-template <bool RO = true>
-__device__ __forceinline__ void tri_row(const double* Kt, size_t n, int t, int k, double& d,
-                                        double& o1, double& o2, double& mT) {
-  const int k2 = (k == 0) ? 2 : k - 1;  // k + 2 mod 3
-  d = ld<RO>(Kt + (size_t)k * n + t);
-  o1 = ld<RO>(Kt + (size_t)(3 + k) * n + t);   // pair (k, k+1)
-  o2 = ld<RO>(Kt + (size_t)(3 + k2) * n + t);  // pair (k+2, k)
-  mT = ld<RO>(Kt + 6 * n + t);
+// Entries of row k of a record: L_{k,k+1}, L_{k+2,k} (k+2 = k-1 mod 3).
+template <typename V>
+__device__ __forceinline__ void row_pick(V l01, V l12, V l20, int k, V& o1, V& o2) {
+  o1 = k == 0 ? l01 : (k == 1 ? l12 : l20);
+  o2 = k == 0 ? l20 : (k == 1 ? l01 : l12);
 }
 
 struct EdgeRow {
@@ -129,43 +184,33 @@ struct EdgeRow {
   double mass;    // sum of |T|/3 over the owners
 };
 
-// Row of edge e from the element blocks of T+ (tp, local kp) and T- (tm, km;
+// Row of edge e from the records of T+ (tp, local kp) and T- (tm, km;
 // tm < 0 on the boundary); sK scales K^CR and sM the mass (elliptic 1, 0;
 // Crank-Nicolson dt/2, 1).  Dirichlet rows are identity rows holding u_D.
-// ELLIPTIC: sK = 1 and sM = 0 (no scaling products).
+// The diagonal is rpart + sum of l.  ELLIPTIC: sK = 1 and sM = 0 (no
+// scaling products).
 template <bool RO = true, bool ELLIPTIC = false>
-__device__ __forceinline__ EdgeRow edge_row(const double* Kt, size_t n, int tp, int kp, int tm,
-                                            int km, uint8_t cls, double f, double bc, double elen, double sK,
-                                            double sM, double delta, bool have_f, bool have_bc) {
+__device__ __forceinline__ EdgeRow edge_row(const double* rec, int tp, int kp, int tm, int km, uint8_t cls,
+                                            double f, double bc, double elen, double sK, double sM, double delta,
+                                            bool have_f, bool have_bc) {
   EdgeRow R;
-  double d, o1, o2, mT;
-  tri_row<RO>(Kt, n, tp, kp, d, o1, o2, mT);
-  double diag, v1, v2, v3 = 0.0, v4 = 0.0, mass = mT;
-  if (ELLIPTIC) {
-    diag = d;
-    v1 = o1;
-    v2 = o2;
-  } else {
-    diag = sK * d + sM * mT;
-    v1 = sK * o1;
-    v2 = sK * o2;
-  }
+  double r[4], v1, v2, v3 = 0.0, v4 = 0.0;
+  load_record<RO>(rec, tp, r);
+  row_pick(r[0], r[1], r[2], kp, v1, v2);
+  double mass = r[3];
   if (tm >= 0) {
-    tri_row<RO>(Kt, n, tm, km, d, o1, o2, mT);
-    if (ELLIPTIC) {
-      diag += d;
-      v3 = o1;
-      v4 = o2;
-    } else {
-      diag += sK * d + sM * mT;
-      v3 = sK * o1;
-      v4 = sK * o2;
-    }
-    mass += mT;
+    load_record<RO>(rec, tm, r);
+    row_pick(r[0], r[1], r[2], km, v3, v4);
+    mass += r[3];
+  }
+  if (!ELLIPTIC) {
+    v1 *= sK;
+    v2 *= sK;
+    v3 *= sK;
+    v4 *= sK;
   }
   double rhs, rpart;
   if (cls == PHFEM_EDGE_DIRICHLET) {
-    diag = 1.0;
     v1 = v2 = v3 = v4 = 0.0;
     rhs = have_bc ? bc : 0.0;
     rpart = 1.0;
@@ -175,14 +220,37 @@ __device__ __forceinline__ EdgeRow edge_row(const double* Kt, size_t n, int tp, 
     rpart = ELLIPTIC ? delta * mass : (sK * delta + sM) * mass;
   }
   R.rpart = rpart;
-  R.l[0] = -v1;
-  R.l[1] = -v2;
-  R.l[2] = -v3;
-  R.l[3] = -v4;
-  R.diag = diag;
+  R.l[0] = v1;
+  R.l[1] = v2;
+  R.l[2] = v3;
+  R.l[3] = v4;
+  R.diag = rpart + v1 + v2 + v3 + v4;
   R.rhs = rhs;
   R.mass = mass;
   return R;
+}
+
+// Inner-precision values of a row: the FP64 ones rounded to floats (integer
+// operations, no conversion instructions) and the Jacobi inverse of their
+// diagonal in FP32 arithmetic; float or double lval, rdiag, dinv.
+template <typename T>
+__device__ __forceinline__ void store_inner(const EdgeRow& R, size_t m, int e, T* lval, T* rdiag, T* dinv) {
+  if constexpr (sizeof(T) == sizeof(float)) {
+    float d = c32::narrow(R.rpart);
+    rdiag[e] = d;
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const float l = c32::narrow(R.l[s]);
+      lval[s * m + e] = l;
+      d += l;
+    }
+    dinv[e] = c32::frcp(d);  // to 2^-24; a Jacobi scaling needs no correct rounding
+  } else {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) lval[s * m + e] = R.l[s];
+    rdiag[e] = R.rpart;
+    dinv[e] = 1.0 / R.diag;
+  }
 }
 
 // (S p)_e in difference form: rdiag_e p_e + sum_s l_es (p_e - p_s).

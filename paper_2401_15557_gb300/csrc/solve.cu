@@ -372,12 +372,13 @@ __global__ void k_init_x(int nE, const uint8_t* __restrict__ eclass, uint8_t ide
 // Flux form: w_T = (K^CR_T)^-1 (F^CR_T + diag(sigma |E|) Lambda_T), U = R^-1 w_T.
 __global__ void k_recover_flux(int nT, const int32_t* __restrict__ t2e, const int8_t* __restrict__ sigma,
                                const uint8_t* __restrict__ eclass, const double* __restrict__ elen,
-                               const double* __restrict__ Kt, const double* __restrict__ f,
+                               const double* __restrict__ rec, double delta, const double* __restrict__ f,
                                const double* __restrict__ bc, const double* __restrict__ lam, double* __restrict__ U) {
-  const size_t n = (size_t)nT;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nT; t += gridDim.x * blockDim.x) {
-    const double a = Kt[t], b = Kt[n + t], c = Kt[2 * n + t];
-    const double d = Kt[3 * n + t], e = Kt[4 * n + t], g = Kt[5 * n + t], mT = Kt[6 * n + t];
+    double r[4], K[6];
+    load_record<true>(rec, t, r);
+    record_block(r, delta, K);
+    const double a = K[0], b = K[1], c = K[2], d = K[3], e = K[4], g = K[5], mT = r[3];
     const double C00 = b * c - e * e, C11 = a * c - g * g, C22 = a * b - d * d;
     const double C01 = e * g - d * c, C12 = d * g - a * e, C20 = d * e - b * g;
     const double inv = 1.0 / (a * C00 + d * C01 + g * C20);
@@ -408,12 +409,13 @@ __global__ void k_copy_lambda(int nE, const int32_t* __restrict__ lam_id, const 
 
 // U = R^-1 w per triangle (u at the vertices); with Lambda: the element row
 // residual mT (wa - wb)/dt + K^CR_T (theta wa + (1 - theta) wb) - mT f, divided
-// by |E_k|, on the T+ side of every multiplier edge.
+// by |E_k|, on the T+ side of every multiplier edge.  K^CR_T w is applied in
+// difference form from the record; conv: [3][nT] convection columns or NULL.
 __global__ void k_recover(int nT, const int32_t* __restrict__ t2e, const int8_t* __restrict__ sigma,
-                          const int32_t* __restrict__ lam_id, const double* __restrict__ Kt,
-                          const double* __restrict__ elen, const double* __restrict__ wa,
-                          const double* __restrict__ wb, const double* __restrict__ f, double inv_dt,
-                          double theta, int conv, double* __restrict__ U, double* __restrict__ Lambda) {
+                          const int32_t* __restrict__ lam_id, const double* __restrict__ rec, double delta,
+                          const double* __restrict__ conv, const double* __restrict__ elen,
+                          const double* __restrict__ wa, const double* __restrict__ wb, const double* __restrict__ f,
+                          double inv_dt, double theta, double* __restrict__ U, double* __restrict__ Lambda) {
   const size_t n = (size_t)nT;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nT; t += gridDim.x * blockDim.x) {
     const int e0 = t2e[3 * t], e1 = t2e[3 * t + 1], e2 = t2e[3 * t + 2];
@@ -434,12 +436,16 @@ __global__ void k_recover(int nT, const int32_t* __restrict__ t2e, const int8_t*
     const double m0 = theta * a0 + (1.0 - theta) * b0;
     const double m1 = theta * a1 + (1.0 - theta) * b1;
     const double m2 = theta * a2 + (1.0 - theta) * b2;
-    const double K00 = Kt[t], K11 = Kt[n + t], K22 = Kt[2 * n + t];
-    const double K01 = Kt[3 * n + t], K12 = Kt[4 * n + t], K20 = Kt[5 * n + t], mT = Kt[6 * n + t];
-    // convection adds the same sum_j c_j m_j to every row
-    const double cv = conv ? Kt[7 * n + t] * m0 + Kt[8 * n + t] * m1 + Kt[9 * n + t] * m2 : 0.0;
-    const double res[3] = {K00 * m0 + K01 * m1 + K20 * m2 + cv, K01 * m0 + K11 * m1 + K12 * m2 + cv,
-                           K20 * m0 + K12 * m1 + K22 * m2 + cv};
+    double r4[4], res[3];
+    load_record<true>(rec, t, r4);
+    record_apply(r4, delta, m0, m1, m2, res);
+    const double mT = r4[3];
+    if (conv) {  // convection adds the same sum_j c_j m_j to every row
+      const double cv = conv[t] * m0 + conv[n + t] * m1 + conv[2 * n + t] * m2;
+      res[0] += cv;
+      res[1] += cv;
+      res[2] += cv;
+    }
     const double dw[3] = {a0 - b0, a1 - b1, a2 - b2};
     const int ee[3] = {e0, e1, e2};
 #pragma unroll
@@ -1026,9 +1032,10 @@ int recover(phfem_sys sys, const double* x_new, const double* x_old, const doubl
   const int nT = m->info.nT;
   if (!U && !Lambda) return PHFEM_OK;
   prof_start(ctx, kProfRecover);
-  k_recover<<<grid_for(ctx, nT), kBlock, 0, ctx->stream>>>(nT, m->t2e, m->sigma, m->lam_id, sys->Kt, m->elen,
-                                                           x_new, x_old, f_eff, inv_dt, theta, sys->conv ? 1 : 0,
-                                                           U, Lambda);
+  const double* conv = sys->conv ? sys->Kt + (size_t)kRec * nT : nullptr;
+  k_recover<<<grid_for(ctx, nT), kBlock, 0, ctx->stream>>>(nT, m->t2e, m->sigma, m->lam_id, sys->Kt, sys->c.delta,
+                                                           conv, m->elen, x_new, x_old, f_eff, inv_dt, theta, U,
+                                                           Lambda);
   prof_stop(ctx, kProfRecover);
   return check_launch(ctx, "k_recover");
 }
@@ -1054,7 +1061,8 @@ PHFEM_API int phfem_solve(phfem_sys sys, const phfem_solve_opts* opts, const dou
       phfem_ctx ctx = m->ctx;
       if (U) {
         k_recover_flux<<<grid_for(ctx, m->info.nT), kBlock, 0, s>>>(m->info.nT, m->t2e, m->sigma, m->eclass, m->elen,
-                                                                    sys->Kt, sys->f, sys->bc, sys->x, U);
+                                                                    sys->Kt, sys->c.delta, sys->f, sys->bc, sys->x,
+                                                                    U);
         PH_TRY(check_launch(ctx, "k_recover_flux"));
       }
       if (Lambda) {
