@@ -124,14 +124,11 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
     for (int t = threadIdx.x; t < nT; t += BS) {
       const double a = A.aT ? A.aT[D.t0 + t] : P.a_const;
       const double2 p0 = xy[tri[3 * t]], p1 = xy[tri[3 * t + 1]], p2 = xy[tri[3 * t + 2]];
-      double* dst = Kt + (size_t)kRec * t;
-      if constexpr (sizeof(T) == sizeof(float)) {
-        tri_record32_store(p0, p1, p2, a, dst, true);
-      } else {
-        double R[4];
-        tri_record64(p0, p1, p2, a, R);
-        store_record(dst, R);
-      }
+      // FP64 records in both precisions: the meshes are small and the time is
+      // the iteration's; the compensated path's registers would cost occupancy
+      double R[4];
+      tri_record64(p0, p1, p2, a, R);
+      store_record(Kt + (size_t)kRec * t, R);
     }
     __syncthreads();
     // 2. edge rows; x starts at 0 on free edges and u_D on Dirichlet edges
@@ -146,7 +143,10 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
 #pragma unroll
       for (int s = 0; s < 4; ++s) val[(s + 1) * m + e] = R.l[s];
       b[e] = R.rhs;
-      store_inner(R, m, e, lval, rdiag, dinv);
+#pragma unroll
+      for (int s = 0; s < 4; ++s) lval[s * m + e] = (T)R.l[s];
+      rdiag[e] = (T)R.rpart;
+      dinv[e] = (T)(1.0 / R.diag);
       x[e] = (cls == PHFEM_EDGE_DIRICHLET) ? R.rhs : 0.0;
     }
     __syncthreads();
@@ -278,17 +278,18 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
           U[3 * t + 1] = s - 2.0 * a1;
           U[3 * t + 2] = s - 2.0 * a2;
         }
-        if (A.Lambda) {
-          double r4[4], res[3];
-          load_record<false>(Kt, t, r4);
-          record_apply(r4, delta, a0, a1, a2, res);
-          const double mT = r4[3];
+        if (A.Lambda) {  // row k of K^CR_T x in difference form, from the record, per multiplier edge
           const int ee[3] = {e0, e1, e2};
+          const double aa[3] = {a0, a1, a2};
+          const double* rt = Kt + (size_t)kRec * t;
 #pragma unroll
           for (int kk = 0; kk < 3; ++kk) {
             const int li = lam[ee[kk]];
             if (li < 0 || sg[3 * t + kk] < 0) continue;
-            const double rr = res[kk] - mT * (f ? f[ee[kk]] : 0.0);
+            const int k1 = kk == 2 ? 0 : kk + 1, k2 = kk == 0 ? 2 : kk - 1;
+            const double mT = rt[3];
+            const double res = rt[kk] * (aa[kk] - aa[k1]) + rt[k2] * (aa[kk] - aa[k2]) + delta * mT * aa[kk];
+            const double rr = res - mT * (f ? f[ee[kk]] : 0.0);
             A.Lambda[D.l0 + li] = rr / elen[ee[kk]];
           }
         }

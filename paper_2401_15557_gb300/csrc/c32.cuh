@@ -132,11 +132,13 @@ PH_HD int top_bit(uint32_t k) {
 #endif
 }
 
-// The finite float x as a double, exactly, with 32-bit integer operations
-// only (GB300 runs conversions involving FP64 on its narrow FP64 pipe).
+// The float x as a double, exactly (infinities and NaNs included), with
+// 32-bit integer operations only (GB300 runs conversions involving FP64 on
+// its narrow FP64 pipe).
 PH_HD double widen(float x) {
   const uint32_t u = fbits(x);
   const uint32_t sign = u & 0x80000000u, E = (u >> 23) & 0xFFu, m = u & 0x7FFFFFu;
+  if (E == 255u) return bdouble(sign | 0x7FF00000u | (m >> 3), (m & 7u) << 29);  // the payload keeps a NaN a NaN
   if (E == 0) {  // zero or subnormal: x = m 2^-149
     if (m == 0) return bdouble(sign, 0u);
     const int p = top_bit(m);       // x = 1.f 2^(p - 149), f = the p bits below the top one

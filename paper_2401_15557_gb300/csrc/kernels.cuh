@@ -1,6 +1,8 @@
 // Per-triangle and per-edge arithmetic shared by the grid-wide kernels and the
-// batched (one block per mesh) kernels, so both compute bitwise the same
-// values.  See assemble.cu for the derivation of the condensed blocks.
+// batched (one block per mesh) kernels.  FP64 systems compute bitwise the same
+// values on both; FP32 systems take compensated FP32 element records on the
+// grid and FP64 ones in the batch (within a few 1e-14 of each other).  See
+// assemble.cu for the derivation of the condensed blocks.
 #pragma once
 
 #include "c32.cuh"
@@ -169,13 +171,6 @@ __device__ __forceinline__ void tri_conv(double2 p0, double2 p1, double2 p2, dou
   out[2] = (px * (p1.y - p0.y) - py * (p1.x - p0.x)) * (1.0 / 3.0);
 }
 
-// Entries of row k of a record: L_{k,k+1}, L_{k+2,k} (k+2 = k-1 mod 3).
-template <typename V>
-__device__ __forceinline__ void row_pick(V l01, V l12, V l20, int k, V& o1, V& o2) {
-  o1 = k == 0 ? l01 : (k == 1 ? l12 : l20);
-  o2 = k == 0 ? l20 : (k == 1 ? l01 : l12);
-}
-
 struct EdgeRow {
   double rpart;   // reaction/mass part of the diagonal (difference form)
   double l[4];    // -S_{e, nbr_s}
@@ -189,19 +184,26 @@ struct EdgeRow {
 // Crank-Nicolson dt/2, 1).  Dirichlet rows are identity rows holding u_D.
 // The diagonal is rpart + sum of l.  ELLIPTIC: sK = 1 and sM = 0 (no
 // scaling products).
+// Row k of the record of triangle t: L_{k,k+1}, L_{k+2,k} and |T|/3, three
+// loads from the record's one sector.
+template <bool RO>
+__device__ __forceinline__ void record_row(const double* rec, int t, int k, double& o1, double& o2, double& mT) {
+  const double* r = rec + (size_t)kRec * t;
+  o1 = ld<RO>(r + k);
+  o2 = ld<RO>(r + (k == 0 ? 2 : k - 1));
+  mT = ld<RO>(r + 3);
+}
+
 template <bool RO = true, bool ELLIPTIC = false>
 __device__ __forceinline__ EdgeRow edge_row(const double* rec, int tp, int kp, int tm, int km, uint8_t cls,
                                             double f, double bc, double elen, double sK, double sM, double delta,
                                             bool have_f, bool have_bc) {
   EdgeRow R;
-  double r[4], v1, v2, v3 = 0.0, v4 = 0.0;
-  load_record<RO>(rec, tp, r);
-  row_pick(r[0], r[1], r[2], kp, v1, v2);
-  double mass = r[3];
+  double v1, v2, v3 = 0.0, v4 = 0.0, mass, m2;
+  record_row<RO>(rec, tp, kp, v1, v2, mass);
   if (tm >= 0) {
-    load_record<RO>(rec, tm, r);
-    row_pick(r[0], r[1], r[2], km, v3, v4);
-    mass += r[3];
+    record_row<RO>(rec, tm, km, v3, v4, m2);
+    mass += m2;
   }
   if (!ELLIPTIC) {
     v1 *= sK;

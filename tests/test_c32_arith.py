@@ -90,9 +90,11 @@ def test_widen_is_exact(lib):
     fs = np.concatenate([(rng.standard_normal(200) * 10.0 ** rng.integers(-30, 30, 200)).astype(np.float32),
                          np.array([0.0, -0.0, 1e-40, -1e-44, 3.4e38], dtype=np.float32)])
     sub = np.array([1e-40, -3e-42, 1.4e-45, 1.1754942e-38], dtype=np.float32)  # subnormals
-    for f in np.concatenate([fs, sub]):
+    for f in np.concatenate([fs, sub, np.array([np.inf, -np.inf], dtype=np.float32)]):
         w = lib.c32_widen(float(f))
         assert w == float(f) and np.signbit(w) == np.signbit(f), f
+    for bits in (0x7FC00000, 0xFFC00001, 0x7F800001, 0x7FBFFFFF):  # quiet and signalling NaNs
+        assert np.isnan(lib.c32_widen(float(np.array([bits], dtype=np.uint32).view(np.float32)[0])))
 
 
 def test_narrow_rounds_to_nearest_even(lib):
