@@ -26,21 +26,36 @@ def _rowscaled_err(row_ptr, val_a, val_b):
     return err
 
 
+def _scaled(m, sx, sy):
+    """The mesh with its coordinates scaled by (sx, sy)."""
+    import dataclasses
+    return dataclasses.replace(m, xy=np.ascontiguousarray(m.xy * np.array([sx, sy])))
+
+
+# stretched8: triangles (ll, lr, ur) have a 2.9-degree angle at P0, so FP32 systems take
+# the FP64 element records for them (and compensated FP32 for the others); tiny6: edges
+# below 2^-40, every triangle takes the FP64 records.  tiny6 solves a linear u of size
+# one: with the sine data the solution is ~1e-13 there, and the FP32 inner iteration's
+# residual products underflow (an FP32 system needs data whose residuals stay in the
+# float range; FP64 systems have no such limit).
+SINE, LINEAR = I.problem_sine_exp, I.problem_linear
 CASES = [
-    ("square17", lambda: I.square_mesh(17), 0.0, False),
-    ("lshape6", lambda: I.lshape_mesh(n=6, seed=I.seed_for(1, 21)), 0.7, True),
-    ("lshape5r1", lambda: I.lshape_mesh(n=5, seed=I.seed_for(1, 22), levels=1), 1.0, True),
-    ("crisscross3", lambda: I.criss_cross(3), 0.3, True),
-    ("two", lambda: I.square_mesh(1), 0.0, False),
+    ("square17", lambda: I.square_mesh(17), 0.0, False, SINE),
+    ("stretched8", lambda: _scaled(I.square_mesh(8), 1.0, 1.0 / 20.0), 0.5, False, SINE),
+    ("tiny6", lambda: _scaled(I.square_mesh(6), 2.0 ** -45, 2.0 ** -45), 1.0, False, LINEAR),
+    ("lshape6", lambda: I.lshape_mesh(n=6, seed=I.seed_for(1, 21)), 0.7, True, SINE),
+    ("lshape5r1", lambda: I.lshape_mesh(n=5, seed=I.seed_for(1, 22), levels=1), 1.0, True, SINE),
+    ("crisscross3", lambda: I.criss_cross(3), 0.3, True, SINE),
+    ("two", lambda: I.square_mesh(1), 0.0, False, SINE),
 ]
 
 
-@pytest.mark.parametrize("name,mk,delta,var", CASES, ids=[c[0] for c in CASES])
+@pytest.mark.parametrize("name,mk,delta,var,problem", CASES, ids=[c[0] for c in CASES])
 @pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32ir"])
-def test_assembled_values(ctx, name, mk, delta, var, precision):
+def test_assembled_values(ctx, name, mk, delta, var, problem, precision):
     from phfem_gpu import GpuMesh, solve
     mesh = mk()
-    pb = I.problem_sine_exp()
+    pb = problem()
     pb.delta = delta
     aT = I.element_mean_at_midpoints(mesh.xy, mesh.tri, I.coeff_lshape) if var else None
     cs = O.condensed_system(mesh, pb, aT=aT)
