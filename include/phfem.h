@@ -188,7 +188,11 @@ typedef struct {
   double a;           /* coefficient used when a_T == NULL                       */
   double delta;       /* reaction coefficient delta >= 0 (Eq. eq1)                */
   double dt;          /* 0: elliptic; > 0: Crank-Nicolson matrix M + dt/2 K (Sec. 4) */
-  int32_t precision;  /* PHFEM_FP64 or PHFEM_FP32_IR (FP32 inner solve + FP64 refinement) */
+  int32_t precision;  /* PHFEM_FP64, or PHFEM_FP32_IR: FP32 inner solve + FP64 refinement,
+                         element arithmetic in compensated FP32 (the FP64 operator
+                         within a few 1e-14 of the row scale; FP64 for triangles whose
+                         angle at P0 has a sine below 1/4, for coordinates or a
+                         coefficient outside [2^-40, 2^40], and for a tensor A)      */
   int32_t form;       /* PHFEM_FORM_TRACE (edge-midpoint values, default) or
                          PHFEM_FORM_FLUX (multipliers; elliptic with delta > 0)     */
   double A[3];        /* constant SPD tensor (A11, A12, A22) of Eq. eq1, scaled per
