@@ -9,9 +9,11 @@
 // bits: the trace-form entries come out within a few 1e-14 of the FP64 ones
 // relative to the row scale.
 //
-// Everything here is __host__ __device__ and spelled with explicitly rounded
-// operations (no contraction), so a host build computes bitwise the same
-// values; the CPU tests check the arithmetic against exact rational results.
+// Everything here is __host__ __device__, spelled with explicitly rounded
+// FP32 operations (no contraction) and integer operations only (the one
+// reciprocal is seeded from the bits, not by a special-function unit), so a
+// host build computes bitwise the same values; the CPU tests check the
+// arithmetic against exact rational results.
 #pragma once
 
 #include <cstdint>
@@ -197,9 +199,6 @@ PH_HD double to_double(f2 a) {
   }
   return bdouble((uh & 0x80000000u) | (Ed << 20) | (mh & 0xFFFFFu), ml);
 }
-
-// h + l rounded to a float.
-PH_HD float to_float(f2 a) { return fadd(a.h, a.l); }
 
 // a b + c d for compensated a, b, c, d with |l| < 2^-23 |h|: the two leading
 // products and their sum are exact; the cross terms, the products' errors
