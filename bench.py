@@ -63,9 +63,9 @@ def hbm_peak():
     except Exception:
         pass
     return 6800.0, "fallback"
-# DRAM traffic of one cg_spmv launch at the full workload, from the ncu capture
-# summarised in profiles/cg_kernels_l2_window_lshape_l5.md; valid only for the
-# kernel source and launch policy whose hash is recorded with it.
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one cg_spmv
+# launch at the full workload, from one ncu capture; valid only for the kernel
+# source and launch policy whose hash is recorded with it.
 # Kernel timing inside the timed region brackets every 16th launch of each
 # kernel with CUDA events (an event between two launches keeps the second from
 # overlapping the first's drain, so timing every launch would slow the step).

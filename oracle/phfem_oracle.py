@@ -28,7 +28,7 @@ What it computes, in the paper's order and notation:
     system (reaction delta > 0) and its recovery of U;
   * error norms: L2, broken H1 seminorm, and a mesh M-norm of kappa - kappa_h.
 
-Readings of passages that are ambiguous (all listed in the design notes):
+Readings of passages that are ambiguous:
   * Convection uses the listing's column-constant D_T[r, c] = |T|/3 p.grad(lambda_c)
     (the test function is the row), which is the sign that Example 1's f needs.
   * The Neumann datum g is the scalar normal flux; the outward normal of a
@@ -38,9 +38,10 @@ Readings of passages that are ambiguous (all listed in the design notes):
     trapezoid rule (F^n + F^{n-1})/2 as printed; U^0 = R^{-1}[u0(m_E)] per
     element, Lambda^0 given (default 0).
   * The M-norm of the multiplier error is computed as
-    sqrt(sum_{E not Neumann} |E| int_E (kappa - kappa_h,E)^2); its VALUES are
-    "parity unpinned" (the paper does not print PHerror); only its rate is
-    checked.
+    sqrt(sum_{E not Neumann} |E| int_E (kappa - kappa_h,E)^2) (the paper does
+    not print PHerror).  The formula is pinned by values worked out by hand on
+    the two-triangle square; the paper's M-norm column is not reproduced by it
+    (only its rate is).
 """
 from __future__ import annotations
 
@@ -696,9 +697,11 @@ def _flux(grad, X, nrm, t=None, A=None, a=None):
 
 
 def m_norm_error(st, Lambda, grad, t=None, A=None, nq=6) -> float:
-    """Mesh M-norm of kappa - kappa_h (parity unpinned: the paper does not print
-    PHerror), sqrt(sum over multiplier edges E of |E| * int_E (kappa - Lambda_E)^2),
-    the edge integral by nq-point Gauss-Legendre; it decreases like h."""
+    """Mesh M-norm of kappa - kappa_h (the paper does not print PHerror):
+    sqrt(sum over multiplier edges E of |E| * int_E (kappa - Lambda_E)^2), the
+    edge integral by nq-point Gauss-Legendre; it decreases like h.  Pinned by
+    hand-worked values on the two-triangle square (constant offsets, a flux
+    linear along an edge, Neumann edges left out), not by the paper's column."""
     Redges = st["bsets"]["Redges"]
     ed2el = st["topo"]["ed2el"]
     a = st["xy"][ed2el[Redges, 0]]
