@@ -538,33 +538,39 @@ PHFEM_API int phfem_error_norms(phfem_mesh mesh, int32_t nq, const double* U, co
 /* Solve without device allocation                                           */
 /* ------------------------------------------------------------------------ */
 
-/* The paper has no counterpart of this entry point; it exists for callers that
- * cannot allocate device memory while they call the library: work being
- * captured into a CUDA graph (an allocation inside the capture fails or is
- * recorded into the graph), programs whose device memory belongs to another
- * framework's pool, and latency-critical loops that must not allocate.
+/* The paper has no counterpart of this entry point.  It exists for callers
+ * that cannot allocate device memory while they call the library: programs
+ * whose device memory is owned by another framework's pool or a fixed arena
+ * (an allocation outside it would go uncounted or fail), and loops with a
+ * latency or memory budget, where cudaMalloc may synchronise the device or
+ * fail under memory pressure in the middle of a run.
  *
  * Jacobi-preconditioned conjugate gradients (FP64) on a symmetric positive
  * definite CSR system A x = rhs given by the caller, for instance the export
  * of phfem_sys_csr.  It allocates nothing: its temporaries live in one
- * fixed-size device array of the library (about 8 MB per device, reserved when
- * the library is loaded on a device and kept until the process exits).
+ * fixed-size file-scope device array of the library (about 8 MB per device,
+ * which every device that loads the library holds until the process exits).
  *   cuda_stream  cudaStream_t the work is ordered on (NULL = legacy stream)
  *   n            rows, 1 <= n <= PHFEM_NOALLOC_MAX_ROWS (else PHFEM_EINVAL)
  *   row_ptr [n+1], col [nnz] int32, val [nnz] double   the matrix (device);
- *                every row must hold a positive diagonal entry
+ *                every row must hold a positive diagonal entry (else
+ *                PHFEM_EINVAL)
  *   rhs [n] double (device); x [n] double (device): initial guess on entry,
  *                solution on return
- *   rtol         stop when ||rhs - A x||_2 <= rtol ||rhs||_2 (recursive
- *                residual); <= 0 -> 1e-10
+ *   rtol         stop when the recursive residual r (updated by the
+ *                iteration, r = rhs - A x in exact arithmetic; not recomputed
+ *                from x) satisfies ||r||_2 <= rtol ||rhs||_2; <= 0 -> 1e-10
  *   max_iter     iteration limit; <= 0 -> 100000 (PHFEM_ENOCONV when reached)
- *   iterations, rel_residual   host outputs, may be NULL
- * The array is shared by every call on a device and keeps the last call's
- * contents; each call clears the state it needs at its start.  Calls whose
- * GPU work overlaps (different streams or threads without ordering) race on
- * it.  The first call on a device looks the array's address up
- * (cudaGetSymbolAddress) with that device current: make it before any stream
- * capture begins.  Blocks the host until the result is known. */
+ *   iterations, rel_residual   host outputs, may be NULL; rel_residual is
+ *                ||r||_2 / ||rhs||_2 of that recursive residual
+ * Every pointer must refer to memory of the current device.  The array is
+ * shared by every call on a device and keeps the last call's contents; each
+ * call clears the state that must start at zero.  Calls whose GPU work
+ * overlaps (different streams or host threads without ordering between them)
+ * race on it.  The first call on a device looks the array's device address up
+ * (cudaGetSymbolAddress) with that device current.  The call returns once the
+ * solve has finished: every 32 iterations it copies the iteration state to the
+ * host and waits for its stream. */
 #define PHFEM_NOALLOC_MAX_ROWS 262144
 PHFEM_API int phfem_csr_pcg_noalloc(void* cuda_stream, int32_t n, const int32_t* row_ptr,
                                     const int32_t* col, const double* val, const double* rhs,

@@ -1,14 +1,14 @@
 // Jacobi-PCG on a caller-given CSR system without any device allocation.
 //
 // Some callers cannot allocate device memory while they call into this
-// library: code being captured into a CUDA graph (an allocation inside the
-// capture either fails or becomes part of the graph), applications whose
-// device memory is owned by another framework's pool, and latency-critical
-// loops that must not pay for, or risk failing, an allocation.  This entry
+// library: programs whose device memory is owned by another framework's pool
+// or a fixed arena (an allocation outside it goes uncounted or fails), and
+// loops with a latency or memory budget, where cudaMalloc may synchronise the
+// device or fail under memory pressure in the middle of a run.  This entry
 // point serves them: every temporary lives in one file-scope device array of
-// fixed size, reserved once when the library is loaded on a device and held
-// until the process exits.  The caller still passes the matrix, the
-// right-hand side and the solution buffer.
+// fixed size, which every device that loads the library holds until the
+// process exits.  The caller still passes the matrix, the right-hand side and
+// the solution buffer.
 //
 // Limits and sharing rules:
 //   * at most PHFEM_NOALLOC_MAX_ROWS rows (larger systems are rejected);
@@ -18,8 +18,11 @@
 //   * calls whose work overlaps on the GPU (different streams, or host
 //     threads, without ordering between them) race on the scratch array;
 //   * the first call on a device looks up the array's device address with
-//     cudaGetSymbolAddress while that device is current; make that first call
-//     before any stream capture.
+//     cudaGetSymbolAddress while that device is current;
+//   * the reported relative residual is that of the recursive residual the
+//     iteration updates, not one recomputed from x;
+//   * the call returns when the solve has finished: every 32 iterations it
+//     copies the state to the host and waits for the stream.
 #include <cmath>
 #include <cstring>
 #include <mutex>

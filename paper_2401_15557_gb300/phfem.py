@@ -566,11 +566,18 @@ NOALLOC_MAX_ROWS = 262144
 
 def phfem_csr_pcg_noalloc(row_ptr, col, val, rhs, x, rtol=1e-10, max_iter=0, stream=None) -> dict:
     """Jacobi-PCG on a CSR system using only the library's fixed device scratch
-    (see include/phfem.h); x holds the initial guess and receives the solution."""
+    (for callers that cannot allocate device memory during the call); x holds
+    the initial guess and receives the solution.  rel_residual is that of the
+    iteration's recursive residual.  All tensors must be on one device; the
+    call runs with that device current, whose scratch array it uses."""
     n = rhs.numel()
+    devs = {t.device for t in (row_ptr, col, val, rhs, x) if isinstance(t, torch.Tensor)}
+    if len(devs) != 1:
+        raise ValueError(f"phfem_csr_pcg_noalloc: tensors on several devices: {sorted(map(str, devs))}")
     it, rel = C.c_int32(), C.c_double()
-    _check(lib().phfem_csr_pcg_noalloc(_stream_ptr(stream), n, _ptr(row_ptr, torch.int32, n + 1),
-                                       _ptr(col, torch.int32), _ptr(val, torch.float64), _ptr(rhs, torch.float64, n),
-                                       _ptr(x, torch.float64, n), float(rtol), int(max_iter), C.byref(it),
-                                       C.byref(rel)), "phfem_csr_pcg_noalloc")
+    with torch.cuda.device(rhs.device):
+        _check(lib().phfem_csr_pcg_noalloc(_stream_ptr(stream), n, _ptr(row_ptr, torch.int32, n + 1),
+                                           _ptr(col, torch.int32), _ptr(val, torch.float64),
+                                           _ptr(rhs, torch.float64, n), _ptr(x, torch.float64, n), float(rtol),
+                                           int(max_iter), C.byref(it), C.byref(rel)), "phfem_csr_pcg_noalloc")
     return {"iterations": int(it.value), "rel_residual": float(rel.value)}
