@@ -98,6 +98,14 @@ PHFEM_API int64_t phfem_ctx_launches(phfem_ctx ctx);
  * reset after each solve.  Contexts driven from several host threads at once
  * (the request server's) should turn the window off: the limit is shared. */
 PHFEM_API int phfem_ctx_set_l2_window(phfem_ctx ctx, int enable);
+/* Kernels of the FP32 Jacobi iteration in the locality order (a tuning choice,
+ * not part of the method): 0 = the direction update p = u + beta p is folded
+ * into the operator product (two kernels per iteration, the default); 1 = it
+ * runs as a kernel of its own (three kernels).  Both compute the same p and
+ * q per row; the sums are grouped alike, so results agree to rounding.  FP64
+ * systems always use the separate direction kernel.  Other values:
+ * PHFEM_EINVAL. */
+PHFEM_API int phfem_ctx_set_cg_kernel(phfem_ctx ctx, int variant);
 /* Instrumentation (not part of the method): when enabled, launches of the
  * kernels "cg_spmv", "cg_update", "cg_dir", "residual", "asm_tri", "asm_rows",
  * "recover" and of whole multigrid V-cycles ("mg_vcycle") are bracketed by
@@ -251,7 +259,11 @@ typedef struct {
   int32_t max_refine;   /* reliable updates (FP64 residual evaluations); 0 -> 1000    */
   int32_t check_every;  /* inner iterations between host convergence checks; 0 -> 64
                            (2 with a multigrid preconditioner, 16 with convection)  */
-  int32_t reserved;
+  int32_t order;        /* Jacobi iteration without multigrid or convection:
+                           0 = in the locality order of the edges (Morton order of
+                           their midpoints; solution kept as an FP64 pair plus the
+                           correction since the last reliable update), 1 = in the
+                           paper's edge order (FP64 solution); other solvers ignore it */
 } phfem_solve_opts;
 
 typedef struct {
@@ -533,6 +545,17 @@ PHFEM_API int phfem_error_points(phfem_mesh mesh, int32_t nq, double* tri_xy, do
 PHFEM_API int phfem_error_norms(phfem_mesh mesh, int32_t nq, const double* U, const double* u_q,
                                 const double* grad_q, const double* Lambda, const double* kappa_q,
                                 phfem_errors* out);
+
+/* The locality order in which the Jacobi iteration stores the edge system
+ * (not in the paper, whose numbering every other entry point keeps): edges
+ * sorted by the Morton code of their midpoints on a 2^q x 2^q grid over the
+ * vertices' bounding box (4 nE <= 4^q, q <= 15), ties in the paper's order.
+ *   perm [nE] int32 (device, may be NULL): perm[i] = edge of internal row i
+ *   n_overflow (host, may be NULL): rows whose four neighbours are not all
+ *                within 32767 rows, stored with full indices
+ * Builds the order on first use (also done by the first solve); blocks the
+ * host until it is built. */
+PHFEM_API int phfem_mesh_order(phfem_mesh mesh, int32_t* perm, int32_t* n_overflow);
 
 /* ------------------------------------------------------------------------ */
 /* Solve without device allocation                                           */

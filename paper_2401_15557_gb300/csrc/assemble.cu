@@ -289,6 +289,7 @@ void sys_free(phfem_sys s) {
   dfree(c, s->ri);  // p and q live in the same allocation
   dfree(c, s->partials);
   dfree(c, s->st);
+  fcg_free(s);
   delete s;
 }
 

@@ -1,0 +1,774 @@
+// Jacobi-preconditioned conjugate gradients on the condensed trace-form edge
+// system (Section 3.5 after elimination of the element unknowns) in the
+// locality order of the edges (order.cu), two kernels per iteration.
+//
+// Same method as the paper-order iteration of solve.cu (Jacobi-PCG with
+// reliable updates: FP32 or FP64 inner vectors, FP64 true residual in
+// difference form replacing the recursive one whenever it has fallen by
+// inner_rtol, the direction kept with a line search or restarted), arranged
+// to move fewer bytes per iteration:
+//   * the operator rows are stored in the locality order: four l_es as one
+//     16-byte (FP32) vector, the reaction part, and the neighbours as four
+//     16-bit differences, so an operator product reads 28 bytes of matrix per
+//     row in FP32 and its gathers hit lines that neighbouring rows just read;
+//   * the preconditioned residual u = D^-1 r is the stored vector (r = u / d
+//     is never needed), and the direction update p = u + beta p is folded
+//     into the operator product: each row forms p at itself and at its four
+//     neighbours from u and the previous p (two buffers, swapped each
+//     iteration), writes its own p and q = S p, and sums p.q;
+//   * the second kernel adds alpha p to the solution correction y, updates u
+//     and sums r.z = u.u / D^-1;
+//   * the solution is x = (xh + xl) + y: xh + xl an unevaluated FP64 pair
+//     ("double-double"), y the correction since the last reliable update,
+//     accumulated every iteration as an unevaluated pair of floats (FP32
+//     systems: about 48 bits with FP32 arithmetic only) or in FP64.  At every
+//     reliable update y is added into the pair and cleared, and the true
+//     residual b - S x is evaluated from the pair: the solution then carries
+//     more than FP64 precision, which the relative residual 1e-10 needs on
+//     fine meshes, where b scales like h^2 while S does not and no FP64 vector
+//     has a residual below ~1.3e-10 (L-shaped domain, h = 1/1024).
+// The true residual evaluates (x_e - x_s) from the pairs (TwoSum on the
+// leading parts), so its own rounding is ~2^-53 of sum |l_es (x_e - x_s)| per
+// row; that estimate is the floor reported with the result.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+
+#include "kernels.cuh"
+
+namespace phfem {
+
+template <typename T>
+struct Inner;
+template <>
+struct Inner<float> {
+  using L4 = float4;  // the four l_es of a row
+  using Y = float2;   // solution correction: unevaluated pair of floats
+};
+template <>
+struct Inner<double> {
+  struct __align__(32) L4 {
+    double x, y, z, w;
+  };
+  using Y = double;
+};
+
+struct FastCG {
+  int n = 0;
+  bool fp32 = true;
+  void* l4 = nullptr;     // [n] Inner<T>::L4
+  void* rd = nullptr;     // [n] T: reaction/mass part of the diagonal
+  void* di = nullptr;     // [n] T: 1 / S_ee
+  void* dg = nullptr;     // [n] T: S_ee (FP64 systems only)
+  double* val = nullptr;  // [5][n] FP64 rows in difference form
+  double* b = nullptr;    // [n] right-hand side of the current solve
+  double* xh = nullptr;   // [n] solution, leading part
+  double* xl = nullptr;   // [n] solution, trailing part
+  void* y = nullptr;      // [n] Inner<T>::Y correction since the last reliable update
+  void* vec = nullptr;    // u, p0, p1, q: [4] slots of `slot` bytes
+  size_t slot = 0;
+  void* u() const { return vec; }
+  void* p0() const { return (char*)vec + slot; }
+  void* p1() const { return (char*)vec + 2 * slot; }
+  void* q() const { return (char*)vec + 3 * slot; }
+};
+
+namespace {
+
+__device__ __forceinline__ void row_nbrs(const short4* __restrict__ nb, const int4* __restrict__ ovf, int i,
+                                         int c[4]) {
+  const short4 s = __ldg(nb + i);
+  if (s.x != (short)-32768) {
+    c[0] = i + s.x;
+    c[1] = i + s.y;
+    c[2] = i + s.z;
+    c[3] = i + s.w;
+  } else {
+    const int k = (int)(uint16_t)s.y | ((int)(uint16_t)s.z << 16);
+    const int4 o = __ldg(ovf + k);
+    c[0] = o.x;
+    c[1] = o.y;
+    c[2] = o.z;
+    c[3] = o.w;
+  }
+}
+
+__device__ __forceinline__ void load_l4(const float4* __restrict__ l, int i, float v[4]) {
+  const float4 a = __ldg(l + i);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = a.z;
+  v[3] = a.w;
+}
+__device__ __forceinline__ void load_l4(const Inner<double>::L4* __restrict__ l, int i, double v[4]) {
+  const double2* p = reinterpret_cast<const double2*>(l + i);
+  const double2 a = __ldg(p), b = __ldg(p + 1);
+  v[0] = a.x;
+  v[1] = a.y;
+  v[2] = b.x;
+  v[3] = b.y;
+}
+
+// y += alpha p with alpha = ah + al (FP32 systems): the product as an exact
+// pair plus al p, added to the pair y by TwoSum; FP32 arithmetic only.
+__device__ __forceinline__ float2 y_add(float2 y, float ah, float al, float p) {
+  const c32::f2 pr = c32::two_prod(ah, p);
+  const float pe = c32::ffma(al, p, pr.l);
+  const c32::f2 s = c32::two_sum(y.x, pr.h);
+  const float t = c32::fadd(c32::fadd(s.l, y.y), pe);
+  const float hi = c32::fadd(s.h, t);
+  return make_float2(hi, c32::fsub(t, c32::fsub(hi, s.h)));
+}
+__device__ __forceinline__ double y_add(double y, double a, double, double p) { return fma(a, p, y); }
+
+__device__ __forceinline__ double y_value(float2 y) { return (double)y.x + (double)y.y; }
+__device__ __forceinline__ double y_value(double y) { return y; }
+__device__ __forceinline__ void y_zero(float2& y) { y = make_float2(0.f, 0.f); }
+__device__ __forceinline__ void y_zero(double& y) { y = 0.0; }
+
+// (h, l) += v in FP64: TwoSum of the leading parts, then renormalised.
+__device__ __forceinline__ void dd_add(double& h, double& l, double v) {
+  const double s = h + v;
+  const double bb = s - h;
+  const double e = (h - (s - bb)) + (v - bb);
+  const double t = e + l;
+  h = s + t;
+  l = t - (h - s);
+}
+
+// Operator rows in the locality order (once per system).
+template <typename T>
+__global__ void k_fcg_op(int n, const int32_t* __restrict__ perm, const T* __restrict__ lval,
+                         const T* __restrict__ rdiag, const T* __restrict__ dinv, const double* __restrict__ val,
+                         typename Inner<T>::L4* __restrict__ l4, T* __restrict__ rd, T* __restrict__ di,
+                         T* __restrict__ dg, double* __restrict__ vi) {
+  const size_t m = (size_t)n;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int e = perm[i];
+    typename Inner<T>::L4 l;
+    l.x = lval[e];
+    l.y = lval[m + e];
+    l.z = lval[2 * m + e];
+    l.w = lval[3 * m + e];
+    l4[i] = l;
+    rd[i] = rdiag[e];
+    di[i] = dinv[e];
+    double v[5];
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+      v[s] = val[s * m + e];
+      vi[s * m + i] = v[s];
+    }
+    if (dg) dg[i] = (T)((((v[0] + v[1]) + v[2]) + v[3]) + v[4]);  // the diagonal, summed as assembled
+  }
+}
+
+// Start of a solve: b and x from the paper's order, y = 0.
+template <typename Y>
+__global__ void k_fcg_in(int n, const int32_t* __restrict__ perm, const double* __restrict__ b_paper,
+                         const double* __restrict__ x_paper, double* __restrict__ b, double* __restrict__ xh,
+                         double* __restrict__ xl, Y* __restrict__ y) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int e = perm[i];
+    b[i] = b_paper[e];
+    xh[i] = x_paper[e];
+    xl[i] = 0.0;
+    Y z;
+    y_zero(z);
+    y[i] = z;
+  }
+}
+
+// End of a solve: x = (xh + xl) + y, rounded to FP64, in the paper's order.
+template <typename Y>
+__global__ void k_fcg_out(int n, const int32_t* __restrict__ perm, const double* __restrict__ xh,
+                          const double* __restrict__ xl, const Y* __restrict__ y, double* __restrict__ x_paper) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double h = xh[i], l = xl[i];
+    dd_add(h, l, y_value(y[i]));
+    x_paper[perm[i]] = h + l;
+  }
+}
+
+// (xh, xl) += y, y = 0; with cond only when the iteration asked for a
+// reliable update (done == 1).
+template <typename Y>
+__global__ void k_fcg_fold(int n, double* __restrict__ xh, double* __restrict__ xl, Y* __restrict__ y,
+                           const SolveState* st, int cond) {
+  if (cond && st->done != 1) return;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    double h = xh[i], l = xl[i];
+    Y v = y[i];
+    dd_add(h, l, y_value(v));
+    xh[i] = h;
+    xl[i] = l;
+    y_zero(v);
+    y[i] = v;
+  }
+}
+
+// The kernels take F (fused): true folds the direction update p = u + beta p
+// into the operator product (FP32 systems may choose it); false runs it as a
+// kernel of its own after the update, which FP64 systems always do: on GB300
+// FP64 arithmetic, not memory, bounds their iteration, and forming p at the
+// four neighbours would add four FP64 operations per row.
+
+__device__ __forceinline__ float fmadd(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fmadd(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// True residual r = b - S x (FP64, difference form, x = xh + xl) and the
+// start of the inner iteration from it: u = D^-1 r, r.z, r.p for the line
+// search, ||r||^2 and the evaluation floor.  Modes as in solve.cu: 0 the norm
+// of the free-edge right-hand side with the Dirichlet lifting, 1 start, 2
+// reliable update, 3 = 2 only if the iteration asked for it.
+// Directions: at the start p = u (unfused: written here; fused: by the next
+// product kernel in restart mode).  At a reliable update the kept direction
+// is the one the next iteration would have taken, p = u + beta p with the
+// recursive u: the unfused iteration already formed it before pausing, the
+// fused one forms it here from the recursive u before u is replaced.
+template <typename T, bool F>
+__global__ void k_fcg_residual(int n, const short4* __restrict__ nb, const int4* __restrict__ ovf,
+                               const double* __restrict__ val, const double* __restrict__ b,
+                               const double* __restrict__ xh, const double* __restrict__ xl,
+                               const uint8_t* __restrict__ ecl, uint8_t ident, const T* __restrict__ di,
+                               const T* __restrict__ dg, T* __restrict__ u, T* p0, T* p1, double* partials,
+                               SolveState* st, double rtol2, double inner_rtol2, int mode) {
+  if (mode == 3) {
+    if (st->done != 1) return;  // every block reads done before the last block rewrites it
+    mode = 2;
+  }
+  __shared__ double smem[kBlock / 32];
+  const size_t m = (size_t)n;
+  T* __restrict__ pc = (F && st->par) ? p1 : p0;
+  const T beta = (T)st->beta;
+  double acc_r = 0.0, acc_z = 0.0, acc_f = 0.0, acc_p = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int c[4];
+    row_nbrs(nb, ovf, i, c);
+    if (mode == 0) {
+      double r = 0.0;
+      if (ecl[i] != ident) {
+        r = b[i];
+#pragma unroll
+        for (int s = 0; s < 4; ++s)
+          if (c[s] != i && ecl[c[s]] == ident) r += val[(s + 1) * m + i] * b[c[s]];
+      }
+      acc_r += r * r;
+      continue;
+    }
+    const double he = xh[i], le = xl[i];
+    const double rho = val[i];
+    double sx = rho * he + rho * le;
+    double fl = fabs(rho * he);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const double l = val[(s + 1) * m + i];
+      const double nh = -xh[c[s]];
+      const double sh = he + nh;  // (x_e - x_s) from the pairs: TwoSum of the leading parts
+      const double bb = sh - he;
+      const double eh = (he - (sh - bb)) + (nh - bb);
+      const double d = sh + (eh + (le - xl[c[s]]));
+      sx += l * d;
+      fl += fabs(l * d);
+    }
+    const double r = b[i] - sx;
+    acc_r += r * r;
+    fl *= 0x1p-53;
+    acc_f += fl * fl;
+    const double dd = (double)di[i];
+    const T ue = (T)(dd * r);
+    if (mode == 1 && !F) pc[i] = ue;
+    if (mode == 2) {
+      T pk = pc[i];
+      if (F) {
+        pk = fmadd(beta, pk, u[i]);
+        pc[i] = pk;
+      }
+      acc_p += r * (double)pk;
+    }
+    u[i] = ue;
+    if constexpr (sizeof(T) == sizeof(float)) acc_z += dd > 0.0 ? (double)ue * (double)ue / dd : 0.0;
+    else acc_z += (double)ue * (double)ue * (double)dg[i];  // the stored diagonal: FP64 systems only
+  }
+  acc_r = block_sum(acc_r, smem);
+  acc_z = block_sum(acc_z, smem);
+  acc_f = block_sum(acc_f, smem);
+  acc_p = block_sum(acc_p, smem);
+  if (threadIdx.x == 0) {
+    partials[blockIdx.x] = acc_r;
+    partials[kMaxGrid + blockIdx.x] = acc_z;
+    partials[2 * kMaxGrid + blockIdx.x] = acc_f;
+    partials[3 * kMaxGrid + blockIdx.x] = acc_p;
+  }
+  if (!arrive_last(&st->counter[0])) return;
+  const double rr = sum_partials(partials, smem);
+  const double rz = sum_partials(partials + kMaxGrid, smem);
+  const double ff = sum_partials(partials + 2 * kMaxGrid, smem);
+  const double rp = sum_partials(partials + 3 * kMaxGrid, smem);
+  if (threadIdx.x == 0) {
+    st->counter[0] = 0;
+    if (mode == 0) {
+      st->bb = rr;
+      return;
+    }
+    decide(st, rr, rz, ff, rp, mode, rtol2, inner_rtol2);
+    if (mode == 1 && F) st->restart = 1;  // the product kernel forms p = u
+  }
+}
+
+// q = S p with, fused (F), the direction update folded in: p = u + beta
+// p_old (restart: p = u; right after a reliable update that keeps the
+// direction: p = p_old) at the row and at its four neighbours, the same
+// rounded operation for every row, so all rows use the same p.  p_old is read
+// from one buffer and p written to the other; the last block swaps them.
+// Unfused: the stored p (restart: p = u, each row writing its own p).  Then
+// p.q -> alpha = r.z / p.q (or r.p / p.q after a reliable update).
+// One row per thread and grid stride, at full occupancy; the gathers go
+// through L1 and L2 (in the locality order most neighbours were just read by
+// nearby rows).  Measured variants (tiles staged in shared memory, with and
+// without cp.async; several rows per thread; a software pipeline over rows)
+// were all slower on GB300.
+template <typename T, bool F>
+__global__ void __launch_bounds__(kBlock) k_fcg_spmv(int n, const short4* __restrict__ nb,
+                                                     const int4* __restrict__ ovf,
+                                                     const typename Inner<T>::L4* __restrict__ lv,
+                                                     const T* __restrict__ rd, const T* __restrict__ u, T* p0, T* p1,
+                                                     T* __restrict__ q, double* partials, SolveState* st) {
+  pdl_enter();
+  if (!F && blockIdx.x == 0 && threadIdx.x == 0) st->dir_pending = 0;  // no block of this kernel reads it
+  if (st->done) return;
+  const int par = F ? st->par : 0;
+  const T* __restrict__ po = par ? p1 : p0;
+  T* __restrict__ pn = F ? (par ? p0 : p1) : p0;
+  const int mode = st->restart ? 1 : (st->use_rp ? 2 : 0);
+  const T beta = (T)st->beta;
+  __shared__ double smem[kBlock / 32];
+  auto pval = [&](T uv, T pv) -> T {
+    if (mode == 1) return uv;
+    if (F && mode == 0) return fmadd(beta, pv, uv);
+    return pv;
+  };
+  T acc = (T)0;  // this thread's few rows in T; across threads and blocks in FP64
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    int c[4];
+    row_nbrs(nb, ovf, i, c);
+    T l[4];
+    load_l4(lv, i, l);
+    const T pe = pval(mode != 2 ? __ldg(u + i) : (T)0, mode != 1 ? __ldg(po + i) : (T)0);
+    T gu[4], gp[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      gu[m] = mode != 2 ? __ldg(u + c[m]) : (T)0;
+      gp[m] = mode != 1 ? __ldg(po + c[m]) : (T)0;
+    }
+    T s = __ldg(rd + i) * pe;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) s = fmadd(l[m], pe - pval(gu[m], gp[m]), s);
+    if (F || mode == 1) pn[i] = pe;
+    q[i] = s;
+    acc = fmadd(pe, s, acc);
+  }
+  const double accd = block_sum((double)acc, smem);
+  if (threadIdx.x == 0) partials[blockIdx.x] = accd;
+  if (!arrive_last(&st->counter[1])) return;
+  const double pq = sum_partials(partials, smem);
+  if (threadIdx.x == 0) {
+    st->counter[1] = 0;
+    if (F) st->par = par ^ 1;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      st->done = 3;
+      st->status = isfinite(pq) ? PHFEM_EBREAKDOWN : PHFEM_ENAN;
+    } else {
+      st->alpha = (st->use_rp ? st->rp : st->rz) / pq;
+      st->use_rp = 0;
+      st->restart = 0;
+    }
+  }
+}
+
+// One row of the update: y += alpha p, u -= alpha D^-1 q, and its r.z term.
+__device__ __forceinline__ void update_row(float2& y, float pe, float qe, float d, float& ue, float ah, float al,
+                                           float& acc) {
+  y = y_add(y, ah, al, pe);
+  ue = fmadd(-ah, d * qe, ue);
+  acc += d > 0.f ? __fdividef(ue * ue, d) : 0.f;
+}
+
+// y += alpha p, u -= alpha D^-1 q, r.z = u.u / D^-1 (FP32) or u.u D (FP64,
+// with the stored diagonal: no FP64 division) -> beta.  Fused: then the test
+// of the recursive residual (done = 1 asks for a reliable update); unfused:
+// the direction kernel follows and tests it.  FP32 rows go four at a time
+// through 16-byte loads and stores.
+template <typename T, bool F>
+__global__ void __launch_bounds__(kBlock) k_fcg_update(int n, const T* p0, const T* p1, const T* __restrict__ q,
+                                                       const T* __restrict__ di, const T* __restrict__ dg,
+                                                       T* __restrict__ u, typename Inner<T>::Y* __restrict__ y,
+                                                       double* partials, SolveState* st) {
+  pdl_enter();
+  if (st->done) return;
+  const T* __restrict__ p = (F && st->par) ? p1 : p0;  // the direction of this iteration
+  const double a64 = st->alpha;
+  const T ah = (T)a64;
+  const T al = (T)(a64 - (double)ah);
+  __shared__ double smem[kBlock / 32];
+  T acc = (T)0;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    const int n4 = n / 4;
+    const float4* __restrict__ p4 = reinterpret_cast<const float4*>(p);
+    const float4* __restrict__ q4 = reinterpret_cast<const float4*>(q);
+    const float4* __restrict__ d4 = reinterpret_cast<const float4*>(di);
+    float4* __restrict__ u4 = reinterpret_cast<float4*>(u);
+    float4* __restrict__ y4 = reinterpret_cast<float4*>(y);  // two rows' pairs per float4
+    // two groups of four rows per thread and pass: all twelve 16-byte loads
+    // are issued before the first store
+    const int stride = gridDim.x * blockDim.x;
+    for (int j0 = blockIdx.x * blockDim.x + threadIdx.x; j0 < n4; j0 += 2 * stride) {
+      float4 pv[2], qv[2], dv[2], uv[2], ya[2], yb[2];
+      bool ok[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int j = j0 + h * stride;
+        ok[h] = j < n4;
+        if (ok[h]) {
+          pv[h] = p4[j];
+          qv[h] = q4[j];
+          dv[h] = d4[j];
+          uv[h] = u4[j];
+          ya[h] = y4[2 * j];
+          yb[h] = y4[2 * j + 1];
+        }
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (!ok[h]) continue;
+        const int j = j0 + h * stride;
+        float2 y0 = make_float2(ya[h].x, ya[h].y), y1 = make_float2(ya[h].z, ya[h].w);
+        float2 y2 = make_float2(yb[h].x, yb[h].y), y3 = make_float2(yb[h].z, yb[h].w);
+        update_row(y0, pv[h].x, qv[h].x, dv[h].x, uv[h].x, ah, al, acc);
+        update_row(y1, pv[h].y, qv[h].y, dv[h].y, uv[h].y, ah, al, acc);
+        update_row(y2, pv[h].z, qv[h].z, dv[h].z, uv[h].z, ah, al, acc);
+        update_row(y3, pv[h].w, qv[h].w, dv[h].w, uv[h].w, ah, al, acc);
+        u4[j] = uv[h];
+        y4[2 * j] = make_float4(y0.x, y0.y, y1.x, y1.y);
+        y4[2 * j + 1] = make_float4(y2.x, y2.y, y3.x, y3.y);
+      }
+    }
+    // the last n % 4 rows
+    const int i = 4 * n4 + blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+      float ue = u[i];
+      float2 yi = y[i];
+      update_row(yi, p[i], q[i], di[i], ue, ah, al, acc);
+      u[i] = ue;
+      y[i] = yi;
+    }
+  } else {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+      y[i] = y_add(y[i], ah, al, p[i]);
+      const T d = di[i];
+      const T ue = fmadd(-ah, d * q[i], u[i]);
+      u[i] = ue;
+      acc = fmadd(ue * ue, dg[i], acc);
+    }
+  }
+  const double accd = block_sum((double)acc, smem);
+  if (threadIdx.x == 0) partials[kMaxGrid + blockIdx.x] = accd;
+  if (!arrive_last(&st->counter[2])) return;
+  const double rz = sum_partials(partials + kMaxGrid, smem);
+  if (threadIdx.x == 0) {
+    st->counter[2] = 0;
+    st->beta = st->rz > 0.0 ? rz / st->rz : 0.0;
+    st->rz = rz;
+    st->it += 1;
+    if (!isfinite(rz)) {
+      st->done = 3;
+      st->status = PHFEM_ENAN;
+    } else if (F && rz <= st->tol2) {
+      st->done = 1;
+    } else if (!F) {
+      st->dir_pending = 1;
+    }
+  }
+}
+
+// Unfused: p = u + beta p, then the test of the recursive residual, so that
+// the direction is complete when the iteration pauses for a reliable update.
+// Runs only after an update kernel that did run (dir_pending).
+template <typename T>
+__global__ void __launch_bounds__(kBlock) k_fcg_dir(int n, const T* __restrict__ u, T* __restrict__ p,
+                                                    SolveState* st) {
+  pdl_enter();
+  if (!st->dir_pending) return;
+  const T beta = (T)st->beta;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) p[i] = fmadd(beta, p[i], u[i]);
+  if (blockIdx.x == 0 && threadIdx.x == 0 && st->done == 0 && st->rz <= st->tol2) st->done = 1;
+}
+
+__global__ void k_fcg_loop_control(SolveState* st, cudaGraphConditionalHandle handle, int max_iter,
+                                   int max_bodies) {
+  st->bodies += 1;
+  const bool more = st->done == 0 && st->it < max_iter && st->bodies < max_bodies;
+  cudaGraphSetConditional(handle, more ? 1u : 0u);
+}
+
+template <typename T, bool F>
+struct FLaunch {
+  using L4 = typename Inner<T>::L4;
+  using Y = typename Inner<T>::Y;
+  phfem_sys sys;
+  cudaStream_t s;
+  int g, n;
+  double rtol2, irtol2;
+  const FastCG* f() const { return sys->fcg; }
+  int prologue() const {
+    phfem_ctx ctx = sys->mesh->ctx;
+    k_fcg_in<Y><<<g, kBlock, 0, s>>>(n, sys->mesh->perm, sys->b, sys->x, f()->b, f()->xh, f()->xl, (Y*)f()->y);
+    return check_launch(ctx, "k_fcg_in");
+  }
+  int epilogue() const {
+    phfem_ctx ctx = sys->mesh->ctx;
+    k_fcg_out<Y><<<g, kBlock, 0, s>>>(n, sys->mesh->perm, f()->xh, f()->xl, (const Y*)f()->y, sys->x);
+    return check_launch(ctx, "k_fcg_out");
+  }
+  int residual(int mode) const {
+    phfem_ctx ctx = sys->mesh->ctx;
+    phfem_mesh m = sys->mesh;
+    if (mode >= 2) {
+      k_fcg_fold<Y><<<g, kBlock, 0, s>>>(n, f()->xh, f()->xl, (Y*)f()->y, sys->st, mode == 3);
+      PH_TRY(check_launch(ctx, "k_fcg_fold"));
+    }
+    prof_start(ctx, kProfResidual);
+    k_fcg_residual<T, F><<<g, kBlock, 0, s>>>(n, m->nbr16, m->nbr_ovf, f()->val, f()->b, f()->xh, f()->xl,
+                                           m->eclass_i, sys->ident_class, (const T*)f()->di, (const T*)f()->dg,
+                                           (T*)f()->u(), (T*)f()->p0(), (T*)f()->p1(), sys->partials, sys->st,
+                                           rtol2, irtol2, mode);
+    prof_stop(ctx, kProfResidual);
+    return check_launch(ctx, "k_fcg_residual");
+  }
+  int iteration() const {
+    phfem_ctx ctx = sys->mesh->ctx;
+    phfem_mesh m = sys->mesh;
+    prof_start(ctx, kProfSpmv);
+    PH_CUDA(launch_pdl(k_fcg_spmv<T, F>, g, s, n, (const short4*)m->nbr16, (const int4*)m->nbr_ovf,
+                       (const L4*)f()->l4, (const T*)f()->rd, (const T*)f()->u(), (T*)f()->p0(), (T*)f()->p1(),
+                       (T*)f()->q(), sys->partials, sys->st));
+    prof_stop(ctx, kProfSpmv);
+    prof_start(ctx, kProfUpdate);
+    PH_CUDA(launch_pdl(k_fcg_update<T, F>, g, s, n, (const T*)f()->p0(), (const T*)f()->p1(), (const T*)f()->q(),
+                       (const T*)f()->di, (const T*)f()->dg, (T*)f()->u(), (Y*)f()->y, sys->partials, sys->st));
+    prof_stop(ctx, kProfUpdate);
+    ctx->launches += 1;
+    if (!F) {
+      prof_start(ctx, kProfDir);
+      PH_CUDA(launch_pdl(k_fcg_dir<T>, g, s, n, (const T*)f()->u(), (T*)f()->p0(), sys->st));
+      prof_stop(ctx, kProfDir);
+      ctx->launches += 1;
+    }
+    return check_launch(ctx, "k_fcg");
+  }
+};
+
+int read_state(phfem_sys sys) {
+  cudaStream_t s = sys->mesh->ctx->stream;
+  PH_CUDA(cudaMemcpyAsync(sys->st_host, sys->st, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+  PH_CUDA(cudaStreamSynchronize(s));
+  return PHFEM_OK;
+}
+
+template <typename T, bool F>
+int fcg_solve_typed(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats) {
+  phfem_ctx ctx = sys->mesh->ctx;
+  const int n = sys->mesh->info.nE;
+  const FLaunch<T, F> L{sys, ctx->stream, grid_for(ctx, n), n, o.rtol * o.rtol, o.inner_rtol * o.inner_rtol};
+  static const bool verbose = getenv("PHFEM_VERBOSE") != nullptr;
+  PH_TRY(L.prologue());
+  PH_TRY(L.residual(0));
+  PH_TRY(L.residual(1));
+  PH_TRY(read_state(sys));
+  int status = PHFEM_OK, stagnant = 0, last_updates = 0;
+  double best = 1e300;
+  for (;;) {
+    const SolveState& h = *sys->st_host;
+    if (h.updates != last_updates) {  // a new true residual: progress bookkeeping
+      last_updates = h.updates;
+      const double rel = h.bb > 0 ? std::sqrt(h.rr64 / h.bb) : 0.0;
+      if (verbose)
+        fprintf(stderr, "phfem: update %d  iterations %d  relative residual %.3e  floor %.3e  restart %d\n", h.updates,
+                h.it, rel, h.bb > 0 ? std::sqrt(h.floor2 / h.bb) : 0.0, h.restart);
+      stagnant = (rel > 0.5 * best) ? stagnant + 1 : 0;
+      best = rel < best ? rel : best;
+    }
+    if (h.done == 3) {
+      status = h.status;
+      break;
+    }
+    if (h.done == 2) break;
+    if (h.it >= o.max_iter || h.updates > o.max_refine || stagnant >= 8) {
+      status = PHFEM_ENOCONV;
+      break;
+    }
+    if (h.done == 1) {  // reliable update requested by the iteration
+      PH_TRY(L.residual(2));
+      PH_TRY(read_state(sys));
+      continue;
+    }
+    int chunk = o.check_every;
+    if (h.it + chunk > o.max_iter) chunk = o.max_iter - h.it;
+    for (int k = 0; k < chunk; ++k) PH_TRY(L.iteration());
+    PH_TRY(read_state(sys));
+  }
+  PH_TRY(L.epilogue());
+  const SolveState& h = *sys->st_host;
+  const double rel = h.bb > 0 ? std::sqrt(h.rr64 / h.bb) : 0.0;
+  if (stats) {
+    stats->iterations += h.it;
+    stats->refinements += h.updates;
+    stats->converged = h.done == 2 ? h.conv : 0;
+    stats->rel_residual = rel;
+    stats->fp64_floor = h.bb > 0 ? std::sqrt(h.floor2 / h.bb) : 0.0;
+  }
+  if (status != PHFEM_OK) {
+    char buf[200];
+    snprintf(buf, sizeof(buf), "solve: %s after %d iterations, %d residual updates, relative residual %.3e",
+             phfem_status_str(status), h.it, h.updates, rel);
+    return fail(status, buf);
+  }
+  return PHFEM_OK;
+}
+
+// The prologue and start kernels, a WHILE node whose body runs `per_body`
+// iterations, the conditional reliable update and the loop control, then the
+// epilogue.
+template <typename T, bool F>
+int fcg_capture_typed(phfem_sys sys, const phfem_solve_opts& o, cudaStream_t cs, int per_body) {
+  phfem_ctx ctx = sys->mesh->ctx;
+  const int n = sys->mesh->info.nE;
+  const FLaunch<T, F> L{sys, cs, grid_for(ctx, n), n, o.rtol * o.rtol, o.inner_rtol * o.inner_rtol};
+  PH_TRY(L.prologue());
+  PH_TRY(L.residual(0));
+  PH_TRY(L.residual(1));
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t graph;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t ndeps = 0;
+  PH_CUDA(cudaStreamGetCaptureInfo(cs, &cst, nullptr, &graph, &deps, nullptr, &ndeps));
+  if (cst != cudaStreamCaptureStatusActive) return fail(PHFEM_ECUDA, "capture_solve: stream is not capturing");
+  cudaGraphConditionalHandle handle;
+  PH_CUDA(cudaGraphConditionalHandleCreate(&handle, graph, 1, cudaGraphCondAssignDefault));
+  cudaGraphNodeParams cp = {};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = handle;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  cudaGraphNode_t cnode;
+  PH_CUDA(cudaGraphAddNode(&cnode, graph, deps, nullptr, ndeps, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  PH_CUDA(cudaStreamUpdateCaptureDependencies(cs, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies));
+  cudaStream_t bs;
+  PH_CUDA(cudaStreamCreateWithFlags(&bs, cudaStreamNonBlocking));
+  int st = PHFEM_OK;
+  cudaError_t e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamBeginCaptureToGraph", __FILE__, __LINE__);
+  if (st == PHFEM_OK) {
+    const FLaunch<T, F> B{sys, bs, L.g, n, L.rtol2, L.irtol2};
+    for (int k = 0; k < per_body && st == PHFEM_OK; ++k) st = B.iteration();
+    if (st == PHFEM_OK) st = B.residual(3);
+    if (st == PHFEM_OK) {
+      const int max_bodies = o.max_iter / (per_body > 0 ? per_body : 1) + o.max_refine + 16;
+      k_fcg_loop_control<<<1, 1, 0, bs>>>(sys->st, handle, o.max_iter, max_bodies);
+      st = check_launch(ctx, "k_fcg_loop_control");
+    }
+    cudaGraph_t out;
+    e = cudaStreamEndCapture(bs, &out);
+    if (e != cudaSuccess && st == PHFEM_OK) st = cuda_fail(e, "cudaStreamEndCapture(body)", __FILE__, __LINE__);
+  }
+  cudaStreamDestroy(bs);
+  if (st == PHFEM_OK) st = L.epilogue();
+  return st;
+}
+
+}  // namespace
+
+// FP32 systems fold the direction update into the product unless the
+// context chose the unfused kernels.
+static bool fused_fp32(phfem_sys sys) { return sys->mesh->ctx->cg_variant == 0; }
+
+bool fcg_eligible(phfem_sys sys, const phfem_solve_opts& o) {
+  return o.order == 0 && sys->form == PHFEM_FORM_TRACE && !sys->conv && !sys->mg;
+}
+
+int fcg_prepare(phfem_sys sys) {
+  if (sys->fcg) return PHFEM_OK;
+  phfem_mesh m = sys->mesh;
+  phfem_ctx ctx = m->ctx;
+  PH_TRY(mesh_order(m));
+  const int n = m->info.nE;
+  const size_t isz = sys->fp32 ? sizeof(float) : sizeof(double);
+  FastCG* f = new FastCG();
+  f->n = n;
+  f->fp32 = sys->fp32;
+  f->slot = ((size_t)n * isz + 255) / 256 * 256;
+  int st = PHFEM_OK;
+  auto chk = [&](int r) {
+    if (st == PHFEM_OK) st = r;
+  };
+  chk(dalloc(ctx, &f->l4, (size_t)n * 4 * isz + 32));
+  chk(dalloc(ctx, &f->rd, (size_t)n * isz + 16));
+  chk(dalloc(ctx, &f->di, (size_t)n * isz + 16));
+  if (!sys->fp32) chk(dalloc(ctx, &f->dg, (size_t)n * isz + 16));
+  chk(dalloc_n(ctx, &f->val, 5 * (size_t)n));
+  chk(dalloc_n(ctx, &f->b, (size_t)n));
+  chk(dalloc_n(ctx, &f->xh, (size_t)n));
+  chk(dalloc_n(ctx, &f->xl, (size_t)n));
+  chk(dalloc(ctx, &f->y, (size_t)n * 8 + 16));
+  chk(dalloc(ctx, &f->vec, 4 * f->slot + 16));
+  sys->fcg = f;
+  if (st == PHFEM_OK) {
+    const int g = grid_for(ctx, n);
+    if (sys->fp32)
+      k_fcg_op<float><<<g, kBlock, 0, ctx->stream>>>(n, m->perm, (const float*)sys->lval, (const float*)sys->rdiag,
+                                                     (const float*)sys->dinv, sys->val, (float4*)f->l4,
+                                                     (float*)f->rd, (float*)f->di, nullptr, f->val);
+    else
+      k_fcg_op<double><<<g, kBlock, 0, ctx->stream>>>(n, m->perm, (const double*)sys->lval,
+                                                      (const double*)sys->rdiag, (const double*)sys->dinv, sys->val,
+                                                      (Inner<double>::L4*)f->l4, (double*)f->rd, (double*)f->di,
+                                                      (double*)f->dg, f->val);
+    chk(check_launch(ctx, "k_fcg_op"));
+  }
+  if (st != PHFEM_OK) fcg_free(sys);
+  return st;
+}
+
+void fcg_free(phfem_sys sys) {
+  FastCG* f = sys->fcg;
+  if (!f) return;
+  phfem_ctx c = sys->mesh->ctx;
+  dfree(c, f->l4);
+  dfree(c, f->rd);
+  dfree(c, f->di);
+  dfree(c, f->dg);
+  dfree(c, f->val);
+  dfree(c, f->b);
+  dfree(c, f->xh);
+  dfree(c, f->xl);
+  dfree(c, f->y);
+  dfree(c, f->vec);
+  delete f;
+  sys->fcg = nullptr;
+}
+
+int fcg_solve(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats) {
+  PH_TRY(fcg_prepare(sys));
+  if (!sys->fp32) return fcg_solve_typed<double, false>(sys, o, stats);
+  return fused_fp32(sys) ? fcg_solve_typed<float, true>(sys, o, stats) : fcg_solve_typed<float, false>(sys, o, stats);
+}
+
+int fcg_capture(phfem_sys sys, const phfem_solve_opts& o, cudaStream_t cs, int per_body) {
+  if (!sys->fcg) return fail(PHFEM_ECUDA, "capture_solve: the locality-order operator must be built before capture");
+  if (!sys->fp32) return fcg_capture_typed<double, false>(sys, o, cs, per_body);
+  return fused_fp32(sys) ? fcg_capture_typed<float, true>(sys, o, cs, per_body)
+                         : fcg_capture_typed<float, false>(sys, o, cs, per_body);
+}
+
+}  // namespace phfem

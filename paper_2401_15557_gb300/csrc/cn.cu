@@ -187,6 +187,8 @@ int enqueue_post(phfem_cn cn) {
 // WHILE node controlled on the device, so a step needs no host round trip.
 int build_step_graph(phfem_cn cn, const phfem_solve_opts& o) {
   phfem_ctx ctx = cn->sys->mesh->ctx;
+  // the locality-order operator is allocated and built before the capture
+  if (fcg_eligible(cn->sys, o)) PH_TRY(fcg_prepare(cn->sys));
   PH_CUDA(cudaStreamSynchronize(ctx->stream));
   cudaStream_t cs;
   PH_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));

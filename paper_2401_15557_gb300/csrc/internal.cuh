@@ -63,6 +63,8 @@ struct SolveState {
   int status;      // phfem_status of a failure
   int dir_pending; // set by the update kernel, cleared by the next SpMV: gates the direction kernel
   unsigned int counter[4];  // last-block counters of the reductions
+  int par;         // locality-order CG: which of its two direction buffers holds the current p
+  int pad3;
 };
 
 }  // namespace phfem
@@ -89,6 +91,7 @@ struct phfem_ctx_s {
   size_t l2_window_max = 0;   // largest access-policy window
   size_t l2_limit = 0;        // the set-aside reserved now (cudaLimitPersistingL2CacheSize)
   bool l2_window = true;      // solves may use an L2 persistence window
+  int cg_variant = 0;         // FP32 locality-order CG: 0 direction update fused into the product, 1 separate
   int64_t launches;
   bool profile = false;
   int profile_every = 1;   // time every n-th launch of each kernel
@@ -118,7 +121,18 @@ struct phfem_mesh_s {
   int32_t* col;          // [nnz]
   int32_t* bpairs;       // [nD + nN][2] copies of the listed Dirichlet then Neumann pairs
   int32_t* bedge;        // [nD + nN] edge id of each listed pair
+  // locality order of the iteration kernels (built on first use, mesh_order):
+  int32_t* perm = nullptr;     // [nE] internal row -> edge (Morton order of the midpoints)
+  int32_t* iperm = nullptr;    // [nE] edge -> internal row
+  short4* nbr16 = nullptr;     // [nE] neighbours of internal row i as i + delta; x = -32768: see nbr_ovf
+  int4* nbr_ovf = nullptr;     // [novf] the four internal neighbours of the marked rows
+  uint8_t* eclass_i = nullptr; // [nE] class of internal row i
+  int novf = 0;
 };
+
+namespace phfem {
+struct FastCG;  // the conjugate-gradient operator and vectors in the locality order (cg.cu)
+}
 
 struct phfem_sys_s {
   phfem_mesh mesh;
@@ -154,6 +168,7 @@ struct phfem_sys_s {
   phfem::SolveState* st;       // device
   phfem::SolveState* st_host;  // pinned host mirror (the context's)
   phfem_mg mg;                 // multigrid preconditioner (not owned), or NULL: Jacobi
+  phfem::FastCG* fcg = nullptr;  // Jacobi-PCG in the locality order (built on the first solve)
 };
 
 namespace phfem {
@@ -192,6 +207,17 @@ int solve_bicgstab(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats)
 // coefficients the library derived itself).
 int assemble_system(phfem_mesh mesh, const phfem_coeffs& c, const double* f_mid, const double* bc_mid,
                     phfem_sys* out, bool check);
+// Locality order of a mesh's edges for the iteration kernels (order.cu).
+int mesh_order(phfem_mesh m);
+void mesh_order_free(phfem_mesh m);
+int radix_sort_pairs(phfem_ctx ctx, uint32_t* k0, int32_t* v0, uint32_t* k1, int32_t* v1, int n, int bits);
+// Jacobi-PCG on the trace-form system in the locality order (cg.cu): used for
+// systems without convection and without multigrid.
+bool fcg_eligible(phfem_sys sys, const phfem_solve_opts& o);
+int fcg_solve(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats);
+int fcg_capture(phfem_sys sys, const phfem_solve_opts& o, cudaStream_t cs, int per_body);
+int fcg_prepare(phfem_sys sys);
+void fcg_free(phfem_sys sys);
 int recover(phfem_sys sys, const double* x_new, const double* x_old, const double* f_eff,
             double inv_dt, double theta, double* U, double* Lambda);
 // z = V-cycle(r) on the multigrid's finest level (into mg_fine_z(mg)); with

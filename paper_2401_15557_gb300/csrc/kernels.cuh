@@ -69,6 +69,50 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, cudaStream_t s, Args.
   return launch_pdl_w(L2Window{}, kernel, grid, s, args...);
 }
 
+// Decision after a true residual (the last block of a residual kernel, thread
+// 0): the iteration's state, convergence (rtol, or twice the estimated floor
+// of the residual's evaluation), and for a reliable update the line-search
+// step along the kept direction or a restart of the direction.
+// mode 1 = start, 2 = reliable update.
+__device__ inline void decide(SolveState* st, double rr, double rz, double ff, double rp, int mode, double rtol2,
+                              double inner_rtol2) {
+  const double rz_recursive = st->rz;
+  st->rr64 = rr;
+  st->floor2 = ff;
+  st->rz = rz;
+  st->rp = rp;
+  st->tol2 = inner_rtol2 * rz;
+  st->status = 0;
+  if (mode == 1) {
+    st->rz0 = rz;
+    st->it = 0;
+    st->updates = 1;
+    st->bodies = 0;
+    st->use_rp = 0;
+    st->restart = 0;
+  } else {
+    st->updates += 1;
+    // line search along the kept direction, or restart it when it no longer
+    // fits the replaced residual
+    const int restart = (rz > 4.0 * rz_recursive) || !(rp > 0.0);
+    st->restart = restart;
+    st->use_rp = !restart;
+  }
+  st->conv = 0;
+  if (!isfinite(rr) || !isfinite(rz)) {
+    st->done = 3;
+    st->status = PHFEM_ENAN;
+  } else if (rr <= rtol2 * st->bb || rr == 0.0) {
+    st->done = 2;
+    st->conv = 1;
+  } else if (rr <= 4.0 * ff) {  // relative residual within twice the estimated floor
+    st->done = 2;
+    st->conv = 2;
+  } else {
+    st->done = 0;
+  }
+}
+
 // Per-triangle record of the trace-form block K^CR_T = (a/|T|) e_i' A~ e_j +
 // delta |T|/3 I, e_k = P_{k+2} - P_{k+1}, A~ = [[A22, -A12], [-A12, A11]]
 // (|T| grad lambda_k is the edge vector e_k turned by a right angle, over 2).

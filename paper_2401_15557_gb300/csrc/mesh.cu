@@ -329,6 +329,7 @@ void mesh_free(phfem_mesh m) {
   dfree(c, m->col);
   dfree(c, m->bpairs);
   dfree(c, m->bedge);
+  mesh_order_free(m);
   delete m;
 }
 

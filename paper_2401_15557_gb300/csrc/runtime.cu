@@ -261,6 +261,13 @@ PHFEM_API int phfem_ctx_destroy(phfem_ctx ctx) {
 
 PHFEM_API int64_t phfem_ctx_launches(phfem_ctx ctx) { return ctx ? ctx->launches : -1; }
 
+PHFEM_API int phfem_ctx_set_cg_kernel(phfem_ctx ctx, int variant) {
+  if (!ctx) return fail(PHFEM_EINVAL, "phfem_ctx_set_cg_kernel: NULL context");
+  if (variant != 0 && variant != 1) return fail(PHFEM_EINVAL, "phfem_ctx_set_cg_kernel: variant must be 0 or 1");
+  ctx->cg_variant = variant;
+  return PHFEM_OK;
+}
+
 PHFEM_API int phfem_ctx_set_l2_window(phfem_ctx ctx, int enable) {
   if (!ctx) return fail(PHFEM_EINVAL, "phfem_ctx_set_l2_window: NULL context");
   ctx->l2_window = enable != 0;

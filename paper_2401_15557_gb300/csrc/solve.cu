@@ -51,45 +51,6 @@ namespace {
 // Decision after a true residual (last block, thread 0): the iteration's
 // state, convergence (rtol, or twice the FP64 floor), and for a reliable
 // update the line-search step or a restart of the direction.
-__device__ void decide(SolveState* st, double rr, double rz, double ff, double rp, int mode, double rtol2,
-                       double inner_rtol2) {
-  const double rz_recursive = st->rz;
-  st->rr64 = rr;
-  st->floor2 = ff;
-  st->rz = rz;
-  st->rp = rp;
-  st->tol2 = inner_rtol2 * rz;
-  st->status = 0;
-  if (mode == 1) {
-    st->rz0 = rz;
-    st->it = 0;
-    st->updates = 1;
-    st->bodies = 0;
-    st->use_rp = 0;
-    st->restart = 0;
-  } else {
-    st->updates += 1;
-    // line search along the kept direction, or restart it when it no longer
-    // fits the replaced residual
-    const int restart = (rz > 4.0 * rz_recursive) || !(rp > 0.0);
-    st->restart = restart;
-    st->use_rp = !restart;
-  }
-  st->conv = 0;
-  if (!isfinite(rr) || !isfinite(rz)) {
-    st->done = 3;
-    st->status = PHFEM_ENAN;
-  } else if (rr <= rtol2 * st->bb || rr == 0.0) {
-    st->done = 2;
-    st->conv = 1;
-  } else if (rr <= 4.0 * ff) {  // relative residual within twice the FP64 floor
-    st->done = 2;
-    st->conv = 2;
-  } else {
-    st->done = 0;
-  }
-}
-
 // With precond != 0 (multigrid) the kernel only forms r and the sums ||r||^2
 // and the floor; the preconditioner and k_mg_finish complete the step.
 template <typename T>
@@ -1002,6 +963,7 @@ int capture_solve(phfem_sys sys, const phfem_solve_opts* opts, cudaStream_t capt
   phfem_solve_opts o{};
   if (opts) o = *opts;
   fill_opts(sys, o);
+  if (fcg_eligible(sys, o)) return fcg_capture(sys, o, capture, iters_per_body);
   return sys->fp32 ? capture_typed<float>(sys, o, capture, iters_per_body)
                    : capture_typed<double>(sys, o, capture, iters_per_body);
 }
@@ -1022,6 +984,7 @@ int solve_system(phfem_sys sys, const phfem_solve_opts* opts, phfem_stats* stats
   if (opts) o = *opts;
   fill_opts(sys, o);
   if (sys->conv) return solve_bicgstab(sys, o, stats);
+  if (fcg_eligible(sys, o)) return fcg_solve(sys, o, stats);
   return sys->fp32 ? solve_typed<float>(sys, o, stats) : solve_typed<double>(sys, o, stats);
 }
 

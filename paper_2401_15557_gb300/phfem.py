@@ -42,7 +42,7 @@ class Coeffs(C.Structure):
 
 class SolveOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("inner_rtol", C.c_double), ("max_iter", C.c_int32),
-                ("max_refine", C.c_int32), ("check_every", C.c_int32), ("reserved", C.c_int32)]
+                ("max_refine", C.c_int32), ("check_every", C.c_int32), ("order", C.c_int32)]
 
 
 class Stats(C.Structure):
@@ -117,6 +117,7 @@ def lib() -> C.CDLL:
         sig = {
             "phfem_ctx_create": (C.c_int, [_P, C.POINTER(_H)]),
             "phfem_ctx_set_l2_window": (C.c_int, [_H, C.c_int]),
+            "phfem_ctx_set_cg_kernel": (C.c_int, [_H, C.c_int]),
             "phfem_ctx_create_with_allocator": (C.c_int, [_P, _ALLOC_FN, _FREE_FN, _P, C.POINTER(_H)]),
             "phfem_ctx_destroy": (C.c_int, [_H]),
             "phfem_status_str": (C.c_char_p, [C.c_int]),
@@ -159,6 +160,7 @@ def lib() -> C.CDLL:
             "phfem_mg_destroy": (C.c_int, [_H]),
             "phfem_error_points": (C.c_int, [_H, C.c_int32, _P, _P, _P]),
             "phfem_error_norms": (C.c_int, [_H, C.c_int32, _P, _P, _P, _P, _P, C.POINTER(Errors)]),
+            "phfem_mesh_order": (C.c_int, [_H, _P, C.POINTER(C.c_int32)]),
             "phfem_csr_pcg_noalloc": (C.c_int, [_P, C.c_int32, _P, _P, _P, _P, _P, C.c_double, C.c_int32,
                                                 C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
         }
@@ -226,6 +228,11 @@ def phfem_ctx_create(stream=None, torch_allocator=False):
 def phfem_ctx_create_with_allocator(stream=None):
     """The context of phfem_ctx_create(stream, torch_allocator=True)."""
     return phfem_ctx_create(stream, torch_allocator=True)
+
+
+def phfem_ctx_set_cg_kernel(ctx, variant=0):
+    """FP32 Jacobi iteration in the locality order: 0 direction update fused into the product, 1 separate."""
+    _check(lib().phfem_ctx_set_cg_kernel(ctx, int(variant)), "phfem_ctx_set_cg_kernel")
 
 
 def phfem_ctx_set_l2_window(ctx, enable=True):
@@ -347,8 +354,9 @@ def phfem_sys_destroy(sys):
     _check(lib().phfem_sys_destroy(sys), "phfem_sys_destroy")
 
 
-def solve_opts(rtol=1e-10, inner_rtol=0.0, max_iter=0, max_refine=0, check_every=0) -> SolveOpts:
-    return SolveOpts(float(rtol), float(inner_rtol), int(max_iter), int(max_refine), int(check_every), 0)
+def solve_opts(rtol=1e-10, inner_rtol=0.0, max_iter=0, max_refine=0, check_every=0, order=0) -> SolveOpts:
+    """order: 0 = the Jacobi iteration in the locality order of the edges, 1 = in the paper's edge order."""
+    return SolveOpts(float(rtol), float(inner_rtol), int(max_iter), int(max_refine), int(check_every), int(order))
 
 
 def phfem_solve(sys, opts=None, w0=None, w=None, U=None, Lambda=None, raise_on_noconv=True) -> dict:
@@ -557,6 +565,18 @@ def phfem_error_norms(mesh, nq, U=None, u_q=None, grad_q=None, Lambda=None, kapp
                                    _ptr(Lambda, torch.float64, I["nL"]), _ptr(kappa_q, torch.float64, nq * I["nL"]),
                                    C.byref(out)), "phfem_error_norms")
     return out.as_dict()
+
+
+def phfem_mesh_order(mesh, perm=None) -> dict:
+    """The locality order of the iteration kernels: perm[i] = the edge held by
+    internal row i (a CUDA int32 tensor of nE), and the number of rows whose
+    neighbours are stored as full indices."""
+    n = phfem_mesh_info_get(mesh)["nE"]
+    if perm is None:
+        perm = torch.empty(n, dtype=torch.int32, device="cuda")
+    novf = C.c_int32()
+    _check(lib().phfem_mesh_order(mesh, _ptr(perm, torch.int32, n), C.byref(novf)), "phfem_mesh_order")
+    return {"perm": perm, "overflow_rows": int(novf.value)}
 
 
 # --- solve without device allocation -------------------------------------------
