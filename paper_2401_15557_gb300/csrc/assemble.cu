@@ -285,6 +285,8 @@ void sys_free(phfem_sys s) {
   dfree(c, s->bw);
   if (s->mg) mg_forget_system(s->mg);
   dfree(c, s->x);
+  dfree(c, s->xh);
+  dfree(c, s->xl);
   dfree(c, s->r64);
   dfree(c, s->ri);  // p and q live in the same allocation
   dfree(c, s->partials);
@@ -416,6 +418,8 @@ int assemble_system(phfem_mesh mesh, const phfem_coeffs& c, const double* f_mid,
   chk(dalloc_n(ctx, &sys->bc, nE));
   if (c.form == PHFEM_FORM_FLUX) chk(dalloc_n(ctx, &sys->St, 9 * nT));
   chk(dalloc_n(ctx, &sys->x, nE));
+  chk(dalloc_n(ctx, &sys->xh, nE));
+  chk(dalloc_n(ctx, &sys->xl, nE));
   chk(dalloc_n(ctx, &sys->r64, nE));
   {  // r, p and q in one allocation: the iteration keeps them resident in L2 as one window
     const size_t vb = (nE * isz + 255) / 256 * 256;

@@ -126,16 +126,6 @@ __device__ __forceinline__ double y_value(double y) { return y; }
 __device__ __forceinline__ void y_zero(float2& y) { y = make_float2(0.f, 0.f); }
 __device__ __forceinline__ void y_zero(double& y) { y = 0.0; }
 
-// (h, l) += v in FP64: TwoSum of the leading parts, then renormalised.
-__device__ __forceinline__ void dd_add(double& h, double& l, double v) {
-  const double s = h + v;
-  const double bb = s - h;
-  const double e = (h - (s - bb)) + (v - bb);
-  const double t = e + l;
-  h = s + t;
-  l = t - (h - s);
-}
-
 // Operator rows in the locality order (once per system).
 template <typename T>
 __global__ void k_fcg_op(int n, const int32_t* __restrict__ perm, const T* __restrict__ lval,

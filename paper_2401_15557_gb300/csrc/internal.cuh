@@ -158,7 +158,10 @@ struct phfem_sys_s {
   void* dinv;            // [nE]: 1 / S_ee (Jacobi)
   double* f;             // [nE]: copy of f at the midpoints (elliptic recovery)
   // solver workspace
-  double* x;             // [nE] current midpoint values (FP64)
+  double* x;             // [nE] current midpoint values (FP64); during a paper-order solve the
+                         //      correction since the last reliable update
+  double* xh;            // [nE] paper-order solve: the solution as an FP64 pair xh + xl
+  double* xl;            // [nE]
   double* r64;           // [nE]
   size_t l2_vec;         // bytes of one inner vector slot (r, p, q are consecutive slots)
   void* ri;              // [nE] inner vectors (float or double); pi and qi follow ri in one allocation

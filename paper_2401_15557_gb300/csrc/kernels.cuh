@@ -314,11 +314,38 @@ __device__ __forceinline__ T spmv_row(const int32_t* nbr, const T* lval,
   return s;
 }
 
-// b_e - (S x)_e in FP64 difference form, and the row's |S| |x| (the scale of
-// the rounding of x to FP64).
-__device__ __forceinline__ double residual_row(const int32_t* nbr, const double* val,
-                                               const double* b, const double* x, size_t m,
-                                               int e, double& absrow) {
+// b_e - (S x)_e in FP64 difference form with x = xh + xl (an unevaluated
+// FP64 pair): each difference x_e - x_s is formed from the pairs with TwoSum
+// on the leading parts, so the row's own rounding is about 2^-53 of
+// |rho x_e| + sum_s |l_es (x_e - x_s)|, returned in absrow (the evaluation
+// floor).
+__device__ __forceinline__ double residual_row(const int32_t* nbr, const double* val, const double* b,
+                                               const double* xh, const double* xl, size_t m, int e,
+                                               double& absrow) {
+  const double he = xh[e], le = xl[e];
+  const double rho = val[e];
+  double sx = rho * he + rho * le;
+  double fl = fabs(rho * he);
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    const double l = val[(s + 1) * m + e];
+    const int c = nbr[s * m + e];
+    const double nh = -xh[c];
+    const double sh = he + nh;
+    const double bb = sh - he;
+    const double eh = (he - (sh - bb)) + (nh - bb);
+    const double d = sh + (eh + (le - xl[c]));
+    sx += l * d;
+    fl += fabs(l * d);
+  }
+  absrow = fl;
+  return b[e] - sx;
+}
+
+// The same with x in plain FP64 (the batched kernel), absrow the scale of
+// the FP64 rounding of x: sum |S_es| |x_s| over the row.
+__device__ __forceinline__ double residual_row(const int32_t* nbr, const double* val, const double* b,
+                                               const double* x, size_t m, int e, double& absrow) {
   const double xe = x[e];
   double sx = val[e] * xe;
   double fl = fabs(val[e] * xe);
@@ -330,6 +357,16 @@ __device__ __forceinline__ double residual_row(const int32_t* nbr, const double*
   }
   absrow = fl;
   return b[e] - sx;
+}
+
+// (h, l) += v in FP64: TwoSum of the leading parts, then renormalised.
+__device__ __forceinline__ void dd_add(double& h, double& l, double v) {
+  const double s = h + v;
+  const double bb = s - h;
+  const double e = (h - (s - bb)) + (v - bb);
+  const double t = e + l;
+  h = s + t;
+  l = t - (h - s);
 }
 
 }  // namespace phfem

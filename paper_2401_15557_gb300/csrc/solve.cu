@@ -40,24 +40,56 @@
 namespace phfem {
 namespace {
 
-// r = b - S x (FP64); inner start vectors; reductions ||r||^2, r.D^-1 r, the
-// FP64 floor estimate and (after an update) r.p.  Modes:
+// The solution of a solve is x = (xh + xl) + y: an unevaluated FP64 pair
+// and the FP64 correction y accumulated by the iterations since the last
+// reliable update (the vector sys->x during the solve).  k_dd_begin moves the
+// start vector into the pair, k_dd_fold adds y into it before every true
+// residual, and k_dd_end leaves the rounded sum in sys->x.
+__global__ void k_dd_begin(int nE, double* __restrict__ x, double* __restrict__ xh, double* __restrict__ xl) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    xh[e] = x[e];
+    xl[e] = 0.0;
+    x[e] = 0.0;
+  }
+}
+
+__global__ void k_dd_fold(int nE, double* __restrict__ x, double* __restrict__ xh, double* __restrict__ xl,
+                          const SolveState* st, int cond) {
+  if (cond && st->done != 1) return;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    double h = xh[e], l = xl[e];
+    dd_add(h, l, x[e]);
+    xh[e] = h;
+    xl[e] = l;
+    x[e] = 0.0;
+  }
+}
+
+__global__ void k_dd_end(int nE, double* __restrict__ x, const double* __restrict__ xh,
+                         const double* __restrict__ xl) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    double h = xh[e], l = xl[e];
+    dd_add(h, l, x[e]);
+    x[e] = h + l;
+  }
+}
+
+// r = b - S x (FP64, x = xh + xl after the fold); inner start vectors;
+// reductions ||r||^2, r.D^-1 r, the evaluation floor and (after an update)
+// r.p.  Modes:
 //   0  ||b_free||^2 with the Dirichlet lifting (x replaced by (0, u_D));
 //   1  start: p = D^-1 r;
 //   2  reliable update: the true residual replaces the recursive one, p kept;
 //   3  as 2, but only if the iteration asked for an update (done == 1).
-// The last block decides on the device: converged (rtol, or twice the FP64
-// floor), the line-search step, or a restart of the direction.
-// Decision after a true residual (last block, thread 0): the iteration's
-// state, convergence (rtol, or twice the FP64 floor), and for a reliable
-// update the line-search step or a restart of the direction.
+// The last block decides on the device (decide()): converged (rtol, or twice
+// the evaluation floor), the line-search step, or a restart of the direction.
 // With precond != 0 (multigrid) the kernel only forms r and the sums ||r||^2
 // and the floor; the preconditioner and k_mg_finish complete the step.
 template <typename T>
 __global__ void k_residual(int nE, const int32_t* __restrict__ nbr, const double* __restrict__ val,
-                           const double* __restrict__ b, const double* __restrict__ x,
-                           const uint8_t* __restrict__ eclass, uint8_t ident, const T* __restrict__ dinv,
-                           T* __restrict__ ri, T* __restrict__ pi, double* partials,
+                           const double* __restrict__ b, const double* __restrict__ xh,
+                           const double* __restrict__ xl, const uint8_t* __restrict__ eclass, uint8_t ident,
+                           const T* __restrict__ dinv, T* __restrict__ ri, T* __restrict__ pi, double* partials,
                            SolveState* st, double rtol2, double inner_rtol2, int mode, int precond) {
   if (mode == 3) {
     if (st->done != 1) return;  // every block reads done before the last block rewrites it
@@ -81,8 +113,8 @@ __global__ void k_residual(int nE, const int32_t* __restrict__ nbr, const double
       }
       acc_r += r * r;
     } else {
-      double fl;  // |S| |x| of the row: scale of the FP64 rounding of x
-      r = residual_row(nbr, val, b, x, m, e, fl);
+      double fl;  // scale of the row's own rounding
+      r = residual_row(nbr, val, b, xh, xl, m, e, fl);
       acc_r += r * r;
       fl *= 0x1p-53;
       acc_f += fl * fl;
@@ -682,7 +714,11 @@ struct Launch {
     phfem_ctx ctx = sys->mesh->ctx;
     const int pre = (sys->mg && mode != 0) ? 1 : 0;
     prof_start(ctx, kProfResidual);
-    k_residual<T><<<g, kBlock, 0, s>>>(nE, sys->mesh->nbr, sys->val, sys->b, sys->x, sys->mesh->eclass,
+    if (mode >= 2) {
+      k_dd_fold<<<g, kBlock, 0, s>>>(nE, sys->x, sys->xh, sys->xl, sys->st, mode == 3);
+      PH_TRY(check_launch(ctx, "k_dd_fold"));
+    }
+    k_residual<T><<<g, kBlock, 0, s>>>(nE, sys->mesh->nbr, sys->val, sys->b, sys->xh, sys->xl, sys->mesh->eclass,
                                        sys->ident_class, (const T*)sys->dinv, (T*)sys->ri, (T*)sys->pi,
                                        sys->partials, sys->st, rtol2, irtol2, mode, pre);
     prof_stop(ctx, kProfResidual);
@@ -746,6 +782,8 @@ int solve_typed(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats) {
                     rp_window(sys)};
   static const bool verbose = getenv("PHFEM_VERBOSE") != nullptr;
   // ||b|| of the free-edge system (with the Dirichlet lifting), then the start
+  k_dd_begin<<<L.g, kBlock, 0, L.s>>>(nE, sys->x, sys->xh, sys->xl);
+  PH_TRY(check_launch(ctx, "k_dd_begin"));
   PH_TRY(L.residual(0));
   PH_TRY(L.residual(1));
   PH_TRY(read_state(sys));
@@ -781,6 +819,8 @@ int solve_typed(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats) {
     for (int k = 0; k < chunk; ++k) PH_TRY(L.iteration());
     PH_TRY(read_state(sys));
   }
+  k_dd_end<<<L.g, kBlock, 0, L.s>>>(nE, sys->x, sys->xh, sys->xl);
+  PH_TRY(check_launch(ctx, "k_dd_end"));
   if (L.win.bytes > 0) {  // the window's lines and the set-aside go back to normal L2 use
     cudaCtxResetPersistingL2Cache();
     cudaGetLastError();
@@ -822,7 +862,11 @@ int bicgstab_typed(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats)
   const double rtol2 = o.rtol * o.rtol, irtol2 = o.inner_rtol * o.inner_rtol;
   auto residual = [&](int mode) -> int {
     prof_start(ctx, kProfResidual);
-    k_residual<T><<<g, kBlock, 0, s>>>(nE, m->nbr, sys->val, sys->b, sys->x, m->eclass, sys->ident_class, dinv, r,
+    if (mode >= 2) {
+      k_dd_fold<<<g, kBlock, 0, s>>>(nE, sys->x, sys->xh, sys->xl, sys->st, mode == 3);
+      PH_TRY(check_launch(ctx, "k_dd_fold"));
+    }
+    k_residual<T><<<g, kBlock, 0, s>>>(nE, m->nbr, sys->val, sys->b, sys->xh, sys->xl, m->eclass, sys->ident_class, dinv, r,
                                        (T*)sys->pi, sys->partials, sys->st, rtol2, irtol2, mode, mode == 0 ? 0 : 1);
     prof_stop(ctx, kProfResidual);
     PH_TRY(check_launch(ctx, "k_residual"));
@@ -843,6 +887,8 @@ int bicgstab_typed(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats)
     ctx->launches += 4;
     return check_launch(ctx, "k_bi");
   };
+  k_dd_begin<<<g, kBlock, 0, s>>>(nE, sys->x, sys->xh, sys->xl);
+  PH_TRY(check_launch(ctx, "k_dd_begin"));
   PH_TRY(residual(0));
   PH_TRY(residual(1));
   PH_TRY(read_state(sys));
@@ -875,6 +921,8 @@ int bicgstab_typed(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats)
     for (int k = 0; k < chunk; ++k) PH_TRY(iteration());
     PH_TRY(read_state(sys));
   }
+  k_dd_end<<<g, kBlock, 0, s>>>(nE, sys->x, sys->xh, sys->xl);
+  PH_TRY(check_launch(ctx, "k_dd_end"));
   const SolveState& h = *sys->st_host;
   const double rel = h.bb > 0 ? std::sqrt(h.rr64 / h.bb) : 0.0;
   if (stats) {
@@ -900,6 +948,8 @@ int capture_typed(phfem_sys sys, const phfem_solve_opts& o, cudaStream_t cs, int
   phfem_ctx ctx = sys->mesh->ctx;
   const int nE = sys->mesh->info.nE;
   const Launch<T> L{sys, cs, grid_for(ctx, nE), nE, o.rtol * o.rtol, o.inner_rtol * o.inner_rtol, rp_window(sys)};
+  k_dd_begin<<<L.g, kBlock, 0, cs>>>(nE, sys->x, sys->xh, sys->xl);
+  PH_TRY(check_launch(ctx, "k_dd_begin"));
   PH_TRY(L.residual(0));
   PH_TRY(L.residual(1));
   cudaStreamCaptureStatus cst;
@@ -939,6 +989,10 @@ int capture_typed(phfem_sys sys, const phfem_solve_opts& o, cudaStream_t cs, int
     if (e != cudaSuccess && st == PHFEM_OK) st = cuda_fail(e, "cudaStreamEndCapture(body)", __FILE__, __LINE__);
   }
   cudaStreamDestroy(bs);
+  if (st == PHFEM_OK) {
+    k_dd_end<<<L.g, kBlock, 0, cs>>>(nE, sys->x, sys->xh, sys->xl);
+    st = check_launch(ctx, "k_dd_end");
+  }
   return st;
 }
 

@@ -279,15 +279,18 @@ def test_full_size_lshape_multigrid(ctx):
     U = torch.empty(3 * info["nT"], dtype=torch.float64, device="cuda")
     w = torch.empty(info["nE"], dtype=torch.float64, device="cuda")
     st = P.phfem_solve(sysh, P.solve_opts(rtol=1e-10), w=w, U=U)
-    assert st["converged"] in (1, 2) and st["iterations"] <= 60, st
-    target = max(1e-10, 2.0 * st["fp64_floor"])
-    assert st["rel_residual"] <= target, st
+    # the solver's iterate (an FP64 pair plus the last correction) meets 1e-10
+    assert st["converged"] == 1 and st["iterations"] <= 60 and st["rel_residual"] <= 1e-10, st
     T = {k: v.cpu().numpy() for k, v in P.phfem_mesh_tables(hs[-1]).items()}
     val = torch.empty(info["nnz"], dtype=torch.float64, device="cuda")
     rhs = torch.empty(info["nF"], dtype=torch.float64, device="cuda")
     P.phfem_sys_csr(sysh, val, rhs)
     S = sp.csr_matrix((val.cpu().numpy(), T["col"], T["row_ptr"]), shape=(info["nF"], info["nF"]))
-    assert O.relative_residual(S, rhs.cpu().numpy(), w.cpu().numpy()[T["free_id"] >= 0]) <= 1.2 * target
+    wf = w.cpu().numpy()[T["free_id"] >= 0]
+    bf = rhs.cpu().numpy()
+    # its rounding to FP64 (the exported w) may add up to 2^-53 || |S| |w| || / ||b||
+    rounding = 2.0 ** -53 * np.linalg.norm(abs(S) @ np.abs(wf)) / np.linalg.norm(bf)
+    assert O.relative_residual(S, bf, wf) <= 1e-10 + rounding
     # the same solution as Jacobi-PCG on the generator's numbering of the mesh
     pb = I.Problem(f=lambda x, y: 1.0 + 0 * x, g=lambda x, y, nx, ny: 0 * x, uD=lambda x, y: 0 * x, delta=1.0)
     gm = GpuMesh(fine, ctx)
