@@ -36,7 +36,16 @@ METRIC = "triangles/s & solves/s, FP32+refine vs FP64 at 1e-10 rel. residual; p5
 UNIT = "triangles/s"
 LEVELS = 5
 CPU_SAMPLE_LEVEL = 2
-SPMV_BYTES_PER_ROW = 4 * 4 + 4 * 4 + 4 + 4 + 4   # nbr, l (FP32), r, p, q
+# The dominant kernel of the FP32 iteration is the operator product with the
+# direction update folded in (k_fcg_spmv<float, fused>).  Per edge row it must
+# move the values of the row (four l_es and the reaction part: 20 B), the
+# preconditioned residual u and the previous direction p_old it forms p from
+# (8 B), and write p and q = S p (8 B): 36 B.  The plain product y = S x needs
+# values + x + y = 28 B (x read once); the four 16-bit neighbour differences
+# (8 B) are index data and are reported apart.
+SPMV_ALG_BYTES_PER_ROW = 20 + 4 + 4 + 4 + 4
+SPMV_PLAIN_BYTES_PER_ROW = 20 + 4 + 4
+SPMV_INDEX_BYTES_PER_ROW = 8
 
 
 def assembly_bytes(nT, nE, nV, nD, nN, fp32=True):
@@ -54,6 +63,16 @@ def assembly_bytes(nT, nE, nV, nD, nN, fp32=True):
     return tri, rows
 
 
+def _json_default(o):
+    """NumPy scalars and arrays in the printed line."""
+    import numpy as np
+    if isinstance(o, np.generic):
+        return o.item()
+    if isinstance(o, np.ndarray):
+        return o.tolist()
+    raise TypeError(f"not serialisable: {type(o).__name__}")
+
+
 def hbm_peak():
     """(GB/s, source) of the measured copy bandwidth, else the fallback figure."""
     try:
@@ -63,15 +82,15 @@ def hbm_peak():
     except Exception:
         pass
     return 6800.0, "fallback"
-# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one cg_spmv
-# launch at the full workload, from one ncu capture; valid only for the kernel
-# source and launch policy whose hash is recorded with it.
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the product kernel at the full workload, from one ncu capture; valid only for
+# the kernel source whose hash is recorded with it.
 # Kernel timing inside the timed region brackets every 16th launch of each
 # kernel with CUDA events (an event between two launches keeps the second from
 # overlapping the first's drain, so timing every launch would slow the step).
 PROFILE_EVERY = 16
-SPMV_TRAFFIC = 478.84e6
-SPMV_TRAFFIC_SRC_SHA = "c0c7c313896d081d"
+SPMV_TRAFFIC = 402.4e6
+SPMV_TRAFFIC_SRC_SHA = "694a49c147611b7c"
 
 
 def _function_src(path, signature):
@@ -84,13 +103,13 @@ def _function_src(path, signature):
 
 
 def _sha_spmv_src():
-    """Hash of the SpMV kernel's own source (k_cg_spmv, spmv_row) and of the L2
-    window it is launched with (rp_window), so that the captured traffic stays
-    valid while unrelated code changes."""
-    csrc = os.path.join(ROOT, "paper_2401_15557_gb300", "csrc")
-    text = (_function_src(os.path.join(csrc, "solve.cu"), "__global__ void __launch_bounds__(kBlock) k_cg_spmv(")
-            + _function_src(os.path.join(csrc, "kernels.cuh"), "__device__ __forceinline__ T spmv_row(")
-            + _function_src(os.path.join(csrc, "solve.cu"), "L2Window rp_window(phfem_sys sys) {"))
+    """Hash of the product kernel's own source (k_fcg_spmv and the row helpers
+    it calls), so that the captured traffic stays valid while unrelated code
+    changes."""
+    cg = os.path.join(ROOT, "paper_2401_15557_gb300", "csrc", "cg.cu")
+    text = (_function_src(cg, "__global__ void __launch_bounds__(kBlock) k_fcg_spmv(")
+            + _function_src(cg, "__device__ __forceinline__ void row_nbrs(")
+            + _function_src(cg, "__device__ __forceinline__ void load_l4(const float4*"))
     return hashlib.sha256(text.encode()).hexdigest()[:16]
 
 
@@ -124,6 +143,14 @@ def parse():
                     help="do not sample nvidia-smi clocks (profiling runs under ncu)")
     ap.add_argument("--max-iter", type=int, default=0,
                     help="cap the CG iterations (short runs for profiling only; not a benchmark)")
+    ap.add_argument("--batch-sample", type=int, default=128,
+                    help="main line: meshes of the batched workload measured beside the step (0: skip)")
+    ap.add_argument("--cn-steps", type=int, default=64,
+                    help="main line: Crank-Nicolson steps on 512 x 512 measured beside the step (0: skip)")
+    ap.add_argument("--serve-requests", type=int, default=100,
+                    help="main line: measured requests of the served stream beside the step (0: skip)")
+    ap.add_argument("--serve-warmup", type=int, default=20)
+    ap.add_argument("--cpu-procs", type=int, default=0, help="oracle processes of the all-core CPU leg (0: nproc)")
     return ap.parse_args()
 
 
@@ -159,6 +186,79 @@ def cpu_sample():
                       "oracle topology + saddle-point assembly + sparse direct solve (scipy SuperLU)")
 
 
+def cpu_info():
+    """nproc and the CPU model of this host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "hardware", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"nproc": os.cpu_count(), "cpu_model": model}
+
+
+def _oracle_job(job):
+    """One timed oracle run in a worker process (one thread): ("direct", level)
+    = topology + saddle-point assembly + SuperLU; ("pcg", level) = the condensed
+    edge system + plain Jacobi-PCG to 1e-10 + recovery."""
+    kind, level = job
+    sys.path.insert(0, ROOT)
+    from oracle import phfem_oracle as O
+    mesh, aT = workload(level)
+    t = time.perf_counter()
+    if kind == "direct":
+        O.solve_saddle(mesh, problem(), aT=aT)
+        info = {}
+    else:
+        r = O.solve_condensed(mesh, problem(), aT=aT, method="pcg", rtol=1e-10)
+        info = {"iterations": int(r["info"]["iterations"]), "rel_residual": float(r["info"]["rel_residual"])}
+    return time.perf_counter() - t, mesh.nT, info
+
+
+def cpu_baseline_legs(procs=0):
+    """The oracle on the host cores, each process single-threaded: the direct
+    solve at 1 core on the level-1 and level-2 samples, the condensed
+    Jacobi-PCG oracle at 1 core on level 2, and `procs` (default nproc)
+    concurrent direct solves of the level-2 sample (all-core throughput).
+    Processes are spawned, not forked, and start with one BLAS/OpenMP thread."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[k] = "1"
+    info = cpu_info()
+    procs = procs or info["nproc"] or 1
+    ctx = mp.get_context("spawn")
+    legs = {}
+    with cf.ProcessPoolExecutor(max_workers=1, mp_context=ctx) as ex:
+        ex.submit(_oracle_job, ("direct", 0)).result()  # imports and first-touch outside the timing
+        for lev in (1, CPU_SAMPLE_LEVEL):
+            el, nT, _ = ex.submit(_oracle_job, ("direct", lev)).result()
+            legs[f"direct_level{lev}_1core"] = {"triangles": nT, "s": el, "triangles_per_s": nT / el}
+        el, nT, inf = ex.submit(_oracle_job, ("pcg", CPU_SAMPLE_LEVEL)).result()
+        legs[f"condensed_pcg_level{CPU_SAMPLE_LEVEL}_1core"] = {"triangles": nT, "s": el, "triangles_per_s": nT / el,
+                                                               **inf}
+    with cf.ProcessPoolExecutor(max_workers=procs, mp_context=ctx) as ex:
+        list(ex.map(_oracle_job, [("direct", 0)] * procs))  # warm every worker
+        t = time.perf_counter()
+        res = list(ex.map(_oracle_job, [("direct", CPU_SAMPLE_LEVEL)] * procs))
+        wall = time.perf_counter() - t
+    nT = res[0][1]
+    legs[f"direct_level{CPU_SAMPLE_LEVEL}_all_cores"] = {"processes": procs, "triangles": nT * procs, "wall_s": wall,
+                                                          "triangles_per_s": nT * procs / wall}
+    return info, legs
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -176,9 +276,9 @@ def run_reference(args):
             "config": {"workload": f"lshape-jitter-level{args.levels}", "sampled_level": CPU_SAMPLE_LEVEL,
                        "sampled_triangles": mesh.nT, "rtol": 1e-10,
                        "step": "oracle topology + saddle-point assembly + direct solve"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample, **cpu_info()},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(line), flush=True)
+    print(json.dumps(line, default=_json_default), flush=True)
     return 0
 
 
@@ -235,39 +335,43 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def run_batched(args):
-    """4096 unit-square meshes with sides log-uniform in [8, 256], a = exp(0.5 z)
-    (seeded Fourier field), delta ~ U[0, 2], f = 1, u = 0 on x = 0, 1, zero flux
-    on y = 0, 1: assembly + FP32/FP64-refined solve of all meshes in one
-    persistent launch (block size from the autotuner), against the single-mesh
-    FP64 path on a sample."""
-    import numpy as np
+def _gpu_setup():
     import torch
     import __graft_entry__
+    __graft_entry__.build()
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    return torch.device("cuda", torch.cuda.current_device())
+
+
+def batched_measure(count, steps=2, warmup=1, single_sample=32, parity=True, no_clocks=True):
+    """Meshes 0..count-1 of the batched workload (unit squares with sides
+    log-uniform in [8, 256], a = exp(0.5 z) from a seeded Fourier field,
+    delta ~ U[0, 2], f = 1, u = 0 on x = 0, 1, zero flux on y = 0, 1):
+    assembly + solve + recovery of every mesh in one persistent launch, FP32 +
+    refinement and FP64 (block size from the autotuner), against the plain
+    single-mesh FP64 path (assemble + solve per mesh) on the first meshes."""
+    import numpy as np
+    import torch
     from paper_2401_15557_gb300 import inputs as I
     from paper_2401_15557_gb300 import phfem as P
-    __graft_entry__.build()
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
+    dev = _gpu_setup()
     t0 = time.perf_counter()
-    sides = I.batch_sides(args.batch_count)
+    sides = I.batch_sides(4096)[:count]
     members = [I.batch_member(i, n) for i, n in enumerate(sides)]
     t_gen = time.perf_counter() - t0
     stream = torch.cuda.current_stream()
     ctx = P.phfem_ctx_create(stream)
     d = lambda a, t: torch.as_tensor(np.ascontiguousarray(a), dtype=t, device=dev)
     t0 = time.perf_counter()
-    meshes = []
-    for m, _, _ in members:
-        meshes.append(P.phfem_mesh_build(ctx, d(m.xy, torch.float64), d(m.tri, torch.int32),
-                                         d(m.dirichlet, torch.int32), d(m.neumann, torch.int32)))
+    meshes = [P.phfem_mesh_build(ctx, d(m.xy, torch.float64), d(m.tri, torch.int32), d(m.dirichlet, torch.int32),
+                                 d(m.neumann, torch.int32)) for m, _, _ in members]
     batch = P.phfem_batch_create(ctx, meshes)
     torch.cuda.synchronize()
     t_tables = time.perf_counter() - t0
-    infos = [P.phfem_mesh_info_get(h) for h in meshes[:128]]
-    for h in meshes[128:]:
+    keep = min(single_sample, count)
+    infos = [P.phfem_mesh_info_get(h) for h in meshes[:keep]]
+    for h in meshes[keep:]:
         P.phfem_mesh_destroy(h)
-    count = len(members)
     toff, eoff, loff = P.phfem_batch_offsets(batch, count)
     nT, nE = int(toff[-1]), int(eoff[-1])
     aT = d(np.concatenate([a for _, a, _ in members]), torch.float64)
@@ -276,36 +380,37 @@ def run_batched(args):
     U = torch.empty(3 * nT, dtype=torch.float64, device=dev)
     L = torch.empty(int(loff[-1]), dtype=torch.float64, device=dev)
     opts = P.solve_opts(rtol=1e-10)
+    out = {"meshes": count, "triangles": nT, "edges": nE, "sides": [int(sides.min()), int(sides.max())],
+           "setup_s": {"host_generation": t_gen, "tables": t_tables}}
+    clocks = None if no_clocks else ClockSampler(torch.cuda.current_device())
+    # the block size is tuned once, on the FP32 + refinement launch, and kept for FP64
     chosen, tune_ms = P.phfem_batch_tune(batch, delta, a_T=aT, f_mid=f, precision=P.PHFEM_FP32_IR, opts=opts)
-    res = None
-    for _ in range(args.warmup):
-        res = P.phfem_batch_solve(batch, count, delta, a_T=aT, f_mid=f, precision=P.PHFEM_FP32_IR, opts=opts,
-                                  U=U, Lambda=L)
-    clocks = ClockSampler(0) if not args.no_clocks else None
-    if clocks:
-        clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    e0.record(stream)
-    for _ in range(args.steps):
-        res = P.phfem_batch_solve(batch, count, delta, a_T=aT, f_mid=f, precision=P.PHFEM_FP32_IR, opts=opts,
-                                  U=U, Lambda=L)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    clk = clocks.stop() if clocks else None
-    ms = e0.elapsed_time(e1) / args.steps
-    r64 = P.phfem_batch_solve(batch, count, delta, a_T=aT, f_mid=f, precision=P.PHFEM_FP64, opts=opts, U=U)
-    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e2.record(stream)
-    r64 = P.phfem_batch_solve(batch, count, delta, a_T=aT, f_mid=f, precision=P.PHFEM_FP64, opts=opts, U=U)
-    e3.record(stream)
-    torch.cuda.synchronize()
-    ms64 = e2.elapsed_time(e3)
-    # the plain FP64 single-mesh path (assemble + solve per mesh) on the first 128 meshes
-    sample = min(128, count)
+    for prec, name in ((P.PHFEM_FP32_IR, "fp32_refined"), (P.PHFEM_FP64, "fp64")):
+        res = None
+        for _ in range(warmup):
+            res = P.phfem_batch_solve(batch, count, delta, a_T=aT, f_mid=f, precision=prec, opts=opts, U=U, Lambda=L)
+        if clocks and name == "fp32_refined":
+            clocks.start()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(steps):
+            res = P.phfem_batch_solve(batch, count, delta, a_T=aT, f_mid=f, precision=prec, opts=opts, U=U, Lambda=L)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if clocks and name == "fp32_refined":
+            out["clocks"] = clocks.stop()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"ms_per_launch": ms, "solves_per_s": count * 1e3 / ms, "triangles_per_s": nT * 1e3 / ms,
+                     "block": chosen, "tune_ms_per_block": tune_ms,
+                     "iterations": {"median": float(np.median(res["iterations"])), "max": int(res["iterations"].max())},
+                     "converged": {"rtol": int((res["converged"] == 1).sum()), "floor": int((res["converged"] == 2).sum()),
+                                   "not": int((res["converged"] == 0).sum())},
+                     "rel_residual_max": float(res["rel_residual"].max())}
+    # the plain FP64 single-mesh path (assemble + solve per mesh) on the first meshes
     t0 = time.perf_counter()
     tri_sample = 0
-    for i in range(sample):
+    for i in range(keep):
         m, a, dl = members[i]
         fm = torch.ones(infos[i]["nE"], dtype=torch.float64, device=dev)
         sh = P.phfem_assemble(meshes[i], fm, None, a_T=d(a, torch.float64), delta=dl, precision=P.PHFEM_FP64)
@@ -314,112 +419,108 @@ def run_batched(args):
         tri_sample += m.nT
     torch.cuda.synchronize()
     t_single = time.perf_counter() - t0
-    # the batch's FP32 + refinement U of the eight smallest meshes against the
-    # oracle's direct saddle-point solve (the CPU-baseline leg)
-    parity = None
-    if not args.no_cpu:
+    out["single_mesh_fp64"] = {"meshes": keep, "triangles_per_s": tri_sample / t_single, "solves_per_s": keep / t_single}
+    if parity:
+        # FP32 + refinement U of the four smallest meshes against the oracle's direct saddle-point solve
         from oracle import phfem_oracle as O
         P.phfem_batch_solve(batch, count, delta, a_T=aT, f_mid=f, precision=P.PHFEM_FP32_IR, opts=opts, U=U)
         Uh = U.cpu().numpy()
         worst = 0.0
-        picks = np.argsort(sides, kind="stable")[:8]
+        picks = np.argsort(sides, kind="stable")[:4]
         for i in picks:
             m, a, dl = members[i]
-            pb = I.Problem(f=lambda x, y: 1.0 + 0 * x, g=lambda x, y, nx, ny: 0 * x, uD=lambda x, y: 0 * x,
-                           delta=dl)
+            pb = I.Problem(f=lambda x, y: 1.0 + 0 * x, g=lambda x, y, nx, ny: 0 * x, uD=lambda x, y: 0 * x, delta=dl)
             ref = O.solve_saddle(m, pb, aT=a)
             got = Uh[3 * int(toff[i]):3 * int(toff[i + 1])]
             worst = max(worst, float(np.max(np.abs(got - ref["U"])) / np.max(np.abs(ref["U"]))))
-        parity = {"meshes": [int(i) for i in picks], "U_max_rel_error": worst}
-    line = {
-        "metric": METRIC, "value": nT * 1e3 / ms, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"batched-{count}-unit-squares", "meshes": count, "triangles": nT, "edges": nE,
-                   "sides": [int(sides.min()), int(sides.max())], "block": chosen,
-                   "step": "assemble+solve+recover of every mesh, one launch"},
-        "solves_per_s": count * 1e3 / ms,
-        "iterations": {"median": float(np.median(res["iterations"])), "max": int(res["iterations"].max())},
-        "converged": {"rtol": int((res["converged"] == 1).sum()), "floor": int((res["converged"] == 2).sum())},
-        "rel_residual_max": float(res["rel_residual"].max()),
-        "fp64_batched": {"value": nT * 1e3 / ms64, "ms_per_step": ms64, "solves_per_s": count * 1e3 / ms64},
-        "single_mesh_fp64_sample": {"meshes": sample, "triangles_per_s": tri_sample / t_single,
-                                    "solves_per_s": sample / t_single},
-        "tune_ms_per_block": tune_ms, "setup_s": {"host_generation": t_gen, "tables": t_tables},
-        "clocks": clk, "oracle_parity": parity,
-    }
-    print(json.dumps(line), flush=True)
-    for h in meshes[:128]:
+        out["oracle_parity"] = {"meshes": [int(i) for i in picks], "U_max_rel_error": worst}
+    for h in meshes[:keep]:
         P.phfem_mesh_destroy(h)
     P.phfem_batch_destroy(batch)
     P.phfem_ctx_destroy(ctx)
+    return out
+
+
+def run_batched(args):
+    """All 4096 meshes of the batched workload (separate line)."""
+    b = batched_measure(args.batch_count, steps=args.steps, warmup=args.warmup, single_sample=128,
+                        parity=not args.no_cpu, no_clocks=args.no_clocks)
+    g = b["fp32_refined"]
+    line = {"metric": METRIC, "value": g["triangles_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": g["ms_per_launch"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"batched-{b['meshes']}-unit-squares", "meshes": b["meshes"],
+                       "triangles": b["triangles"], "edges": b["edges"], "sides": b["sides"],
+                       "step": "assemble+solve+recover of every mesh, one launch"},
+            "solves_per_s": g["solves_per_s"], "batched": b, "clocks": b.get("clocks")}
+    print(json.dumps(line, default=_json_default), flush=True)
     return 0
 
 
-def run_heat(args):
-    """Crank-Nicolson for u_t - Lap u = f on the unit square, n x n squares
-    (n = 512: 524,288 triangles), dt = 1/n, T = 1: u = e^-t sin(pi x) sin(pi y),
-    u = 0 on x = 0, 1 and the exact flux on y = 0, 1.  One step = right-hand
-    side, solve to 1e-10 (warm start) and multiplier recovery; steps replayed
-    from the captured CUDA graph against host-driven steps."""
+def heat_measure(n, steps, host=False, mg=True):
+    """Crank-Nicolson for u_t - Lap u = f on the unit square, n x n squares,
+    dt = 1/n: u = e^-t sin(pi x) sin(pi y), u = 0 on x = 0, 1 and the exact flux
+    on y = 0, 1.  One step = right-hand side, solve to 1e-10 (warm start) and
+    multiplier recovery, replayed from the captured CUDA graph (and, with
+    host=True, host-driven), FP32 + refinement and FP64, Jacobi and (mg=True)
+    the multigrid preconditioner over the n = n0 2^k hierarchy.  `steps` steps
+    are timed after two warm-up steps; the vertex error is taken after them."""
     import numpy as np
     import torch
-    import __graft_entry__
     from paper_2401_15557_gb300 import inputs as I
     from paper_2401_15557_gb300 import phfem as P
-    __graft_entry__.build()
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    n = args.heat_n
+    dev = _gpu_setup()
     mesh = I.square_mesh(n)
     pi = np.pi
     sfun = lambda x, y: np.sin(pi * x) * np.sin(pi * y)
-    stream = torch.cuda.current_stream()
-    ctx = P.phfem_ctx_create(stream)
+    ctx = P.phfem_ctx_create(torch.cuda.current_stream())
     d = lambda a, t: torch.as_tensor(np.ascontiguousarray(a), dtype=t, device=dev)
+    dt = 1.0 / n
+    nt = steps + 2
+    phi = np.exp(-dt * np.arange(nt + 1))[None]
+    t_end = dt * nt
+    fsrc = lambda x, y: (2 * pi * pi - 1.0) * sfun(x, y)
+    gsrc = lambda x, y, nx, ny: pi * (np.cos(pi * x) * np.sin(pi * y) * nx + np.sin(pi * x) * np.cos(pi * y) * ny)
+
+    def data(xy, tabs):
+        f0, g0 = I.edge_data(xy, tabs["ed2el"], tabs["eclass"], fsrc, gsrc, lambda x, y: 0 * x)
+        w0, _ = I.edge_data(xy, tabs["ed2el"], tabs["eclass"], sfun)
+        return d(f0[None], torch.float64), d(g0[None], torch.float64), d(w0, torch.float64)
+
+    def run(sysh, F, G, W, mode, xy, tri):
+        cn = P.phfem_cn_create(sysh, F, G, phi, W)
+        stepf = P.phfem_cn_step_graph if mode == "graph" else P.phfem_cn_step
+        stepf(cn, 2, P.solve_opts(rtol=1e-10))  # capture (graph) and warm up
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st = stepf(cn, steps, P.solve_opts(rtol=1e-10))
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        U = torch.empty(3 * tri.shape[0], dtype=torch.float64, device=dev)
+        P.phfem_cn_read(cn, U=U)
+        P.phfem_cn_destroy(cn)
+        P_ = xy[tri]
+        ue = np.exp(-t_end) * sfun(P_[..., 0], P_[..., 1]).ravel()
+        return {"steps_per_s": steps / el, "ms_per_step": 1e3 * el / steps, "triangles_per_s": steps * tri.shape[0] / el,
+                "iterations_per_step": st["iterations"] / max(1, steps), "converged": st["converged"],
+                "rel_residual_max": st["rel_residual"], "max_vertex_error": float(np.max(np.abs(U.cpu().numpy() - ue)))}
+
+    out = {"n": n, "triangles": mesh.nT, "dt": dt, "steps": steps, "t_end": t_end}
     mh = P.phfem_mesh_build(ctx, d(mesh.xy, torch.float64), d(mesh.tri, torch.int32),
                             d(mesh.dirichlet, torch.int32), d(mesh.neumann, torch.int32))
-    info = P.phfem_mesh_info_get(mh)
+    out["edges"] = P.phfem_mesh_info_get(mh)["nE"]
     T_ = {k: v.cpu().numpy() for k, v in P.phfem_mesh_tables(mh).items()}
-    f0, g0 = I.edge_data(mesh.xy, T_["ed2el"], T_["eclass"], lambda x, y: (2 * pi * pi - 1.0) * sfun(x, y),
-                         lambda x, y, nx, ny: pi * (np.cos(pi * x) * np.sin(pi * y) * nx
-                                                    + np.sin(pi * x) * np.cos(pi * y) * ny),
-                         lambda x, y: 0 * x)
-    w0, _ = I.edge_data(mesh.xy, T_["ed2el"], T_["eclass"], sfun)
-    dt = 1.0 / n
-    nsteps = n
-    phi = np.exp(-dt * np.arange(nsteps + 1))[None]
-    F, G, W0 = d(f0[None], torch.float64), d(g0[None], torch.float64), d(w0, torch.float64)
-    out = {}
-    U = torch.empty(3 * info["nT"], dtype=torch.float64, device=dev)
+    F, G, W = data(mesh.xy, T_)
     for prec, name in ((P.PHFEM_FP32_IR, "fp32_refined"), (P.PHFEM_FP64, "fp64")):
         sysh = P.phfem_assemble(mh, None, None, delta=0.0, dt=dt, precision=prec)
-        for mode in ("graph", "host"):
-            cn = P.phfem_cn_create(sysh, F, G, phi, W0)
-            stepf = P.phfem_cn_step_graph if mode == "graph" else P.phfem_cn_step
-            stepf(cn, 2, P.solve_opts(rtol=1e-10))  # capture (graph) and warm up
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            st = stepf(cn, nsteps - 2, P.solve_opts(rtol=1e-10))
-            torch.cuda.synchronize()
-            el = time.perf_counter() - t0
-            P.phfem_cn_read(cn, U=U)
-            P.phfem_cn_destroy(cn)
-            out[f"{name}_{mode}"] = {"steps_per_s": (nsteps - 2) / el, "ms_per_step": 1e3 * el / (nsteps - 2),
-                                     "iterations_per_step": st["iterations"] / max(1, nsteps - 2),
-                                     "converged": st["converged"], "rel_residual_max": st["rel_residual"]}
-        # error at t = 1 against the exact solution at the vertices
-        P_ = mesh.xy[mesh.tri]
-        ue = np.exp(-1.0) * sfun(P_[..., 0], P_[..., 1]).ravel()
-        out[f"{name}_graph"]["max_vertex_error_t1"] = float(np.max(np.abs(U.cpu().numpy() - ue)))
+        for mode in ("graph", "host") if host else ("graph",):
+            out[f"jacobi_{name}_{mode}"] = run(sysh, F, G, W, mode, mesh.xy, mesh.tri)
         P.phfem_sys_destroy(sysh)
-    # ---- the same run under the multigrid preconditioner: the n x n square is
-    # the k-fold device refinement of an (n / 2^k)-square mesh
+    P.phfem_mesh_destroy(mh)
     k = 0
     while n % (2 ** (k + 1)) == 0:
         k += 1
-    mg_info = None
-    if args.heat_mg and k >= 1:
+    if mg and k >= 1:  # the n x n square as the k-fold device refinement of an (n / 2^k)-square mesh
         m0 = I.square_mesh(n >> k)
         hs = [P.phfem_mesh_build(ctx, d(m0.xy, torch.float64), d(m0.tri, torch.int32),
                                  d(m0.dirichlet, torch.int32), d(m0.neumann, torch.int32))]
@@ -429,50 +530,36 @@ def run_heat(args):
         hs.append(hf)
         xyf, trif = arr["xy"].cpu().numpy(), arr["tri"].cpu().numpy()
         Tf = {kk: v.cpu().numpy() for kk, v in P.phfem_mesh_tables(hf).items()}
-        f1, g1 = I.edge_data(xyf, Tf["ed2el"], Tf["eclass"], lambda x, y: (2 * pi * pi - 1.0) * sfun(x, y),
-                             lambda x, y, nx, ny: pi * (np.cos(pi * x) * np.sin(pi * y) * nx
-                                                        + np.sin(pi * x) * np.cos(pi * y) * ny),
-                             lambda x, y: 0 * x)
-        w1, _ = I.edge_data(xyf, Tf["ed2el"], Tf["eclass"], sfun)
-        F1, G1, W1 = d(f1[None], torch.float64), d(g1[None], torch.float64), d(w1, torch.float64)
+        F1, G1, W1 = data(xyf, Tf)
         for prec, name in ((P.PHFEM_FP32_IR, "fp32_refined"), (P.PHFEM_FP64, "fp64")):
             sysh = P.phfem_assemble(hf, None, None, delta=0.0, dt=dt, precision=prec)
-            mg = P.phfem_mg_create(sysh, hs)
-            mg_info = P.phfem_mg_info(mg)
-            P.phfem_sys_set_mg(sysh, mg)
-            cn = P.phfem_cn_create(sysh, F1, G1, phi, W1)
-            P.phfem_cn_step_graph(cn, 2, P.solve_opts(rtol=1e-10))
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            st = P.phfem_cn_step_graph(cn, nsteps - 2, P.solve_opts(rtol=1e-10))
-            torch.cuda.synchronize()
-            el = time.perf_counter() - t0
-            P.phfem_cn_read(cn, U=U)
-            P.phfem_cn_destroy(cn)
-            P_ = xyf[trif]
-            ue = np.exp(-1.0) * sfun(P_[..., 0], P_[..., 1]).ravel()
-            out[f"mg_{name}_graph"] = {"steps_per_s": (nsteps - 2) / el, "ms_per_step": 1e3 * el / (nsteps - 2),
-                                       "iterations_per_step": st["iterations"] / max(1, nsteps - 2),
-                                       "converged": st["converged"], "rel_residual_max": st["rel_residual"],
-                                       "max_vertex_error_t1": float(np.max(np.abs(U.cpu().numpy() - ue))),
-                                       "levels": k + 1}
-            P.phfem_mg_destroy(mg)
+            mgh = P.phfem_mg_create(sysh, hs)
+            out["mg_levels"] = P.phfem_mg_info(mgh)["levels"]
+            P.phfem_sys_set_mg(sysh, mgh)
+            out[f"multigrid_{name}_graph"] = run(sysh, F1, G1, W1, "graph", xyf, trif)
+            P.phfem_mg_destroy(mgh)
             P.phfem_sys_destroy(sysh)
         for h in reversed(hs):
             P.phfem_mesh_destroy(h)
-    g = out["fp32_refined_graph"]
-    line = {"metric": METRIC, "value": g["steps_per_s"] * mesh.nT, "unit": UNIT + " (per CN step)", "n_gpus": 1,
-            "steps": nsteps - 2, "warmup": 2, "ms_per_step": g["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": f"heat-cn-{n}x{n}", "triangles": mesh.nT, "edges": info["nE"], "dt": dt,
-                       "steps": nsteps}, "cn": out, "multigrid": mg_info}
-    print(json.dumps(line), flush=True)
-    P.phfem_mesh_destroy(mh)
     P.phfem_ctx_destroy(ctx)
+    return out
+
+
+def run_heat(args):
+    """Crank-Nicolson on 512 x 512 squares, 512 steps (separate line)."""
+    h = heat_measure(args.heat_n, args.heat_n - 2, host=True, mg=bool(args.heat_mg))
+    g = h["jacobi_fp32_refined_graph"]
+    line = {"metric": METRIC, "value": g["triangles_per_s"], "unit": UNIT + " (per CN step)", "n_gpus": 1,
+            "steps": h["steps"], "warmup": 2, "ms_per_step": g["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": f"heat-cn-{h['n']}x{h['n']}", "triangles": h["triangles"], "edges": h["edges"],
+                       "dt": h["dt"], "steps": h["steps"] + 2}, "cn": h}
+    print(json.dumps(line, default=_json_default), flush=True)
     return 0
 
 
-def run_serve(args):
+def serve_measure(requests, warmup, rate, slots, modes=("jacobi", "multigrid"), precisions=("fp32_refined",),
+                  no_clocks=True):
     """Poisson arrivals (seeded; mean rate 200/s) of 70 % elliptic and 30 %
     Crank-Nicolson requests (16..128 steps, dt = 1/n), meshes with triangle
     counts log-uniform in [1e3, 4e6] (n x n unit squares, n = round(sqrt(nT/2))),
@@ -482,16 +569,16 @@ def run_serve(args):
     latency = finish - submit.  The same arrival stream is served twice: with
     the meshes as given (Jacobi-PCG), and as refinement requests (the side n
     realised as n0 2^k, n0 in [4, 8), the coarse n0-square refined k times by
-    the server, which then solves with the multigrid preconditioner)."""
+    the server, which then solves with the multigrid preconditioner).  Each
+    stream is served in every precision of `precisions` (FP32 + refinement
+    and/or FP64).  Saturated, the completion rate is the server's capacity:
+    the highest arrival rate it sustains."""
     import numpy as np
     import torch
-    import __graft_entry__
     from paper_2401_15557_gb300 import inputs as I
     from paper_2401_15557_gb300 import phfem as P
-    __graft_entry__.build()
-    torch.cuda.set_device(0)
-    dev = torch.device("cuda", 0)
-    R = args.requests + args.warmup
+    dev = _gpu_setup()
+    R = requests + warmup
     seed = I.seed_for(4, 0)
     u = I.uniform(seed ^ 0x5E5E, 4 * R)
     nT_target = np.exp(np.log(1e3) + u[0::4] * (np.log(4e6) - np.log(1e3)))
@@ -499,7 +586,7 @@ def run_serve(args):
     sides = np.maximum(2, np.rint(n_target)).astype(int)
     kinds = (u[1::4] < 0.3).astype(int)
     steps = 16 + np.floor(u[2::4] * 113).astype(int)
-    arrivals = I.poisson_arrivals(R, args.rate, seed)
+    arrivals = I.poisson_arrivals(R, rate, seed)
     d = lambda a, t: torch.as_tensor(np.ascontiguousarray(a), dtype=t, device=dev)
     ctx = P.phfem_ctx_create(torch.cuda.current_stream())
 
@@ -557,8 +644,8 @@ def run_serve(args):
         return reqs, keep
 
     def serve(reqs):
-        srv = P.phfem_server_create(args.slots, 120e9, P.solve_opts(rtol=1e-10))
-        clocks = ClockSampler(0) if not args.no_clocks else None
+        srv = P.phfem_server_create(slots, 120e9, P.solve_opts(rtol=1e-10))
+        clocks = ClockSampler(torch.cuda.current_device()) if not no_clocks else None
         if clocks:
             clocks.start()
         start = time.perf_counter()
@@ -572,41 +659,52 @@ def run_serve(args):
         clk = clocks.stop() if clocks else None
         res = [P.phfem_server_poll(srv, i, wait=False) for i in ids]
         P.phfem_server_destroy(srv)
-        meas = res[args.warmup:]
+        meas = res[warmup:]
         lat = np.array([r["t_finish"] - r["t_submit"] for r in meas]) * 1e3
         wait = np.array([r["t_admit"] - r["t_submit"] for r in meas]) * 1e3
         span = max(r["t_finish"] for r in meas) - min(r["t_submit"] for r in meas)
-        tri = sum(nt for (_, nt) in reqs[args.warmup:])
+        tri = sum(nt for (_, nt) in reqs[warmup:])
         ok = sum(1 for r in meas if r["status"] == 0)
         return {"solves_per_s": ok / span, "span_s": span, "p50_ms": float(np.percentile(lat, 50)),
                 "p99_ms": float(np.percentile(lat, 99)), "mean_queue_wait_ms": float(wait.mean()),
                 "triangles_per_s": tri / span, "ok": ok, "failed": len(meas) - ok,
-                "offered_triangles_per_s": tri / (arrivals[-1] - arrivals[args.warmup]) if len(meas) > 1 else None,
+                "offered_triangles_per_s": tri / (arrivals[-1] - arrivals[warmup]) if len(meas) > 1 else None,
+                "offered_requests_per_s": (len(meas) - 1) / (arrivals[-1] - arrivals[warmup]) if len(meas) > 1 else None,
                 "iterations_median": float(np.median([r["iterations"] for r in meas])), "clocks": clk}
 
-    out = {}
-    for mode in ("jacobi", "multigrid"):
+    out = {"requests": requests, "warmup": warmup, "rate_per_s": rate, "slots": slots, "hbm_budget_gb": 120,
+           "mix": "70% elliptic / 30% Crank-Nicolson 16-128 steps", "triangles": "log-uniform 1e3..4e6"}
+    pmap = {"fp32_refined": P.PHFEM_FP32_IR, "fp64": P.PHFEM_FP64}
+    for mode in modes:
         t0 = time.perf_counter()
         reqs, keep = build(mode)
         t_setup = time.perf_counter() - t0
-        out[mode] = serve(reqs)
-        out[mode]["setup_s"] = t_setup
+        for pname in precisions:
+            for rq, _ in reqs:
+                rq.precision = pmap[pname]
+            r = serve(reqs)
+            r["setup_s"] = t_setup
+            r["saturated"] = bool(r["offered_requests_per_s"] is not None
+                                  and r["solves_per_s"] < 0.9 * r["offered_requests_per_s"])
+            out[f"{mode}_{pname}"] = r
         del keep
         torch.cuda.empty_cache()
     P.phfem_ctx_destroy(ctx)
-    j = out["jacobi"]
-    nmeas = args.requests
-    line = {"metric": METRIC, "value": j["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": nmeas,
-            "warmup": args.warmup, "ms_per_step": 1e3 * j["span_s"] / nmeas, "higher_is_better": True,
+    return out
+
+
+def run_serve(args):
+    """The request stream of the serving workload (separate line)."""
+    sv = serve_measure(args.requests, args.warmup, args.rate, args.slots, modes=("jacobi", "multigrid"),
+                       precisions=("fp32_refined", "fp64"), no_clocks=args.no_clocks)
+    j = sv["jacobi_fp32_refined"]
+    line = {"metric": METRIC, "value": j["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.requests,
+            "warmup": args.warmup, "ms_per_step": 1e3 * j["span_s"] / args.requests, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": "serve-poisson", "rate_per_s": args.rate, "requests": nmeas,
-                       "slots": args.slots, "hbm_budget_gb": 120, "mix": "70% elliptic / 30% CN 16-128 steps",
-                       "triangles": "log-uniform 1e3..4e6"},
-            "p50_ms": j["p50_ms"], "p99_ms": j["p99_ms"], "mean_queue_wait_ms": j["mean_queue_wait_ms"],
-            "triangles_per_s": j["triangles_per_s"], "ok": j["ok"], "failed": j["failed"],
-            "offered_triangles_per_s": j["offered_triangles_per_s"], "setup_s": j["setup_s"], "clocks": j["clocks"],
-            "multigrid": out["multigrid"]}
-    print(json.dumps(line), flush=True)
+            "config": {"workload": "serve-poisson", "rate_per_s": args.rate, "requests": args.requests,
+                       "slots": args.slots, "hbm_budget_gb": 120},
+            "p50_ms": j["p50_ms"], "p99_ms": j["p99_ms"], "serve": sv, "clocks": j["clocks"]}
+    print(json.dumps(line, default=_json_default), flush=True)
     return 0
 
 
@@ -744,7 +842,7 @@ def main():
     ktimes = {k: P.phfem_ctx_kernel_time(ctx, k, reset=True)
               for k in ("cg_spmv", "cg_update", "cg_dir", "residual", "asm_tri", "asm_rows", "recover")}
     ph = {"mesh_build": [], "assemble": [], "solve_recover": []}
-    iters, refs, rel = [], [], []
+    iters, refs, rel, conv = [], [], [], []
     for e0, e1, e2, e3, st in phases:
         ph["mesh_build"].append(e0.elapsed_time(e1))
         ph["assemble"].append(e1.elapsed_time(e2))
@@ -752,6 +850,7 @@ def main():
         iters.append(st["iterations"])
         refs.append(st["refinements"])
         rel.append(st["rel_residual"])
+        conv.append(st["converged"])
     value = weak_throughput(world, nT, ms_step)
 
     # ---- FP64 path ----------------------------------------------------------
@@ -769,7 +868,7 @@ def main():
         ms64 = max_over_ranks(a0.elapsed_time(a1)) / args.fp64_steps
         fp64 = {"value": weak_throughput(world, nT, ms64), "unit": UNIT, "ms_per_step": ms64,
                 "solves_per_s": world * 1e3 / ms64, "iterations": ph64[-1][4]["iterations"],
-                "rel_residual": ph64[-1][4]["rel_residual"]}
+                "rel_residual": ph64[-1][4]["rel_residual"], "converged": ph64[-1][4]["converged"]}
 
     # ---- end to end from pinned host buffers ---------------------------------
     e2e = None
@@ -942,31 +1041,44 @@ def main():
                   "step": "phfem_mesh_refine: refined arrays and their tables in closed form"}
         P.phfem_mesh_destroy(mL)
 
-    # ---- roofline of the dominant kernel (cg_spmv) ----------------------------
+    # ---- roofline of the dominant kernel (the product kernel) -----------------
     spmv_ms, spmv_n = ktimes["cg_spmv"]
     peak, peak_src = hbm_peak()
     roof = None
     if spmv_n:
         avg = spmv_ms / spmv_n * 1e-3
-        achieved = SPMV_BYTES_PER_ROW * nE / avg / 1e9
+        alg = SPMV_ALG_BYTES_PER_ROW * nE
+        achieved = alg / avg / 1e9
         traffic = SPMV_TRAFFIC if SPMV_TRAFFIC_SRC_SHA == _sha_spmv_src() else None
         roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_cg_spmv<float>", "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": SPMV_BYTES_PER_ROW * nE, "avg_launch_ms": avg * 1e3}
+                "traffic": traffic, "kernel": "k_fcg_spmv<float, fused>", "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": alg, "algorithmic_bytes_per_row": SPMV_ALG_BYTES_PER_ROW,
+                "index_bytes_per_row": SPMV_INDEX_BYTES_PER_ROW, "avg_launch_ms": avg * 1e3,
+                "plain_product_bytes_per_row": SPMV_PLAIN_BYTES_PER_ROW,
+                "frac_plain_product_bytes": SPMV_PLAIN_BYTES_PER_ROW * nE / avg / 1e9 / peak,
+                "note": "algorithmic bytes: values 20 + u 4 + p_old 4 + p 4 + q 4 per row (the direction update is "
+                        "folded into the product); frac_plain_product_bytes counts values + x + y = 28 B only"}
+        if traffic:
+            roof["traffic_over_algorithmic"] = traffic / alg
 
     tot_k = sum(v[0] for v in ktimes.values())
     kernel_share = {k: {"ms_timed": v[0], "timed_launches": v[1], "share": v[0] / tot_k if tot_k else None}
                     for k, v in ktimes.items()}
     kernel_share["timed"] = f"every {PROFILE_EVERY}th launch of each kernel"
 
-    # ---- CPU oracle on a bounded sample ---------------------------------------
+    # ---- CPU oracle on bounded samples ----------------------------------------
     cpu = None
     parity = None
     if rank == 0 and not args.no_cpu:
         cm, caT, sample = cpu_sample()
         ref = {}
-        ts = [oracle_step(cm, caT, keep=ref) for _ in range(2)]
-        cpu = {"value": cm.nT * len(ts) / sum(ts), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+        oracle_step(cm, caT, keep=ref)  # the solution the parity check below compares with
+        hinfo, legs = cpu_baseline_legs(args.cpu_procs)
+        one = legs[f"direct_level{CPU_SAMPLE_LEVEL}_1core"]
+        cpu = {"value": one["triangles_per_s"], "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+               **hinfo, "legs": legs,
+               "size_trend": "the direct solve's fill grows like n^1.5 and the PCG iterations like n^0.5, "
+                             "so the oracle's triangles/s falls with mesh size (level 1 vs level 2 above)"}
         # the same sample through the CUDA path: forward errors against the oracle's
         # solution and the CSR pattern against the oracle's condensed system
         from oracle import phfem_oracle as O
@@ -991,6 +1103,26 @@ def main():
             parity[name] = {"U_max_rel_error": eu, "Lambda_max_rel_error": el, "rel_residual": stc["rel_residual"]}
         P.phfem_mesh_destroy(mh)
 
+    # ---- the batched, Crank-Nicolson and served forms (compact samples) -----------
+    forms = {}
+    if rank == 0:
+        if args.batch_sample > 0:
+            forms["batched"] = batched_measure(args.batch_sample, steps=2, warmup=1, single_sample=16,
+                                               parity=not args.no_cpu)
+            forms["batched"]["sample"] = (f"meshes 0..{args.batch_sample - 1} of the 4096-mesh batched workload; "
+                                          "FP32 + refinement and FP64 in one persistent launch each, the plain "
+                                          "single-mesh FP64 path on the first 16")
+        if args.cn_steps > 0:
+            forms["heat_cn"] = heat_measure(args.heat_n, args.cn_steps, host=False, mg=True)
+            forms["heat_cn"]["sample"] = (f"{args.cn_steps} of the 512 Crank-Nicolson steps on 512 x 512 squares, "
+                                          "graph-captured, FP32 + refinement and FP64, Jacobi and multigrid")
+        if args.serve_requests > 0:
+            forms["serve"] = serve_measure(args.serve_requests, args.serve_warmup, args.rate, args.slots,
+                                           modes=("multigrid",), precisions=("fp32_refined", "fp64"))
+            forms["serve"]["sample"] = (f"{args.serve_requests} measured requests after {args.serve_warmup} of the "
+                                        "Poisson stream (200/s), served as refinement requests with the multigrid "
+                                        "preconditioner; completion rate = capacity when saturated")
+
     if rank == 0:
         med = lambda v: statistics.median(v) if v else None
         line = {
@@ -1005,13 +1137,18 @@ def main():
             "phases_ms_median": {k: med(v) for k, v in ph.items()},
             "assembly_triangles_per_s": nT * 1e3 / med(ph["assemble"]) if ph["assemble"] else None,
             "mesh_build_triangles_per_s": nT * 1e3 / med(ph["mesh_build"]) if ph["mesh_build"] else None,
-            "solve": {"iterations": med(iters), "refinements": med(refs), "rel_residual_max": max(rel) if rel else None},
+            "solve": {"iterations": med(iters), "refinements": med(refs), "rel_residual_max": max(rel) if rel else None,
+                      "converged": sorted(set(conv)), "order": "locality (Morton) order, solution as FP64 pair"},
             "fp64": fp64, "e2e": e2e, "multigrid": mgres, "refine": refine, "roofline": roof,
             "kernels": kernel_share,
             "gpu_launches": launches, "clocks": clk, "cpu_baseline": cpu, "oracle_parity": parity,
             "assembly_median_of_20": asm20,
+            **forms,
         }
-        print(json.dumps(line), flush=True)
+        if "serve" in forms:
+            sv = forms["serve"]["multigrid_fp32_refined"]
+            line["p50_ms"], line["p99_ms"] = sv["p50_ms"], sv["p99_ms"]
+        print(json.dumps(line, default=_json_default), flush=True)
     P.phfem_ctx_destroy(ctx)
     ranks.close()
     return 0
