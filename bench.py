@@ -402,7 +402,7 @@ def batched_measure(count, steps=2, warmup=1, single_sample=32, parity=True, no_
             out["clocks"] = clocks.stop()
         ms = e0.elapsed_time(e1) / steps
         out[name] = {"ms_per_launch": ms, "solves_per_s": count * 1e3 / ms, "triangles_per_s": nT * 1e3 / ms,
-                     "block": chosen, "tune_ms_per_block": tune_ms,
+                     "shape": {"block": chosen[0], "cluster": chosen[1]}, "tune_ms_per_shape": tune_ms,
                      "iterations": {"median": float(np.median(res["iterations"])), "max": int(res["iterations"].max())},
                      "converged": {"rtol": int((res["converged"] == 1).sum()), "floor": int((res["converged"] == 2).sum()),
                                    "not": int((res["converged"] == 0).sum())},

@@ -421,29 +421,37 @@ PHFEM_API int phfem_batch_create(phfem_ctx ctx, int32_t count, const phfem_mesh*
 PHFEM_API int phfem_batch_offsets(phfem_batch batch, int64_t* tri_off, int64_t* edge_off,
                                   int64_t* lam_off);
 /* Assembles and solves every mesh of the batch in ONE kernel launch: each
- * thread block takes the next mesh (largest first) and runs the condensed
- * assembly (as phfem_assemble), Jacobi-PCG with reliable updates (as
- * phfem_solve, block-wide reductions) and the recovery of U and Lambda.
+ * thread block (or thread-block cluster) takes the next mesh (largest first)
+ * and runs the condensed assembly (as phfem_assemble), Jacobi-PCG with
+ * reliable updates (as phfem_solve, reductions over the block or cluster) and
+ * the recovery of U and Lambda.
  *   a_T    [sum nT] double per-triangle coefficient, or NULL for a = 1
  *   delta  [count] double reaction coefficient per mesh (device)
  *   f_mid, bc_mid [sum nE] double as in phfem_assemble (either may be NULL)
  *   precision PHFEM_FP64 or PHFEM_FP32_IR; opts as in phfem_solve
  *   w [sum nE], U [3 sum nT], Lambda [sum nL] double outputs (each may be NULL)
- *   block  threads per block: 128, 256, 512, 1024, or 0 for the tuned value
+ *   block, cluster  launch shape: threads per block and CTAs per mesh (a
+ *          thread-block cluster; its reductions read the CTAs' partial sums
+ *          through distributed shared memory): (128|256|512|1024, 1) or
+ *          (256|512|1024, 4|8); (0, 0) for the tuned shape (256, 1 before tuning)
  *   iterations, converged [count] int32, rel_residual [count] double: host
  *          outputs per mesh (each may be NULL)
  * Blocks until the batch is done.  Returns the first failing mesh's status. */
 PHFEM_API int phfem_batch_solve(phfem_batch batch, const double* a_T, const double* delta,
                                 const double* f_mid, const double* bc_mid, int32_t precision,
                                 const phfem_solve_opts* opts, double* w, double* U, double* Lambda,
-                                int32_t block, int32_t* iterations, int32_t* converged,
+                                int32_t block, int32_t cluster, int32_t* iterations, int32_t* converged,
                                 double* rel_residual);
-/* Autotuner: times phfem_batch_solve with 128, 256, 512 and 1024 threads per
- * block on these inputs, keeps the fastest for block = 0, and reports it
- * (chosen, host) with the four host wall times in ms (ms_per_block[4], host). */
+/* Autotuner: times phfem_batch_solve on these inputs with the ten launch
+ * shapes (block, cluster) = (128,1) (256,1) (512,1) (1024,1) (256,4) (512,4)
+ * (1024,4) (256,8) (512,8) (1024,8), in that order, keeps the fastest for
+ * (0, 0), and reports it (chosen_block, chosen_cluster, host) with the ten
+ * host wall times in ms (ms_per_shape[10], host; may be NULL). */
+#define PHFEM_BATCH_SHAPES 10
 PHFEM_API int phfem_batch_tune(phfem_batch batch, const double* a_T, const double* delta,
                                const double* f_mid, const double* bc_mid, int32_t precision,
-                               const phfem_solve_opts* opts, int32_t* chosen, double* ms_per_block);
+                               const phfem_solve_opts* opts, int32_t* chosen_block, int32_t* chosen_cluster,
+                               double* ms_per_shape);
 PHFEM_API int phfem_batch_destroy(phfem_batch batch);
 
 /* ------------------------------------------------------------------------ */

@@ -10,12 +10,22 @@
 // products are block reductions (FP64 across threads), so one launch solves
 // the whole batch.  The per-element and per-row arithmetic is the same code as
 // the single-mesh kernels (kernels.cuh).
+//
+// A mesh can also be taken by a thread-block cluster of C CTAs (C = 2, 4, 8)
+// instead of one block, so that the largest meshes, which set the launch's
+// tail, run on C SMs: triangles and rows are split over the cluster's threads,
+// cluster barriers replace the block barriers, and every reduction sums the C
+// block totals read from the CTAs' shared memory (distributed shared memory,
+// fixed rank order, so every CTA gets the same value and takes the same
+// branch).  The tuner picks the block size and the cluster size.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <numeric>
 #include <vector>
+
+#include <cooperative_groups.h>
 
 #include "kernels.cuh"
 
@@ -40,8 +50,22 @@ struct MeshStats {
   double dbg[4];       // pq, rz, rz of the last update, alpha at the failure
 };
 
-template <int BS>
-__device__ __forceinline__ double bsum(double v, double* smem) {
+namespace cgr = cooperative_groups;
+
+// Barrier over the mesh's threads: the block, or the whole cluster (which also
+// orders the threads' global-memory writes for the cluster).
+template <int C>
+__device__ __forceinline__ void msync() {
+  if constexpr (C == 1) __syncthreads();
+  else cgr::this_cluster().sync();
+}
+
+// Sum of v over the mesh's threads, the same value in every thread: warp sums,
+// then the block total in fixed order; with a cluster, each CTA publishes its
+// total in slot `slot` (alternating between consecutive reductions, so one
+// barrier suffices) and every thread adds the C totals in rank order.
+template <int BS, int C>
+__device__ __forceinline__ double bsum(double v, double* smem, double* cl_part, int& slot) {
   v = warp_sum(v);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   __syncthreads();  // smem may still be read by the previous reduction
@@ -49,7 +73,17 @@ __device__ __forceinline__ double bsum(double v, double* smem) {
   __syncthreads();
   double t = 0.0;
   for (int i = 0; i < BS / 32; ++i) t += smem[i];  // every thread, same order
-  return t;
+  if constexpr (C == 1) {
+    return t;
+  } else {
+    cgr::cluster_group cl = cgr::this_cluster();
+    if (threadIdx.x == 0) cl_part[slot] = t;
+    cl.sync();
+    double u = 0.0;
+    for (unsigned r = 0; r < (unsigned)C; ++r) u += *cl.map_shared_rank(cl_part + slot, r);
+    slot ^= 1;
+    return u;
+  }
 }
 
 template <typename T>
@@ -83,17 +117,29 @@ struct BatchArrays {
   double* w;             // [sum nE] or NULL
 };
 
-template <typename T, int BS>
+template <typename T, int BS, int C>
 __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restrict__ desc,
                                               const int* __restrict__ order, int* next, BatchArrays<T> A,
                                               BatchParams P, MeshStats* stats) {
   __shared__ double smem[BS / 32];
+  __shared__ double cl_part[2];
   __shared__ int s_mesh;
+  int slot = 0;
+  unsigned crank = 0;  // rank of this CTA in its cluster
+  if constexpr (C > 1) crank = cgr::this_cluster().block_rank();
+  const int tid0 = (int)crank * BS + threadIdx.x;  // thread index within the mesh's threads
+  constexpr int STR = C * BS;                      // threads working on one mesh
   for (;;) {
-    __syncthreads();
-    if (threadIdx.x == 0) s_mesh = atomicAdd(next, 1);
-    __syncthreads();
-    const int k = s_mesh;
+    msync<C>();
+    if (crank == 0 && threadIdx.x == 0) s_mesh = atomicAdd(next, 1);
+    msync<C>();
+    int k;
+    if constexpr (C == 1) {
+      k = s_mesh;
+    } else {
+      k = *cgr::this_cluster().map_shared_rank(&s_mesh, 0);
+      msync<C>();  // no CTA leaves while another still reads rank 0's s_mesh
+    }
     if (k >= count) return;
     const int id = order[k];
     const MeshDesc D = desc[id];
@@ -121,7 +167,7 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
     const double* bc = A.bc_mid ? A.bc_mid + D.e0 : nullptr;
 
     // 1. triangle pass
-    for (int t = threadIdx.x; t < nT; t += BS) {
+    for (int t = tid0; t < nT; t += STR) {
       const double a = A.aT ? A.aT[D.t0 + t] : P.a_const;
       const double2 p0 = xy[tri[3 * t]], p1 = xy[tri[3 * t + 1]], p2 = xy[tri[3 * t + 2]];
       // FP64 records in both precisions: the meshes are small and the time is
@@ -130,9 +176,9 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
       tri_record64(p0, p1, p2, a, R);
       store_record(Kt + (size_t)kRec * t, R);
     }
-    __syncthreads();
+    msync<C>();
     // 2. edge rows; x starts at 0 on free edges and u_D on Dirichlet edges
-    for (int e = threadIdx.x; e < nE; e += BS) {
+    for (int e = tid0; e < nE; e += STR) {
       const int4 qd = reinterpret_cast<const int4*>(ed2el)[e];
       const int kk = lk[e];
       const uint8_t cls = ecl[e];
@@ -149,18 +195,18 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
       dinv[e] = (T)(1.0 / R.diag);
       x[e] = (cls == PHFEM_EDGE_DIRICHLET) ? R.rhs : 0.0;
     }
-    __syncthreads();
+    msync<C>();
     // ||b_free|| with the Dirichlet lifting (x is (0, u_D) now)
     double bb = 0.0;
     {
       double acc = 0.0;
-      for (int e = threadIdx.x; e < nE; e += BS) {
+      for (int e = tid0; e < nE; e += STR) {
         if (ecl[e] == PHFEM_EDGE_DIRICHLET) continue;
         double fl;
         const double rr = residual_row(nbr, val, b, x, m, e, fl);
         acc += rr * rr;
       }
-      bb = bsum<BS>(acc, smem);
+      bb = bsum<BS, C>(acc, smem, cl_part, slot);
     }
     // 3. Jacobi-PCG with reliable updates
     int it = 0, updates = 0, converged = 0, status = 0, stagnant = 0, where = 0;
@@ -169,7 +215,7 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
     for (;;) {
       // true residual (FP64, difference form), inner residual replaced
       double a_r = 0.0, a_z = 0.0, a_f = 0.0, a_p = 0.0;
-      for (int e = threadIdx.x; e < nE; e += BS) {
+      for (int e = tid0; e < nE; e += STR) {
         double fl;
         const double rr = residual_row(nbr, val, b, x, m, e, fl);
         a_r += rr * rr;
@@ -182,10 +228,10 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
         else a_p += (double)rs * (double)p[e];
         a_z += (double)rs * (double)zs;
       }
-      const double rr64 = bsum<BS>(a_r, smem);
-      const double rz_true = bsum<BS>(a_z, smem);
-      const double ff = bsum<BS>(a_f, smem);
-      const double rp = bsum<BS>(a_p, smem);
+      const double rr64 = bsum<BS, C>(a_r, smem, cl_part, slot);
+      const double rz_true = bsum<BS, C>(a_z, smem, cl_part, slot);
+      const double ff = bsum<BS, C>(a_f, smem, cl_part, slot);
+      const double rp = bsum<BS, C>(a_p, smem, cl_part, slot);
       ++updates;
       rel = bb > 0 ? sqrt(rr64 / bb) : 0.0;
       floor_rel = bb > 0 ? sqrt(ff / bb) : 0.0;
@@ -213,22 +259,22 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
       // restart the direction if it no longer fits the replaced residual
       bool line_search = !first;
       if (!first && (rz_true > 4.0 * rz || !(rp > 0.0))) {
-        for (int e = threadIdx.x; e < nE; e += BS) p[e] = dinv[e] * r[e];
+        for (int e = tid0; e < nE; e += STR) p[e] = dinv[e] * r[e];
         line_search = false;
       }
       first = false;
       rz = rz_true;
       tol2 = P.upd2 * rz;
-      __syncthreads();
+      msync<C>();
       // iterate until the recursive residual fell by the update factor
       while (it < P.max_iter) {
         T acc = (T)0;
-        for (int e = threadIdx.x; e < nE; e += BS) {
+        for (int e = tid0; e < nE; e += STR) {
           const T s = spmv_row<T, false>(nbr, lval, rdiag, p, m, e);
           q[e] = s;
           acc += p[e] * s;
         }
-        const double pq = bsum<BS>((double)acc, smem);
+        const double pq = bsum<BS, C>((double)acc, smem, cl_part, slot);
         dpq = pq;
         if (!(pq > 0.0) || !isfinite(pq)) {
           status = isfinite(pq) ? PHFEM_EBREAKDOWN : PHFEM_ENAN;
@@ -240,18 +286,18 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
         dal = alpha64;
         const T alpha = (T)alpha64;
         T acc2 = (T)0;
-        for (int e = threadIdx.x; e < nE; e += BS) {
+        for (int e = tid0; e < nE; e += STR) {
           x[e] += alpha64 * (double)p[e];
           const T re = r[e] - alpha * q[e];
           r[e] = re;
           acc2 += re * (dinv[e] * re);
         }
-        const double rzn = bsum<BS>((double)acc2, smem);
+        const double rzn = bsum<BS, C>((double)acc2, smem, cl_part, slot);
         const T beta = (T)(rz > 0.0 ? rzn / rz : 0.0);
         rz = rzn;
         ++it;
-        for (int e = threadIdx.x; e < nE; e += BS) p[e] = dinv[e] * r[e] + beta * p[e];
-        __syncthreads();
+        for (int e = tid0; e < nE; e += STR) p[e] = dinv[e] * r[e] + beta * p[e];
+        msync<C>();
         if (!isfinite(rz)) {
           status = PHFEM_ENAN;
           where = 3;
@@ -260,15 +306,15 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
         if (rz <= tol2) break;
       }
       if (status) break;
-      __syncthreads();
+      msync<C>();
     }
-    __syncthreads();
+    msync<C>();
     // 4. recovery: U = R^-1 w per triangle, Lambda from the T+ rows
     if (A.U || A.Lambda) {
       const int32_t* t2e = A.t2e + 3 * D.t0;
       const int8_t* sg = A.sigma + 3 * D.t0;
       const int32_t* lam = A.lam_id + D.e0;
-      for (int t = threadIdx.x; t < nT; t += BS) {
+      for (int t = tid0; t < nT; t += STR) {
         const int e0 = t2e[3 * t], e1 = t2e[3 * t + 1], e2 = t2e[3 * t + 2];
         const double a0 = x[e0], a1 = x[e1], a2 = x[e2];
         if (A.U) {
@@ -296,8 +342,8 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
       }
     }
     if (A.w)
-      for (int e = threadIdx.x; e < nE; e += BS) A.w[D.e0 + e] = x[e];
-    if (threadIdx.x == 0) {
+      for (int e = tid0; e < nE; e += STR) A.w[D.e0 + e] = x[e];
+    if (crank == 0 && threadIdx.x == 0) {
       MeshStats s;
       s.iterations = it;
       s.updates = updates;
@@ -351,7 +397,8 @@ struct phfem_batch_s {
   void* r = nullptr;
   void* p = nullptr;
   void* q = nullptr;
-  int block = 0;  // 0: not tuned yet
+  int block = 0;    // 0: not tuned yet
+  int cluster = 1;  // CTAs per mesh
 };
 
 namespace phfem {
@@ -367,26 +414,62 @@ void batch_free(phfem_batch B) {
   delete B;
 }
 
-template <typename T, int BS>
+template <typename T, int BS, int C>
 int launch_batch(phfem_batch B, const BatchArrays<T>& A, const BatchParams& P) {
   phfem_ctx ctx = B->ctx;
-  int per_sm = 0;
-  PH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<T, BS>, BS, 0));
-  if (per_sm < 1) per_sm = 1;
-  int grid = ctx->num_sms * per_sm;
-  if (grid > B->count) grid = B->count;
   PH_CUDA(cudaMemsetAsync(B->next, 0, sizeof(int), ctx->stream));
-  k_batch<T, BS><<<grid, BS, 0, ctx->stream>>>(B->count, B->desc, B->order, B->next, A, P, B->stats);
-  return check_launch(ctx, "k_batch");
+  auto K = k_batch<T, BS, C>;
+  if constexpr (C == 1) {
+    int per_sm = 0;
+    PH_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, K, BS, 0));
+    if (per_sm < 1) per_sm = 1;
+    int grid = ctx->num_sms * per_sm;
+    if (grid > B->count) grid = B->count;
+    K<<<grid, BS, 0, ctx->stream>>>(B->count, B->desc, B->order, B->next, A, P, B->stats);
+    return check_launch(ctx, "k_batch");
+  } else {
+    cudaLaunchConfig_t cfg = {};
+    cfg.blockDim = dim3(BS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = ctx->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cfg.gridDim = dim3(C * ctx->num_sms);
+    int clusters = 0;
+    PH_CUDA(cudaOccupancyMaxActiveClusters(&clusters, K, &cfg));
+    if (clusters < 1) clusters = 1;
+    if (clusters > B->count) clusters = B->count;
+    cfg.gridDim = dim3(C * clusters);
+    PH_CUDA(cudaLaunchKernelEx(&cfg, K, B->count, (const MeshDesc*)B->desc, (const int*)B->order, B->next, A, P,
+                               B->stats));
+    return check_launch(ctx, "k_batch");
+  }
 }
 
+// The launch shapes the tuner tries: threads per block, CTAs per cluster.
+constexpr int kShapes = 10;
+constexpr int kShapeBlock[kShapes] = {128, 256, 512, 1024, 256, 512, 1024, 256, 512, 1024};
+constexpr int kShapeCluster[kShapes] = {1, 1, 1, 1, 4, 4, 4, 8, 8, 8};
+
 template <typename T>
-int run_batch(phfem_batch B, int block, const BatchArrays<T>& A, const BatchParams& P) {
-  switch (block) {
-    case 128: return launch_batch<T, 128>(B, A, P);
-    case 256: return launch_batch<T, 256>(B, A, P);
-    case 512: return launch_batch<T, 512>(B, A, P);
-    default: return launch_batch<T, 1024>(B, A, P);
+int run_batch(phfem_batch B, int block, int cluster, const BatchArrays<T>& A, const BatchParams& P) {
+  switch (cluster * 10000 + block) {
+    case 10128: return launch_batch<T, 128, 1>(B, A, P);
+    case 10256: return launch_batch<T, 256, 1>(B, A, P);
+    case 10512: return launch_batch<T, 512, 1>(B, A, P);
+    case 11024: return launch_batch<T, 1024, 1>(B, A, P);
+    case 40256: return launch_batch<T, 256, 4>(B, A, P);
+    case 40512: return launch_batch<T, 512, 4>(B, A, P);
+    case 41024: return launch_batch<T, 1024, 4>(B, A, P);
+    case 80256: return launch_batch<T, 256, 8>(B, A, P);
+    case 80512: return launch_batch<T, 512, 8>(B, A, P);
+    case 81024: return launch_batch<T, 1024, 8>(B, A, P);
+    default: return fail(PHFEM_EINVAL, "phfem_batch_solve: unsupported block/cluster shape");
   }
 }
 
@@ -497,13 +580,18 @@ PHFEM_API int phfem_batch_offsets(phfem_batch B, int64_t* tri_off, int64_t* edge
 
 PHFEM_API int phfem_batch_solve(phfem_batch B, const double* a_T, const double* delta, const double* f_mid,
                                 const double* bc_mid, int32_t precision, const phfem_solve_opts* opts, double* w,
-                                double* U, double* Lambda, int32_t block, int32_t* iterations, int32_t* converged,
-                                double* rel_residual) {
+                                double* U, double* Lambda, int32_t block, int32_t cluster, int32_t* iterations,
+                                int32_t* converged, double* rel_residual) {
   if (!B || !delta) return fail(PHFEM_EINVAL, "phfem_batch_solve: NULL argument");
   if (precision != PHFEM_FP64 && precision != PHFEM_FP32_IR)
     return fail(PHFEM_EINVAL, "phfem_batch_solve: unknown precision");
-  if (block != 0 && block != 128 && block != 256 && block != 512 && block != 1024)
-    return fail(PHFEM_EINVAL, "phfem_batch_solve: block must be 0, 128, 256, 512 or 1024");
+  {
+    bool ok = block == 0 && cluster == 0;
+    for (int i = 0; i < kShapes && !ok; ++i) ok = block == kShapeBlock[i] && cluster == kShapeCluster[i];
+    if (!ok)
+      return fail(PHFEM_EINVAL, "phfem_batch_solve: (block, cluster) must be (0, 0) or a tuner shape: (128|256|512|1024, 1), "
+                                "(256|512|1024, 4|8)");
+  }
   phfem_ctx ctx = B->ctx;
   cudaStream_t s = ctx->stream;
   // host copy of delta to check solvability (no Dirichlet edge needs delta > 0)
@@ -544,17 +632,18 @@ PHFEM_API int phfem_batch_solve(phfem_batch B, const double* a_T, const double* 
   if (o.max_refine <= 0) o.max_refine = 1000;
   BatchParams P{o.rtol * o.rtol, o.inner_rtol * o.inner_rtol, o.max_iter, o.max_refine, 1.0};
   const int bs = block ? block : (B->block ? B->block : 256);
+  const int cs = block ? cluster : (B->block ? B->cluster : 1);
   int st;
   if (fp32) {
     BatchArrays<float> A{B->xy, B->tri, B->ed2el, B->lk, B->eclass, B->nbr, B->elen, B->t2e, B->sigma, B->lam_id,
                          a_T, delta, f_mid, bc_mid, B->Kt, B->val, B->b, (float*)B->lval, (float*)B->rdiag,
                          (float*)B->dinv, B->x, (float*)B->r, (float*)B->p, (float*)B->q, U, Lambda, w};
-    st = run_batch<float>(B, bs, A, P);
+    st = run_batch<float>(B, bs, cs, A, P);
   } else {
     BatchArrays<double> A{B->xy, B->tri, B->ed2el, B->lk, B->eclass, B->nbr, B->elen, B->t2e, B->sigma, B->lam_id,
                           a_T, delta, f_mid, bc_mid, B->Kt, B->val, B->b, (double*)B->lval, (double*)B->rdiag,
                           (double*)B->dinv, B->x, (double*)B->r, (double*)B->p, (double*)B->q, U, Lambda, w};
-    st = run_batch<double>(B, bs, A, P);
+    st = run_batch<double>(B, bs, cs, A, P);
   }
   if (st != PHFEM_OK) return st;
   std::vector<MeshStats> hs(B->count);
@@ -585,25 +674,26 @@ PHFEM_API int phfem_batch_solve(phfem_batch B, const double* a_T, const double* 
 
 PHFEM_API int phfem_batch_tune(phfem_batch B, const double* a_T, const double* delta, const double* f_mid,
                                const double* bc_mid, int32_t precision, const phfem_solve_opts* opts,
-                               int32_t* chosen, double* ms_per_block) {
+                               int32_t* chosen_block, int32_t* chosen_cluster, double* ms_per_shape) {
   if (!B) return fail(PHFEM_EINVAL, "phfem_batch_tune: NULL batch");
-  static const int cand[4] = {128, 256, 512, 1024};
   double best = 1e300;
-  int pick = 256;
-  for (int i = 0; i < 4; ++i) {
+  int pick = 1;
+  for (int i = 0; i < kShapes; ++i) {
     auto t0 = std::chrono::steady_clock::now();
-    int st = phfem_batch_solve(B, a_T, delta, f_mid, bc_mid, precision, opts, nullptr, nullptr, nullptr, cand[i],
-                               nullptr, nullptr, nullptr);
+    int st = phfem_batch_solve(B, a_T, delta, f_mid, bc_mid, precision, opts, nullptr, nullptr, nullptr,
+                               kShapeBlock[i], kShapeCluster[i], nullptr, nullptr, nullptr);
     double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     if (st != PHFEM_OK && st != PHFEM_ENOCONV) return st;
-    if (ms_per_block) ms_per_block[i] = ms;
+    if (ms_per_shape) ms_per_shape[i] = ms;
     if (ms < best) {
       best = ms;
-      pick = cand[i];
+      pick = i;
     }
   }
-  B->block = pick;
-  if (chosen) *chosen = pick;
+  B->block = kShapeBlock[pick];
+  B->cluster = kShapeCluster[pick];
+  if (chosen_block) *chosen_block = B->block;
+  if (chosen_cluster) *chosen_cluster = B->cluster;
   return PHFEM_OK;
 }
 

@@ -144,9 +144,9 @@ def lib() -> C.CDLL:
             "phfem_batch_create": (C.c_int, [_H, C.c_int32, C.POINTER(_H), C.POINTER(_H)]),
             "phfem_batch_offsets": (C.c_int, [_H, _P, _P, _P]),
             "phfem_batch_solve": (C.c_int, [_H, _P, _P, _P, _P, C.c_int32, C.POINTER(SolveOpts), _P, _P, _P,
-                                            C.c_int32, _P, _P, _P]),
+                                            C.c_int32, C.c_int32, _P, _P, _P]),
             "phfem_batch_tune": (C.c_int, [_H, _P, _P, _P, _P, C.c_int32, C.POINTER(SolveOpts), C.POINTER(C.c_int32),
-                                           _P]),
+                                           C.POINTER(C.c_int32), _P]),
             "phfem_batch_destroy": (C.c_int, [_H]),
             "phfem_server_create": (C.c_int, [C.c_int32, C.c_double, C.POINTER(SolveOpts), C.POINTER(_H)]),
             "phfem_server_submit": (C.c_int, [_H, C.POINTER(Request), C.POINTER(C.c_int64)]),
@@ -440,7 +440,7 @@ def phfem_batch_offsets(batch, count):
 
 
 def phfem_batch_solve(batch, count, delta, a_T=None, f_mid=None, bc_mid=None, precision=PHFEM_FP32_IR,
-                      opts=None, w=None, U=None, Lambda=None, block=0):
+                      opts=None, w=None, U=None, Lambda=None, block=0, cluster=None):
     import numpy as np
     it = np.zeros(count, dtype=np.int32)
     cv = np.zeros(count, dtype=np.int32)
@@ -449,20 +449,26 @@ def phfem_batch_solve(batch, count, delta, a_T=None, f_mid=None, bc_mid=None, pr
     _check(lib().phfem_batch_solve(batch, _ptr(a_T, torch.float64), _ptr(delta, torch.float64, count),
                                    _ptr(f_mid, torch.float64), _ptr(bc_mid, torch.float64), int(precision),
                                    C.byref(o), _ptr(w, torch.float64), _ptr(U, torch.float64),
-                                   _ptr(Lambda, torch.float64), int(block), it.ctypes.data, cv.ctypes.data,
+                                   _ptr(Lambda, torch.float64), int(block),
+                                   int((1 if block else 0) if cluster is None else cluster), it.ctypes.data, cv.ctypes.data,
                                    rel.ctypes.data), "phfem_batch_solve")
     return {"iterations": it, "converged": cv, "rel_residual": rel}
 
 
+BATCH_SHAPES = [(128, 1), (256, 1), (512, 1), (1024, 1), (256, 4), (512, 4), (1024, 4), (256, 8), (512, 8), (1024, 8)]
+
+
 def phfem_batch_tune(batch, delta, a_T=None, f_mid=None, bc_mid=None, precision=PHFEM_FP32_IR, opts=None):
+    """Times every launch shape (threads per block, CTAs per mesh); returns the
+    chosen shape and {shape: host ms}."""
     import numpy as np
-    ms = np.zeros(4, dtype=np.float64)
-    ch = C.c_int32()
+    ms = np.zeros(len(BATCH_SHAPES), dtype=np.float64)
+    cb, cc = C.c_int32(), C.c_int32()
     o = opts if opts is not None else solve_opts()
     _check(lib().phfem_batch_tune(batch, _ptr(a_T, torch.float64), _ptr(delta, torch.float64),
                                   _ptr(f_mid, torch.float64), _ptr(bc_mid, torch.float64), int(precision),
-                                  C.byref(o), C.byref(ch), ms.ctypes.data), "phfem_batch_tune")
-    return int(ch.value), dict(zip((128, 256, 512, 1024), ms.tolist()))
+                                  C.byref(o), C.byref(cb), C.byref(cc), ms.ctypes.data), "phfem_batch_tune")
+    return (int(cb.value), int(cc.value)), {f"{b}x{c}": float(t) for (b, c), t in zip(BATCH_SHAPES, ms.tolist())}
 
 
 def phfem_batch_destroy(batch):

@@ -88,16 +88,27 @@ def test_batch_matches_oracle_and_single_mesh(ctx, precision):
         assert O.relative_residual(cs["S"], cs["rhs"], wi[cs["st"]["bsets"]["free"]]) <= 1.2e-10, i
         single = solve(gm, pb, aT=aT, precision=precision, rtol=1e-10)
         assert np.max(np.abs(Ui - single["U"])) <= 1e-7 * max(1.0, np.max(np.abs(single["U"]))), i
-    # every block size gives a converged, consistent answer; the tuner picks one
-    for bs in (128, 512, 1024):
+    # every launch shape (threads per block, CTAs per mesh as a thread-block
+    # cluster) gives a converged, consistent answer; a shape's result does not
+    # depend on the batch's other meshes (the same mesh alone, bitwise); the
+    # tuner picks one shape
+    for bs, cl in P.BATCH_SHAPES:
         U2 = torch.empty_like(U)
         r2 = P.phfem_batch_solve(batch, count, data["delta"], a_T=data["aT"], f_mid=data["f"], bc_mid=data["bc"],
-                                 precision=precision, U=U2, block=bs)
-        assert np.all(r2["converged"] == 1)
-        assert np.max(np.abs(U2.cpu().numpy() - Uh)) <= 1e-7 * np.max(np.abs(Uh))
+                                 precision=precision, U=U2, block=bs, cluster=cl)
+        assert np.all(r2["converged"] == 1), (bs, cl)
+        assert np.max(np.abs(U2.cpu().numpy() - Uh)) <= 1e-7 * np.max(np.abs(Uh)), (bs, cl)
+        if (bs, cl) in ((256, 1), (512, 4)):
+            one = P.phfem_batch_create(ctx, [gms[1].h])
+            U1 = torch.empty(3 * int(toff[2] - toff[1]), dtype=torch.float64, device="cuda")
+            P.phfem_batch_solve(one, 1, data["delta"][1:2], a_T=data["aT"][toff[1]:toff[2]],
+                                f_mid=data["f"][eoff[1]:eoff[2]], bc_mid=data["bc"][eoff[1]:eoff[2]],
+                                precision=precision, U=U1, block=bs, cluster=cl)
+            assert np.array_equal(U1.cpu().numpy(), U2.cpu().numpy()[3 * toff[1]:3 * toff[2]]), (bs, cl)
+            P.phfem_batch_destroy(one)
     chosen, ms = P.phfem_batch_tune(batch, data["delta"], a_T=data["aT"], f_mid=data["f"], bc_mid=data["bc"],
                                     precision=precision)
-    assert chosen in (128, 256, 512, 1024) and all(v > 0 for v in ms.values())
+    assert chosen in P.BATCH_SHAPES and len(ms) == len(P.BATCH_SHAPES) and all(v > 0 for v in ms.values())
     P.phfem_batch_destroy(batch)
     for gm in gms:
         gm.close()
