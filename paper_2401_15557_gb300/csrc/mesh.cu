@@ -5,10 +5,13 @@
 // Edge numbering of nodes2edge = column-major order of the nonzeros of
 // triu(B): edges sorted by (larger vertex, smaller vertex).  The directed edge
 // occurrences o = 3t + j (edge P_{j+1} -> P_{j+2} of triangle t, element-major
-// as in Listing 3) are bucketed by their larger vertex (a counting sort), each
-// bucket is sorted by (smaller vertex, occurrence), and a scan of the number of
-// distinct edges per bucket numbers the edges.  The first occurrence of an
-// edge is its T+ (Eq. ed2el), the second its T-.
+// as in Listing 3) are put in (larger vertex, smaller vertex, occurrence)
+// order by two stable radix sorts (by the smaller vertex, then by the larger
+// one; equal keys keep the occurrence order); an entry that differs from the
+// previous one starts an edge, and a scan of those starts numbers the edges.
+// Every step runs one thread per entry, so the cost does not depend on vertex
+// valence.  The first occurrence of an edge is its T+ (Eq. ed2el), the second
+// its T-.
 #include <algorithm>
 #include <vector>
 
@@ -57,91 +60,86 @@ __global__ void k_count(int nT, int nV, const int32_t* __restrict__ tri, const d
   }
 }
 
-__global__ void k_scatter(int nT, const int32_t* __restrict__ tri, const int32_t* __restrict__ bstart,
-                          int32_t* __restrict__ fill, unsigned long long* __restrict__ buf) {
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < nT; t += gridDim.x * blockDim.x) {
-    for (int j = 0; j < 3; ++j) {
-      int a = tri[3 * t + j], b = tri[3 * t + (j + 1) % 3];
-      int hi = max(a, b), lo = min(a, b);
-      int pos = bstart[hi] + atomicAdd(&fill[hi], 1);
-      buf[pos] = ((unsigned long long)(unsigned)lo << 32) | (unsigned)(3 * t + j);
-    }
+// Keys of the directed edges in occurrence order: smaller and larger vertex.
+__global__ void k_keys(int nT, const int32_t* __restrict__ tri, uint32_t* __restrict__ lo_o,
+                       uint32_t* __restrict__ hi_o, uint32_t* __restrict__ key, int32_t* __restrict__ occ) {
+  const int n = 3 * nT;
+  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n; o += gridDim.x * blockDim.x) {
+    const int t = o / 3, j = o - 3 * t;
+    const int a = tri[o], b = tri[3 * t + (j == 2 ? 0 : j + 1)];
+    const uint32_t lo = (uint32_t)min(a, b), hi = (uint32_t)max(a, b);
+    lo_o[o] = lo;
+    hi_o[o] = hi;
+    key[o] = lo;
+    occ[o] = o;
   }
 }
 
-// One thread per bucket (vertex): insertion sort by (lo, occurrence), then
-// count distinct edges and check that each edge has one or two occurrences of
-// opposite direction.
-__global__ void k_bucket_sort(int nV, const int32_t* __restrict__ tri, const int32_t* __restrict__ bstart,
-                              unsigned long long* __restrict__ buf, int32_t* __restrict__ ecount,
-                              DevStatus* err) {
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nV; v += gridDim.x * blockDim.x) {
-    const int s = bstart[v], e = bstart[v + 1];
-    for (int i = s + 1; i < e; ++i) {
-      unsigned long long key = buf[i];
-      int j = i - 1;
-      while (j >= s && buf[j] > key) {
-        buf[j + 1] = buf[j];
-        --j;
+// key[i] = larger vertex of the entry now at position i (for the second sort).
+__global__ void k_hi_key(int n, const uint32_t* __restrict__ hi_o, const int32_t* __restrict__ occ,
+                         uint32_t* __restrict__ key) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) key[i] = hi_o[occ[i]];
+}
+
+// Entries in (larger, smaller, occurrence) order: the packed entry
+// (smaller << 32 | occurrence), whether it starts an edge, and the checks that
+// an edge has at most two occurrences of opposite direction.
+__global__ void k_entries(int n, const int32_t* __restrict__ tri, const uint32_t* __restrict__ lo_o,
+                          const uint32_t* __restrict__ hi_o, const int32_t* __restrict__ occ,
+                          unsigned long long* __restrict__ buf, int32_t* __restrict__ start, DevStatus* err) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int o = occ[i];
+    const uint32_t lo = lo_o[o], hi = hi_o[o];
+    buf[i] = ((unsigned long long)lo << 32) | (unsigned)o;
+    bool same = false;
+    if (i > 0) {
+      const int op = occ[i - 1];
+      same = lo_o[op] == lo && hi_o[op] == hi;
+      if (same) {
+        if (tri[op] == tri[o]) record(err, PHFEM_EMESH, (int)hi, kSameDirection);  // same initial vertex
+        if (i > 1) {
+          const int oq = occ[i - 2];
+          if (lo_o[oq] == lo && hi_o[oq] == hi) record(err, PHFEM_EMESH, (int)hi, kEdgeInThree);
+        }
       }
-      buf[j + 1] = key;
     }
-    int n = 0;
-    int i = s;
-    while (i < e) {
-      unsigned lo = (unsigned)(buf[i] >> 32);
-      int run = 1;
-      while (i + run < e && (unsigned)(buf[i + run] >> 32) == lo) ++run;
-      if (run > 2) record(err, PHFEM_EMESH, v, kEdgeInThree);
-      if (run == 2) {
-        unsigned o1 = (unsigned)buf[i], o2 = (unsigned)buf[i + 1];
-        int a1 = tri[o1], a2 = tri[o2];  // initial vertices of the two directed edges
-        if (a1 == a2) record(err, PHFEM_EMESH, v, kSameDirection);
-      }
-      ++n;
-      i += run;
-    }
-    ecount[v] = n;
+    start[i] = same ? 0 : 1;
   }
 }
 
 __device__ __forceinline__ int next3(int j) { return j == 2 ? 0 : j + 1; }
 
-__global__ void k_edges(int nV, const int32_t* __restrict__ tri, const int32_t* __restrict__ bstart,
-                        const unsigned long long* __restrict__ buf, const int32_t* __restrict__ ebase,
+// One thread per entry that starts an edge: edge number = number of starts
+// before it; T+ is this occurrence, T- the next entry's if it is the same edge.
+__global__ void k_edges(int n, const int32_t* __restrict__ tri, const unsigned long long* __restrict__ buf,
+                        const int32_t* __restrict__ start, const int32_t* __restrict__ enr,
                         int32_t* __restrict__ ed2el, int32_t* __restrict__ t2e, int8_t* __restrict__ sigma,
                         uint8_t* __restrict__ lk, int32_t* __restrict__ pos_edge) {
-  for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < nV; v += gridDim.x * blockDim.x) {
-    const int s = bstart[v], e = bstart[v + 1];
-    int edge = ebase[v];
-    int i = s;
-    while (i < e) {
-      unsigned lo = (unsigned)(buf[i] >> 32);
-      int run = (i + 1 < e && (unsigned)(buf[i + 1] >> 32) == lo) ? 2 : 1;
-      const int op = (int)(unsigned)buf[i];
-      const int tp = op / 3, jp = op - 3 * tp;
-      const int kp = (jp + 2) % 3;  // directed edge P_{j+1}P_{j+2} is E_{j+3 mod 3}
-      ed2el[4 * edge + 0] = tri[3 * tp + jp];
-      ed2el[4 * edge + 1] = tri[3 * tp + next3(jp)];
-      ed2el[4 * edge + 2] = tp;
-      t2e[3 * tp + kp] = edge;
-      sigma[3 * tp + kp] = 1;
-      int km = 0;
-      if (run == 2) {
-        const int om = (int)(unsigned)buf[i + 1];
-        const int tm = om / 3, jm = om - 3 * tm;
-        km = (jm + 2) % 3;
-        ed2el[4 * edge + 3] = tm;
-        t2e[3 * tm + km] = edge;
-        sigma[3 * tm + km] = -1;
-      } else {
-        ed2el[4 * edge + 3] = -1;
-      }
-      lk[edge] = (uint8_t)(kp | (km << 2));
-      for (int r = 0; r < run; ++r) pos_edge[i + r] = edge;
-      i += run;
-      ++edge;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    if (!start[i]) continue;
+    const int edge = enr[i];
+    const int run = (i + 1 < n && !start[i + 1]) ? 2 : 1;
+    const int op = (int)(unsigned)buf[i];
+    const int tp = op / 3, jp = op - 3 * tp;
+    const int kp = (jp + 2) % 3;  // directed edge P_{j+1}P_{j+2} is E_{j+3 mod 3}
+    ed2el[4 * edge + 0] = tri[3 * tp + jp];
+    ed2el[4 * edge + 1] = tri[3 * tp + next3(jp)];
+    ed2el[4 * edge + 2] = tp;
+    t2e[3 * tp + kp] = edge;
+    sigma[3 * tp + kp] = 1;
+    int km = 0;
+    if (run == 2) {
+      const int om = (int)(unsigned)buf[i + 1];
+      const int tm = om / 3, jm = om - 3 * tm;
+      km = (jm + 2) % 3;
+      ed2el[4 * edge + 3] = tm;
+      t2e[3 * tm + km] = edge;
+      sigma[3 * tm + km] = -1;
+    } else {
+      ed2el[4 * edge + 3] = -1;
     }
+    lk[edge] = (uint8_t)(kp | (km << 2));
+    for (int r = 0; r < run; ++r) pos_edge[i + r] = edge;
   }
 }
 
@@ -157,12 +155,14 @@ __global__ void k_bclass(int nB, const int32_t* __restrict__ pairs, int code, in
       continue;
     }
     int hi = max(a, b), lo = min(a, b);
-    int found = -1;
-    for (int p = bstart[hi]; p < bstart[hi + 1]; ++p)
-      if ((int)(buf[p] >> 32) == lo) {
-        found = p;
-        break;
-      }
+    int found = -1;  // the bucket of hi is sorted by the smaller vertex: binary search
+    int l0 = bstart[hi], l1 = bstart[hi + 1];
+    while (l0 < l1) {
+      const int mid = (l0 + l1) >> 1;
+      if ((int)(buf[mid] >> 32) < lo) l0 = mid + 1;
+      else l1 = mid;
+    }
+    if (l0 < bstart[hi + 1] && (int)(buf[l0] >> 32) == lo) found = l0;
     if (found < 0) {
       record(err, PHFEM_EMESH, i, kNotAnEdge);
       continue;
@@ -351,29 +351,44 @@ int build(phfem_ctx ctx, int nV, const double* xy, int nT, const int32_t* tri, i
   DevStatus* err;
   PH_TRY(tmp.get(&err, 1));
   PH_CUDA(cudaMemsetAsync(err, 0, sizeof(DevStatus), s));
-  int32_t *cnt, *bstart, *fill, *ecount, *ebase;
+  int32_t *cnt, *bstart;
   PH_TRY(tmp.get(&cnt, nV));
   PH_TRY(tmp.get(&bstart, (size_t)nV + 1));
-  PH_TRY(tmp.get(&fill, nV));
-  PH_TRY(tmp.get(&ecount, nV));
-  PH_TRY(tmp.get(&ebase, (size_t)nV + 1));
-  unsigned long long* buf;
-  PH_TRY(tmp.get(&buf, 3 * (size_t)nT));
   PH_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * nV, s));
-  PH_CUDA(cudaMemsetAsync(fill, 0, sizeof(int32_t) * nV, s));
 
   k_count<<<grid_for(ctx, nT), kBlock, 0, s>>>(nT, nV, m->tri, m->xy, cnt, err);
   PH_TRY(check_launch(ctx, "k_count"));
   PH_TRY(check_status(ctx, err, "phfem_mesh_build"));
-  PH_TRY(exclusive_scan(ctx, cnt, bstart, nV, bstart + nV));
-  k_scatter<<<grid_for(ctx, nT), kBlock, 0, s>>>(nT, m->tri, bstart, fill, buf);
-  PH_TRY(check_launch(ctx, "k_scatter"));
-  k_bucket_sort<<<grid_for(ctx, nV), kBlock, 0, s>>>(nV, m->tri, bstart, buf, ecount, err);
-  PH_TRY(check_launch(ctx, "k_bucket_sort"));
+  PH_TRY(exclusive_scan(ctx, cnt, bstart, nV, bstart + nV));  // bucket of each larger vertex
+
+  // directed edges in (larger vertex, smaller vertex, occurrence) order
+  const int n = 3 * nT;
+  uint32_t *lo_o, *hi_o, *key, *key2;
+  int32_t *occ, *occ2, *start, *enr;
+  unsigned long long* buf;
+  PH_TRY(tmp.get(&lo_o, (size_t)n));
+  PH_TRY(tmp.get(&hi_o, (size_t)n));
+  PH_TRY(tmp.get(&key, (size_t)n));
+  PH_TRY(tmp.get(&key2, (size_t)n));
+  PH_TRY(tmp.get(&occ, (size_t)n));
+  PH_TRY(tmp.get(&occ2, (size_t)n));
+  PH_TRY(tmp.get(&start, (size_t)n + 1));
+  PH_TRY(tmp.get(&enr, (size_t)n + 1));
+  PH_TRY(tmp.get(&buf, (size_t)n));
+  int vbits = 1;
+  while (vbits < 31 && (1ll << vbits) < (long long)nV) ++vbits;
+  k_keys<<<grid_for(ctx, n), kBlock, 0, s>>>(nT, m->tri, lo_o, hi_o, key, occ);
+  PH_TRY(check_launch(ctx, "k_keys"));
+  PH_TRY(radix_sort_pairs(ctx, key, occ, key2, occ2, n, vbits));   // by the smaller vertex
+  k_hi_key<<<grid_for(ctx, n), kBlock, 0, s>>>(n, hi_o, occ, key);
+  PH_TRY(check_launch(ctx, "k_hi_key"));
+  PH_TRY(radix_sort_pairs(ctx, key, occ, key2, occ2, n, vbits));   // then, stably, by the larger one
+  k_entries<<<grid_for(ctx, n), kBlock, 0, s>>>(n, m->tri, lo_o, hi_o, occ, buf, start, err);
+  PH_TRY(check_launch(ctx, "k_entries"));
   PH_TRY(check_status(ctx, err, "phfem_mesh_build"));
-  PH_TRY(exclusive_scan(ctx, ecount, ebase, nV, ebase + nV));
+  PH_TRY(exclusive_scan(ctx, start, enr, n, enr + n));
   int32_t nE = 0;
-  PH_TRY(read_int(ctx, ebase + nV, &nE));
+  PH_TRY(read_int(ctx, enr + n, &nE));
   m->info.nE = nE;
 
   int32_t* pos_edge;
@@ -382,8 +397,8 @@ int build(phfem_ctx ctx, int nV, const double* xy, int nT, const int32_t* tri, i
   PH_TRY(dalloc_n(ctx, &m->t2e, 3 * (size_t)nT));
   PH_TRY(dalloc_n(ctx, &m->sigma, 3 * (size_t)nT));
   PH_TRY(dalloc_n(ctx, &m->lk, (size_t)nE));
-  k_edges<<<grid_for(ctx, nV), kBlock, 0, s>>>(nV, m->tri, bstart, buf, ebase, m->ed2el, m->t2e, m->sigma,
-                                               m->lk, pos_edge);
+  k_edges<<<grid_for(ctx, n), kBlock, 0, s>>>(n, m->tri, buf, start, enr, m->ed2el, m->t2e, m->sigma, m->lk,
+                                              pos_edge);
   PH_TRY(check_launch(ctx, "k_edges"));
 
   int32_t *ecode, *isfree, *islam;

@@ -89,6 +89,19 @@ def _as_pairs(lst) -> np.ndarray:
 # Structured unit-square meshes
 # ----------------------------------------------------------------------------
 
+def fan_mesh(n: int) -> Mesh:
+    """n triangles around one vertex: ring vertices 0..n-1 on the unit circle,
+    the centre last (vertex n, so every spoke has it as its larger vertex),
+    triangles (ring i, ring i+1, centre) counter-clockwise; the ring edges are
+    Dirichlet.  The centre has valence n."""
+    ang = 2.0 * np.pi * np.arange(n) / n
+    xy = np.concatenate([np.stack([np.cos(ang), np.sin(ang)], axis=1), np.zeros((1, 2))]).astype(np.float64)
+    i = np.arange(n)
+    tri = np.stack([i, (i + 1) % n, np.full(n, n)], axis=1).astype(np.int32)
+    dirichlet = np.stack([i, (i + 1) % n], axis=1).astype(np.int32)
+    return Mesh(xy, tri, dirichlet, np.zeros((0, 2), np.int32), name="fan")
+
+
 def square_mesh(n: int, dirichlet_sides=("left", "right"), x0=0.0, y0=0.0, size=1.0) -> Mesh:
     """n x n squares on [x0, x0+size] x [y0, y0+size]; every square is split by
     the diagonal from its lower-left to its upper-right corner.  Squares are
