@@ -398,6 +398,22 @@ PHFEM_API int phfem_cn_step(phfem_cn cn, int32_t nsteps, const phfem_solve_opts*
  * stream for nothing: capture runs on a private stream. */
 PHFEM_API int phfem_cn_step_graph(phfem_cn cn, int32_t nsteps, const phfem_solve_opts* opts,
                                   phfem_stats* stats);
+/* Crank-Nicolson with general sources (Section 4, Eqs. parabolicRight_*):
+ * instead of separable terms, every step supplies the data at its new time.
+ *   f0_mid, bc0_mid [nE] double: f at the midpoints and the boundary datum
+ *          (g on Neumann, u_D on Dirichlet edges) at t_0 (NULL = 0)
+ *   w0, Lambda0 as in phfem_cn_create; max_steps: steps the handle may take
+ * phfem_cn_step_data advances one step, t_{n-1} -> t_n = t_{n-1} + dt:
+ *   f_mid, bc_mid [nE] double: the data at t_n (NULL = 0).  The load is the
+ *   trapezoid average of the data at t_{n-1} (kept from the previous call or
+ *   f0/bc0) and t_n, the Dirichlet rows hold u_D(t_n).  Blocks the host.
+ * phfem_cn_step / phfem_cn_step_graph refuse such a handle (PHFEM_EINVAL),
+ * and phfem_cn_step_data a separable one. */
+PHFEM_API int phfem_cn_create_data(phfem_sys sys, const double* f0_mid, const double* bc0_mid,
+                                   const double* w0, const double* Lambda0, int32_t max_steps,
+                                   phfem_cn* out);
+PHFEM_API int phfem_cn_step_data(phfem_cn cn, const double* f_mid, const double* bc_mid,
+                                 const phfem_solve_opts* opts, phfem_stats* stats);
 /* Reads the state after the last step (any pointer may be NULL):
  *   w [nE], U [3 nT], Lambda_n [nL], Lambda_half [nL] (Lambda^{n-1/2}),
  *   step: host int32, number of steps done. */

@@ -19,7 +19,7 @@
 
 struct phfem_cn_s {
   phfem_sys sys;
-  int Q;
+  int Q;             // separable terms; 0: per-step data (fq, bcq hold the previous step's arrays)
   int nt;
   int step;
   double* fq;        // [Q][nE]
@@ -103,6 +103,33 @@ __global__ void k_cn_rhs(int nE, const int32_t* __restrict__ nbr, const double* 
       for (int q = 0; q < Q; ++q) g += ph.avg[q] * bcq[q * m + e];
       load += elen[e] * g;
     }
+    b[e] = 2.0 * me[e] * x[e] - aw + dt * load;
+  }
+}
+
+// The same right-hand side from per-step data (general sources): f and g
+// averaged over t_{n-1} and t_n from the two arrays, u_D(t_n) on Dirichlet rows.
+__global__ void k_cn_rhs_data(int nE, const int32_t* __restrict__ nbr, const double* __restrict__ val,
+                              const double* __restrict__ x, const double* __restrict__ me,
+                              const uint8_t* __restrict__ eclass, const double* __restrict__ elen,
+                              const double* __restrict__ f_now, const double* __restrict__ f_prev,
+                              const double* __restrict__ bc_now, const double* __restrict__ bc_prev, double dt,
+                              double* __restrict__ b, double* __restrict__ f_eff) {
+  const size_t m = (size_t)nE;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+    const uint8_t cls = eclass[e];
+    const double fav = 0.5 * ((f_now ? f_now[e] : 0.0) + f_prev[e]);
+    f_eff[e] = fav;
+    if (cls == PHFEM_EDGE_DIRICHLET) {
+      b[e] = bc_now ? bc_now[e] : 0.0;
+      continue;
+    }
+    const double xe = x[e];
+    double aw = val[e] * xe;  // (A+ w)_e in difference form
+#pragma unroll
+    for (int s = 0; s < 4; ++s) aw += val[(s + 1) * m + e] * (xe - x[nbr[s * m + e]]);
+    double load = me[e] * fav;
+    if (cls == PHFEM_EDGE_NEUMANN) load += elen[e] * 0.5 * ((bc_now ? bc_now[e] : 0.0) + bc_prev[e]);
     b[e] = 2.0 * me[e] * x[e] - aw + dt * load;
   }
 }
@@ -306,6 +333,7 @@ PHFEM_API int phfem_cn_create(phfem_sys sys, const phfem_source* src, const doub
 
 PHFEM_API int phfem_cn_step(phfem_cn cn, int32_t nsteps, const phfem_solve_opts* opts, phfem_stats* stats) {
   if (!cn || nsteps < 0) return fail(PHFEM_EINVAL, "phfem_cn_step: bad argument");
+  if (cn->Q == 0) return fail(PHFEM_EINVAL, "phfem_cn_step: created for per-step data (use phfem_cn_step_data)");
   if (cn->step + nsteps >= cn->nt)
     return fail(PHFEM_EINVAL, "phfem_cn_step: the source has no time factors for the requested steps");
   auto t0 = std::chrono::steady_clock::now();
@@ -331,6 +359,7 @@ PHFEM_API int phfem_cn_step(phfem_cn cn, int32_t nsteps, const phfem_solve_opts*
 
 PHFEM_API int phfem_cn_step_graph(phfem_cn cn, int32_t nsteps, const phfem_solve_opts* opts, phfem_stats* stats) {
   if (!cn || nsteps < 0) return fail(PHFEM_EINVAL, "phfem_cn_step_graph: bad argument");
+  if (cn->Q == 0) return fail(PHFEM_EINVAL, "phfem_cn_step_graph: created for per-step data (use phfem_cn_step_data)");
   if (cn->step + nsteps >= cn->nt)
     return fail(PHFEM_EINVAL, "phfem_cn_step_graph: the source has no time factors for the requested steps");
   auto t0 = std::chrono::steady_clock::now();
@@ -350,6 +379,98 @@ PHFEM_API int phfem_cn_step_graph(phfem_cn cn, int32_t nsteps, const phfem_solve
   if (stats) *stats = st;
   if (status != PHFEM_OK) return fail(status, "phfem_cn_step_graph: a step did not converge");
   return PHFEM_OK;
+}
+
+PHFEM_API int phfem_cn_create_data(phfem_sys sys, const double* f0_mid, const double* bc0_mid, const double* w0,
+                                   const double* Lambda0, int32_t max_steps, phfem_cn* out) {
+  if (!out) return fail(PHFEM_EINVAL, "phfem_cn_create_data: out is NULL");
+  *out = nullptr;
+  if (!sys || max_steps < 1) return fail(PHFEM_EINVAL, "phfem_cn_create_data: bad argument");
+  if (!(sys->c.dt > 0)) return fail(PHFEM_EINVAL, "phfem_cn_create_data: the system was assembled with dt = 0");
+  phfem_mesh m = sys->mesh;
+  phfem_ctx ctx = m->ctx;
+  cudaStream_t s = ctx->stream;
+  const size_t nE = m->info.nE, nL = m->info.nL;
+  phfem_cn cn = new phfem_cn_s();
+  cn->sys = sys;
+  cn->Q = 0;
+  cn->nt = max_steps + 1;
+  cn->step = 0;
+  int st = PHFEM_OK;
+  auto chk = [&](int r) {
+    if (st == PHFEM_OK) st = r;
+  };
+  chk(dalloc_n(ctx, &cn->fq, nE));   // f and g / u_D of the previous step
+  chk(dalloc_n(ctx, &cn->bcq, nE));
+  chk(dalloc_n(ctx, &cn->step_dev, 1));
+  chk(dalloc_n(ctx, &cn->it_dev, cn->nt));
+  chk(dalloc_n(ctx, &cn->conv_dev, cn->nt));
+  chk(dalloc_n(ctx, &cn->rel_dev, cn->nt));
+  chk(dalloc_n(ctx, &cn->xprev, nE));
+  chk(dalloc_n(ctx, &cn->f_eff, nE));
+  chk(dalloc_n(ctx, &cn->lam_half, nL));
+  chk(dalloc_n(ctx, &cn->lam_n, nL));
+  if (st == PHFEM_OK) {
+    if (f0_mid) cudaMemcpyAsync(cn->fq, f0_mid, sizeof(double) * nE, cudaMemcpyDeviceToDevice, s);
+    else cudaMemsetAsync(cn->fq, 0, sizeof(double) * nE, s);
+    if (bc0_mid) cudaMemcpyAsync(cn->bcq, bc0_mid, sizeof(double) * nE, cudaMemcpyDeviceToDevice, s);
+    else cudaMemsetAsync(cn->bcq, 0, sizeof(double) * nE, s);
+    if (Lambda0) cudaMemcpyAsync(cn->lam_n, Lambda0, sizeof(double) * nL, cudaMemcpyDeviceToDevice, s);
+    else cudaMemsetAsync(cn->lam_n, 0, sizeof(double) * nL, s);
+    cudaMemsetAsync(cn->lam_half, 0, sizeof(double) * nL, s);
+    cudaMemsetAsync(cn->step_dev, 0, sizeof(int), s);
+    cudaMemsetAsync(cn->it_dev, 0, sizeof(int) * cn->nt, s);
+    cudaMemsetAsync(cn->conv_dev, 0, sizeof(int) * cn->nt, s);
+    cudaMemsetAsync(cn->rel_dev, 0, sizeof(double) * cn->nt, s);
+    Phi one{};
+    one.now[0] = 1.0;  // x = w0, and u_D(t_0) on Dirichlet rows
+    k_cn_init<<<grid_for(ctx, nE), kBlock, 0, s>>>((int)nE, m->eclass, w0, cn->bcq, 1, one, sys->x);
+    st = check_launch(ctx, "k_cn_init");
+  }
+  if (st == PHFEM_OK && cudaStreamSynchronize(s) != cudaSuccess)
+    st = cuda_fail(cudaGetLastError(), "phfem_cn_create_data", __FILE__, __LINE__);
+  if (st != PHFEM_OK) {
+    cudaStreamSynchronize(s);
+    cn_free(cn);
+    return st;
+  }
+  *out = cn;
+  return PHFEM_OK;
+}
+
+PHFEM_API int phfem_cn_step_data(phfem_cn cn, const double* f_mid, const double* bc_mid,
+                                 const phfem_solve_opts* opts, phfem_stats* stats) {
+  if (!cn) return fail(PHFEM_EINVAL, "phfem_cn_step_data: NULL handle");
+  if (cn->Q != 0) return fail(PHFEM_EINVAL, "phfem_cn_step_data: created for a separable source (use phfem_cn_step)");
+  if (cn->step + 1 >= cn->nt) return fail(PHFEM_EINVAL, "phfem_cn_step_data: max_steps reached");
+  auto t0 = std::chrono::steady_clock::now();
+  phfem_sys sys = cn->sys;
+  phfem_mesh m = sys->mesh;
+  phfem_ctx ctx = m->ctx;
+  cudaStream_t s = ctx->stream;
+  const int nE = m->info.nE;
+  PH_CUDA(cudaMemcpyAsync(cn->xprev, sys->x, sizeof(double) * nE, cudaMemcpyDeviceToDevice, s));
+  k_cn_rhs_data<<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, m->nbr, sys->val, sys->x, sys->me, m->eclass, m->elen, f_mid,
+                                                     cn->fq, bc_mid, cn->bcq, sys->c.dt, sys->b, cn->f_eff);
+  PH_TRY(check_launch(ctx, "k_cn_rhs_data"));
+  k_set_dirichlet<<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, m->eclass, sys->b, sys->x);
+  PH_TRY(check_launch(ctx, "k_set_dirichlet"));
+  phfem_stats st{};
+  int status = solve_system(sys, opts, &st, true);
+  if (status == PHFEM_OK) {
+    PH_TRY(enqueue_post(cn));
+    // this step's data become the previous step's
+    if (f_mid) PH_CUDA(cudaMemcpyAsync(cn->fq, f_mid, sizeof(double) * nE, cudaMemcpyDeviceToDevice, s));
+    else PH_CUDA(cudaMemsetAsync(cn->fq, 0, sizeof(double) * nE, s));
+    if (bc_mid) PH_CUDA(cudaMemcpyAsync(cn->bcq, bc_mid, sizeof(double) * nE, cudaMemcpyDeviceToDevice, s));
+    else PH_CUDA(cudaMemsetAsync(cn->bcq, 0, sizeof(double) * nE, s));
+    cn->step += 1;
+    st.steps = 1;
+  }
+  PH_CUDA(cudaStreamSynchronize(s));
+  st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (stats) *stats = st;
+  return status;
 }
 
 PHFEM_API int phfem_cn_read(phfem_cn cn, double* w, double* U, double* Lambda_n, double* Lambda_half,

@@ -138,6 +138,8 @@ def lib() -> C.CDLL:
             "phfem_solve": (C.c_int, [_H, C.POINTER(SolveOpts), _P, _P, _P, _P, C.POINTER(Stats)]),
             "phfem_cn_create": (C.c_int, [_H, C.POINTER(Source), _P, _P, C.POINTER(_H)]),
             "phfem_cn_step": (C.c_int, [_H, C.c_int32, C.POINTER(SolveOpts), C.POINTER(Stats)]),
+            "phfem_cn_create_data": (C.c_int, [_H, _P, _P, _P, _P, C.c_int32, C.POINTER(_H)]),
+            "phfem_cn_step_data": (C.c_int, [_H, _P, _P, C.POINTER(SolveOpts), C.POINTER(Stats)]),
             "phfem_cn_step_graph": (C.c_int, [_H, C.c_int32, C.POINTER(SolveOpts), C.POINTER(Stats)]),
             "phfem_cn_read": (C.c_int, [_H, _P, _P, _P, _P, C.POINTER(C.c_int32)]),
             "phfem_cn_destroy": (C.c_int, [_H]),
@@ -386,6 +388,24 @@ def phfem_cn_create(sys, f_mid, bc_mid, phi, w0, Lambda0=None):
     _check(lib().phfem_cn_create(sys, C.byref(src), _ptr(w0, torch.float64), _ptr(Lambda0, torch.float64),
                                  C.byref(h)), "phfem_cn_create")
     return h
+
+
+def phfem_cn_create_data(sys, f0_mid, bc0_mid, w0, max_steps, Lambda0=None):
+    """Crank-Nicolson with per-step data (general sources); the data at t_0 here."""
+    h = _H()
+    _check(lib().phfem_cn_create_data(sys, _ptr(f0_mid, torch.float64), _ptr(bc0_mid, torch.float64),
+                                      _ptr(w0, torch.float64), _ptr(Lambda0, torch.float64), int(max_steps),
+                                      C.byref(h)), "phfem_cn_create_data")
+    return h
+
+
+def phfem_cn_step_data(cn, f_mid, bc_mid, opts=None) -> dict:
+    """One step with the data at the new time level (f and g / u_D at the midpoints)."""
+    st = Stats()
+    o = opts if opts is not None else solve_opts()
+    _check(lib().phfem_cn_step_data(cn, _ptr(f_mid, torch.float64), _ptr(bc_mid, torch.float64), C.byref(o),
+                                    C.byref(st)), "phfem_cn_step_data")
+    return st.as_dict()
 
 
 def phfem_cn_step(cn, nsteps, opts=None) -> dict:

@@ -117,3 +117,58 @@ def test_graph_steps_equal_host_steps(ctx, precision):
     assert np.array_equal(a["U"], b["U"]) and np.array_equal(a["Lambda"], b["Lambda"])
     assert np.array_equal(a["Lambda_half"], b["Lambda_half"])
     assert a["stats"]["iterations"] == b["stats"]["iterations"]
+
+
+def _problem_nonseparable():
+    """u = sin(pi y) exp(-x t), which no finite sum of f_q(x) phi_q(t) gives:
+    u_t = -x u, -Lap u = (pi^2 - t^2) u, so f = (pi^2 - t^2 - x) u; u_D on x = 0
+    (sin(pi y)) and x = 1 (e^-t sin(pi y)) varies in time; g = grad u . n on
+    y = 0, 1."""
+    pi = np.pi
+    u = lambda x, y, t: np.sin(pi * y) * np.exp(-x * t)
+    grad = lambda x, y, t: (-t * u(x, y, t), pi * np.cos(pi * y) * np.exp(-x * t))
+    f = lambda x, y, t: (pi * pi - t * t - x) * u(x, y, t)
+
+    def g(x, y, nx, ny, t):
+        gx, gy = grad(x, y, t)
+        return gx * nx + gy * ny
+
+    return I.Problem(f=f, g=g, uD=u, u=u, grad=grad, delta=0.0, u0=lambda x, y: u(x, y, 0.0))
+
+
+@pytest.mark.parametrize("precision", [0, 1], ids=["fp64", "fp32ir"])
+def test_general_source_matches_oracle(ctx, precision):
+    """Per-step data (phfem_cn_create_data / phfem_cn_step_data) for a source,
+    flux and Dirichlet datum that are not separable in x and t, against the
+    oracle's stepping of the saddle-point system with the same functions."""
+    from paper_2401_15557_gb300 import phfem as P
+    from phfem_gpu import GpuMesh
+    pb = _problem_nonseparable()
+    mesh = I.square_mesh(8)
+    dt, nsteps = 0.05, 6
+    gm = GpuMesh(mesh, ctx)
+    data = lambda t: gm.edge_data(lambda x, y: pb.f(x, y, t), lambda x, y, nx, ny: pb.g(x, y, nx, ny, t),
+                                  lambda x, y: pb.uD(x, y, t))
+    f0, bc0 = data(0.0)
+    w0, _ = gm.edge_data(pb.u0)
+    sysh = P.phfem_assemble(gm.h, None, None, delta=0.0, dt=dt, precision=precision)
+    cn = P.phfem_cn_create_data(sysh, f0, bc0, w0, nsteps)
+    with pytest.raises(P.PhfemError):
+        P.phfem_cn_step(cn, 1, P.solve_opts(rtol=1e-13))
+    for n in range(1, nsteps + 1):
+        fn, bcn = data(n * dt)
+        st = P.phfem_cn_step_data(cn, fn, bcn, P.solve_opts(rtol=1e-12))
+        assert st["converged"] == 1, (n, st)
+    with pytest.raises(P.PhfemError):  # max_steps reached
+        P.phfem_cn_step_data(cn, fn, bcn, P.solve_opts(rtol=1e-12))
+    I_ = gm.info
+    U = torch.empty(3 * I_["nT"], dtype=torch.float64, device="cuda")
+    Lh = torch.empty(I_["nL"], dtype=torch.float64, device="cuda")
+    P.phfem_cn_read(cn, U=U, Lambda_half=Lh)
+    ref = O.cn_solve(mesh, pb, dt, nsteps)
+    Ug, Lg = U.cpu().numpy(), Lh.cpu().numpy()
+    assert np.max(np.abs(Ug - ref["U"])) <= 1e-9 * np.max(np.abs(ref["U"]))
+    assert np.max(np.abs(Lg - ref["Lambda_half"])) <= 1e-8 * np.max(np.abs(ref["Lambda_half"]))
+    P.phfem_cn_destroy(cn)
+    P.phfem_sys_destroy(sysh)
+    gm.close()
