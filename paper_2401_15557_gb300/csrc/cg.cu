@@ -157,7 +157,8 @@ __global__ void k_fcg_op(int n, const int32_t* __restrict__ perm, const T* __res
 template <typename Y>
 __global__ void k_fcg_in(int n, const int32_t* __restrict__ perm, const double* __restrict__ b_paper,
                          const double* __restrict__ x_paper, double* __restrict__ b, double* __restrict__ xh,
-                         double* __restrict__ xl, Y* __restrict__ y) {
+                         double* __restrict__ xl, Y* __restrict__ y, SolveState* st) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) st->ypend = 0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int e = perm[i];
     b[i] = b_paper[e];
@@ -169,27 +170,41 @@ __global__ void k_fcg_in(int n, const int32_t* __restrict__ perm, const double* 
   }
 }
 
-// End of a solve: x = (xh + xl) + y, rounded to FP64, in the paper's order.
-template <typename Y>
+// The pending term alpha_prev p of the fused FP32 iteration (the update adds
+// two iterations' terms to y at once), or 0.
+template <typename T>
+__device__ __forceinline__ double pending_term(const SolveState* st, const T* p0, const T* p1, int i) {
+  if (!st->ypend) return 0.0;
+  const T* p = st->par ? p1 : p0;
+  return st->alpha_prev * (double)p[i];
+}
+
+// End of a solve: x = (xh + xl) + y (+ a pending term), rounded to FP64, in
+// the paper's order.
+template <typename Y, typename T>
 __global__ void k_fcg_out(int n, const int32_t* __restrict__ perm, const double* __restrict__ xh,
-                          const double* __restrict__ xl, const Y* __restrict__ y, double* __restrict__ x_paper) {
+                          const double* __restrict__ xl, const Y* __restrict__ y, const T* p0, const T* p1,
+                          const SolveState* st, double* __restrict__ x_paper) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double h = xh[i], l = xl[i];
     dd_add(h, l, y_value(y[i]));
+    dd_add(h, l, pending_term(st, p0, p1, i));
     x_paper[perm[i]] = h + l;
   }
 }
 
-// (xh, xl) += y, y = 0; with cond only when the iteration asked for a
-// reliable update (done == 1).
-template <typename Y>
+// (xh, xl) += y (+ a pending term), y = 0; with cond only when the iteration
+// asked for a reliable update (done == 1).  The residual kernel that follows
+// clears the pending flag.
+template <typename Y, typename T>
 __global__ void k_fcg_fold(int n, double* __restrict__ xh, double* __restrict__ xl, Y* __restrict__ y,
-                           const SolveState* st, int cond) {
+                           const T* p0, const T* p1, const SolveState* st, int cond) {
   if (cond && st->done != 1) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double h = xh[i], l = xl[i];
     Y v = y[i];
     dd_add(h, l, y_value(v));
+    dd_add(h, l, pending_term(st, p0, p1, i));
     xh[i] = h;
     xl[i] = l;
     y_zero(v);
@@ -302,6 +317,7 @@ __global__ void k_fcg_residual(int n, const short4* __restrict__ nb, const int4*
       return;
     }
     decide(st, rr, rz, ff, rp, mode, rtol2, inner_rtol2);
+    st->ypend = 0;  // folded into the pair before this residual
     if (mode == 1 && F) st->restart = 1;  // the product kernel forms p = u
   }
 }
@@ -376,19 +392,27 @@ __global__ void __launch_bounds__(kBlock) k_fcg_spmv(int n, const short4* __rest
   }
 }
 
-// One row of the update: y += alpha p, u -= alpha D^-1 q, and its r.z term.
-__device__ __forceinline__ void update_row(float2& y, float pe, float qe, float d, float& ue, float ah, float al,
-                                           float& acc) {
-  y = y_add(y, ah, al, pe);
+// One row of the update: u -= alpha D^-1 q and its r.z term; y takes
+// alpha_prev p_prev (two == true) and alpha p when with_y.
+__device__ __forceinline__ void update_row(float2& y, float pe, float pp, float qe, float d, float& ue, float ah,
+                                           float al, float aph, float apl, bool with_y, bool two, float& acc) {
+  if (with_y) {
+    if (two) y = y_add(y, aph, apl, pp);
+    y = y_add(y, ah, al, pe);
+  }
   ue = fmadd(-ah, d * qe, ue);
   acc += d > 0.f ? __fdividef(ue * ue, d) : 0.f;
 }
 
-// y += alpha p, u -= alpha D^-1 q, r.z = u.u / D^-1 (FP32) or u.u D (FP64,
-// with the stored diagonal: no FP64 division) -> beta.  Fused: then the test
-// of the recursive residual (done = 1 asks for a reliable update); unfused:
-// the direction kernel follows and tests it.  FP32 rows go four at a time
-// through 16-byte loads and stores.
+// u -= alpha D^-1 q, r.z = u.u / D^-1 (FP32) or u.u D (FP64, with the stored
+// diagonal: no FP64 division) -> beta, and the solution correction y.
+// Fused FP32: p of the previous iteration is still in the other direction
+// buffer, so y takes alpha_prev p_prev + alpha p every second iteration (and
+// the other iterations leave alpha p pending, which the fold and the end of
+// the solve add); then the test of the recursive residual (done = 1 asks for
+// a reliable update).  Unfused: y += alpha p every iteration, and the
+// direction kernel follows and tests the residual.  FP32 rows go four at a
+// time through 16-byte loads and stores.
 template <typename T, bool F>
 __global__ void __launch_bounds__(kBlock) k_fcg_update(int n, const T* p0, const T* p1, const T* __restrict__ q,
                                                        const T* __restrict__ di, const T* __restrict__ dg,
@@ -400,32 +424,43 @@ __global__ void __launch_bounds__(kBlock) k_fcg_update(int n, const T* p0, const
   const double a64 = st->alpha;
   const T ah = (T)a64;
   const T al = (T)(a64 - (double)ah);
+  const int pend = F ? st->ypend : 0;
   __shared__ double smem[kBlock / 32];
   T acc = (T)0;
   if constexpr (sizeof(T) == sizeof(float)) {
+    const bool with_y = !F || pend, two = F && pend;
+    const float* __restrict__ pprev = (F && st->par) ? p0 : p1;  // fused: the previous iteration's direction
+    const double ap64 = st->alpha_prev;
+    const float aph = (float)ap64, apl = (float)(ap64 - (double)aph);
     const int n4 = n / 4;
     const float4* __restrict__ p4 = reinterpret_cast<const float4*>(p);
+    const float4* __restrict__ pp4 = reinterpret_cast<const float4*>(pprev);
     const float4* __restrict__ q4 = reinterpret_cast<const float4*>(q);
     const float4* __restrict__ d4 = reinterpret_cast<const float4*>(di);
     float4* __restrict__ u4 = reinterpret_cast<float4*>(u);
     float4* __restrict__ y4 = reinterpret_cast<float4*>(y);  // two rows' pairs per float4
-    // two groups of four rows per thread and pass: all twelve 16-byte loads
-    // are issued before the first store
+    // two groups of four rows per thread and pass: all loads are issued before
+    // the first store
     const int stride = gridDim.x * blockDim.x;
+    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
     for (int j0 = blockIdx.x * blockDim.x + threadIdx.x; j0 < n4; j0 += 2 * stride) {
-      float4 pv[2], qv[2], dv[2], uv[2], ya[2], yb[2];
+      float4 pv[2], ppv[2], qv[2], dv[2], uv[2], ya[2], yb[2];
       bool ok[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int j = j0 + h * stride;
         ok[h] = j < n4;
+        pv[h] = ppv[h] = ya[h] = yb[h] = z4;
         if (ok[h]) {
-          pv[h] = p4[j];
           qv[h] = q4[j];
           dv[h] = d4[j];
           uv[h] = u4[j];
-          ya[h] = y4[2 * j];
-          yb[h] = y4[2 * j + 1];
+          if (with_y) {
+            pv[h] = p4[j];
+            ya[h] = y4[2 * j];
+            yb[h] = y4[2 * j + 1];
+            if (two) ppv[h] = pp4[j];
+          }
         }
       }
 #pragma unroll
@@ -434,23 +469,25 @@ __global__ void __launch_bounds__(kBlock) k_fcg_update(int n, const T* p0, const
         const int j = j0 + h * stride;
         float2 y0 = make_float2(ya[h].x, ya[h].y), y1 = make_float2(ya[h].z, ya[h].w);
         float2 y2 = make_float2(yb[h].x, yb[h].y), y3 = make_float2(yb[h].z, yb[h].w);
-        update_row(y0, pv[h].x, qv[h].x, dv[h].x, uv[h].x, ah, al, acc);
-        update_row(y1, pv[h].y, qv[h].y, dv[h].y, uv[h].y, ah, al, acc);
-        update_row(y2, pv[h].z, qv[h].z, dv[h].z, uv[h].z, ah, al, acc);
-        update_row(y3, pv[h].w, qv[h].w, dv[h].w, uv[h].w, ah, al, acc);
+        update_row(y0, pv[h].x, ppv[h].x, qv[h].x, dv[h].x, uv[h].x, ah, al, aph, apl, with_y, two, acc);
+        update_row(y1, pv[h].y, ppv[h].y, qv[h].y, dv[h].y, uv[h].y, ah, al, aph, apl, with_y, two, acc);
+        update_row(y2, pv[h].z, ppv[h].z, qv[h].z, dv[h].z, uv[h].z, ah, al, aph, apl, with_y, two, acc);
+        update_row(y3, pv[h].w, ppv[h].w, qv[h].w, dv[h].w, uv[h].w, ah, al, aph, apl, with_y, two, acc);
         u4[j] = uv[h];
-        y4[2 * j] = make_float4(y0.x, y0.y, y1.x, y1.y);
-        y4[2 * j + 1] = make_float4(y2.x, y2.y, y3.x, y3.y);
+        if (with_y) {
+          y4[2 * j] = make_float4(y0.x, y0.y, y1.x, y1.y);
+          y4[2 * j + 1] = make_float4(y2.x, y2.y, y3.x, y3.y);
+        }
       }
     }
     // the last n % 4 rows
     const int i = 4 * n4 + blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
       float ue = u[i];
-      float2 yi = y[i];
-      update_row(yi, p[i], q[i], di[i], ue, ah, al, acc);
+      float2 yi = with_y ? y[i] : make_float2(0.f, 0.f);
+      update_row(yi, with_y ? p[i] : 0.f, two ? pprev[i] : 0.f, q[i], di[i], ue, ah, al, aph, apl, with_y, two, acc);
       u[i] = ue;
-      y[i] = yi;
+      if (with_y) y[i] = yi;
     }
   } else {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
@@ -470,6 +507,10 @@ __global__ void __launch_bounds__(kBlock) k_fcg_update(int n, const T* p0, const
     st->beta = st->rz > 0.0 ? rz / st->rz : 0.0;
     st->rz = rz;
     st->it += 1;
+    if (F) {  // alpha p of this iteration is added to y with the next one's
+      st->ypend = pend ? 0 : 1;
+      st->alpha_prev = a64;
+    }
     if (!isfinite(rz)) {
       st->done = 3;
       st->status = PHFEM_ENAN;
@@ -512,19 +553,22 @@ struct FLaunch {
   const FastCG* f() const { return sys->fcg; }
   int prologue() const {
     phfem_ctx ctx = sys->mesh->ctx;
-    k_fcg_in<Y><<<g, kBlock, 0, s>>>(n, sys->mesh->perm, sys->b, sys->x, f()->b, f()->xh, f()->xl, (Y*)f()->y);
+    k_fcg_in<Y><<<g, kBlock, 0, s>>>(n, sys->mesh->perm, sys->b, sys->x, f()->b, f()->xh, f()->xl, (Y*)f()->y,
+                                     sys->st);
     return check_launch(ctx, "k_fcg_in");
   }
   int epilogue() const {
     phfem_ctx ctx = sys->mesh->ctx;
-    k_fcg_out<Y><<<g, kBlock, 0, s>>>(n, sys->mesh->perm, f()->xh, f()->xl, (const Y*)f()->y, sys->x);
+    k_fcg_out<Y, T><<<g, kBlock, 0, s>>>(n, sys->mesh->perm, f()->xh, f()->xl, (const Y*)f()->y,
+                                         (const T*)f()->p0(), (const T*)f()->p1(), sys->st, sys->x);
     return check_launch(ctx, "k_fcg_out");
   }
   int residual(int mode) const {
     phfem_ctx ctx = sys->mesh->ctx;
     phfem_mesh m = sys->mesh;
     if (mode >= 2) {
-      k_fcg_fold<Y><<<g, kBlock, 0, s>>>(n, f()->xh, f()->xl, (Y*)f()->y, sys->st, mode == 3);
+      k_fcg_fold<Y, T><<<g, kBlock, 0, s>>>(n, f()->xh, f()->xl, (Y*)f()->y, (const T*)f()->p0(),
+                                            (const T*)f()->p1(), sys->st, mode == 3);
       PH_TRY(check_launch(ctx, "k_fcg_fold"));
     }
     prof_start(ctx, kProfResidual);

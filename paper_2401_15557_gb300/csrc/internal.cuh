@@ -64,7 +64,8 @@ struct SolveState {
   int dir_pending; // set by the update kernel, cleared by the next SpMV: gates the direction kernel
   unsigned int counter[4];  // last-block counters of the reductions
   int par;         // locality-order CG: which of its two direction buffers holds the current p
-  int pad3;
+  int ypend;       // fused FP32 locality-order CG: alpha_prev p (in p[par]) not yet added to y
+  double alpha_prev;
 };
 
 }  // namespace phfem
