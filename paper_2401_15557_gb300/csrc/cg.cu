@@ -158,7 +158,10 @@ template <typename Y>
 __global__ void k_fcg_in(int n, const int32_t* __restrict__ perm, const double* __restrict__ b_paper,
                          const double* __restrict__ x_paper, double* __restrict__ b, double* __restrict__ xh,
                          double* __restrict__ xl, Y* __restrict__ y, SolveState* st) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) st->ypend = 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->ypend = 0;
+    st->sc = 1.0;
+  }
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     const int e = perm[i];
     b[i] = b_paper[e];
@@ -179,6 +182,13 @@ __device__ __forceinline__ double pending_term(const SolveState* st, const T* p0
   return st->alpha_prev * (double)p[i];
 }
 
+// y and the pending term carry the scale of the inner vectors (a power of
+// two): dividing by it is exact.
+template <typename Y, typename T>
+__device__ __forceinline__ double correction(const SolveState* st, const Y& y, const T* p0, const T* p1, int i) {
+  return (y_value(y) + pending_term(st, p0, p1, i)) / st->sc;
+}
+
 // End of a solve: x = (xh + xl) + y (+ a pending term), rounded to FP64, in
 // the paper's order.
 template <typename Y, typename T>
@@ -187,8 +197,7 @@ __global__ void k_fcg_out(int n, const int32_t* __restrict__ perm, const double*
                           const SolveState* st, double* __restrict__ x_paper) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double h = xh[i], l = xl[i];
-    dd_add(h, l, y_value(y[i]));
-    dd_add(h, l, pending_term(st, p0, p1, i));
+    dd_add(h, l, correction(st, y[i], p0, p1, i));
     x_paper[perm[i]] = h + l;
   }
 }
@@ -203,8 +212,7 @@ __global__ void k_fcg_fold(int n, double* __restrict__ xh, double* __restrict__ 
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double h = xh[i], l = xl[i];
     Y v = y[i];
-    dd_add(h, l, y_value(v));
-    dd_add(h, l, pending_term(st, p0, p1, i));
+    dd_add(h, l, correction(st, v, p0, p1, i));
     xh[i] = h;
     xl[i] = l;
     y_zero(v);
@@ -231,6 +239,12 @@ __device__ __forceinline__ double fmadd(double a, double b, double c) { return _
 // is the one the next iteration would have taken, p = u + beta p with the
 // recursive u: the unfused iteration already formed it before pausing, the
 // fused one forms it here from the recursive u before u is replaced.
+// Scaling: the inner vectors of the next cycle carry sc, a power of two that
+// brings the previous true residual (or b at the start) to an RMS of about
+// one per row, so FP32 quantities and their squares stay in range whatever
+// the size of the data; alpha and beta do not depend on it, the kept
+// direction is rescaled by sc_new / sc_old (exact), and y is divided by sc
+// when it is folded into the solution.
 template <typename T, bool F>
 __global__ void k_fcg_residual(int n, const short4* __restrict__ nb, const int4* __restrict__ ovf,
                                const double* __restrict__ val, const double* __restrict__ b,
@@ -246,6 +260,15 @@ __global__ void k_fcg_residual(int n, const short4* __restrict__ nb, const int4*
   const size_t m = (size_t)n;
   T* __restrict__ pc = (F && st->par) ? p1 : p0;
   const T beta = (T)st->beta;
+  double sc = 1.0;  // scale of the next cycle's inner vectors
+  if (mode != 0) {
+    const double prev = mode == 1 ? st->bb : st->rr64;
+    if (prev > 0.0 && isfinite(prev)) {
+      const int ex = ilogb(sqrt(prev / (double)n));
+      sc = ldexp(1.0, -max(-900, min(900, ex)));
+    }
+  }
+  const T ratio = (T)(sc / st->sc);  // a power of two
   double acc_r = 0.0, acc_z = 0.0, acc_f = 0.0, acc_p = 0.0;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     int c[4];
@@ -281,15 +304,15 @@ __global__ void k_fcg_residual(int n, const short4* __restrict__ nb, const int4*
     fl *= 0x1p-53;
     acc_f += fl * fl;
     const double dd = (double)di[i];
-    const T ue = (T)(dd * r);
+    const double rs = sc * r;
+    const T ue = (T)(dd * rs);
     if (mode == 1 && !F) pc[i] = ue;
     if (mode == 2) {
       T pk = pc[i];
-      if (F) {
-        pk = fmadd(beta, pk, u[i]);
-        pc[i] = pk;
-      }
-      acc_p += r * (double)pk;
+      if (F) pk = fmadd(beta, pk, u[i]);
+      pk *= ratio;
+      pc[i] = pk;
+      acc_p += rs * (double)pk;
     }
     u[i] = ue;
     if constexpr (sizeof(T) == sizeof(float)) acc_z += dd > 0.0 ? (double)ue * (double)ue / dd : 0.0;
@@ -316,7 +339,10 @@ __global__ void k_fcg_residual(int n, const short4* __restrict__ nb, const int4*
       st->bb = rr;
       return;
     }
+    const double rsc = sc / st->sc;
+    st->rz *= rsc * rsc;  // the recursive r.z in the new scale, for decide's comparison
     decide(st, rr, rz, ff, rp, mode, rtol2, inner_rtol2);
+    st->sc = sc;
     st->ypend = 0;  // folded into the pair before this residual
     if (mode == 1 && F) st->restart = 1;  // the product kernel forms p = u
   }

@@ -66,6 +66,7 @@ struct SolveState {
   int par;         // locality-order CG: which of its two direction buffers holds the current p
   int ypend;       // fused FP32 locality-order CG: alpha_prev p (in p[par]) not yet added to y
   double alpha_prev;
+  double sc;       // locality-order CG: power-of-two scale of the inner vectors since the last true residual
 };
 
 }  // namespace phfem

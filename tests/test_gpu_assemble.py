@@ -35,9 +35,8 @@ def _scaled(m, sx, sy):
 # stretched8: triangles (ll, lr, ur) have a 2.9-degree angle at P0, so FP32 systems take
 # the FP64 element records for them (and compensated FP32 for the others); tiny6: edges
 # below 2^-40, every triangle takes the FP64 records.  tiny6 solves a linear u of size
-# one: with the sine data the solution is ~1e-13 there, and the FP32 inner iteration's
-# residual products underflow (an FP32 system needs data whose residuals stay in the
-# float range; FP64 systems have no such limit).
+# one here; the sine data on it (u ~ 1e-13) are solved in test_gpu_order.py, where the
+# scaling of the FP32 inner vectors keeps them in range.
 SINE, LINEAR = I.problem_sine_exp, I.problem_linear
 CASES = [
     ("square17", lambda: I.square_mesh(17), 0.0, False, SINE),

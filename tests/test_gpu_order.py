@@ -128,3 +128,34 @@ def test_unfused_fp32_iteration_matches_fused():
     P.phfem_sys_destroy(sysh)
     gm.close()
     P.phfem_ctx_destroy(ctx)
+
+
+def test_fp32_solve_of_tiny_data():
+    """The square scaled by 2^-45 with the sine data: u ~ 1e-13, so FP32 squares
+    of the residual would underflow without the power-of-two scaling of the
+    inner vectors at each true residual.  FP32 + refinement converges to the
+    FP64 solution and to the oracle's."""
+    import dataclasses
+    from paper_2401_15557_gb300 import phfem as P
+    from phfem_gpu import GpuMesh, solve
+
+    ctx = P.phfem_ctx_create()
+    base = I.square_mesh(6)
+    mesh = dataclasses.replace(base, xy=np.ascontiguousarray(base.xy * 2.0 ** -45))
+    pb = I.problem_sine_exp()
+    pb.delta = 1.0
+    gm = GpuMesh(mesh, ctx)
+    out = {}
+    for prec in (P.PHFEM_FP64, P.PHFEM_FP32_IR):
+        r = solve(gm, pb, precision=prec, rtol=1e-10)
+        assert r["stats"]["converged"] == 1 and r["stats"]["rel_residual"] <= 1e-10, (prec, r["stats"])
+        out[prec] = r
+        P.phfem_sys_destroy(r["sys"])
+    w64, w32 = out[P.PHFEM_FP64]["w"], out[P.PHFEM_FP32_IR]["w"]
+    assert np.max(np.abs(w64)) < 1e-12  # the data really are tiny
+    assert np.max(np.abs(w32 - w64)) <= 1e-8 * np.max(np.abs(w64))
+    ref = O.solve_saddle(mesh, pb)
+    U = out[P.PHFEM_FP32_IR]["U"]
+    assert np.max(np.abs(U - ref["U"])) <= 1e-7 * np.max(np.abs(ref["U"]))
+    gm.close()
+    P.phfem_ctx_destroy(ctx)
