@@ -86,7 +86,7 @@ def hbm_peak():
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the product kernel at the full workload, from one ncu capture; valid only for
 # the kernel source whose hash is recorded with it.
-# Kernel timing inside the timed region brackets every 16th launch of each
+# Kernel timing inside the timed region brackets every 17th launch of each
 # kernel with CUDA events (an event between two launches keeps the second from
 # overlapping the first's drain, so timing every launch would slow the step).
 PROFILE_EVERY = 17  # odd: the update kernel alternates a light and a heavy launch (y every second iteration)
@@ -137,6 +137,9 @@ def parse():
     ap.add_argument("--heat-n", type=int, default=512)
     ap.add_argument("--heat-mg", type=int, default=1, help="heat: also run under the multigrid preconditioner")
     ap.add_argument("--requests", type=int, default=120, help="serve: measured requests")
+    ap.add_argument("--serve-modes", default="jacobi,multigrid", help="serve: request streams (jacobi, multigrid)")
+    ap.add_argument("--serve-precisions", default="fp32_refined,fp64", help="serve: precisions served")
+    ap.add_argument("--rates", default="", help="serve: comma-separated arrival rates of a sweep (requests/s)")
     ap.add_argument("--rate", type=float, default=200.0, help="serve: Poisson arrival rate (requests/s)")
     ap.add_argument("--slots", type=int, default=8, help="serve: worker slots")
     ap.add_argument("--batch-count", type=int, default=4096)
@@ -695,16 +698,33 @@ def serve_measure(requests, warmup, rate, slots, modes=("jacobi", "multigrid"), 
 
 
 def run_serve(args):
-    """The request stream of the serving workload (separate line)."""
-    sv = serve_measure(args.requests, args.warmup, args.rate, args.slots, modes=("jacobi", "multigrid"),
-                       precisions=("fp32_refined", "fp64"), no_clocks=args.no_clocks)
-    j = sv["jacobi_fp32_refined"]
-    line = {"metric": METRIC, "value": j["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.requests,
-            "warmup": args.warmup, "ms_per_step": 1e3 * j["span_s"] / args.requests, "higher_is_better": True,
+    """The request stream of the serving workload (separate line); with --rates
+    a sweep of arrival rates, whose knee is the highest rate the server keeps
+    up with."""
+    modes = tuple(m for m in args.serve_modes.split(",") if m)
+    precs = tuple(p for p in args.serve_precisions.split(",") if p)
+    sv = serve_measure(args.requests, args.warmup, args.rate, args.slots, modes=modes, precisions=precs,
+                       no_clocks=args.no_clocks)
+    sweep = []
+    for r in [float(x) for x in args.rates.split(",") if x]:
+        one = serve_measure(args.requests, args.warmup, r, args.slots, modes=modes[-1:], precisions=precs[:1],
+                            no_clocks=True)
+        key = f"{modes[-1]}_{precs[0]}"
+        res = one[key]
+        sweep.append({"rate_per_s": r, "mode": key, "solves_per_s": res["solves_per_s"], "p50_ms": res["p50_ms"],
+                      "p99_ms": res["p99_ms"], "saturated": res["saturated"],
+                      "offered_requests_per_s": res["offered_requests_per_s"]})
+    head = sv[f"{modes[0]}_{precs[0]}"]
+    line = {"metric": METRIC, "value": head["solves_per_s"], "unit": "solves/s", "n_gpus": 1, "steps": args.requests,
+            "warmup": args.warmup, "ms_per_step": 1e3 * head["span_s"] / args.requests, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "serve-poisson", "rate_per_s": args.rate, "requests": args.requests,
-                       "slots": args.slots, "hbm_budget_gb": 120},
-            "p50_ms": j["p50_ms"], "p99_ms": j["p99_ms"], "serve": sv, "clocks": j["clocks"]}
+                       "slots": args.slots, "hbm_budget_gb": 120, "modes": list(modes), "precisions": list(precs)},
+            "p50_ms": head["p50_ms"], "p99_ms": head["p99_ms"], "serve": sv, "rate_sweep": sweep,
+            "clocks": head["clocks"]}
+    if sweep:
+        ok = [x["rate_per_s"] for x in sweep if not x["saturated"]]
+        line["knee_requests_per_s"] = max(ok) if ok else None
     print(json.dumps(line, default=_json_default), flush=True)
     return 0
 
