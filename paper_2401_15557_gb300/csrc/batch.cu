@@ -264,7 +264,7 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
       }
       first = false;
       rz = rz_true;
-      tol2 = P.upd2 * rz;
+      tol2 = rz * fmax(P.upd2, fmin(bb > 0.0 ? 0.8 * P.rtol2 * bb / rr64 : 0.0, 1.0));  // as update_target
       msync<C>();
       // iterate until the recursive residual fell by the update factor
       while (it < P.max_iter) {

@@ -14,15 +14,17 @@
 //   * the preconditioned residual u = D^-1 r is the stored vector (r = u / d
 //     is never needed), and the direction update p = u + beta p is folded
 //     into the operator product: each row forms p at itself and at its four
-//     neighbours from u and the previous p (two buffers, swapped each
-//     iteration), writes its own p and q = S p, and sums p.q;
-//   * the second kernel adds alpha p to the solution correction y, updates u
-//     and sums r.z = u.u / D^-1;
+//     neighbours from u and the previous p (four buffers in rotation), writes
+//     its own p and q = S p, and sums p.q;
+//   * the second kernel updates u and sums r.z = u.u / D^-1; every fourth
+//     iteration it also adds alpha p of the last four directions (still in
+//     their buffers) to the solution correction y, so y is read and written
+//     once per four iterations;
 //   * the solution is x = (xh + xl) + y: xh + xl an unevaluated FP64 pair
 //     ("double-double"), y the correction since the last reliable update,
-//     accumulated every iteration as an unevaluated pair of floats (FP32
-//     systems: about 48 bits with FP32 arithmetic only) or in FP64.  At every
-//     reliable update y is added into the pair and cleared, and the true
+//     accumulated as an unevaluated pair of floats (FP32 systems: about 48
+//     bits with FP32 arithmetic only) or in FP64.  At every reliable update
+//     y (and any pending terms) is added into the pair and cleared, and the true
 //     residual b - S x is evaluated from the pair: the solution then carries
 //     more than FP64 precision, which the relative residual 1e-10 needs on
 //     fine meshes, where b scales like h^2 while S does not and no FP64 vector
@@ -53,6 +55,19 @@ struct Inner<double> {
   using Y = double;
 };
 
+// Direction buffers of the iteration.  The fused FP32 iteration rotates
+// through all four: the product kernel writes the direction after the
+// newest, and the update kernel adds alpha p of four iterations to y at once
+// every fourth iteration (the three before stay pending in their buffers).
+// The unfused iteration uses buffer 0 only.
+constexpr int kDirs = 4;
+template <typename T>
+struct Dirs {
+  T* base;        // buffer 0
+  size_t stride;  // elements from one buffer to the next
+  __host__ __device__ T* b(int k) const { return base + (size_t)k * stride; }
+};
+
 struct FastCG {
   int n = 0;
   bool fp32 = true;
@@ -65,12 +80,19 @@ struct FastCG {
   double* xh = nullptr;   // [n] solution, leading part
   double* xl = nullptr;   // [n] solution, trailing part
   void* y = nullptr;      // [n] Inner<T>::Y correction since the last reliable update
-  void* vec = nullptr;    // u, p0, p1, q: [4] slots of `slot` bytes
+  void* vec = nullptr;    // u, the kDirs direction buffers, q: slots of `slot` bytes
   size_t slot = 0;
+  // resident blocks per SM of the iteration kernels, [F] (fused or not): the
+  // grids are one wave of resident blocks, so no kernel runs a partial last
+  // wave (the FP32 update kernel holds 3 blocks per SM, the product kernel 8)
+  int per_spmv[2] = {1, 1}, per_update[2] = {1, 1}, per_dir = 1;
   void* u() const { return vec; }
-  void* p0() const { return (char*)vec + slot; }
-  void* p1() const { return (char*)vec + 2 * slot; }
-  void* q() const { return (char*)vec + 3 * slot; }
+  void* pk(int k) const { return (char*)vec + (1 + k) * slot; }
+  void* q() const { return (char*)vec + (1 + kDirs) * slot; }
+  template <typename T>
+  Dirs<T> dirs() const {
+    return Dirs<T>{(T*)pk(0), slot / sizeof(T)};
+  }
 };
 
 namespace {
@@ -107,6 +129,18 @@ __device__ __forceinline__ void load_l4(const Inner<double>::L4* __restrict__ l,
   v[1] = a.y;
   v[2] = b.x;
   v[3] = b.y;
+}
+
+// Tiles the product kernel prefetches into L2 ahead of the one it processes:
+// one tile is a visit later, ~3 us at level 5, several DRAM latencies;
+// 2 and 4 were slower (the prefetched lines are evicted before use).
+constexpr int kPrefetchAhead = 1;
+
+// L2 prefetch of bytes (rounded down to 16) from a 16-byte aligned address
+// by the bulk-copy engine; no registers, no completion to wait for.
+__device__ __forceinline__ void prefetch_l2(const void* a, int bytes) {
+  bytes &= ~15;
+  if (bytes > 0) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(bytes) : "memory");
 }
 
 // y += alpha p with alpha = ah + al (FP32 systems): the product as an exact
@@ -173,46 +207,50 @@ __global__ void k_fcg_in(int n, const int32_t* __restrict__ perm, const double* 
   }
 }
 
-// The pending term alpha_prev p of the fused FP32 iteration (the update adds
-// two iterations' terms to y at once), or 0.
+// The pending terms of the fused FP32 iteration: alpha p of the newest
+// ypend directions, oldest first (the update adds four iterations' terms to
+// y at once), or 0.
 template <typename T>
-__device__ __forceinline__ double pending_term(const SolveState* st, const T* p0, const T* p1, int i) {
-  if (!st->ypend) return 0.0;
-  const T* p = st->par ? p1 : p0;
-  return st->alpha_prev * (double)p[i];
+__device__ __forceinline__ double pending_terms(const SolveState* st, const Dirs<const T>& d, int i) {
+  double s = 0.0;
+  for (int j = st->ypend - 1; j >= 0; --j) {
+    const int k = (st->par - j) & (kDirs - 1);
+    s += st->alpha_dir[k] * (double)d.b(k)[i];
+  }
+  return s;
 }
 
-// y and the pending term carry the scale of the inner vectors (a power of
+// y and the pending terms carry the scale of the inner vectors (a power of
 // two): dividing by it is exact.
 template <typename Y, typename T>
-__device__ __forceinline__ double correction(const SolveState* st, const Y& y, const T* p0, const T* p1, int i) {
-  return (y_value(y) + pending_term(st, p0, p1, i)) / st->sc;
+__device__ __forceinline__ double correction(const SolveState* st, const Y& y, const Dirs<const T>& d, int i) {
+  return (y_value(y) + pending_terms(st, d, i)) / st->sc;
 }
 
-// End of a solve: x = (xh + xl) + y (+ a pending term), rounded to FP64, in
+// End of a solve: x = (xh + xl) + y (+ pending terms), rounded to FP64, in
 // the paper's order.
 template <typename Y, typename T>
 __global__ void k_fcg_out(int n, const int32_t* __restrict__ perm, const double* __restrict__ xh,
-                          const double* __restrict__ xl, const Y* __restrict__ y, const T* p0, const T* p1,
+                          const double* __restrict__ xl, const Y* __restrict__ y, Dirs<const T> d,
                           const SolveState* st, double* __restrict__ x_paper) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double h = xh[i], l = xl[i];
-    dd_add(h, l, correction(st, y[i], p0, p1, i));
+    dd_add(h, l, correction(st, y[i], d, i));
     x_paper[perm[i]] = h + l;
   }
 }
 
-// (xh, xl) += y (+ a pending term), y = 0; with cond only when the iteration
+// (xh, xl) += y (+ pending terms), y = 0; with cond only when the iteration
 // asked for a reliable update (done == 1).  The residual kernel that follows
-// clears the pending flag.
+// clears the pending count.
 template <typename Y, typename T>
 __global__ void k_fcg_fold(int n, double* __restrict__ xh, double* __restrict__ xl, Y* __restrict__ y,
-                           const T* p0, const T* p1, const SolveState* st, int cond) {
+                           Dirs<const T> d, const SolveState* st, int cond) {
   if (cond && st->done != 1) return;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
     double h = xh[i], l = xl[i];
     Y v = y[i];
-    dd_add(h, l, correction(st, v, p0, p1, i));
+    dd_add(h, l, correction(st, v, d, i));
     xh[i] = h;
     xl[i] = l;
     y_zero(v);
@@ -250,7 +288,7 @@ __global__ void k_fcg_residual(int n, const short4* __restrict__ nb, const int4*
                                const double* __restrict__ val, const double* __restrict__ b,
                                const double* __restrict__ xh, const double* __restrict__ xl,
                                const uint8_t* __restrict__ ecl, uint8_t ident, const T* __restrict__ di,
-                               const T* __restrict__ dg, T* __restrict__ u, T* p0, T* p1, double* partials,
+                               const T* __restrict__ dg, T* __restrict__ u, Dirs<T> dirs, double* partials,
                                SolveState* st, double rtol2, double inner_rtol2, int mode) {
   if (mode == 3) {
     if (st->done != 1) return;  // every block reads done before the last block rewrites it
@@ -258,7 +296,7 @@ __global__ void k_fcg_residual(int n, const short4* __restrict__ nb, const int4*
   }
   __shared__ double smem[kBlock / 32];
   const size_t m = (size_t)n;
-  T* __restrict__ pc = (F && st->par) ? p1 : p0;
+  T* __restrict__ pc = dirs.b(F ? st->par & (kDirs - 1) : 0);
   const T beta = (T)st->beta;
   double sc = 1.0;  // scale of the next cycle's inner vectors
   if (mode != 0) {
@@ -352,26 +390,55 @@ __global__ void k_fcg_residual(int n, const short4* __restrict__ nb, const int4*
 // p_old (restart: p = u; right after a reliable update that keeps the
 // direction: p = p_old) at the row and at its four neighbours, the same
 // rounded operation for every row, so all rows use the same p.  p_old is read
-// from one buffer and p written to the other; the last block swaps them.
+// from the newest direction buffer and p written to the next one; the last
+// block advances the rotation.
 // Unfused: the stored p (restart: p = u, each row writing its own p).  Then
 // p.q -> alpha = r.z / p.q (or r.p / p.q after a reliable update).
 // One row per thread and grid stride, at full occupancy; the gathers go
 // through L1 and L2 (in the locality order most neighbours were just read by
-// nearby rows).  Measured variants (tiles staged in shared memory, with and
-// without cp.async; several rows per thread; a software pipeline over rows)
-// were all slower on GB300.
+// nearby rows); the bulk L2 prefetch of the next tile takes the DRAM latency
+// out of the chain index load -> gathers (93 -> 83 us at level 5).  Measured
+// variants without it (tiles staged in shared memory, with and without
+// cp.async; several rows per thread; a software pipeline over rows;
+// contiguous runs of tiles per block) were all slower on GB300.
 template <typename T, bool F>
 __global__ void __launch_bounds__(kBlock) k_fcg_spmv(int n, const short4* __restrict__ nb,
                                                      const int4* __restrict__ ovf,
                                                      const typename Inner<T>::L4* __restrict__ lv,
-                                                     const T* __restrict__ rd, const T* __restrict__ u, T* p0, T* p1,
-                                                     T* __restrict__ q, double* partials, SolveState* st) {
+                                                     const T* __restrict__ rd, const T* __restrict__ u, Dirs<T> dirs,
+                                                     T* __restrict__ q, double* partials, SolveState* st,
+                                                     int ahead) {
+  // The block visits tiles of kBlock rows, blockIdx.x + k gridDim.x.  The
+  // five streamed arrays of the tile `ahead` visits on are prefetched into L2
+  // by the bulk-copy engine (the neighbour differences are then an L2 hit,
+  // and the gathers that depend on them wait for L2 instead of DRAM).  L2 is
+  // the point of coherence, so the first tiles are prefetched before the wait
+  // on the previous kernel.
+  const int ntiles = (n + kBlock - 1) / kBlock;
+  auto tile = [&](int k) { return blockIdx.x + k * (int)gridDim.x; };
+  // the previous direction's buffer: before the wait a hint (a stale value
+  // costs one useless prefetch), after it the value read below
+  const T* pfo = dirs.b(F ? (*(volatile const int*)&st->par) & (kDirs - 1) : 0);
+  auto prefetch = [&](int k) {
+    const int t = tile(k);
+    if (t >= ntiles || threadIdx.x >= 5) return;
+    const int r0 = t * kBlock, cnt = min(kBlock, n - r0);
+    switch (threadIdx.x) {
+      case 0: prefetch_l2(nb + r0, cnt * sizeof(short4)); break;
+      case 1: prefetch_l2(lv + r0, cnt * sizeof(typename Inner<T>::L4)); break;
+      case 2: prefetch_l2(rd + r0, cnt * sizeof(T)); break;
+      case 3: prefetch_l2(u + r0, cnt * sizeof(T)); break;
+      default: prefetch_l2(pfo + r0, cnt * sizeof(T)); break;
+    }
+  };
+  for (int k = 0; k < ahead; ++k) prefetch(k);
   pdl_enter();
   if (!F && blockIdx.x == 0 && threadIdx.x == 0) st->dir_pending = 0;  // no block of this kernel reads it
   if (st->done) return;
-  const int par = F ? st->par : 0;
-  const T* __restrict__ po = par ? p1 : p0;
-  T* __restrict__ pn = F ? (par ? p0 : p1) : p0;
+  const int par = F ? st->par & (kDirs - 1) : 0;
+  const T* __restrict__ po = dirs.b(par);
+  T* __restrict__ pn = dirs.b(F ? (par + 1) & (kDirs - 1) : 0);
+  pfo = po;
   const int mode = st->restart ? 1 : (st->use_rp ? 2 : 0);
   const T beta = (T)st->beta;
   __shared__ double smem[kBlock / 32];
@@ -381,7 +448,12 @@ __global__ void __launch_bounds__(kBlock) k_fcg_spmv(int n, const short4* __rest
     return pv;
   };
   T acc = (T)0;  // this thread's few rows in T; across threads and blocks in FP64
-  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (int k = 0;; ++k) {
+    const int t = tile(k);
+    if (t >= ntiles) break;
+    if (ahead) prefetch(k + ahead);
+    const int i = t * kBlock + threadIdx.x;
+    if (i >= n) continue;
     int c[4];
     row_nbrs(nb, ovf, i, c);
     T l[4];
@@ -406,7 +478,7 @@ __global__ void __launch_bounds__(kBlock) k_fcg_spmv(int n, const short4* __rest
   const double pq = sum_partials(partials, smem);
   if (threadIdx.x == 0) {
     st->counter[1] = 0;
-    if (F) st->par = par ^ 1;
+    if (F) st->par = (par + 1) & (kDirs - 1);
     if (!(pq > 0.0) || !isfinite(pq)) {
       st->done = 3;
       st->status = isfinite(pq) ? PHFEM_EBREAKDOWN : PHFEM_ENAN;
@@ -418,35 +490,37 @@ __global__ void __launch_bounds__(kBlock) k_fcg_spmv(int n, const short4* __rest
   }
 }
 
-// One row of the update: u -= alpha D^-1 q and its r.z term; y takes
-// alpha_prev p_prev (two == true) and alpha p when with_y.
-__device__ __forceinline__ void update_row(float2& y, float pe, float pp, float qe, float d, float& ue, float ah,
-                                           float al, float aph, float apl, bool with_y, bool two, float& acc) {
-  if (with_y) {
-    if (two) y = y_add(y, aph, apl, pp);
-    y = y_add(y, ah, al, pe);
-  }
+// One row of the update: u -= alpha D^-1 q and its r.z term.
+__device__ __forceinline__ void update_u(float qe, float d, float& ue, float ah, float& acc) {
   ue = fmadd(-ah, d * qe, ue);
   acc += d > 0.f ? __fdividef(ue * ue, d) : 0.f;
+}
+__device__ __forceinline__ void update_u4(const float4& qv, const float4& dv, float4& uv, float ah, float& acc) {
+  update_u(qv.x, dv.x, uv.x, ah, acc);
+  update_u(qv.y, dv.y, uv.y, ah, acc);
+  update_u(qv.z, dv.z, uv.z, ah, acc);
+  update_u(qv.w, dv.w, uv.w, ah, acc);
 }
 
 // u -= alpha D^-1 q, r.z = u.u / D^-1 (FP32) or u.u D (FP64, with the stored
 // diagonal: no FP64 division) -> beta, and the solution correction y.
-// Fused FP32: p of the previous iteration is still in the other direction
-// buffer, so y takes alpha_prev p_prev + alpha p every second iteration (and
-// the other iterations leave alpha p pending, which the fold and the end of
-// the solve add); then the test of the recursive residual (done = 1 asks for
-// a reliable update).  Unfused: y += alpha p every iteration, and the
-// direction kernel follows and tests the residual.  FP32 rows go four at a
-// time through 16-byte loads and stores.
+// Fused FP32: the directions of the last kDirs iterations are still in their
+// buffers, so every kDirs-th iteration y takes their kDirs terms alpha p at
+// once, oldest first (the other iterations leave alpha p pending, which the
+// fold and the end of the solve add); then the test of the recursive residual
+// (done = 1 asks for a reliable update).  Unfused: y += alpha p every
+// iteration, and the direction kernel follows and tests the residual.  FP32
+// rows go four at a time through 16-byte loads and stores: two groups of four
+// per thread and pass (all loads issued before the first store) when y is not
+// touched, one group with its directions and y when it is.
 template <typename T, bool F>
-__global__ void __launch_bounds__(kBlock) k_fcg_update(int n, const T* p0, const T* p1, const T* __restrict__ q,
+__global__ void __launch_bounds__(kBlock) k_fcg_update(int n, Dirs<const T> dirs, const T* __restrict__ q,
                                                        const T* __restrict__ di, const T* __restrict__ dg,
                                                        T* __restrict__ u, typename Inner<T>::Y* __restrict__ y,
                                                        double* partials, SolveState* st) {
   pdl_enter();
   if (st->done) return;
-  const T* __restrict__ p = (F && st->par) ? p1 : p0;  // the direction of this iteration
+  const int par = F ? st->par & (kDirs - 1) : 0;
   const double a64 = st->alpha;
   const T ah = (T)a64;
   const T al = (T)(a64 - (double)ah);
@@ -454,68 +528,85 @@ __global__ void __launch_bounds__(kBlock) k_fcg_update(int n, const T* p0, const
   __shared__ double smem[kBlock / 32];
   T acc = (T)0;
   if constexpr (sizeof(T) == sizeof(float)) {
-    const bool with_y = !F || pend, two = F && pend;
-    const float* __restrict__ pprev = (F && st->par) ? p0 : p1;  // fused: the previous iteration's direction
-    const double ap64 = st->alpha_prev;
-    const float aph = (float)ap64, apl = (float)(ap64 - (double)aph);
+    constexpr int NT = F ? kDirs : 1;  // terms added to y when it is touched
+    const bool with_y = !F || pend == kDirs - 1;
     const int n4 = n / 4;
-    const float4* __restrict__ p4 = reinterpret_cast<const float4*>(p);
-    const float4* __restrict__ pp4 = reinterpret_cast<const float4*>(pprev);
+    const int stride = gridDim.x * blockDim.x;
     const float4* __restrict__ q4 = reinterpret_cast<const float4*>(q);
     const float4* __restrict__ d4 = reinterpret_cast<const float4*>(di);
     float4* __restrict__ u4 = reinterpret_cast<float4*>(u);
-    float4* __restrict__ y4 = reinterpret_cast<float4*>(y);  // two rows' pairs per float4
-    // two groups of four rows per thread and pass: all loads are issued before
-    // the first store
-    const int stride = gridDim.x * blockDim.x;
-    const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int j0 = blockIdx.x * blockDim.x + threadIdx.x; j0 < n4; j0 += 2 * stride) {
-      float4 pv[2], ppv[2], qv[2], dv[2], uv[2], ya[2], yb[2];
-      bool ok[2];
+    // term t: the direction in buffer par + 1 + t (fused: oldest first, the
+    // last one this iteration's), its alpha as a pair of floats
+    const float* pt[NT];
+    float th[NT], tl[NT];
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int j = j0 + h * stride;
-        ok[h] = j < n4;
-        pv[h] = ppv[h] = ya[h] = yb[h] = z4;
-        if (ok[h]) {
-          qv[h] = q4[j];
-          dv[h] = d4[j];
-          uv[h] = u4[j];
-          if (with_y) {
-            pv[h] = p4[j];
-            ya[h] = y4[2 * j];
-            yb[h] = y4[2 * j + 1];
-            if (two) ppv[h] = pp4[j];
+    for (int t = 0; t < NT; ++t) {
+      const int k = F ? (par + 1 + t) & (kDirs - 1) : 0;
+      pt[t] = dirs.b(k);
+      const double at = t < NT - 1 ? st->alpha_dir[k] : a64;
+      th[t] = (float)at;
+      tl[t] = (float)(at - (double)th[t]);
+    }
+    if (!with_y) {
+      for (int j0 = blockIdx.x * blockDim.x + threadIdx.x; j0 < n4; j0 += 2 * stride) {
+        float4 qv[2], dv[2], uv[2];
+        bool ok[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int j = j0 + h * stride;
+          ok[h] = j < n4;
+          if (ok[h]) {
+            qv[h] = q4[j];
+            dv[h] = d4[j];
+            uv[h] = u4[j];
           }
         }
-      }
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        if (!ok[h]) continue;
-        const int j = j0 + h * stride;
-        float2 y0 = make_float2(ya[h].x, ya[h].y), y1 = make_float2(ya[h].z, ya[h].w);
-        float2 y2 = make_float2(yb[h].x, yb[h].y), y3 = make_float2(yb[h].z, yb[h].w);
-        update_row(y0, pv[h].x, ppv[h].x, qv[h].x, dv[h].x, uv[h].x, ah, al, aph, apl, with_y, two, acc);
-        update_row(y1, pv[h].y, ppv[h].y, qv[h].y, dv[h].y, uv[h].y, ah, al, aph, apl, with_y, two, acc);
-        update_row(y2, pv[h].z, ppv[h].z, qv[h].z, dv[h].z, uv[h].z, ah, al, aph, apl, with_y, two, acc);
-        update_row(y3, pv[h].w, ppv[h].w, qv[h].w, dv[h].w, uv[h].w, ah, al, aph, apl, with_y, two, acc);
-        u4[j] = uv[h];
-        if (with_y) {
-          y4[2 * j] = make_float4(y0.x, y0.y, y1.x, y1.y);
-          y4[2 * j + 1] = make_float4(y2.x, y2.y, y3.x, y3.y);
+        for (int h = 0; h < 2; ++h) {
+          if (!ok[h]) continue;
+          update_u4(qv[h], dv[h], uv[h], ah, acc);
+          u4[j0 + h * stride] = uv[h];
         }
+      }
+    } else {
+      float4* __restrict__ y4 = reinterpret_cast<float4*>(y);  // two rows' pairs per float4
+      for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n4; j += stride) {
+        float4 pv[NT];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) pv[t] = reinterpret_cast<const float4*>(pt[t])[j];
+        const float4 qv = q4[j], dv = d4[j];
+        float4 uv = u4[j];
+        const float4 ya = y4[2 * j], yb = y4[2 * j + 1];
+        float2 y0 = make_float2(ya.x, ya.y), y1 = make_float2(ya.z, ya.w);
+        float2 y2 = make_float2(yb.x, yb.y), y3 = make_float2(yb.z, yb.w);
+#pragma unroll
+        for (int t = 0; t < NT; ++t) {
+          y0 = y_add(y0, th[t], tl[t], pv[t].x);
+          y1 = y_add(y1, th[t], tl[t], pv[t].y);
+          y2 = y_add(y2, th[t], tl[t], pv[t].z);
+          y3 = y_add(y3, th[t], tl[t], pv[t].w);
+        }
+        update_u4(qv, dv, uv, ah, acc);
+        u4[j] = uv;
+        y4[2 * j] = make_float4(y0.x, y0.y, y1.x, y1.y);
+        y4[2 * j + 1] = make_float4(y2.x, y2.y, y3.x, y3.y);
       }
     }
     // the last n % 4 rows
     const int i = 4 * n4 + blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
+      if (with_y) {
+        float2 yi = y[i];
+#pragma unroll
+        for (int t = 0; t < NT; ++t) yi = y_add(yi, th[t], tl[t], pt[t][i]);
+        y[i] = yi;
+      }
       float ue = u[i];
-      float2 yi = with_y ? y[i] : make_float2(0.f, 0.f);
-      update_row(yi, with_y ? p[i] : 0.f, two ? pprev[i] : 0.f, q[i], di[i], ue, ah, al, aph, apl, with_y, two, acc);
+      update_u(q[i], di[i], ue, ah, acc);
       u[i] = ue;
-      if (with_y) y[i] = yi;
     }
   } else {
+    const T* __restrict__ p = dirs.b(0);
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
       y[i] = y_add(y[i], ah, al, p[i]);
       const T d = di[i];
@@ -533,9 +624,9 @@ __global__ void __launch_bounds__(kBlock) k_fcg_update(int n, const T* p0, const
     st->beta = st->rz > 0.0 ? rz / st->rz : 0.0;
     st->rz = rz;
     st->it += 1;
-    if (F) {  // alpha p of this iteration is added to y with the next one's
-      st->ypend = pend ? 0 : 1;
-      st->alpha_prev = a64;
+    if (F) {  // alpha p of this iteration stays pending unless y took it
+      st->alpha_dir[par] = a64;
+      st->ypend = pend == kDirs - 1 ? 0 : pend + 1;
     }
     if (!isfinite(rz)) {
       st->done = 3;
@@ -586,41 +677,49 @@ struct FLaunch {
   int epilogue() const {
     phfem_ctx ctx = sys->mesh->ctx;
     k_fcg_out<Y, T><<<g, kBlock, 0, s>>>(n, sys->mesh->perm, f()->xh, f()->xl, (const Y*)f()->y,
-                                         (const T*)f()->p0(), (const T*)f()->p1(), sys->st, sys->x);
+                                         f()->template dirs<const T>(), sys->st, sys->x);
     return check_launch(ctx, "k_fcg_out");
   }
   int residual(int mode) const {
     phfem_ctx ctx = sys->mesh->ctx;
     phfem_mesh m = sys->mesh;
     if (mode >= 2) {
-      k_fcg_fold<Y, T><<<g, kBlock, 0, s>>>(n, f()->xh, f()->xl, (Y*)f()->y, (const T*)f()->p0(),
-                                            (const T*)f()->p1(), sys->st, mode == 3);
+      k_fcg_fold<Y, T><<<g, kBlock, 0, s>>>(n, f()->xh, f()->xl, (Y*)f()->y, f()->template dirs<const T>(), sys->st,
+                                            mode == 3);
       PH_TRY(check_launch(ctx, "k_fcg_fold"));
     }
     prof_start(ctx, kProfResidual);
     k_fcg_residual<T, F><<<g, kBlock, 0, s>>>(n, m->nbr16, m->nbr_ovf, f()->val, f()->b, f()->xh, f()->xl,
                                            m->eclass_i, sys->ident_class, (const T*)f()->di, (const T*)f()->dg,
-                                           (T*)f()->u(), (T*)f()->p0(), (T*)f()->p1(), sys->partials, sys->st,
+                                           (T*)f()->u(), f()->template dirs<T>(), sys->partials, sys->st,
                                            rtol2, irtol2, mode);
     prof_stop(ctx, kProfResidual);
     return check_launch(ctx, "k_fcg_residual");
+  }
+  int wave(int per) const {
+    phfem_ctx ctx = sys->mesh->ctx;
+    int64_t g = (int64_t)ctx->num_sms * per;
+    const int64_t need = (n + kBlock - 1) / kBlock;
+    if (g > kMaxGrid) g = kMaxGrid;
+    if (g > need) g = need;
+    return g < 1 ? 1 : (int)g;
   }
   int iteration() const {
     phfem_ctx ctx = sys->mesh->ctx;
     phfem_mesh m = sys->mesh;
     prof_start(ctx, kProfSpmv);
-    PH_CUDA(launch_pdl(k_fcg_spmv<T, F>, g, s, n, (const short4*)m->nbr16, (const int4*)m->nbr_ovf,
-                       (const L4*)f()->l4, (const T*)f()->rd, (const T*)f()->u(), (T*)f()->p0(), (T*)f()->p1(),
-                       (T*)f()->q(), sys->partials, sys->st));
+    PH_CUDA(launch_pdl(k_fcg_spmv<T, F>, wave(f()->per_spmv[F]), s, n, (const short4*)m->nbr16, (const int4*)m->nbr_ovf,
+                       (const L4*)f()->l4, (const T*)f()->rd, (const T*)f()->u(), f()->template dirs<T>(),
+                       (T*)f()->q(), sys->partials, sys->st, kPrefetchAhead));
     prof_stop(ctx, kProfSpmv);
     prof_start(ctx, kProfUpdate);
-    PH_CUDA(launch_pdl(k_fcg_update<T, F>, g, s, n, (const T*)f()->p0(), (const T*)f()->p1(), (const T*)f()->q(),
+    PH_CUDA(launch_pdl(k_fcg_update<T, F>, wave(f()->per_update[F]), s, n, f()->template dirs<const T>(), (const T*)f()->q(),
                        (const T*)f()->di, (const T*)f()->dg, (T*)f()->u(), (Y*)f()->y, sys->partials, sys->st));
     prof_stop(ctx, kProfUpdate);
     ctx->launches += 1;
     if (!F) {
       prof_start(ctx, kProfDir);
-      PH_CUDA(launch_pdl(k_fcg_dir<T>, g, s, n, (const T*)f()->u(), (T*)f()->p0(), sys->st));
+      PH_CUDA(launch_pdl(k_fcg_dir<T>, wave(f()->per_dir), s, n, (const T*)f()->u(), (T*)f()->pk(0), sys->st));
       prof_stop(ctx, kProfDir);
       ctx->launches += 1;
     }
@@ -757,6 +856,16 @@ bool fcg_eligible(phfem_sys sys, const phfem_solve_opts& o) {
   return o.order == 0 && sys->form == PHFEM_FORM_TRACE && !sys->conv && !sys->mg;
 }
 
+template <typename K>
+static int resident_blocks(K kernel) {
+  int per = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, kBlock, 0) != cudaSuccess || per < 1) {
+    (void)cudaGetLastError();
+    per = 1;
+  }
+  return per;
+}
+
 int fcg_prepare(phfem_sys sys) {
   if (sys->fcg) return PHFEM_OK;
   phfem_mesh m = sys->mesh;
@@ -781,8 +890,19 @@ int fcg_prepare(phfem_sys sys) {
   chk(dalloc_n(ctx, &f->xh, (size_t)n));
   chk(dalloc_n(ctx, &f->xl, (size_t)n));
   chk(dalloc(ctx, &f->y, (size_t)n * 8 + 16));
-  chk(dalloc(ctx, &f->vec, 4 * f->slot + 16));
+  chk(dalloc(ctx, &f->vec, (2 + kDirs) * f->slot + 16));
   sys->fcg = f;
+  if (sys->fp32) {
+    f->per_spmv[0] = resident_blocks(k_fcg_spmv<float, false>);
+    f->per_spmv[1] = resident_blocks(k_fcg_spmv<float, true>);
+    f->per_update[0] = resident_blocks(k_fcg_update<float, false>);
+    f->per_update[1] = resident_blocks(k_fcg_update<float, true>);
+    f->per_dir = resident_blocks(k_fcg_dir<float>);
+  } else {
+    f->per_spmv[0] = resident_blocks(k_fcg_spmv<double, false>);
+    f->per_update[0] = resident_blocks(k_fcg_update<double, false>);
+    f->per_dir = resident_blocks(k_fcg_dir<double>);
+  }
   if (st == PHFEM_OK) {
     const int g = grid_for(ctx, n);
     if (sys->fp32)

@@ -63,9 +63,9 @@ struct SolveState {
   int status;      // phfem_status of a failure
   int dir_pending; // set by the update kernel, cleared by the next SpMV: gates the direction kernel
   unsigned int counter[4];  // last-block counters of the reductions
-  int par;         // locality-order CG: which of its two direction buffers holds the current p
-  int ypend;       // fused FP32 locality-order CG: alpha_prev p (in p[par]) not yet added to y
-  double alpha_prev;
+  int par;         // locality-order CG: which of its direction buffers holds the current p
+  int ypend;       // fused FP32 locality-order CG: the newest ypend directions' alpha p not yet in y
+  double alpha_dir[4];  // locality-order CG: alpha of the direction held in each buffer
   double sc;       // locality-order CG: power-of-two scale of the inner vectors since the last true residual
 };
 

@@ -74,6 +74,18 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, cudaStream_t s, Args.
 // of the residual's evaluation), and for a reliable update the line-search
 // step along the kept direction or a restart of the direction.
 // mode 1 = start, 2 = reliable update.
+// The value of the recursive r.z at which the next reliable update is taken:
+// a fall by the update factor, or, when that comes sooner, the point where
+// the true residual is predicted to meet the tolerance, r.r being taken to
+// fall in proportion to r.z from the true residual just evaluated, aiming at
+// 0.8 of the tolerance in the squares.  Without the second bound a solve whose
+// true residual lands just above the tolerance iterates a further update
+// factor; a prediction that falls short costs one more reliable update.
+__device__ __forceinline__ double update_target(double rz, double rr, double bb, double rtol2, double inner_rtol2) {
+  const double reach = rr > 0.0 ? 0.8 * rtol2 * bb / rr : 0.0;
+  return rz * fmax(inner_rtol2, fmin(reach, 1.0));
+}
+
 __device__ inline void decide(SolveState* st, double rr, double rz, double ff, double rp, int mode, double rtol2,
                               double inner_rtol2) {
   const double rz_recursive = st->rz;
@@ -81,7 +93,7 @@ __device__ inline void decide(SolveState* st, double rr, double rz, double ff, d
   st->floor2 = ff;
   st->rz = rz;
   st->rp = rp;
-  st->tol2 = inner_rtol2 * rz;
+  st->tol2 = update_target(rz, rr, st->bb, rtol2, inner_rtol2);
   st->status = 0;
   if (mode == 1) {
     st->rz0 = rz;
