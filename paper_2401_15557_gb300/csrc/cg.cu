@@ -80,15 +80,15 @@ struct FastCG {
   double* xh = nullptr;   // [n] solution, leading part
   double* xl = nullptr;   // [n] solution, trailing part
   void* y = nullptr;      // [n] Inner<T>::Y correction since the last reliable update
-  void* vec = nullptr;    // u, the kDirs direction buffers, q: slots of `slot` bytes
+  void* vec = nullptr;    // u, q, the kDirs direction buffers: slots of `slot` bytes (256-aligned)
   size_t slot = 0;
   // resident blocks per SM of the iteration kernels, [F] (fused or not): the
   // grids are one wave of resident blocks, so no kernel runs a partial last
   // wave (the FP32 update kernel holds 3 blocks per SM, the product kernel 8)
   int per_spmv[2] = {1, 1}, per_update[2] = {1, 1}, per_dir = 1;
   void* u() const { return vec; }
-  void* pk(int k) const { return (char*)vec + (1 + k) * slot; }
-  void* q() const { return (char*)vec + (1 + kDirs) * slot; }
+  void* q() const { return (char*)vec + slot; }
+  void* pk(int k) const { return (char*)vec + (2 + k) * slot; }
   template <typename T>
   Dirs<T> dirs() const {
     return Dirs<T>{(T*)pk(0), slot / sizeof(T)};
@@ -483,7 +483,10 @@ __global__ void __launch_bounds__(kBlock) k_fcg_spmv(int n, const short4* __rest
       st->done = 3;
       st->status = isfinite(pq) ? PHFEM_EBREAKDOWN : PHFEM_ENAN;
     } else {
-      st->alpha = (st->use_rp ? st->rp : st->rz) / pq;
+      const double a = (st->use_rp ? st->rp : st->rz) / pq;
+      st->alpha = a;
+      st->alpha_f[0] = (float)a;  // the pair the FP32 update kernel uses (no FP64 work per thread there)
+      st->alpha_f[1] = (float)(a - (double)(float)a);
       st->use_rp = 0;
       st->restart = 0;
     }
@@ -522,8 +525,14 @@ __global__ void __launch_bounds__(kBlock) k_fcg_update(int n, Dirs<const T> dirs
   if (st->done) return;
   const int par = F ? st->par & (kDirs - 1) : 0;
   const double a64 = st->alpha;
-  const T ah = (T)a64;
-  const T al = (T)(a64 - (double)ah);
+  T ah, al;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    ah = st->alpha_f[0];
+    al = st->alpha_f[1];
+  } else {
+    ah = a64;
+    al = 0.0;
+  }
   const int pend = F ? st->ypend : 0;
   __shared__ double smem[kBlock / 32];
   T acc = (T)0;
@@ -543,9 +552,8 @@ __global__ void __launch_bounds__(kBlock) k_fcg_update(int n, Dirs<const T> dirs
     for (int t = 0; t < NT; ++t) {
       const int k = F ? (par + 1 + t) & (kDirs - 1) : 0;
       pt[t] = dirs.b(k);
-      const double at = t < NT - 1 ? st->alpha_dir[k] : a64;
-      th[t] = (float)at;
-      tl[t] = (float)(at - (double)th[t]);
+      th[t] = t < NT - 1 ? st->alpha_dir_f[k][0] : ah;
+      tl[t] = t < NT - 1 ? st->alpha_dir_f[k][1] : al;
     }
     if (!with_y) {
       for (int j0 = blockIdx.x * blockDim.x + threadIdx.x; j0 < n4; j0 += 2 * stride) {
@@ -626,6 +634,8 @@ __global__ void __launch_bounds__(kBlock) k_fcg_update(int n, Dirs<const T> dirs
     st->it += 1;
     if (F) {  // alpha p of this iteration stays pending unless y took it
       st->alpha_dir[par] = a64;
+      st->alpha_dir_f[par][0] = (float)ah;
+      st->alpha_dir_f[par][1] = (float)al;
       st->ypend = pend == kDirs - 1 ? 0 : pend + 1;
     }
     if (!isfinite(rz)) {
@@ -659,6 +669,32 @@ __global__ void k_fcg_loop_control(SolveState* st, cudaGraphConditionalHandle ha
   cudaGraphSetConditional(handle, more ? 1u : 0u);
 }
 
+// The L2 window of the iteration: u, written by the update kernel and read
+// (at every row and gathered at its neighbours) by the next product kernel,
+// and read and written again by the next update, stays in L2 with the
+// set-aside sized to it; the streamed operator, q, the directions and y pass
+// through the rest of L2.  Measured at level 5 (FP32, us per iteration): no
+// window 122.2, u 114.9, q 119.2, u and q 124.2 (a 75 MB set-aside leaves too
+// little L2 for the gathers and the prefetched tiles).  Only when u fits the
+// largest set-aside; while a graph is captured (capturing) the set-aside,
+// which is device-wide, is not changed: the window is used only if the
+// set-aside already has its size.
+L2Window u_window(phfem_sys sys, bool capturing) {
+  phfem_ctx ctx = sys->mesh->ctx;
+  const FastCG* f = sys->fcg;
+  L2Window w;
+  const size_t want = f->slot;
+  if (!ctx->l2_window || want > ctx->l2_persist_max || want > ctx->l2_window_max) {
+    if (ctx->l2_window && !capturing) set_l2_limit(ctx, 0);
+    return w;
+  }
+  if (capturing ? ctx->l2_limit != want : !set_l2_limit(ctx, want)) return w;
+  w.base = f->u();
+  w.bytes = want;
+  w.hit_ratio = 1.0f;
+  return w;
+}
+
 template <typename T, bool F>
 struct FLaunch {
   using L4 = typename Inner<T>::L4;
@@ -667,6 +703,7 @@ struct FLaunch {
   cudaStream_t s;
   int g, n;
   double rtol2, irtol2;
+  L2Window win;
   const FastCG* f() const { return sys->fcg; }
   int prologue() const {
     phfem_ctx ctx = sys->mesh->ctx;
@@ -708,18 +745,18 @@ struct FLaunch {
     phfem_ctx ctx = sys->mesh->ctx;
     phfem_mesh m = sys->mesh;
     prof_start(ctx, kProfSpmv);
-    PH_CUDA(launch_pdl(k_fcg_spmv<T, F>, wave(f()->per_spmv[F]), s, n, (const short4*)m->nbr16, (const int4*)m->nbr_ovf,
+    PH_CUDA(launch_pdl_w(win, k_fcg_spmv<T, F>, wave(f()->per_spmv[F]), s, n, (const short4*)m->nbr16, (const int4*)m->nbr_ovf,
                        (const L4*)f()->l4, (const T*)f()->rd, (const T*)f()->u(), f()->template dirs<T>(),
                        (T*)f()->q(), sys->partials, sys->st, kPrefetchAhead));
     prof_stop(ctx, kProfSpmv);
     prof_start(ctx, kProfUpdate);
-    PH_CUDA(launch_pdl(k_fcg_update<T, F>, wave(f()->per_update[F]), s, n, f()->template dirs<const T>(), (const T*)f()->q(),
+    PH_CUDA(launch_pdl_w(win, k_fcg_update<T, F>, wave(f()->per_update[F]), s, n, f()->template dirs<const T>(), (const T*)f()->q(),
                        (const T*)f()->di, (const T*)f()->dg, (T*)f()->u(), (Y*)f()->y, sys->partials, sys->st));
     prof_stop(ctx, kProfUpdate);
     ctx->launches += 1;
     if (!F) {
       prof_start(ctx, kProfDir);
-      PH_CUDA(launch_pdl(k_fcg_dir<T>, wave(f()->per_dir), s, n, (const T*)f()->u(), (T*)f()->pk(0), sys->st));
+      PH_CUDA(launch_pdl_w(win, k_fcg_dir<T>, wave(f()->per_dir), s, n, (const T*)f()->u(), (T*)f()->pk(0), sys->st));
       prof_stop(ctx, kProfDir);
       ctx->launches += 1;
     }
@@ -738,7 +775,8 @@ template <typename T, bool F>
 int fcg_solve_typed(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats) {
   phfem_ctx ctx = sys->mesh->ctx;
   const int n = sys->mesh->info.nE;
-  const FLaunch<T, F> L{sys, ctx->stream, grid_for(ctx, n), n, o.rtol * o.rtol, o.inner_rtol * o.inner_rtol};
+  const FLaunch<T, F> L{sys, ctx->stream, grid_for(ctx, n), n, o.rtol * o.rtol, o.inner_rtol * o.inner_rtol,
+                        u_window(sys, false)};
   static const bool verbose = getenv("PHFEM_VERBOSE") != nullptr;
   PH_TRY(L.prologue());
   PH_TRY(L.residual(0));
@@ -777,6 +815,11 @@ int fcg_solve_typed(phfem_sys sys, const phfem_solve_opts& o, phfem_stats* stats
     PH_TRY(read_state(sys));
   }
   PH_TRY(L.epilogue());
+  if (L.win.bytes > 0) {  // the window's lines and the set-aside go back to normal L2 use
+    cudaCtxResetPersistingL2Cache();
+    cudaGetLastError();
+    set_l2_limit(ctx, 0);
+  }
   const SolveState& h = *sys->st_host;
   const double rel = h.bb > 0 ? std::sqrt(h.rr64 / h.bb) : 0.0;
   if (stats) {
@@ -802,7 +845,8 @@ template <typename T, bool F>
 int fcg_capture_typed(phfem_sys sys, const phfem_solve_opts& o, cudaStream_t cs, int per_body) {
   phfem_ctx ctx = sys->mesh->ctx;
   const int n = sys->mesh->info.nE;
-  const FLaunch<T, F> L{sys, cs, grid_for(ctx, n), n, o.rtol * o.rtol, o.inner_rtol * o.inner_rtol};
+  const FLaunch<T, F> L{sys, cs, grid_for(ctx, n), n, o.rtol * o.rtol, o.inner_rtol * o.inner_rtol,
+                        u_window(sys, true)};
   PH_TRY(L.prologue());
   PH_TRY(L.residual(0));
   PH_TRY(L.residual(1));
@@ -829,7 +873,7 @@ int fcg_capture_typed(phfem_sys sys, const phfem_solve_opts& o, cudaStream_t cs,
   cudaError_t e = cudaStreamBeginCaptureToGraph(bs, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) st = cuda_fail(e, "cudaStreamBeginCaptureToGraph", __FILE__, __LINE__);
   if (st == PHFEM_OK) {
-    const FLaunch<T, F> B{sys, bs, L.g, n, L.rtol2, L.irtol2};
+    const FLaunch<T, F> B{sys, bs, L.g, n, L.rtol2, L.irtol2, L.win};
     for (int k = 0; k < per_body && st == PHFEM_OK; ++k) st = B.iteration();
     if (st == PHFEM_OK) st = B.residual(3);
     if (st == PHFEM_OK) {

@@ -67,6 +67,8 @@ struct SolveState {
   int ypend;       // fused FP32 locality-order CG: the newest ypend directions' alpha p not yet in y
   double alpha_dir[4];  // locality-order CG: alpha of the direction held in each buffer
   double sc;       // locality-order CG: power-of-two scale of the inner vectors since the last true residual
+  float alpha_f[2];          // alpha as an unevaluated pair of floats (set with alpha)
+  float alpha_dir_f[4][2];   // alpha_dir likewise
 };
 
 }  // namespace phfem
@@ -187,6 +189,9 @@ int dalloc_n(phfem_ctx ctx, T** p, size_t n) {
 }
 
 int grid_for(phfem_ctx ctx, int64_t n);
+// Sets the device's persisting L2 set-aside (0 releases it); false under a
+// stream capture (unless already that size) or when the call fails.
+bool set_l2_limit(phfem_ctx ctx, size_t bytes);
 // Event pair around one launch of kernel k when profiling is on (no-op otherwise).
 void prof_start(phfem_ctx ctx, int k);
 void prof_stop(phfem_ctx ctx, int k);

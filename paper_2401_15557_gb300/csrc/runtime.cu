@@ -46,6 +46,21 @@ void dfree(phfem_ctx ctx, void* p) {
   else cudaFreeAsync(p, ctx->stream);
 }
 
+bool set_l2_limit(phfem_ctx ctx, size_t bytes) {
+  if (ctx->l2_limit == bytes) return true;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return false;
+  }
+  if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  ctx->l2_limit = bytes;
+  return true;
+}
+
 int grid_for(phfem_ctx ctx, int64_t n) {
   int64_t need = (n + kBlock - 1) / kBlock;
   if (need < 1) need = 1;

@@ -663,22 +663,6 @@ int read_state(phfem_sys sys) {
 // when both fit the largest set-aside: measured on the level-5 system, a window
 // that covers more than the set-aside (r, p and q with a 0.75 hit ratio), or a
 // set-aside larger than its window (r alone), is slower than no window at all.
-// Sets the device's persisting set-aside (0 releases it); not under a capture.
-bool set_l2_limit(phfem_ctx ctx, size_t bytes) {
-  if (ctx->l2_limit == bytes) return true;
-  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(ctx->stream, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
-    cudaGetLastError();
-    return false;
-  }
-  if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    return false;
-  }
-  ctx->l2_limit = bytes;
-  return true;
-}
-
 L2Window rp_window(phfem_sys sys) {
   phfem_ctx ctx = sys->mesh->ctx;
   L2Window w;
