@@ -90,8 +90,8 @@ def hbm_peak():
 # kernel with CUDA events (an event between two launches keeps the second from
 # overlapping the first's drain, so timing every launch would slow the step).
 PROFILE_EVERY = 17  # odd: the update kernel alternates a light and a heavy launch (y every second iteration)
-SPMV_TRAFFIC = 402.4e6
-SPMV_TRAFFIC_SRC_SHA = "694a49c147611b7c"
+SPMV_TRAFFIC = 404.4e6
+SPMV_TRAFFIC_SRC_SHA = "1fb4fca7b75481d9"
 
 
 def _function_src(path, signature):
