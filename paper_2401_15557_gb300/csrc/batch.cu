@@ -4,8 +4,10 @@
 // Each thread block takes the next mesh from a device work queue (meshes in
 // decreasing size, so the largest start first) and runs the whole path for it:
 // the triangle pass (condensed element blocks), the edge-row pass (difference
-// form, FP64 and inner precision), Jacobi-PCG with FP64 accumulation of the
-// solution and reliable updates, and the recovery of U and Lambda.  Block-wide
+// form, FP64 and inner precision), Jacobi-PCG with reliable updates (FP32
+// systems: the direction update folded into the product and the solution
+// correction accumulated as a float pair; FP64 systems: three loops and the
+// solution accumulated in FP64), and the recovery of U and Lambda.  Block-wide
 // barriers replace the kernel boundaries of the single-mesh path, and dot
 // products are block reductions (FP64 across threads), so one launch solves
 // the whole batch.  The per-element and per-row arithmetic is the same code as
@@ -61,9 +63,26 @@ __device__ __forceinline__ void msync() {
 }
 
 // Sum of v over the mesh's threads, the same value in every thread: warp sums,
-// then the block total in fixed order; with a cluster, each CTA publishes its
+// then the block total by a butterfly over the warp totals; with a cluster, each CTA publishes its
 // total in slot `slot` (alternating between consecutive reductions, so one
 // barrier suffices) and every thread adds the C totals in rank order.
+// Sum over the 32 lanes by a butterfly: every lane computes the same pairwise
+// sums (a + b and b + a are the same IEEE result), so all lanes, and all
+// warps given the same inputs, get the same value.
+__device__ __forceinline__ double warp_allsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// num / den computed once per warp and broadcast: an FP64 division in every
+// thread would hold GB300's FP64 pipe (num and den are uniform over the block).
+__device__ __forceinline__ double warp_div(double num, double den) {
+  double q = 0.0;
+  if ((threadIdx.x & 31) == 0) q = num / den;
+  return __shfl_sync(0xffffffffu, q, 0);
+}
+
 template <int BS, int C>
 __device__ __forceinline__ double bsum(double v, double* smem, double* cl_part, int& slot) {
   v = warp_sum(v);
@@ -71,8 +90,8 @@ __device__ __forceinline__ double bsum(double v, double* smem, double* cl_part, 
   __syncthreads();  // smem may still be read by the previous reduction
   if (lane == 0) smem[w] = v;
   __syncthreads();
-  double t = 0.0;
-  for (int i = 0; i < BS / 32; ++i) t += smem[i];  // every thread, same order
+  // every warp sums the BS / 32 warp totals by the same butterfly
+  double t = warp_allsum(lane < BS / 32 ? smem[lane] : 0.0);
   if constexpr (C == 1) {
     return t;
   } else {
@@ -109,8 +128,10 @@ struct BatchArrays {
   T* rdiag;
   T* dinv;
   double* x;
+  float2* y;             // [sum nE] FP32 systems: correction since the last reliable update (a float pair)
   T* r;
   T* p;
+  T* p2;                 // FP32 systems: the second direction buffer of the fused iteration
   T* q;
   double* U;             // [3 sum nT] or NULL
   double* Lambda;        // [sum nL] or NULL
@@ -159,9 +180,20 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
     T* rdiag = A.rdiag + D.e0;
     T* dinv = A.dinv + D.e0;
     double* x = A.x + D.e0;
+    float2* y = A.y + D.e0;
+    // FP32 systems: the solution correction as a float pair, and the fused
+    // iteration (r holds u = D^-1 r; the direction update is folded into the
+    // product, which forms p at each row and its neighbours from u and the
+    // previous p in the other buffer: two loops and two barriers per
+    // iteration instead of three).  FP64 systems keep the three loops: GB300's
+    // FP64 rate makes the four extra FP64 operations per row cost more.
+    constexpr bool kPair = sizeof(T) == sizeof(float);
+    constexpr bool kFused = kPair;
     T* r = A.r + D.e0;
     T* p = A.p + D.e0;
     T* q = A.q + D.e0;
+    T* po = p;               // fused: the previous direction
+    T* pn = A.p2 + D.e0;     // fused: the direction being formed (the two swap every iteration)
     const double delta = A.delta[id];
     const double* f = A.f_mid ? A.f_mid + D.e0 : nullptr;
     const double* bc = A.bc_mid ? A.bc_mid + D.e0 : nullptr;
@@ -194,6 +226,7 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
       rdiag[e] = (T)R.rpart;
       dinv[e] = (T)(1.0 / R.diag);
       x[e] = (cls == PHFEM_EDGE_DIRICHLET) ? R.rhs : 0.0;
+      if constexpr (kPair) y[e] = make_float2(0.f, 0.f);
     }
     msync<C>();
     // ||b_free|| with the Dirichlet lifting (x is (0, u_D) now)
@@ -212,7 +245,19 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
     int it = 0, updates = 0, converged = 0, status = 0, stagnant = 0, where = 0;
     double rel = 0.0, floor_rel = 0.0, best = 1e300, rz = 0.0, tol2 = 0.0, dpq = 0.0, dal = 0.0, drzt = 0.0;
     bool first = true;
+    int mode = 1;      // fused: 1 restart (p = u), 2 keep the direction (p = p_old), 0 p = u + beta p_old
+    T beta_f = (T)0;   // fused: the last beta
     for (;;) {
+      if constexpr (kPair) {  // the correction into x before x is read at the neighbours
+        if (!first) {
+          for (int e = tid0; e < nE; e += STR) {
+            const float2 v = y[e];
+            x[e] += (double)v.x + (double)v.y;
+            y[e] = make_float2(0.f, 0.f);
+          }
+          msync<C>();
+        }
+      }
       // true residual (FP64, difference form), inner residual replaced
       double a_r = 0.0, a_z = 0.0, a_f = 0.0, a_p = 0.0;
       for (int e = tid0; e < nE; e += STR) {
@@ -223,9 +268,20 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
         a_f += fl * fl;
         const T rs = (T)rr;
         const T zs = dinv[e] * rs;
-        r[e] = rs;
-        if (first) p[e] = zs;
-        else a_p += (double)rs * (double)p[e];
+        if constexpr (kFused) {
+          // the kept direction is the one the next iteration would take,
+          // p = u + beta p_old from the recursive u, formed before u is replaced
+          if (!first) {
+            const T pk = fmaf(beta_f, po[e], r[e]);
+            po[e] = pk;
+            a_p += (double)rs * (double)pk;
+          }
+          r[e] = zs;
+        } else {
+          r[e] = rs;
+          if (first) p[e] = zs;
+          else a_p += (double)rs * (double)p[e];
+        }
         a_z += (double)rs * (double)zs;
       }
       const double rr64 = bsum<BS, C>(a_r, smem, cl_part, slot);
@@ -259,9 +315,11 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
       // restart the direction if it no longer fits the replaced residual
       bool line_search = !first;
       if (!first && (rz_true > 4.0 * rz || !(rp > 0.0))) {
-        for (int e = tid0; e < nE; e += STR) p[e] = dinv[e] * r[e];
+        if constexpr (!kFused)
+          for (int e = tid0; e < nE; e += STR) p[e] = dinv[e] * r[e];
         line_search = false;
       }
+      mode = line_search ? 2 : 1;
       first = false;
       rz = rz_true;
       tol2 = rz * fmax(P.upd2, fmin(bb > 0.0 ? 0.8 * P.rtol2 * bb / rr64 : 0.0, 1.0));  // as update_target
@@ -269,10 +327,32 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
       // iterate until the recursive residual fell by the update factor
       while (it < P.max_iter) {
         T acc = (T)0;
-        for (int e = tid0; e < nE; e += STR) {
-          const T s = spmv_row<T, false>(nbr, lval, rdiag, p, m, e);
-          q[e] = s;
-          acc += p[e] * s;
+        if constexpr (kFused) {
+          const T bf = beta_f;
+          const int md = mode;
+          auto pval = [&](int i) -> T {
+            if (md == 1) return r[i];
+            if (md == 2) return po[i];
+            return fmaf(bf, po[i], r[i]);
+          };
+          for (int e = tid0; e < nE; e += STR) {
+            const int c0 = nbr[e], c1 = nbr[m + e], c2 = nbr[2 * m + e], c3 = nbr[3 * m + e];
+            const T pe = pval(e);
+            T sv = rdiag[e] * pe;
+            sv += lval[e] * (pe - pval(c0));
+            sv += lval[m + e] * (pe - pval(c1));
+            sv += lval[2 * m + e] * (pe - pval(c2));
+            sv += lval[3 * m + e] * (pe - pval(c3));
+            pn[e] = pe;
+            q[e] = sv;
+            acc += pe * sv;
+          }
+        } else {
+          for (int e = tid0; e < nE; e += STR) {
+            const T sv = spmv_row<T, false>(nbr, lval, rdiag, p, m, e);
+            q[e] = sv;
+            acc += p[e] * sv;
+          }
         }
         const double pq = bsum<BS, C>((double)acc, smem, cl_part, slot);
         dpq = pq;
@@ -281,23 +361,44 @@ __global__ void __launch_bounds__(BS) k_batch(int count, const MeshDesc* __restr
           where = 2;
           break;
         }
-        const double alpha64 = (line_search ? rp : rz) / pq;
+        const double alpha64 = warp_div(line_search ? rp : rz, pq);
         line_search = false;
+        mode = 0;
         dal = alpha64;
         const T alpha = (T)alpha64;
         T acc2 = (T)0;
-        for (int e = tid0; e < nE; e += STR) {
-          x[e] += alpha64 * (double)p[e];
-          const T re = r[e] - alpha * q[e];
-          r[e] = re;
-          acc2 += re * (dinv[e] * re);
+        if constexpr (kFused) {  // y += alpha p (float pair), u -= alpha D^-1 q, r.z = u.u / D^-1
+          const float al = (float)(alpha64 - (double)alpha);
+          for (int e = tid0; e < nE; e += STR) {
+            y[e] = y_add(y[e], alpha, al, pn[e]);
+            const T d = dinv[e];
+            const T ue = fmaf(-alpha, d * q[e], r[e]);
+            r[e] = ue;
+            acc2 += d > (T)0 ? __fdividef(ue * ue, d) : (T)0;
+          }
+        } else {
+          for (int e = tid0; e < nE; e += STR) {
+            x[e] += alpha64 * (double)p[e];
+            const T re = r[e] - alpha * q[e];
+            r[e] = re;
+            acc2 += re * (dinv[e] * re);
+          }
         }
         const double rzn = bsum<BS, C>((double)acc2, smem, cl_part, slot);
-        const T beta = (T)(rz > 0.0 ? rzn / rz : 0.0);
+        const T beta = (T)(rz > 0.0 ? warp_div(rzn, rz) : 0.0);
         rz = rzn;
         ++it;
-        for (int e = tid0; e < nE; e += STR) p[e] = dinv[e] * r[e] + beta * p[e];
-        msync<C>();
+        if constexpr (kFused) {
+          // the reductions' barriers ordered this iteration's writes of p and u
+          // before the next product reads them at the neighbours
+          beta_f = beta;
+          T* t = po;
+          po = pn;
+          pn = t;
+        } else {
+          for (int e = tid0; e < nE; e += STR) p[e] = dinv[e] * r[e] + beta * p[e];
+          msync<C>();
+        }
         if (!isfinite(rz)) {
           status = PHFEM_ENAN;
           where = 3;
@@ -391,11 +492,13 @@ struct phfem_batch_s {
   double* val = nullptr;
   double* b = nullptr;
   double* x = nullptr;
+  float2* y = nullptr;
   void* lval = nullptr;
   void* rdiag = nullptr;
   void* dinv = nullptr;
   void* r = nullptr;
   void* p = nullptr;
+  void* p2 = nullptr;
   void* q = nullptr;
   int block = 0;    // 0: not tuned yet
   int cluster = 1;  // CTAs per mesh
@@ -408,8 +511,8 @@ void batch_free(phfem_batch B) {
   phfem_ctx c = B->ctx;
   for (void* ptr : {(void*)B->desc, (void*)B->order, (void*)B->next, (void*)B->stats, (void*)B->xy, (void*)B->tri,
                     (void*)B->ed2el, (void*)B->lk, (void*)B->eclass, (void*)B->nbr, (void*)B->elen, (void*)B->t2e,
-                    (void*)B->sigma, (void*)B->lam_id, (void*)B->Kt, (void*)B->val, (void*)B->b, (void*)B->x,
-                    B->lval, B->rdiag, B->dinv, B->r, B->p, B->q})
+                    (void*)B->sigma, (void*)B->lam_id, (void*)B->Kt, (void*)B->val, (void*)B->b, (void*)B->x, (void*)B->y,
+                    B->lval, B->rdiag, B->dinv, B->r, B->p, B->p2, B->q})
     dfree(c, ptr);
   delete B;
 }
@@ -616,11 +719,13 @@ PHFEM_API int phfem_batch_solve(phfem_batch B, const double* a_T, const double* 
     chk(dalloc_n(ctx, &B->val, 5 * sE));
     chk(dalloc_n(ctx, &B->b, sE));
     chk(dalloc_n(ctx, &B->x, sE));
+    chk(dalloc_n(ctx, &B->y, sE));
     chk(dalloc(ctx, &B->lval, 4 * sE * sizeof(double)));
     chk(dalloc(ctx, &B->rdiag, sE * sizeof(double)));
     chk(dalloc(ctx, &B->dinv, sE * sizeof(double)));
     chk(dalloc(ctx, &B->r, sE * sizeof(double)));
     chk(dalloc(ctx, &B->p, sE * sizeof(double)));
+    chk(dalloc(ctx, &B->p2, sE * sizeof(float)));
     chk(dalloc(ctx, &B->q, sE * sizeof(double)));
     if (st != PHFEM_OK) return st;
   }
@@ -637,12 +742,12 @@ PHFEM_API int phfem_batch_solve(phfem_batch B, const double* a_T, const double* 
   if (fp32) {
     BatchArrays<float> A{B->xy, B->tri, B->ed2el, B->lk, B->eclass, B->nbr, B->elen, B->t2e, B->sigma, B->lam_id,
                          a_T, delta, f_mid, bc_mid, B->Kt, B->val, B->b, (float*)B->lval, (float*)B->rdiag,
-                         (float*)B->dinv, B->x, (float*)B->r, (float*)B->p, (float*)B->q, U, Lambda, w};
+                         (float*)B->dinv, B->x, B->y, (float*)B->r, (float*)B->p, (float*)B->p2, (float*)B->q, U, Lambda, w};
     st = run_batch<float>(B, bs, cs, A, P);
   } else {
     BatchArrays<double> A{B->xy, B->tri, B->ed2el, B->lk, B->eclass, B->nbr, B->elen, B->t2e, B->sigma, B->lam_id,
                           a_T, delta, f_mid, bc_mid, B->Kt, B->val, B->b, (double*)B->lval, (double*)B->rdiag,
-                          (double*)B->dinv, B->x, (double*)B->r, (double*)B->p, (double*)B->q, U, Lambda, w};
+                          (double*)B->dinv, B->x, B->y, (double*)B->r, (double*)B->p, nullptr, (double*)B->q, U, Lambda, w};
     st = run_batch<double>(B, bs, cs, A, P);
   }
   if (st != PHFEM_OK) return st;

@@ -143,17 +143,6 @@ __device__ __forceinline__ void prefetch_l2(const void* a, int bytes) {
   if (bytes > 0) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(a), "r"(bytes) : "memory");
 }
 
-// y += alpha p with alpha = ah + al (FP32 systems): the product as an exact
-// pair plus al p, added to the pair y by TwoSum; FP32 arithmetic only.
-__device__ __forceinline__ float2 y_add(float2 y, float ah, float al, float p) {
-  const c32::f2 pr = c32::two_prod(ah, p);
-  const float pe = c32::ffma(al, p, pr.l);
-  const c32::f2 s = c32::two_sum(y.x, pr.h);
-  const float t = c32::fadd(c32::fadd(s.l, y.y), pe);
-  const float hi = c32::fadd(s.h, t);
-  return make_float2(hi, c32::fsub(t, c32::fsub(hi, s.h)));
-}
-__device__ __forceinline__ double y_add(double y, double a, double, double p) { return fma(a, p, y); }
 
 __device__ __forceinline__ double y_value(float2 y) { return (double)y.x + (double)y.y; }
 __device__ __forceinline__ double y_value(double y) { return y; }

@@ -74,6 +74,20 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, cudaStream_t s, Args.
 // of the residual's evaluation), and for a reliable update the line-search
 // step along the kept direction or a restart of the direction.
 // mode 1 = start, 2 = reliable update.
+// y += alpha p with alpha = ah + al (FP32 systems): the product as an exact
+// pair plus al p, added to the pair y by TwoSum; FP32 arithmetic only.  The
+// solution correction between reliable updates is accumulated this way
+// (about 48 bits) instead of in FP64, whose rate on GB300 is ~1/64 of FP32's.
+__device__ __forceinline__ float2 y_add(float2 y, float ah, float al, float p) {
+  const c32::f2 pr = c32::two_prod(ah, p);
+  const float pe = c32::ffma(al, p, pr.l);
+  const c32::f2 s = c32::two_sum(y.x, pr.h);
+  const float t = c32::fadd(c32::fadd(s.l, y.y), pe);
+  const float hi = c32::fadd(s.h, t);
+  return make_float2(hi, c32::fsub(t, c32::fsub(hi, s.h)));
+}
+__device__ __forceinline__ double y_add(double y, double a, double, double p) { return fma(a, p, y); }
+
 // The value of the recursive r.z at which the next reliable update is taken:
 // a fall by the update factor, or, when that comes sooner, the point where
 // the true residual is predicted to meet the tolerance, r.r being taken to
