@@ -147,7 +147,7 @@ def parse():
                     help="do not sample nvidia-smi clocks (profiling runs under ncu)")
     ap.add_argument("--max-iter", type=int, default=0,
                     help="cap the CG iterations (short runs for profiling only; not a benchmark)")
-    ap.add_argument("--batch-sample", type=int, default=128,
+    ap.add_argument("--batch-sample", type=int, default=512,
                     help="main line: meshes of the batched workload measured beside the step (0: skip)")
     ap.add_argument("--cn-steps", type=int, default=64,
                     help="main line: Crank-Nicolson steps on 512 x 512 measured beside the step (0: skip)")
@@ -387,19 +387,22 @@ def batched_measure(count, steps=2, warmup=1, single_sample=32, parity=True, no_
     out = {"meshes": count, "triangles": nT, "edges": nE, "sides": [int(sides.min()), int(sides.max())],
            "setup_s": {"host_generation": t_gen, "tables": t_tables}}
     clocks = None if no_clocks else ClockSampler(torch.cuda.current_device())
-    # the block size is tuned once, on the FP32 + refinement launch, and kept for FP64
-    chosen, tune_ms = P.phfem_batch_tune(batch, delta, a_T=aT, f_mid=f, precision=P.PHFEM_FP32_IR, opts=opts)
+    # the launch shape is tuned for each precision (each is compared at its best shape)
     for prec, name in ((P.PHFEM_FP32_IR, "fp32_refined"), (P.PHFEM_FP64, "fp64")):
+        chosen, tune_ms = P.phfem_batch_tune(batch, delta, a_T=aT, f_mid=f, precision=prec, opts=opts)
+        shape = dict(block=chosen[0], cluster=chosen[1])
         res = None
         for _ in range(warmup):
-            res = P.phfem_batch_solve(batch, count, delta, a_T=aT, f_mid=f, precision=prec, opts=opts, U=U, Lambda=L)
+            res = P.phfem_batch_solve(batch, count, delta, a_T=aT, f_mid=f, precision=prec, opts=opts, U=U, Lambda=L,
+                                      **shape)
         if clocks and name == "fp32_refined":
             clocks.start()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record(stream)
         for _ in range(steps):
-            res = P.phfem_batch_solve(batch, count, delta, a_T=aT, f_mid=f, precision=prec, opts=opts, U=U, Lambda=L)
+            res = P.phfem_batch_solve(batch, count, delta, a_T=aT, f_mid=f, precision=prec, opts=opts, U=U, Lambda=L,
+                                      **shape)
         e1.record(stream)
         torch.cuda.synchronize()
         if clocks and name == "fp32_refined":
@@ -1131,8 +1134,8 @@ def main():
             forms["batched"] = batched_measure(args.batch_sample, steps=2, warmup=1, single_sample=16,
                                                parity=not args.no_cpu)
             forms["batched"]["sample"] = (f"meshes 0..{args.batch_sample - 1} of the 4096-mesh batched workload; "
-                                          "FP32 + refinement and FP64 in one persistent launch each, the plain "
-                                          "single-mesh FP64 path on the first 16")
+                                          "FP32 + refinement and FP64 in one persistent launch each, the launch "
+                                          "shape tuned for each, the plain single-mesh FP64 path on the first 16")
         if args.cn_steps > 0:
             forms["heat_cn"] = heat_measure(args.heat_n, args.cn_steps, host=False, mg=True)
             forms["heat_cn"]["sample"] = (f"{args.cn_steps} of the 512 Crank-Nicolson steps on 512 x 512 squares, "
