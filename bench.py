@@ -89,9 +89,16 @@ def hbm_peak():
 # Kernel timing inside the timed region brackets every 17th launch of each
 # kernel with CUDA events (an event between two launches keeps the second from
 # overlapping the first's drain, so timing every launch would slow the step).
-PROFILE_EVERY = 17  # odd: the update kernel alternates a light and a heavy launch (y every second iteration)
+PROFILE_EVERY = 17  # not a multiple of 4: the update kernel adds y every fourth launch
 SPMV_TRAFFIC = 404.4e6
 SPMV_TRAFFIC_SRC_SHA = "1fb4fca7b75481d9"
+# Warp instructions per triangle of the compensated FP32 triangle pass
+# (k_asm_tri<1>), smsp__inst_executed.sum / nT from one ncu capture of the
+# level-5 assembly (137,634,987 / 6,291,456); valid only for the sources whose
+# hash is recorded with it.  The pass is bound by the issue rate: each SM's
+# four schedulers issue one warp instruction per clock.
+ASM_TRI_WARP_INST_PER_TRI = 137634987 / 6291456
+ASM_TRI_SRC_SHA = "ef8c13adb824adfa"
 
 
 def _function_src(path, signature):
@@ -112,6 +119,27 @@ def _sha_spmv_src():
             + _function_src(cg, "__device__ __forceinline__ void row_nbrs(")
             + _function_src(cg, "__device__ __forceinline__ void load_l4(const float4*"))
     return hashlib.sha256(text.encode()).hexdigest()[:16]
+
+
+def _sha_asm_tri_src():
+    """Hash of the compensated triangle pass's source: the kernel, the record
+    functions it calls and the compensated arithmetic."""
+    csrc = os.path.join(ROOT, "paper_2401_15557_gb300", "csrc")
+    text = (_function_src(os.path.join(csrc, "assemble.cu"), "__global__ void k_asm_tri(")
+            + _function_src(os.path.join(csrc, "kernels.cuh"), "__device__ __forceinline__ void tri_record32_store(")
+            + open(os.path.join(csrc, "c32.cuh")).read())
+    return hashlib.sha256(text.encode()).hexdigest()[:16]
+
+
+def sm_max_mhz():
+    """The SM clock the GPU runs at without a throttle reason (nvidia-smi), or None."""
+    import torch
+    try:
+        out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits", "-i",
+                              str(torch.cuda.current_device())], capture_output=True, text=True, timeout=20)
+        return float(out.stdout.strip().splitlines()[0])
+    except Exception:
+        return None
 
 
 def parse():
@@ -958,6 +986,18 @@ def main():
                 kern[k] = {"ms": avg, "bytes": nb, "achieved_gbs": nb / (avg * 1e-3) / 1e9}
             t2 = kern["asm_tri"]["ms"] + kern["asm_rows"]["ms"]
             pk, pk_src = hbm_peak()
+            kern["asm_rows"]["roofline"] = {"bound": "hbm", "achieved": kern["asm_rows"]["achieved_gbs"], "peak": pk,
+                                            "unit": "GB/s", "frac": kern["asm_rows"]["achieved_gbs"] / pk}
+            mhz = sm_max_mhz()
+            if prec == P.PHFEM_FP32_IR and mhz and ASM_TRI_SRC_SHA == _sha_asm_tri_src():
+                sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+                inst = ASM_TRI_WARP_INST_PER_TRI * nT / (kern["asm_tri"]["ms"] * 1e-3) / 1e9
+                peak_i = 4 * sms * mhz * 1e-3
+                kern["asm_tri"]["roofline"] = {"bound": "alu", "achieved": inst, "peak": peak_i,
+                                               "unit": "G warp instructions/s", "frac": inst / peak_i,
+                                               "warp_instructions_per_triangle": ASM_TRI_WARP_INST_PER_TRI,
+                                               "peak_source": f"{sms} SMs x 4 schedulers x 1 warp instruction "
+                                                              f"per clock at {mhz:.0f} MHz"}
             ach = (bt + br) / (t2 * 1e-3) / 1e9
             res[name] = {"ms": mt, "triangles_per_s": nT * 1e3 / mt, "kernels": kern,
                          "roofline": {"bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s",

@@ -94,9 +94,14 @@ __global__ void k_asm_rows(int nE, int nT, const int32_t* __restrict__ ed2el, co
                            const double* __restrict__ conv, const double* __restrict__ f_mid,
                            const double* __restrict__ bc_mid, const double* __restrict__ elen, double sK, double sM,
                            double delta, double* __restrict__ val, double* __restrict__ b, double* __restrict__ me,
-                           T* __restrict__ lval, T* __restrict__ rdiag, T* __restrict__ dinv) {
+                           T* __restrict__ lval, T* __restrict__ rdiag, T* __restrict__ dinv,
+                           const int32_t* __restrict__ tiles) {
   const size_t n = (size_t)nT, m = (size_t)nE;
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < nE; e += gridDim.x * blockDim.x) {
+  // tiles of kBlock consecutive rows, in the mesh's tile order when given
+  const int ntiles = (nE + kBlock - 1) / kBlock;
+  for (int v = blockIdx.x; v < ntiles; v += gridDim.x) {
+    const int e = (tiles ? tiles[v] : v) * kBlock + threadIdx.x;
+    if (e >= nE) continue;
     const int4 q = reinterpret_cast<const int4*>(ed2el)[e];
     const int kk = lk[e];
     const uint8_t cls = eclass[e];
@@ -304,6 +309,16 @@ int assemble_into(phfem_sys sys, const double* f_mid, const double* bc_mid, int*
   cudaStream_t s = ctx->stream;
   const int nT = m->info.nT, nE = m->info.nE;
   const phfem_coeffs& c = sys->c;
+  if (!m->row_tiles && sys->form == PHFEM_FORM_TRACE) {
+    // the rows' visit order, once per mesh (not while a graph is captured: the
+    // rows are then visited in the paper's order, with the same results)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+      if (mesh_row_tiles(m) != PHFEM_OK) cudaGetLastError();  // without it the paper's order is used
+    } else {
+      cudaGetLastError();
+    }
+  }
   prof_start(ctx, kProfAsmTri);
   const bool iso = c.A[0] == 0.0 && c.A[1] == 0.0 && c.A[2] == 0.0;
   double* conv = sys->conv ? sys->Kt + (size_t)kRec * nT : nullptr;
@@ -338,7 +353,7 @@ int assemble_into(phfem_sys sys, const double* f_mid, const double* bc_mid, int*
     using T = std::remove_pointer_t<decltype(inner)>;
     kernel<<<grid_for(ctx, nE), kBlock, 0, s>>>(nE, nT, m->ed2el, m->lk, m->eclass, sys->Kt, conv, f_mid,
                                                 bc_mid, m->elen, sK, sM, c.delta, sys->val, sys->b, sys->me,
-                                                (T*)sys->lval, (T*)sys->rdiag, (T*)sys->dinv);
+                                                (T*)sys->lval, (T*)sys->rdiag, (T*)sys->dinv, m->row_tiles);
   };
   if (sys->fp32 && ell) rows(k_asm_rows<float, true>, (float*)nullptr);
   else if (!sys->fp32 && ell) rows(k_asm_rows<double, true>, (double*)nullptr);

@@ -132,6 +132,10 @@ struct phfem_mesh_s {
   int4* nbr_ovf = nullptr;     // [novf] the four internal neighbours of the marked rows
   uint8_t* eclass_i = nullptr; // [nE] class of internal row i
   int novf = 0;
+  // visit order of the edge-row assembly pass (built on its first use,
+  // mesh_row_tiles): the tiles of kBlock consecutive edges by the Morton code
+  // of their mean midpoint
+  int32_t* row_tiles = nullptr;
 };
 
 namespace phfem {
@@ -219,6 +223,7 @@ int assemble_system(phfem_mesh mesh, const phfem_coeffs& c, const double* f_mid,
                     phfem_sys* out, bool check);
 // Locality order of a mesh's edges for the iteration kernels (order.cu).
 int mesh_order(phfem_mesh m);
+int mesh_row_tiles(phfem_mesh m);
 void mesh_order_free(phfem_mesh m);
 int radix_sort_pairs(phfem_ctx ctx, uint32_t* k0, int32_t* v0, uint32_t* k1, int32_t* v1, int n, int bits);
 // Jacobi-PCG on the trace-form system in the locality order (cg.cu): used for
