@@ -100,9 +100,11 @@ PHFEM_API int64_t phfem_ctx_launches(phfem_ctx ctx);
 PHFEM_API int phfem_ctx_set_l2_window(phfem_ctx ctx, int enable);
 /* Kernels of the FP32 Jacobi iteration in the locality order (a tuning choice,
  * not part of the method): 0 = the direction update p = u + beta p is folded
- * into the operator product (two kernels per iteration, the default); 1 = it
- * runs as a kernel of its own (three kernels).  Both compute the same p and
- * q per row; the sums are grouped alike, so results agree to rounding.  FP64
+ * into the operator product, whose rows' own data are staged in shared memory
+ * by bulk copies (two kernels per iteration, the default); 1 = the direction
+ * update runs as a kernel of its own (three kernels); 2 = as 0 with the rows'
+ * data read through L1/L2 after an L2 prefetch.  All compute the same p and q
+ * per row; the sums are grouped alike, so results agree to rounding.  FP64
  * systems always use the separate direction kernel.  Other values:
  * PHFEM_EINVAL. */
 PHFEM_API int phfem_ctx_set_cg_kernel(phfem_ctx ctx, int variant);

@@ -1,6 +1,8 @@
 // Jacobi-preconditioned conjugate gradients on the condensed trace-form edge
 // system (Section 3.5 after elimination of the element unknowns) in the
-// locality order of the edges (order.cu), two kernels per iteration.
+// locality order of the edges (order.cu), two kernels per iteration; the
+// product kernel stages each tile's own row data in shared memory with bulk
+// copies (k_fcg_spmv_staged, the default for FP32 systems).
 //
 // Same method as the paper-order iteration of solve.cu (Jacobi-PCG with
 // reliable updates: FP32 or FP64 inner vectors, FP64 true residual in
@@ -85,7 +87,7 @@ struct FastCG {
   // resident blocks per SM of the iteration kernels, [F] (fused or not): the
   // grids are one wave of resident blocks, so no kernel runs a partial last
   // wave (the FP32 update kernel holds 3 blocks per SM, the product kernel 8)
-  int per_spmv[2] = {1, 1}, per_update[2] = {1, 1}, per_dir = 1;
+  int per_spmv[2] = {1, 1}, per_update[2] = {1, 1}, per_dir = 1, per_staged = 1;
   void* u() const { return vec; }
   void* q() const { return (char*)vec + slot; }
   void* pk(int k) const { return (char*)vec + (2 + k) * slot; }
@@ -482,6 +484,193 @@ __global__ void __launch_bounds__(kBlock) k_fcg_spmv(int n, const short4* __rest
   }
 }
 
+// ---- product kernel with the tile's row data staged in shared memory ----
+// One stage holds a tile's neighbour differences, l_es, reaction part, u and
+// p_old, copied by the bulk-copy engine (one thread issues five
+// cp.async.bulk copies, completion counted on an mbarrier); two stages, the
+// copies of a tile issued two tiles ahead.
+struct __align__(16) FStage {
+  short4 nb[kBlock];
+  float4 l4[kBlock];
+  float rd[kBlock];
+  float u[kBlock];
+  float po[kBlock];
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* b, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void bulk_copy_g2s(void* dst, const void* src, unsigned bytes, uint64_t* b) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(b))
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* b, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(b)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+// Waits for the phase of parity `parity` to complete; false after a second
+// (the copies of a tile take microseconds: a second means they never will).
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, unsigned parity) {
+  const uint64_t t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(b, parity)) return true;
+    if (global_ns() - t0 > 1000000000ull) return false;
+  }
+}
+
+// The fused FP32 product kernel of k_fcg_spmv<float, true>, the row's own data
+// read from the staged tile: the neighbour differences are then a shared-memory
+// load, and only the gathers of u and p_old at the neighbours go to L1 and L2.
+// The copies are issued after the wait on the previous kernel (unlike an L2
+// prefetch, a shared-memory copy is not updated by later writes).  If a copy
+// never completes the block records PHFEM_ECUDA, waits (bounded) for the copies
+// it still has in flight and leaves the tile loop.
+__global__ void __launch_bounds__(kBlock) k_fcg_spmv_staged(int n, const short4* __restrict__ nb,
+                                                            const int4* __restrict__ ovf,
+                                                            const float4* __restrict__ lv,
+                                                            const float* __restrict__ rd, const float* __restrict__ u,
+                                                            Dirs<float> dirs, float* __restrict__ q, double* partials,
+                                                            SolveState* st) {
+  __shared__ FStage stage[2];
+  __shared__ uint64_t bar[2];
+  __shared__ double smem[kBlock / 32];
+  __shared__ int s_fail;
+  const int ntiles = (n + kBlock - 1) / kBlock;
+  auto tile = [&](int k) { return blockIdx.x + k * (int)gridDim.x; };
+  if (threadIdx.x < 3 && tile(0) < ntiles) {  // the first tile's static arrays into L2 before the wait
+    const int r0 = tile(0) * kBlock, cnt = min(kBlock, n - r0);
+    if (threadIdx.x == 0) prefetch_l2(nb + r0, cnt * (int)sizeof(short4));
+    if (threadIdx.x == 1) prefetch_l2(lv + r0, cnt * (int)sizeof(float4));
+    if (threadIdx.x == 2) prefetch_l2(rd + r0, cnt * (int)sizeof(float));
+  }
+  pdl_enter();
+  if (st->done) return;
+  const int par = st->par & (kDirs - 1);
+  const float* __restrict__ po = dirs.b(par);
+  float* __restrict__ pn = dirs.b((par + 1) & (kDirs - 1));
+  const int mode = st->restart ? 1 : (st->use_rp ? 2 : 0);
+  const float beta = (float)st->beta;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](int k) {  // thread 0: the copies of the block's k-th tile into stage k & 1
+    const int t = tile(k);
+    if (t >= ntiles) return;
+    const int r0 = t * kBlock, cnt = min(kBlock, n - r0);
+    FStage& S = stage[k & 1];
+    const unsigned b8 = (unsigned)(cnt * 8 + 15) & ~15u, b16 = (unsigned)cnt * 16u,
+                   b4 = (unsigned)(cnt * 4 + 15) & ~15u;  // rounded up to 16: the arrays are padded for it
+    mbar_expect_tx(&bar[k & 1], b8 + b16 + 3 * b4);
+    bulk_copy_g2s(S.nb, nb + r0, b8, &bar[k & 1]);
+    bulk_copy_g2s(S.l4, lv + r0, b16, &bar[k & 1]);
+    bulk_copy_g2s(S.rd, rd + r0, b4, &bar[k & 1]);
+    bulk_copy_g2s(S.u, u + r0, b4, &bar[k & 1]);
+    bulk_copy_g2s(S.po, po + r0, b4, &bar[k & 1]);
+  };
+  if (threadIdx.x == 0) {
+    issue(0);
+    issue(1);
+  }
+  auto pval = [&](float uv, float pv) -> float {
+    if (mode == 1) return uv;
+    if (mode == 0) return fmadd(beta, pv, uv);
+    return pv;
+  };
+  float acc = 0.f;
+  int k = 0;
+  for (;; ++k) {
+    const int t = tile(k);
+    if (t >= ntiles) break;
+    if (!mbar_wait(&bar[k & 1], (k >> 1) & 1)) s_fail = 1;
+    const FStage& S = stage[k & 1];
+    const int i = t * kBlock + threadIdx.x;
+    if (i < n && !s_fail) {
+      const short4 s4 = S.nb[threadIdx.x];
+      int c[4];
+      if (s4.x != (short)-32768) {
+        c[0] = i + s4.x;
+        c[1] = i + s4.y;
+        c[2] = i + s4.z;
+        c[3] = i + s4.w;
+      } else {
+        const int4 o = __ldg(ovf + ((int)(uint16_t)s4.y | ((int)(uint16_t)s4.z << 16)));
+        c[0] = o.x;
+        c[1] = o.y;
+        c[2] = o.z;
+        c[3] = o.w;
+      }
+      float gu[4], gp[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        gu[m] = mode != 2 ? __ldg(u + c[m]) : 0.f;
+        gp[m] = mode != 1 ? __ldg(po + c[m]) : 0.f;
+      }
+      const float4 l = S.l4[threadIdx.x];
+      const float pe = pval(S.u[threadIdx.x], S.po[threadIdx.x]);
+      float sv = S.rd[threadIdx.x] * pe;
+      sv = fmadd(l.x, pe - pval(gu[0], gp[0]), sv);
+      sv = fmadd(l.y, pe - pval(gu[1], gp[1]), sv);
+      sv = fmadd(l.z, pe - pval(gu[2], gp[2]), sv);
+      sv = fmadd(l.w, pe - pval(gu[3], gp[3]), sv);
+      pn[i] = pe;
+      q[i] = sv;
+      acc = fmadd(pe, sv, acc);
+    }
+    __syncthreads();  // the stage is read: it may be refilled
+    if (s_fail) break;
+    if (threadIdx.x == 0) issue(k + 2);
+  }
+  if (s_fail && threadIdx.x == 0) {
+    // the copies still in flight (tiles k and k + 1, issued before the
+    // failure) land in this block's shared memory: wait for them, bounded,
+    // before leaving
+    mbar_wait(&bar[k & 1], (k >> 1) & 1);
+    if (tile(k + 1) < ntiles) mbar_wait(&bar[(k + 1) & 1], ((k + 1) >> 1) & 1);
+    st->status = PHFEM_ECUDA;
+    st->done = 3;
+  }
+  const double accd = block_sum((double)acc, smem);
+  if (threadIdx.x == 0) partials[blockIdx.x] = accd;
+  if (!arrive_last(&st->counter[1])) return;
+  const double pq = sum_partials(partials, smem);
+  if (threadIdx.x == 0) {
+    st->counter[1] = 0;
+    st->par = (par + 1) & (kDirs - 1);
+    if (st->done == 3) return;
+    if (!(pq > 0.0) || !isfinite(pq)) {
+      st->done = 3;
+      st->status = isfinite(pq) ? PHFEM_EBREAKDOWN : PHFEM_ENAN;
+    } else {
+      const double a = (st->use_rp ? st->rp : st->rz) / pq;
+      st->alpha = a;
+      st->alpha_f[0] = (float)a;
+      st->alpha_f[1] = (float)(a - (double)(float)a);
+      st->use_rp = 0;
+      st->restart = 0;
+    }
+  }
+}
+
 // One row of the update: u -= alpha D^-1 q and its r.z term.
 __device__ __forceinline__ void update_u(float qe, float d, float& ue, float ah, float& acc) {
   ue = fmadd(-ah, d * qe, ue);
@@ -734,6 +923,17 @@ struct FLaunch {
     phfem_ctx ctx = sys->mesh->ctx;
     phfem_mesh m = sys->mesh;
     prof_start(ctx, kProfSpmv);
+    bool staged = false;
+    if constexpr (F && sizeof(T) == sizeof(float)) {
+      if (sys->mesh->ctx->cg_variant == 0) {
+        PH_CUDA(launch_pdl_w(win, k_fcg_spmv_staged, wave(f()->per_staged), s, n, (const short4*)m->nbr16,
+                             (const int4*)m->nbr_ovf, (const float4*)f()->l4, (const float*)f()->rd,
+                             (const float*)f()->u(), f()->template dirs<float>(), (float*)f()->q(), sys->partials,
+                             sys->st));
+        staged = true;
+      }
+    }
+    if (!staged)
     PH_CUDA(launch_pdl_w(win, k_fcg_spmv<T, F>, wave(f()->per_spmv[F]), s, n, (const short4*)m->nbr16, (const int4*)m->nbr_ovf,
                        (const L4*)f()->l4, (const T*)f()->rd, (const T*)f()->u(), f()->template dirs<T>(),
                        (T*)f()->q(), sys->partials, sys->st, kPrefetchAhead));
@@ -883,7 +1083,7 @@ int fcg_capture_typed(phfem_sys sys, const phfem_solve_opts& o, cudaStream_t cs,
 
 // FP32 systems fold the direction update into the product unless the
 // context chose the unfused kernels.
-static bool fused_fp32(phfem_sys sys) { return sys->mesh->ctx->cg_variant == 0; }
+static bool fused_fp32(phfem_sys sys) { return sys->mesh->ctx->cg_variant != 1; }  // 0 and 2
 
 bool fcg_eligible(phfem_sys sys, const phfem_solve_opts& o) {
   return o.order == 0 && sys->form == PHFEM_FORM_TRACE && !sys->conv && !sys->mg;
@@ -931,6 +1131,35 @@ int fcg_prepare(phfem_sys sys) {
     f->per_update[0] = resident_blocks(k_fcg_update<float, false>);
     f->per_update[1] = resident_blocks(k_fcg_update<float, true>);
     f->per_dir = resident_blocks(k_fcg_dir<float>);
+    // The staged product kernel needs ~150 KB of shared memory per SM for 8
+    // blocks; the update kernel almost none.  Left to choose, the two would
+    // run under different L1 / shared-memory splits, and every switch between
+    // them drains the SM (no overlap of consecutive launches): 125 us per
+    // iteration at level 5 against 105 with one split for both.
+    {
+      int smem_sm = 0, dev = 0;
+      cudaFuncAttributes fa{};
+      cudaGetDevice(&dev);
+      if (cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev) == cudaSuccess &&
+          cudaFuncGetAttributes(&fa, k_fcg_spmv_staged) == cudaSuccess && smem_sm > 0) {
+        const double need = (double)kBlocksPerSM * ((double)fa.sharedSizeBytes + 1024.0);  // + 1 KB per block reserved
+        // The preference is a percentage of the SM's shared memory, and the
+        // driver maps it to one of the sizes the SM supports (KB, compute
+        // capability 9.0 and 10.x): a percentage between two sizes may map to
+        // different sizes for kernels of different needs, so the request is
+        // the smallest supported size that holds 8 staged blocks, exactly.
+        static const int kSizesKB[] = {0, 8, 16, 32, 64, 100, 132, 164, 196, 228};
+        for (int kb : kSizesKB) {
+          if (kb * 1024.0 < need || kb * 1024 > smem_sm) continue;
+          const int carve = (int)std::ceil(100.0 * kb * 1024.0 / smem_sm);
+          cudaFuncSetAttribute(k_fcg_spmv_staged, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+          cudaFuncSetAttribute(k_fcg_update<float, true>, cudaFuncAttributePreferredSharedMemoryCarveout, carve);
+          if (resident_blocks(k_fcg_spmv_staged) >= kBlocksPerSM) break;
+        }
+      }
+      cudaGetLastError();
+    }
+    f->per_staged = resident_blocks(k_fcg_spmv_staged);
   } else {
     f->per_spmv[0] = resident_blocks(k_fcg_spmv<double, false>);
     f->per_update[0] = resident_blocks(k_fcg_update<double, false>);

@@ -95,7 +95,8 @@ struct phfem_ctx_s {
   size_t l2_window_max = 0;   // largest access-policy window
   size_t l2_limit = 0;        // the set-aside reserved now (cudaLimitPersistingL2CacheSize)
   bool l2_window = true;      // solves may use an L2 persistence window
-  int cg_variant = 0;         // FP32 locality-order CG: 0 direction update fused into the product, 1 separate
+  int cg_variant = 0;         // FP32 locality-order CG: 0 fused, rows staged in shared memory; 1 separate
+                              // direction kernel; 2 fused, rows through L1/L2
   int64_t launches;
   bool profile = false;
   int profile_every = 1;   // time every n-th launch of each kernel

@@ -278,7 +278,7 @@ PHFEM_API int64_t phfem_ctx_launches(phfem_ctx ctx) { return ctx ? ctx->launches
 
 PHFEM_API int phfem_ctx_set_cg_kernel(phfem_ctx ctx, int variant) {
   if (!ctx) return fail(PHFEM_EINVAL, "phfem_ctx_set_cg_kernel: NULL context");
-  if (variant != 0 && variant != 1) return fail(PHFEM_EINVAL, "phfem_ctx_set_cg_kernel: variant must be 0 or 1");
+  if (variant < 0 || variant > 2) return fail(PHFEM_EINVAL, "phfem_ctx_set_cg_kernel: variant must be 0, 1 or 2");
   ctx->cg_variant = variant;
   return PHFEM_OK;
 }

@@ -233,7 +233,8 @@ def phfem_ctx_create_with_allocator(stream=None):
 
 
 def phfem_ctx_set_cg_kernel(ctx, variant=0):
-    """FP32 Jacobi iteration in the locality order: 0 direction update fused into the product, 1 separate."""
+    """FP32 Jacobi iteration in the locality order: 0 direction update fused into the product, the rows'
+    own data staged in shared memory (default); 1 separate direction kernel; 2 fused, rows through L1/L2."""
     _check(lib().phfem_ctx_set_cg_kernel(ctx, int(variant)), "phfem_ctx_set_cg_kernel")
 
 

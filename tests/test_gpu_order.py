@@ -100,31 +100,39 @@ def test_locality_order_solve_matches_paper_order_and_oracle(name, prec):
 
 
 def test_unfused_fp32_iteration_matches_fused():
-    """The FP32 iteration with the direction update as a kernel of its own
-    (phfem_ctx_set_cg_kernel 1) against the default fused one: both converge
-    to the same solution within the solve tolerance."""
+    """The FP32 iteration's kernel variants (phfem_ctx_set_cg_kernel): the
+    default fused product with the rows staged in shared memory (0) and the
+    fused product reading them through L1/L2 (2) visit the same rows in the same
+    order with the same arithmetic, so their solutions are bitwise equal; with
+    the direction update as a kernel of its own (1) the solve converges to the
+    same solution within the solve tolerance.  The mesh (85,069 edges) spans
+    332 tiles of 256 rows and a ragged last one of 77."""
     from paper_2401_15557_gb300 import phfem as P
     from phfem_gpu import GpuMesh, dev
     import torch
 
     ctx = P.phfem_ctx_create()
-    mesh = MESHES["lshape_l2"]()
+    mesh = I.lshape_mesh(n=97, jitter=0.2, seed=I.seed_for(1, 73))
     aT = I.element_mean_at_midpoints(mesh.xy, mesh.tri, I.coeff_lshape)
     pb = I.problem_sine_exp()
     pb.delta = 1.0
     gm = GpuMesh(mesh, ctx)
     fm, bc = gm.edge_data(pb.f, pb.g, pb.uD)
     sysh = P.phfem_assemble(gm.h, fm, bc, a_T=dev(aT, torch.float64), delta=pb.delta, precision=P.PHFEM_FP32_IR)
-    ws = []
-    for variant in (0, 1):
+    assert gm.info["nE"] == 85069
+    ws, its = [], []
+    for variant in (0, 1, 2):
         P.phfem_ctx_set_cg_kernel(ctx, variant)
         w = torch.empty(gm.info["nE"], dtype=torch.float64, device="cuda")
         st = P.phfem_solve(sysh, P.solve_opts(rtol=1e-10), w=w)
         assert st["converged"] == 1 and st["rel_residual"] <= 1e-10, (variant, st)
         ws.append(w.cpu().numpy())
+        its.append(st["iterations"])
+    assert np.array_equal(ws[0], ws[2]) and its[0] == its[2]
     assert np.max(np.abs(ws[0] - ws[1])) <= 1e-8 * np.max(np.abs(ws[1]))
-    with pytest.raises(P.PhfemError):
-        P.phfem_ctx_set_cg_kernel(ctx, 2)
+    for bad in (-1, 3):
+        with pytest.raises(P.PhfemError):
+            P.phfem_ctx_set_cg_kernel(ctx, bad)
     P.phfem_sys_destroy(sysh)
     gm.close()
     P.phfem_ctx_destroy(ctx)
