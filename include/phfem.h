@@ -89,6 +89,12 @@ PHFEM_API const char* phfem_status_str(int status);
 PHFEM_API const char* phfem_last_error(void);
 /* Number of kernels the library launched on this context so far. */
 PHFEM_API int64_t phfem_ctx_launches(phfem_ctx ctx);
+/* Device memory held by the context's own allocations (meshes, systems,
+ * solver workspaces: every buffer the library allocated through the context,
+ * not the caller's arrays): now, and at the peak since the last reset;
+ * reset_peak != 0 then sets the peak to the current value.  Either output may
+ * be NULL. */
+PHFEM_API int phfem_ctx_memory(phfem_ctx ctx, int64_t* bytes_now, int64_t* bytes_peak, int32_t reset_peak);
 /* A context, and everything built on it, is used by one host thread at a time
  * (its systems share one pinned host mirror of the solver state). */
 /* Solves keep the iteration's residual and direction resident in L2 with an
@@ -479,12 +485,15 @@ PHFEM_API int phfem_batch_destroy(phfem_batch batch);
 typedef struct phfem_server_s* phfem_server;
 
 /* One request: an elliptic solve (kind 0) or a Crank-Nicolson run (kind 1)
- * with constant data f, u_D, g (and u0 for kind 1).  Every pointer is device
- * memory owned by the caller and must stay valid until the request is done.
- * With levels > 0 the mesh is a coarse mesh that the server refines `levels`
- * times (phfem_mesh_refine) and solves on the finest mesh with the multigrid
- * preconditioner; a_T, U_out and Lambda_out then refer to the finest mesh
- * (nT 4^levels triangles, in the refinement's order). */
+ * with data f, u_D, g (and u0 for kind 1) given as constants, or per edge
+ * midpoint in f_mid, bc_mid and u0_mid (time-independent for kind 1; each may
+ * be NULL, and the constant is then used).  Every pointer is device memory
+ * owned by the caller and must stay valid until the request is done.  With
+ * levels > 0 the mesh is a coarse mesh that the server refines `levels` times
+ * (phfem_mesh_refine) and solves on the finest mesh with the multigrid
+ * preconditioner; a_T, U_out, Lambda_out and the midpoint arrays then refer
+ * to the finest mesh (nT 4^levels triangles, nE its edges, in the
+ * refinement's order). */
 typedef struct {
   int32_t kind;            /* 0 elliptic, 1 Crank-Nicolson                               */
   int32_t nV, nT, nD, nN;
@@ -501,6 +510,11 @@ typedef struct {
   double* Lambda_out;      /* [nE] or NULL (room for nE, the first nL written)             */
   int32_t levels;          /* 0: solve on the given mesh (Jacobi-PCG); > 0: see above      */
   int32_t reserved;
+  const double* f_mid;     /* [nE] or NULL: f at the edge midpoints                         */
+  const double* bc_mid;    /* [nE] or NULL: u_D on Dirichlet edges, g on Neumann edges (as
+                              phfem_assemble's bc_mid)                                     */
+  const double* u0_mid;    /* kind 1, [nE] or NULL: the initial midpoint values (u_D on
+                              Dirichlet edges)                                             */
 } phfem_request;
 
 typedef struct {
@@ -512,14 +526,20 @@ typedef struct {
   int32_t nE, nL;
   double rel_residual;
   double t_submit, t_admit, t_finish;  /* seconds since the server was created          */
+  double bytes_reserved;   /* device bytes the admission reserved for the request          */
+  int64_t bytes_peak;      /* device bytes the request's own allocations held at their peak */
 } phfem_result;
 
 /* Creates a server on the current device with `slots` workers, each a host
  * thread with its own context and CUDA stream, so admitted requests overlap on
  * the GPU.  A request is admitted (first in, first out) when a slot is free
- * and its device-memory estimate (400 bytes per triangle + 1 MB) fits in
- * hbm_budget_bytes minus what admitted requests hold; a request larger than
- * the whole budget runs alone.  opts apply to every solve. */
+ * and its device-memory reservation fits in hbm_budget_bytes minus what
+ * admitted requests hold; a request larger than the whole budget runs alone.
+ * The reservation is the bytes per (finest-mesh) triangle that finished
+ * requests of the same kind (elliptic or Crank-Nicolson, with or without
+ * refinement) of at least 65,536 triangles actually allocated at their peak,
+ * the largest seen, plus 10 % and 4 MB; before any has finished, 400 bytes per
+ * triangle (600 with refinement) + 4 MB.  opts apply to every solve. */
 PHFEM_API int phfem_server_create(int32_t slots, double hbm_budget_bytes, const phfem_solve_opts* opts,
                                   phfem_server* out);
 /* Queues a request (copied) and returns its id; never blocks on the GPU. */

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "phfem.h"
@@ -106,6 +107,10 @@ struct phfem_ctx_s {
   void* alloc_user = nullptr;
   phfem::SolveState* st_pinned = nullptr;  // pinned host mirror of a solver state, shared by the
                                            // context's systems (read right after each copy)
+  // device memory the context holds (its allocations through dalloc, by
+  // pointer), now and at the peak since the last reset
+  std::unordered_map<void*, size_t> live;
+  size_t bytes_now = 0, bytes_peak = 0;
 };
 
 struct phfem_mesh_s {

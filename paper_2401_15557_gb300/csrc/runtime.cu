@@ -22,12 +22,19 @@ int cuda_fail(cudaError_t err, const char* what, const char* file, int line) {
   return err == cudaErrorMemoryAllocation ? PHFEM_ENOMEM : PHFEM_ECUDA;
 }
 
+static void account(phfem_ctx ctx, void* p, size_t bytes) {
+  ctx->live[p] = bytes;
+  ctx->bytes_now += bytes;
+  if (ctx->bytes_now > ctx->bytes_peak) ctx->bytes_peak = ctx->bytes_now;
+}
+
 int dalloc(phfem_ctx ctx, void** p, size_t bytes) {
   *p = nullptr;
   if (ctx->alloc) {
     *p = ctx->alloc(bytes, (void*)ctx->stream, ctx->alloc_user);
     if (!*p) return fail(PHFEM_ENOMEM, std::string("device allocation of ") + std::to_string(bytes) +
                                            " bytes failed (caller's allocator)");
+    account(ctx, *p, bytes);
     return PHFEM_OK;
   }
   cudaError_t e = cudaMallocAsync(p, bytes, ctx->stream);
@@ -37,11 +44,17 @@ int dalloc(phfem_ctx ctx, void** p, size_t bytes) {
     return fail(PHFEM_ENOMEM, std::string("device allocation of ") + std::to_string(bytes) +
                                   " bytes failed: " + cudaGetErrorString(e));
   }
+  account(ctx, *p, bytes);
   return PHFEM_OK;
 }
 
 void dfree(phfem_ctx ctx, void* p) {
   if (!p) return;
+  auto it = ctx->live.find(p);
+  if (it != ctx->live.end()) {
+    ctx->bytes_now -= it->second;
+    ctx->live.erase(it);
+  }
   if (ctx->free_fn) ctx->free_fn(p, (void*)ctx->stream, ctx->alloc_user);
   else cudaFreeAsync(p, ctx->stream);
 }
@@ -275,6 +288,14 @@ PHFEM_API int phfem_ctx_destroy(phfem_ctx ctx) {
 }
 
 PHFEM_API int64_t phfem_ctx_launches(phfem_ctx ctx) { return ctx ? ctx->launches : -1; }
+
+PHFEM_API int phfem_ctx_memory(phfem_ctx ctx, int64_t* bytes_now, int64_t* bytes_peak, int32_t reset_peak) {
+  if (!ctx) return fail(PHFEM_EINVAL, "phfem_ctx_memory: NULL context");
+  if (bytes_now) *bytes_now = (int64_t)ctx->bytes_now;
+  if (bytes_peak) *bytes_peak = (int64_t)ctx->bytes_peak;
+  if (reset_peak) ctx->bytes_peak = ctx->bytes_now;
+  return PHFEM_OK;
+}
 
 PHFEM_API int phfem_ctx_set_cg_kernel(phfem_ctx ctx, int variant) {
   if (!ctx) return fail(PHFEM_EINVAL, "phfem_ctx_set_cg_kernel: NULL context");

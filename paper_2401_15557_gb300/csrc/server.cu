@@ -24,7 +24,8 @@
 namespace phfem {
 namespace {
 
-// f at every edge, u_D on Dirichlet edges and g on Neumann edges (constants).
+// f at every edge, u_D on Dirichlet edges and g on Neumann edges (constants),
+// and the initial values (u_D on Dirichlet edges) when w0 is given.
 __global__ void k_fill_edge_data(int nE, const uint8_t* __restrict__ eclass, double f, double uD, double g,
                                  double* __restrict__ f_mid, double* __restrict__ bc_mid, double u0,
                                  double* __restrict__ w0) {
@@ -61,21 +62,46 @@ struct phfem_server_s {
   std::vector<phfem_ctx> ctxs;
   std::vector<cudaStream_t> streams;
   int64_t completed = 0;
+  // largest device bytes per finest-mesh triangle that finished requests
+  // allocated, by kind (elliptic, Crank-Nicolson) and refinement (none, some);
+  // 0 until one has finished
+  double per_tri[2][2] = {{0.0, 0.0}, {0.0, 0.0}};
 };
 
 namespace phfem {
 namespace {
 
-double estimate_bytes(const phfem_request& r) {
-  // tables (~100 B/triangle), system (~150 B/edge at 1.5 edges/triangle),
-  // solver vectors and CN state: 400 B per triangle covers both kinds; a
-  // refinement hierarchy adds a third and the multigrid vectors
-  const double fine = (double)r.nT * std::pow(4.0, (double)std::max(0, r.levels));
-  return (r.levels > 0 ? 600.0 : 400.0) * fine + (double)(1 << 20);
+double fine_triangles(const phfem_request& r) {
+  return (double)r.nT * std::pow(4.0, (double)std::max(0, r.levels));
 }
+
+// The reservation of a request (the server's lock held): the measured bytes
+// per triangle of its class, plus 10 %, once a request of the class has
+// finished; before that a static guess (tables ~100 B/triangle, system ~150 B
+// per edge at 1.5 edges per triangle, solver vectors and CN state: 400 B per
+// triangle; a refinement hierarchy adds a third and the multigrid vectors),
+// and 4 MB for what does not grow with the mesh.
+double estimate_bytes(const phfem_server_s* S, const phfem_request& r) {
+  const double fine = fine_triangles(r);
+  const double learned = S->per_tri[r.kind == 1][r.levels > 0];
+  if (learned > 0.0) return 1.1 * learned * fine + (double)(4 << 20);
+  return (r.levels > 0 ? 600.0 : 400.0) * fine + (double)(4 << 20);
+}
+// Requests from which the bytes per triangle are learned: large enough that
+// the allocations that do not grow with the mesh (reduction partials, sort
+// scratch, the solver state) are a small part of the peak.
+constexpr double kLearnFrom = 65536.0;
 
 int run_request(phfem_ctx ctx, const phfem_request& r, const phfem_solve_opts& opts, phfem_result& out) {
   cudaStream_t s = ctx->stream;
+  const size_t held0 = ctx->bytes_now;  // the request's own allocations are measured from here
+  ctx->bytes_peak = held0;
+  struct Peak {  // records the peak however the request ends
+    phfem_ctx c;
+    size_t base;
+    phfem_result& o;
+    ~Peak() { o.bytes_peak = (int64_t)(c->bytes_peak - base); }
+  } peak{ctx, held0, out};
   std::vector<phfem_mesh> H;  // the hierarchy, coarsest first (one mesh without refinement)
   {
     phfem_mesh m0 = nullptr;
@@ -96,19 +122,26 @@ int run_request(phfem_ctx ctx, const phfem_request& r, const phfem_solve_opts& o
   const phfem_mesh_info I = m->info;
   out.nL = I.nL;
   out.nE = I.nE;
+  // the data: the caller's midpoint arrays, or constants filled in
   double *f = nullptr, *bc = nullptr, *w0 = nullptr;
-  st = dalloc_n(ctx, &f, I.nE);
-  if (st == PHFEM_OK) st = dalloc_n(ctx, &bc, I.nE);
-  if (st == PHFEM_OK && r.kind == 1) st = dalloc_n(ctx, &w0, I.nE);
-  if (st == PHFEM_OK) {
-    k_fill_edge_data<<<grid_for(ctx, I.nE), kBlock, 0, s>>>(I.nE, m->eclass, r.f, r.uD, r.g, f, bc, r.u0, w0);
-    st = check_launch(ctx, "k_fill_edge_data");
+  const bool fill_w0 = r.kind == 1 && !r.u0_mid;
+  if (!r.f_mid || !r.bc_mid || fill_w0) {
+    st = dalloc_n(ctx, &f, I.nE);
+    if (st == PHFEM_OK) st = dalloc_n(ctx, &bc, I.nE);
+    if (st == PHFEM_OK && fill_w0) st = dalloc_n(ctx, &w0, I.nE);
+    if (st == PHFEM_OK) {
+      k_fill_edge_data<<<grid_for(ctx, I.nE), kBlock, 0, s>>>(I.nE, m->eclass, r.f, r.uD, r.g, f, bc, r.u0, w0);
+      st = check_launch(ctx, "k_fill_edge_data");
+    }
   }
+  const double* fe = r.f_mid ? r.f_mid : f;
+  const double* be = r.bc_mid ? r.bc_mid : bc;
+  const double* we = r.kind == 1 ? (r.u0_mid ? r.u0_mid : w0) : nullptr;
   phfem_sys sys = nullptr;
   phfem_mg mg = nullptr;
   if (st == PHFEM_OK) {
     phfem_coeffs c{r.a_T, 1.0, r.delta, r.kind == 1 ? r.dt : 0.0, r.precision, PHFEM_FORM_TRACE};
-    st = phfem_assemble(m, &c, r.kind == 1 ? nullptr : f, r.kind == 1 ? nullptr : bc, &sys);
+    st = phfem_assemble(m, &c, r.kind == 1 ? nullptr : fe, r.kind == 1 ? nullptr : be, &sys);
   }
   if (st == PHFEM_OK && H.size() > 1) {
     st = phfem_mg_create(sys, (int32_t)H.size(), H.data(), r.a_T, nullptr, &mg);
@@ -121,9 +154,9 @@ int run_request(phfem_ctx ctx, const phfem_request& r, const phfem_solve_opts& o
     out.rel_residual = stats.rel_residual;
   } else if (st == PHFEM_OK) {
     std::vector<double> phi((size_t)r.steps + 1, 1.0);  // constant-in-time data
-    phfem_source src{1, r.steps + 1, f, bc, phi.data()};
+    phfem_source src{1, r.steps + 1, fe, be, phi.data()};
     phfem_cn cn = nullptr;
-    st = phfem_cn_create(sys, &src, w0, nullptr, &cn);
+    st = phfem_cn_create(sys, &src, we, nullptr, &cn);
     if (st == PHFEM_OK) {
       phfem_stats stats{};
       st = phfem_cn_step_graph(cn, r.steps, &opts, &stats);
@@ -156,16 +189,17 @@ void worker(phfem_server S, int slot) {
       S->cv_work.wait(lock, [&] {
         if (S->stop) return true;
         if (S->queue.empty()) return false;
-        const double e = estimate_bytes(S->queue.front().second);
+        const double e = estimate_bytes(S, S->queue.front().second);
         return S->reserved + e <= S->budget || S->reserved == 0.0;
       });
       if (S->stop && S->queue.empty()) return;
       job = S->queue.front();
       S->queue.pop_front();
-      est = estimate_bytes(job.second);
+      est = estimate_bytes(S, job.second);
       S->reserved += est;
       S->results[job.first].t_admit = now_since(S->t0);
       S->results[job.first].slot = slot;
+      S->results[job.first].bytes_reserved = est;
     }
     phfem_result res{};
     const int st = run_request(ctx, job.second, S->opts, res);
@@ -179,7 +213,13 @@ void worker(phfem_server S, int slot) {
       R.rel_residual = res.rel_residual;
       R.nL = res.nL;
       R.nE = res.nE;
+      R.bytes_peak = res.bytes_peak;
       R.t_finish = now_since(S->t0);
+      if (st == PHFEM_OK && res.bytes_peak > 0 && fine_triangles(job.second) >= kLearnFrom) {
+        // what requests of this class actually allocate
+        double& learned = S->per_tri[job.second.kind == 1][job.second.levels > 0];
+        learned = std::max(learned, (double)res.bytes_peak / fine_triangles(job.second));
+      }
       S->completed++;
     }
     S->cv_done.notify_all();

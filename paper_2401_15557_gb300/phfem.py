@@ -65,13 +65,15 @@ class Request(C.Structure):
                 ("a_T", C.c_void_p), ("delta", C.c_double), ("f", C.c_double), ("uD", C.c_double),
                 ("g", C.c_double), ("dt", C.c_double), ("u0", C.c_double), ("steps", C.c_int32),
                 ("precision", C.c_int32), ("U_out", C.c_void_p), ("Lambda_out", C.c_void_p),
-                ("levels", C.c_int32), ("reserved", C.c_int32)]
+                ("levels", C.c_int32), ("reserved", C.c_int32), ("f_mid", C.c_void_p), ("bc_mid", C.c_void_p),
+                ("u0_mid", C.c_void_p)]
 
 
 class Result(C.Structure):
     _fields_ = [("id", C.c_int64), ("status", C.c_int32), ("done", C.c_int32), ("iterations", C.c_int32),
                 ("slot", C.c_int32), ("nE", C.c_int32), ("nL", C.c_int32), ("rel_residual", C.c_double),
-                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_finish", C.c_double)]
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_finish", C.c_double),
+                ("bytes_reserved", C.c_double), ("bytes_peak", C.c_int64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -123,6 +125,7 @@ def lib() -> C.CDLL:
             "phfem_status_str": (C.c_char_p, [C.c_int]),
             "phfem_last_error": (C.c_char_p, []),
             "phfem_ctx_launches": (C.c_int64, [_H]),
+            "phfem_ctx_memory": (C.c_int, [_H, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.c_int32]),
             "phfem_ctx_profile": (C.c_int, [_H, C.c_int]),
             "phfem_ctx_kernel_time": (C.c_int, [_H, C.c_char_p, C.POINTER(C.c_double), C.POINTER(C.c_int64),
                                                 C.c_int]),
@@ -236,6 +239,13 @@ def phfem_ctx_set_cg_kernel(ctx, variant=0):
     """FP32 Jacobi iteration in the locality order: 0 direction update fused into the product, the rows'
     own data staged in shared memory (default); 1 separate direction kernel; 2 fused, rows through L1/L2."""
     _check(lib().phfem_ctx_set_cg_kernel(ctx, int(variant)), "phfem_ctx_set_cg_kernel")
+
+
+def phfem_ctx_memory(ctx, reset_peak=False):
+    """(bytes now, peak bytes) of the context's own device allocations."""
+    now, peak = C.c_int64(), C.c_int64()
+    _check(lib().phfem_ctx_memory(ctx, C.byref(now), C.byref(peak), int(bool(reset_peak))), "phfem_ctx_memory")
+    return now.value, peak.value
 
 
 def phfem_ctx_set_l2_window(ctx, enable=True):
@@ -507,14 +517,17 @@ def phfem_server_create(slots, hbm_budget_bytes, opts=None):
 
 
 def make_request(xy, tri, dirichlet, neumann, kind=0, a_T=None, delta=0.0, f=1.0, uD=0.0, g=0.0, dt=0.0, u0=0.0,
-                 steps=0, precision=PHFEM_FP32_IR, U_out=None, Lambda_out=None, levels=0) -> Request:
+                 steps=0, precision=PHFEM_FP32_IR, U_out=None, Lambda_out=None, levels=0, f_mid=None, bc_mid=None,
+                 u0_mid=None) -> Request:
+    """f_mid, bc_mid, u0_mid: optional midpoint arrays on the finest mesh's edges; the constants otherwise."""
     return Request(int(kind), xy.shape[0], tri.shape[0], dirichlet.shape[0] if dirichlet is not None else 0,
                    neumann.shape[0] if neumann is not None else 0, _ptr(xy, torch.float64), _ptr(tri, torch.int32),
                    _ptr(dirichlet, torch.int32) if dirichlet is not None and dirichlet.numel() else None,
                    _ptr(neumann, torch.int32) if neumann is not None and neumann.numel() else None,
                    _ptr(a_T, torch.float64), float(delta), float(f), float(uD), float(g), float(dt), float(u0),
                    int(steps), int(precision), _ptr(U_out, torch.float64), _ptr(Lambda_out, torch.float64),
-                   int(levels), 0)
+                   int(levels), 0, _ptr(f_mid, torch.float64), _ptr(bc_mid, torch.float64),
+                   _ptr(u0_mid, torch.float64))
 
 
 def phfem_server_submit(server, req: Request) -> int:

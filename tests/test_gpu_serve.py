@@ -149,3 +149,95 @@ def test_refined_requests_use_multigrid():
             ref = O.solve_saddle(fine, pb, aT=aT)
             assert np.max(np.abs(Ua - ref["U"])) <= 1e-7 * np.max(np.abs(ref["U"]))
     assert all(r["status"] == 0 for r in mixed)
+
+
+def test_midpoint_data_requests():
+    """Requests with midpoint arrays instead of constants: arrays holding the
+    constants give bitwise the request with the constants (both kinds); an
+    elliptic request with the sine data of a manufactured problem matches the
+    oracle's saddle solve with that data."""
+    from paper_2401_15557_gb300 import phfem as P
+    from phfem_gpu import GpuMesh
+    dev = lambda a, t: torch.as_tensor(np.ascontiguousarray(a), dtype=t, device="cuda")
+    ctx = P.phfem_ctx_create()
+    srv = P.phfem_server_create(2, 64e9, P.solve_opts(rtol=1e-10))
+    for kind, n in ((0, 24), (1, 20)):
+        m = I.square_mesh(n)
+        gm = GpuMesh(m, ctx)
+        nE, cls = gm.info["nE"], gm.tables["eclass"]
+        t = dict(xy=dev(m.xy, torch.float64), tri=dev(m.tri, torch.int32), d=dev(m.dirichlet, torch.int32),
+                 nn=dev(m.neumann, torch.int32))
+        fm = torch.ones(nE, dtype=torch.float64, device="cuda")
+        # edge classes: 1 Dirichlet, 2 Neumann
+        bcm = dev(np.where(cls == 1, 0.2, np.where(cls == 2, 0.1, 0.0)), torch.float64)
+        u0m = dev(np.where(cls == 1, 0.2, 0.0), torch.float64)
+        outs = []
+        for arrays in (False, True):
+            U = torch.full((3 * m.nT,), np.nan, dtype=torch.float64, device="cuda")
+            kw = dict(f_mid=fm, bc_mid=bcm, u0_mid=u0m if kind == 1 else None) if arrays else {}
+            rq = P.make_request(t["xy"], t["tri"], t["d"], t["nn"], kind=kind, delta=0.5, f=1.0, uD=0.2, g=0.1,
+                                dt=1.0 / n, u0=0.0, steps=8, precision=P.PHFEM_FP32_IR, U_out=U, **kw)
+            r = P.phfem_server_poll(srv, P.phfem_server_submit(srv, rq), wait=True)
+            assert r["status"] == 0 and r["rel_residual"] <= 1e-10, r
+            outs.append((U.cpu().numpy(), r["iterations"]))
+        assert np.array_equal(outs[0][0], outs[1][0]) and outs[0][1] == outs[1][1]
+        gm.close()
+    # non-constant data against the oracle
+    m = I.lshape_mesh(n=10, seed=I.seed_for(1, 92))
+    pb = I.problem_sine_exp()
+    pb.delta = 1.0
+    gm = GpuMesh(m, ctx)
+    fm, bcm = gm.edge_data(pb.f, pb.g, pb.uD)
+    U = torch.full((3 * m.nT,), np.nan, dtype=torch.float64, device="cuda")
+    t = dict(xy=dev(m.xy, torch.float64), tri=dev(m.tri, torch.int32), d=dev(m.dirichlet, torch.int32),
+             nn=dev(m.neumann, torch.int32))
+    rq = P.make_request(t["xy"], t["tri"], t["d"], t["nn"], kind=0, delta=pb.delta, precision=P.PHFEM_FP64,
+                        U_out=U, f_mid=fm, bc_mid=bcm)
+    r = P.phfem_server_poll(srv, P.phfem_server_submit(srv, rq), wait=True)
+    assert r["status"] == 0, r
+    ref = O.solve_saddle(m, pb)
+    assert np.max(np.abs(U.cpu().numpy() - ref["U"])) <= 1e-7 * np.max(np.abs(ref["U"]))
+    gm.close()
+    P.phfem_server_destroy(srv)
+    P.phfem_ctx_destroy(ctx)
+
+
+def test_memory_accounting_and_measured_admission():
+    """The context counts its own allocations (back to where it was once the
+    objects are destroyed); a served request records its peak, and the next
+    request of the same class is reserved the measured bytes per triangle
+    (+10 %, + 4 MB) instead of the static guess."""
+    from paper_2401_15557_gb300 import phfem as P
+    from phfem_gpu import GpuMesh
+    dev = lambda a, t: torch.as_tensor(np.ascontiguousarray(a), dtype=t, device="cuda")
+    ctx = P.phfem_ctx_create()
+    now0, _ = P.phfem_ctx_memory(ctx, reset_peak=True)
+    m = I.square_mesh(64)
+    gm = GpuMesh(m, ctx)
+    fm, bcm = gm.edge_data(lambda x, y: 1.0 + 0 * x, lambda x, y, nx, ny: 0 * x, lambda x, y: 0 * x)
+    sysh = P.phfem_assemble(gm.h, fm, bcm, precision=P.PHFEM_FP32_IR)
+    P.phfem_solve(sysh, P.solve_opts(rtol=1e-10))
+    now1, peak1 = P.phfem_ctx_memory(ctx)
+    assert now1 > now0 and peak1 >= now1
+    P.phfem_sys_destroy(sysh)
+    gm.close()
+    now2, _ = P.phfem_ctx_memory(ctx)
+    assert now2 == now0
+    P.phfem_ctx_destroy(ctx)
+
+    srv = P.phfem_server_create(1, 64e9, P.solve_opts(rtol=1e-10))
+    res = []
+    for n in (256, 200):  # 131,072 and 80,000 triangles: both learn
+        mm = I.square_mesh(n)
+        t = dict(xy=dev(mm.xy, torch.float64), tri=dev(mm.tri, torch.int32), d=dev(mm.dirichlet, torch.int32),
+                 nn=dev(mm.neumann, torch.int32))
+        rq = P.make_request(t["xy"], t["tri"], t["d"], t["nn"], kind=0, delta=0.5, f=1.0,
+                            precision=P.PHFEM_FP32_IR)
+        res.append((mm.nT, P.phfem_server_poll(srv, P.phfem_server_submit(srv, rq), wait=True)))
+    P.phfem_server_destroy(srv)
+    (n1, r1), (n2, r2) = res
+    assert r1["status"] == 0 and r2["status"] == 0
+    assert r1["bytes_peak"] > 0 and r2["bytes_peak"] > 0
+    assert r1["bytes_reserved"] == pytest.approx(400.0 * n1 + 4 * 2 ** 20)  # nothing measured yet
+    assert r2["bytes_reserved"] == pytest.approx(1.1 * r1["bytes_peak"] / n1 * n2 + 4 * 2 ** 20)
+    assert r2["bytes_peak"] <= r2["bytes_reserved"]
