@@ -528,6 +528,8 @@ typedef struct {
   double t_submit, t_admit, t_finish;  /* seconds since the server was created          */
   double bytes_reserved;   /* device bytes the admission reserved for the request          */
   int64_t bytes_peak;      /* device bytes the request's own allocations held at their peak */
+  double t_dev_start, t_dev_end;  /* device time of the request's first and last work on its
+                                     stream (CUDA events), seconds since the server was created */
 } phfem_result;
 
 /* Creates a server on the current device with `slots` workers, each a host

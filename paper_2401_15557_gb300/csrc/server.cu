@@ -61,6 +61,7 @@ struct phfem_server_s {
   std::vector<std::thread> workers;
   std::vector<phfem_ctx> ctxs;
   std::vector<cudaStream_t> streams;
+  cudaEvent_t ref = nullptr;  // device-time origin of the requests' event windows
   int64_t completed = 0;
   // largest device bytes per finest-mesh triangle that finished requests
   // allocated, by kind (elliptic, Crank-Nicolson) and refinement (none, some);
@@ -202,7 +203,23 @@ void worker(phfem_server S, int slot) {
       S->results[job.first].bytes_reserved = est;
     }
     phfem_result res{};
-    const int st = run_request(ctx, job.second, S->opts, res);
+    // the request's device-time window: events on the slot's stream around its work
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    const bool timed = cudaEventCreate(&ev[0]) == cudaSuccess && cudaEventCreate(&ev[1]) == cudaSuccess;
+    if (timed) cudaEventRecord(ev[0], ctx->stream);
+    int st = run_request(ctx, job.second, S->opts, res);
+    if (timed) {
+      float a = 0.f, b = 0.f;
+      if (cudaEventRecord(ev[1], ctx->stream) == cudaSuccess && cudaEventSynchronize(ev[1]) == cudaSuccess &&
+          cudaEventElapsedTime(&a, S->ref, ev[0]) == cudaSuccess &&
+          cudaEventElapsedTime(&b, S->ref, ev[1]) == cudaSuccess) {
+        res.t_dev_start = 1e-3 * a;
+        res.t_dev_end = 1e-3 * b;
+      }
+    }
+    for (cudaEvent_t e : ev)
+      if (e) cudaEventDestroy(e);
+    cudaGetLastError();
     {
       std::lock_guard<std::mutex> lock(S->mu);
       S->reserved -= est;
@@ -214,6 +231,8 @@ void worker(phfem_server S, int slot) {
       R.nL = res.nL;
       R.nE = res.nE;
       R.bytes_peak = res.bytes_peak;
+      R.t_dev_start = res.t_dev_start;
+      R.t_dev_end = res.t_dev_end;
       R.t_finish = now_since(S->t0);
       if (st == PHFEM_OK && res.bytes_peak > 0 && fine_triangles(job.second) >= kLearnFrom) {
         // what requests of this class actually allocate
@@ -243,6 +262,12 @@ PHFEM_API int phfem_server_create(int32_t slots, double hbm_budget_bytes, const 
   S->budget = hbm_budget_bytes;
   S->opts = opts ? *opts : phfem_solve_opts{};
   S->t0 = std::chrono::steady_clock::now();
+  if (cudaEventCreate(&S->ref) != cudaSuccess || cudaEventRecord(S->ref, 0) != cudaSuccess ||
+      cudaEventSynchronize(S->ref) != cudaSuccess) {
+    if (S->ref) cudaEventDestroy(S->ref);
+    delete S;
+    return fail(PHFEM_ECUDA, "phfem_server_create: reference event");
+  }
   for (int i = 0; i < slots; ++i) {
     cudaStream_t s;
     cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
@@ -252,6 +277,7 @@ PHFEM_API int phfem_server_create(int32_t slots, double hbm_budget_bytes, const 
         phfem_ctx_destroy(S->ctxs[j]);
         cudaStreamDestroy(S->streams[j]);
       }
+      cudaEventDestroy(S->ref);
       delete S;
       return fail(PHFEM_ECUDA, "phfem_server_create: stream or context creation failed");
     }
@@ -316,6 +342,7 @@ PHFEM_API int phfem_server_destroy(phfem_server S) {
     phfem_ctx_destroy(S->ctxs[j]);
     cudaStreamDestroy(S->streams[j]);
   }
+  cudaEventDestroy(S->ref);
   delete S;
   return PHFEM_OK;
 }

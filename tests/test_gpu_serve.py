@@ -72,6 +72,12 @@ def test_same_result_alone_and_in_the_mix():
     overlap = any(mixed[i]["t_admit"] < mixed[j]["t_finish"] and mixed[j]["t_admit"] < mixed[i]["t_finish"]
                   for i in range(len(mixed)) for j in range(i + 1, len(mixed)))
     assert overlap  # admitted while others were running
+    # and on the device: the event windows of two requests on different slots intersect
+    assert all(0.0 <= r["t_dev_start"] < r["t_dev_end"] for r in mixed)
+    dev_overlap = any(mixed[i]["slot"] != mixed[j]["slot"] and mixed[i]["t_dev_start"] < mixed[j]["t_dev_end"]
+                      and mixed[j]["t_dev_start"] < mixed[i]["t_dev_end"]
+                      for i in range(len(mixed)) for j in range(i + 1, len(mixed)))
+    assert dev_overlap
     for (Ua, La, ra), (Ub, Lb, rb) in zip(A, B):
         assert ra["status"] == 0 and rb["status"] == 0
         assert ra["rel_residual"] <= 1e-10 and rb["rel_residual"] <= 1e-10
