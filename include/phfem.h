@@ -334,8 +334,11 @@ typedef struct {
   double smooth_ratio;   /* smoothing interval [b / ratio, b]; 0 -> 6                */
   double coarse_eps;     /* coarsest-level error reduction; 0 -> 0.3                 */
   int32_t coarse_degree; /* > 0: fixed coarsest degree instead (<= 2000)            */
-  int32_t reserved;
+  int32_t flags;         /* PHFEM_MG_COARSE_STEPWISE: the coarsest iteration one
+                            launch per step (the default runs it in one launch of a
+                            thread-block cluster when its rows fit; same results) */
 } phfem_mg_opts;
+#define PHFEM_MG_COARSE_STEPWISE 1
 typedef struct {
   int32_t levels, nu, coarse_degree, reserved;
   double coarse_a, coarse_b, smooth_ratio;

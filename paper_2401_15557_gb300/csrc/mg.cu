@@ -28,6 +28,8 @@
 #include <cstring>
 #include <vector>
 
+#include <cooperative_groups.h>
+
 #include "kernels.cuh"
 
 struct phfem_mg_s {
@@ -53,6 +55,12 @@ struct phfem_mg_s {
   double ratio = 6.0;
   double coarse_a = 0.0, coarse_b = 0.0;
   int coarse_deg = 0;
+  // the coarsest iteration in one cluster launch (k_mg_coarse), when its rows
+  // fit the cluster's shared memory and PHFEM_MG_COARSE_STEPWISE is not set
+  bool coarse_fused = false;
+  int coarse_per = 0;          // rows per CTA
+  size_t coarse_smem = 0;      // dynamic shared memory per CTA
+  double* coarse_coef = nullptr;  // [2][coarse_deg]: cd, then cr
 };
 
 namespace phfem {
@@ -64,6 +72,24 @@ __device__ __forceinline__ bool skip(const SolveState* st, int want) { return st
 //   mode 0: d = cr D^-1 rhs, zout = d                       (from zero)
 //   mode 1: d = cr D^-1 (rhs - A zin), zout = zin + d        (from zin)
 //   mode 2: d = cd d + cr D^-1 (rhs - A zin), zout = zin + d
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// One row of a Chebyshev step after the first (mode 1 with cd = 0, mode 2):
+// the residual rhs - (A z)_e in difference form and the new d, with explicit
+// fused multiply-adds so that every kernel that takes a step rounds alike.
+template <typename T>
+__device__ __forceinline__ T cheb_d(T rd, T l0, T l1, T l2, T l3, T pe, T g0, T g1, T g2, T g3, T rhs, T di, T dprev,
+                                    T cd, T cr) {
+  T sv = rd * pe;
+  sv = fma_rn(l0, pe - g0, sv);
+  sv = fma_rn(l1, pe - g1, sv);
+  sv = fma_rn(l2, pe - g2, sv);
+  sv = fma_rn(l3, pe - g3, sv);
+  const T res = rhs - sv;
+  return fma_rn(cd, dprev, cr * (di * res));
+}
+
 template <typename T>
 __global__ void k_mg_cheb(int nE, const int32_t* __restrict__ nbr, const T* __restrict__ lval,
                           const T* __restrict__ rdiag, const T* __restrict__ dinv, const T* __restrict__ rhs,
@@ -78,12 +104,95 @@ __global__ void k_mg_cheb(int nE, const int32_t* __restrict__ nbr, const T* __re
       d[e] = de;
       zout[e] = de;
     } else {
-      const T res = rhs[e] - spmv_row(nbr, lval, rdiag, zin, m, e);
-      const T de = (mode == 1 ? (T)0 : cd * d[e]) + cr * (dinv[e] * res);
+      const T pe = zin[e];
+      const T de = cheb_d(rdiag[e], lval[e], lval[m + e], lval[2 * m + e], lval[3 * m + e], pe,
+                          __ldg(zin + nbr[e]), __ldg(zin + nbr[m + e]), __ldg(zin + nbr[2 * m + e]),
+                          __ldg(zin + nbr[3 * m + e]), rhs[e], dinv[e], mode == 1 ? (T)0 : d[e],
+                          mode == 1 ? (T)0 : cd, cr);
       d[e] = de;
-      zout[e] = zin[e] + de;
+      zout[e] = pe + de;
     }
   }
+}
+
+// The coarsest level's whole Chebyshev iteration in one launch: one cluster of
+// kCoarseCluster CTAs, CTA r owning rows [r per, (r + 1) per).  Each CTA copies
+// its rows' operator, D^-1 and right-hand side into shared memory once and
+// keeps their z (two buffers) and d there; a step reads z at the neighbours
+// from the owning CTA's shared memory (distributed shared memory) and ends
+// with a cluster barrier.  The per-row arithmetic is k_mg_cheb's (cheb_d: from
+// zero, then mode 2), so the result is bitwise the step-per-launch iteration's;
+// ~100 launches of a few microseconds each become one.
+constexpr int kCoarseCluster = 8;
+constexpr int kCoarseThreads = 1024;
+
+template <typename T>
+__global__ void __launch_bounds__(kCoarseThreads) k_mg_coarse(int nE, int per, const int32_t* __restrict__ nbr,
+                                                              const T* __restrict__ lval,
+                                                              const T* __restrict__ rdiag,
+                                                              const T* __restrict__ dinv, const T* __restrict__ rhs,
+                                                              T* __restrict__ zout, int deg,
+                                                              const double* __restrict__ coef, const SolveState* st,
+                                                              int want) {
+  namespace cgr = cooperative_groups;
+  cgr::cluster_group cl = cgr::this_cluster();
+  extern __shared__ __align__(16) unsigned char coarse_smem[];
+  pdl_enter();
+  if (skip(st, want)) return;  // the same for every CTA of the cluster
+  const size_t m = (size_t)nE;
+  const int rank = (int)cl.block_rank();
+  const int e0 = rank * per;
+  const int cnt = max(0, min(per, nE - e0));
+  int* snb = reinterpret_cast<int*>(coarse_smem);  // [4][per]
+  T* sl = reinterpret_cast<T*>(snb + 4 * per);      // [4][per]
+  T* srd = sl + 4 * per;
+  T* sdi = srd + per;
+  T* srh = sdi + per;
+  T* sz = srh + per;  // [2][per]
+  T* sd = sz + 2 * per;
+  for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+    const int e = e0 + j;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      snb[k * per + j] = nbr[k * m + e];
+      sl[k * per + j] = lval[k * m + e];
+    }
+    srd[j] = rdiag[e];
+    sdi[j] = dinv[e];
+    srh[j] = rhs[e];
+  }
+  __syncthreads();
+  auto zat = [&](const T* zc, int c) -> T {  // z of row c, from the CTA that owns it
+    const int owner = c / per, j = c - owner * per;
+    if (owner == rank) return zc[j];
+    return *cl.map_shared_rank(const_cast<T*>(zc) + j, owner);
+  };
+  int cur = 0;
+  for (int k = 0; k < deg; ++k) {
+    const T cd = (T)coef[k], cr = (T)coef[deg + k];
+    T* zc = sz + cur * per;
+    if (k == 0) {  // from zero: d = cr D^-1 rhs, z = d
+      for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+        const T de = cr * (sdi[j] * srh[j]);
+        sd[j] = de;
+        zc[j] = de;
+      }
+    } else {
+      T* zn = sz + (cur ^ 1) * per;
+      for (int j = threadIdx.x; j < cnt; j += blockDim.x) {
+        const T pe = zc[j];
+        const T de = cheb_d(srd[j], sl[j], sl[per + j], sl[2 * per + j], sl[3 * per + j], pe, zat(zc, snb[j]),
+                            zat(zc, snb[per + j]), zat(zc, snb[2 * per + j]), zat(zc, snb[3 * per + j]), srh[j],
+                            sdi[j], sd[j], cd, cr);
+        sd[j] = de;
+        zn[j] = pe + de;
+      }
+      cur ^= 1;
+    }
+    cl.sync();  // this step's z is complete in every CTA before the next reads it
+  }
+  const T* zc = sz + cur * per;
+  for (int j = threadIdx.x; j < cnt; j += blockDim.x) zout[e0 + j] = zc[j];
 }
 
 template <typename T>
@@ -411,6 +520,25 @@ struct MgRun {
     phfem_mg_s::Level& Lv = mg->L[l];
     T* zb = (T*)Lv.zb;
     T* res = nullptr;
+    if (l == 0 && mg->coarse_fused) {
+      phfem_sys sy = Lv.sys;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(kCoarseCluster);
+      cfg.blockDim = dim3(kCoarseThreads);
+      cfg.dynamicSmemBytes = mg->coarse_smem;
+      cfg.stream = s;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = kCoarseCluster;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      PH_CUDA(cudaLaunchKernelEx(&cfg, k_mg_coarse<T>, Lv.nE, mg->coarse_per, (const int32_t*)Lv.mesh->nbr,
+                                 (const T*)sy->lval, (const T*)sy->rdiag, (const T*)sy->dinv, rhs, z_out,
+                                 mg->coarse_deg, (const double*)mg->coarse_coef, st, want));
+      return check_launch(ctx(l), "k_mg_coarse");
+    }
     if (l == 0) {
       std::vector<double> cd, cr;
       cheb_coeffs(mg->coarse_a, mg->coarse_b, mg->coarse_deg, cd, cr);
@@ -462,6 +590,7 @@ void mg_free(phfem_mg mg) {
     dfree(c, Lv.res);
     dfree(c, Lv.ct);
     dfree(c, Lv.parent);
+    if (l == 0) dfree(c, mg->coarse_coef);
     if (Lv.owned && Lv.sys) phfem_sys_destroy(Lv.sys);
   }
   if (mg->fine && mg->fine->mg == mg) mg->fine->mg = nullptr;
@@ -650,6 +779,54 @@ PHFEM_API int phfem_mg_create(phfem_sys sys, int32_t nlevels, const phfem_mesh* 
       const double rho = (std::sqrt(kap) - 1.0) / (std::sqrt(kap) + 1.0);
       const int deg = rho > 0.0 ? (int)std::ceil(std::log(2.0 / o.coarse_eps) / std::log(1.0 / rho)) : 1;
       mg->coarse_deg = std::max(1, std::min(deg, 2000));
+    }
+  }
+  if (st == PHFEM_OK && !(o.flags & PHFEM_MG_COARSE_STEPWISE)) {
+    // the coarsest iteration as one cluster launch, if its rows fit
+    const int n = mg->L[0].nE;
+    const int per = (n + kCoarseCluster - 1) / kCoarseCluster;
+    const size_t tsz = mg->fp32 ? sizeof(float) : sizeof(double);
+    const size_t smem = (size_t)per * (16 + 10 * tsz);
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    auto kern = mg->fp32 ? (const void*)k_mg_coarse<float> : (const void*)k_mg_coarse<double>;
+    // the kernel's shared-memory limit is set to the device's largest, the same
+    // value from every context and thread (the request server creates
+    // hierarchies concurrently: a limit sized to one hierarchy would race with
+    // another's launch)
+    bool ok = smem <= (size_t)optin &&
+              cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) == cudaSuccess;
+    if (ok) {
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(kCoarseCluster);
+      cfg.blockDim = dim3(kCoarseThreads);
+      cfg.dynamicSmemBytes = smem;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = kCoarseCluster;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int clusters = 0;
+      ok = cudaOccupancyMaxActiveClusters(&clusters, kern, &cfg) == cudaSuccess && clusters >= 1;
+    }
+    cudaGetLastError();
+    if (ok) {
+      std::vector<double> cd, cr;
+      cheb_coeffs(mg->coarse_a, mg->coarse_b, mg->coarse_deg, cd, cr);
+      cd.insert(cd.end(), cr.begin(), cr.end());
+      st = dalloc_n(ctx, &mg->coarse_coef, cd.size());
+      if (st == PHFEM_OK) {
+        cudaError_t e = cudaMemcpyAsync(mg->coarse_coef, cd.data(), sizeof(double) * cd.size(),
+                                        cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);  // cd is a host temporary
+        if (e != cudaSuccess) st = cuda_fail(e, "phfem_mg_create coarse coefficients", __FILE__, __LINE__);
+      }
+      mg->coarse_fused = st == PHFEM_OK;
+      mg->coarse_per = per;
+      mg->coarse_smem = smem;
     }
   }
   dfree(ctx, flags);

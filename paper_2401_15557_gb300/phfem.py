@@ -82,7 +82,7 @@ class Result(C.Structure):
 
 class MgOpts(C.Structure):
     _fields_ = [("nu", C.c_int32), ("smooth_ratio", C.c_double), ("coarse_eps", C.c_double),
-                ("coarse_degree", C.c_int32), ("reserved", C.c_int32)]
+                ("coarse_degree", C.c_int32), ("flags", C.c_int32)]
 
 
 class MgInfo(C.Structure):
@@ -553,12 +553,16 @@ def phfem_server_destroy(server):
 
 # --- multigrid preconditioner --------------------------------------------------------
 
-def phfem_mg_create(sys, meshes, a_T=None, nu=0, smooth_ratio=0.0, coarse_eps=0.0, coarse_degree=0):
+PHFEM_MG_COARSE_STEPWISE = 1
+
+
+def phfem_mg_create(sys, meshes, a_T=None, nu=0, smooth_ratio=0.0, coarse_eps=0.0, coarse_degree=0, flags=0):
     """Multigrid over meshes (coarsest first, each the refinement of the one
-    before, the last the system's mesh)."""
+    before, the last the system's mesh).  flags: PHFEM_MG_COARSE_STEPWISE runs
+    the coarsest iteration one launch per step."""
     arr = (_H * len(meshes))(*[m.value if isinstance(m, _H) else m for m in meshes])
     I = phfem_mesh_info_get(meshes[-1])
-    o = MgOpts(int(nu), float(smooth_ratio), float(coarse_eps), int(coarse_degree), 0)
+    o = MgOpts(int(nu), float(smooth_ratio), float(coarse_eps), int(coarse_degree), int(flags))
     h = _H()
     _check(lib().phfem_mg_create(sys, len(meshes), arr, _ptr(a_T, torch.float64, I["nT"]), C.byref(o), C.byref(h)),
            "phfem_mg_create")

@@ -127,6 +127,14 @@ def test_mg_solve_matches_saddle_solve(ctx, precision):
     assert np.max(np.abs(L - ref["Lambda"])) <= 1e-6 * np.max(np.abs(ref["Lambda"]))
     cs = O.condensed_system(mesh, pb, aT=aT)
     assert O.relative_residual(cs["S"], cs["rhs"], w[cs["st"]["bsets"]["free"]]) <= 1.2e-10
+    # the coarsest iteration one launch per step: the same arithmetic per row as
+    # the default single cluster launch (the coarse rows spread over its 8 CTAs,
+    # neighbours read across them), so bitwise the same solve
+    mg_s = P.phfem_mg_create(sysh, H.handles, a_T=dev(aT, torch.float64), flags=P.PHFEM_MG_COARSE_STEPWISE)
+    P.phfem_sys_set_mg(sysh, mg_s)
+    st4, U4, _, w4 = _solve(P, sysh, info)
+    assert np.array_equal(w, w4) and st4["iterations"] == st["iterations"]
+    P.phfem_mg_destroy(mg_s)
     # detached: back to Jacobi with the same answer
     P.phfem_sys_set_mg(sysh, None)
     st3, U3, _, _ = _solve(P, sysh, info)
