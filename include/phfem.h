@@ -532,7 +532,11 @@ typedef struct {
   double bytes_reserved;   /* device bytes the admission reserved for the request          */
   int64_t bytes_peak;      /* device bytes the request's own allocations held at their peak */
   double t_dev_start, t_dev_end;  /* device time of the request's first and last work on its
-                                     stream (CUDA events), seconds since the server was created */
+                                     stream (the GPU's global timer), seconds since the server
+                                     was created                                            */
+  int32_t priority_class;  /* stream priority the request ran at: 0 highest (under 131,072
+                              finest-mesh triangles), 1 (under 1,048,576), 2 lowest         */
+  int32_t pad;
 } phfem_result;
 
 /* Creates a server on the current device with `slots` workers, each a host
@@ -544,7 +548,10 @@ typedef struct {
  * requests of the same kind (elliptic or Crank-Nicolson, with or without
  * refinement) of at least 65,536 triangles actually allocated at their peak,
  * the largest seen, plus 10 % and 4 MB; before any has finished, 400 bytes per
- * triangle (600 with refinement) + 4 MB.  opts apply to every solve. */
+ * triangle (600 with refinement) + 4 MB.  Each slot runs a request on a
+ * stream whose priority falls with the request's size (three classes, see
+ * phfem_result), so small requests are not held up behind the kernels of
+ * large ones.  opts apply to every solve. */
 PHFEM_API int phfem_server_create(int32_t slots, double hbm_budget_bytes, const phfem_solve_opts* opts,
                                   phfem_server* out);
 /* Queues a request (copied) and returns its id; never blocks on the GPU. */

@@ -1135,8 +1135,10 @@ int fcg_prepare(phfem_sys sys) {
     // blocks; the update kernel almost none.  Left to choose, the two would
     // run under different L1 / shared-memory splits, and every switch between
     // them drains the SM (no overlap of consecutive launches): 125 us per
-    // iteration at level 5 against 105 with one split for both.
-    {
+    // iteration at level 5 against 105 with one split for both.  Set once
+    // per process: changing a kernel's attributes can wait for that kernel's
+    // launches in flight on other streams (the request server's slots).
+    static const bool split_set = [] {
       int smem_sm = 0, dev = 0;
       cudaFuncAttributes fa{};
       cudaGetDevice(&dev);
@@ -1158,7 +1160,9 @@ int fcg_prepare(phfem_sys sys) {
         }
       }
       cudaGetLastError();
-    }
+      return true;
+    }();
+    (void)split_set;
     f->per_staged = resident_blocks(k_fcg_spmv_staged);
   } else {
     f->per_spmv[0] = resident_blocks(k_fcg_spmv<double, false>);

@@ -58,6 +58,8 @@ struct phfem_mg_s {
   // the coarsest iteration in one cluster launch (k_mg_coarse), when its rows
   // fit the cluster's shared memory and PHFEM_MG_COARSE_STEPWISE is not set
   bool coarse_fused = false;
+  int coarse_ctas = 1;         // CTAs of the cluster (1: a plain one-block launch)
+  int coarse_threads = 1024;   // threads per CTA
   int coarse_per = 0;          // rows per CTA
   size_t coarse_smem = 0;      // dynamic shared memory per CTA
   double* coarse_coef = nullptr;  // [2][coarse_deg]: cd, then cr
@@ -115,8 +117,9 @@ __global__ void k_mg_cheb(int nE, const int32_t* __restrict__ nbr, const T* __re
   }
 }
 
-// The coarsest level's whole Chebyshev iteration in one launch: one cluster of
-// kCoarseCluster CTAs, CTA r owning rows [r per, (r + 1) per).  Each CTA copies
+// The coarsest level's whole Chebyshev iteration in one launch: one block, or
+// one cluster of up to kCoarseCluster CTAs, CTA r owning rows [r per,
+// (r + 1) per).  Each CTA copies
 // its rows' operator, D^-1 and right-hand side into shared memory once and
 // keeps their z (two buffers) and d there; a step reads z at the neighbours
 // from the owning CTA's shared memory (distributed shared memory) and ends
@@ -523,17 +526,17 @@ struct MgRun {
     if (l == 0 && mg->coarse_fused) {
       phfem_sys sy = Lv.sys;
       cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(kCoarseCluster);
-      cfg.blockDim = dim3(kCoarseThreads);
+      cfg.gridDim = dim3(mg->coarse_ctas);
+      cfg.blockDim = dim3(mg->coarse_threads);
       cfg.dynamicSmemBytes = mg->coarse_smem;
       cfg.stream = s;
       cudaLaunchAttribute attr[1];
       attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = kCoarseCluster;
+      attr[0].val.clusterDim.x = mg->coarse_ctas;
       attr[0].val.clusterDim.y = 1;
       attr[0].val.clusterDim.z = 1;
       cfg.attrs = attr;
-      cfg.numAttrs = 1;
+      cfg.numAttrs = mg->coarse_ctas > 1 ? 1 : 0;
       PH_CUDA(cudaLaunchKernelEx(&cfg, k_mg_coarse<T>, Lv.nE, mg->coarse_per, (const int32_t*)Lv.mesh->nbr,
                                  (const T*)sy->lval, (const T*)sy->rdiag, (const T*)sy->dinv, rhs, z_out,
                                  mg->coarse_deg, (const double*)mg->coarse_coef, st, want));
@@ -783,28 +786,43 @@ PHFEM_API int phfem_mg_create(phfem_sys sys, int32_t nlevels, const phfem_mesh* 
   }
   if (st == PHFEM_OK && !(o.flags & PHFEM_MG_COARSE_STEPWISE)) {
     // the coarsest iteration as one cluster launch, if its rows fit
+    // CTAs: one row per thread where possible, the fewest CTAs that give it (a
+    // coarse level of a few hundred rows takes one small block, which the GPU
+    // can place at once while other work runs; a cluster waits for SMs of
+    // one GPC with room for all its CTAs)
     const int n = mg->L[0].nE;
-    const int per = (n + kCoarseCluster - 1) / kCoarseCluster;
+    int ctas = 1;
+    while (ctas < kCoarseCluster && ctas * kCoarseThreads < n) ctas *= 2;
+    const int per = (n + ctas - 1) / ctas;
+    const int threads = ctas > 1 ? kCoarseThreads : std::max(32, std::min(kCoarseThreads, (per + 31) / 32 * 32));
     const size_t tsz = mg->fp32 ? sizeof(float) : sizeof(double);
     const size_t smem = (size_t)per * (16 + 10 * tsz);
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     auto kern = mg->fp32 ? (const void*)k_mg_coarse<float> : (const void*)k_mg_coarse<double>;
-    // the kernel's shared-memory limit is set to the device's largest, the same
-    // value from every context and thread (the request server creates
-    // hierarchies concurrently: a limit sized to one hierarchy would race with
-    // another's launch)
-    bool ok = smem <= (size_t)optin &&
-              cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) == cudaSuccess;
-    if (ok) {
+    // the kernel's shared-memory limit is set to the device's largest, once
+    // per process: a limit sized to one hierarchy would race with another's
+    // launch (the request server creates hierarchies concurrently), and
+    // changing a kernel's attributes can wait for that kernel's launches in
+    // flight on other streams
+    static const bool limit_set = [optin] {
+      const bool a = cudaFuncSetAttribute(k_mg_coarse<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) ==
+                     cudaSuccess;
+      const bool b = cudaFuncSetAttribute(k_mg_coarse<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin) ==
+                     cudaSuccess;
+      cudaGetLastError();
+      return a && b;
+    }();
+    bool ok = smem <= (size_t)optin && limit_set;
+    if (ok && ctas > 1) {
       cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(kCoarseCluster);
-      cfg.blockDim = dim3(kCoarseThreads);
+      cfg.gridDim = dim3(ctas);
+      cfg.blockDim = dim3(threads);
       cfg.dynamicSmemBytes = smem;
       cudaLaunchAttribute attr[1];
       attr[0].id = cudaLaunchAttributeClusterDimension;
-      attr[0].val.clusterDim.x = kCoarseCluster;
+      attr[0].val.clusterDim.x = ctas;
       attr[0].val.clusterDim.y = 1;
       attr[0].val.clusterDim.z = 1;
       cfg.attrs = attr;
@@ -825,6 +843,8 @@ PHFEM_API int phfem_mg_create(phfem_sys sys, int32_t nlevels, const phfem_mesh* 
         if (e != cudaSuccess) st = cuda_fail(e, "phfem_mg_create coarse coefficients", __FILE__, __LINE__);
       }
       mg->coarse_fused = st == PHFEM_OK;
+      mg->coarse_ctas = ctas;
+      mg->coarse_threads = threads;
       mg->coarse_per = per;
       mg->coarse_smem = smem;
     }

@@ -37,6 +37,16 @@ __global__ void k_fill_edge_data(int nE, const uint8_t* __restrict__ eclass, dou
   }
 }
 
+// The GPU's global nanosecond timer, written by one thread.  (Timing CUDA
+// events recorded on each request's stream, which this replaced, held small
+// requests' host threads for hundreds of milliseconds while large requests
+// ran: p50 77 ms against 16 ms at 8 requests/s.)
+__global__ void k_stamp(uint64_t* out) {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  *out = t;
+}
+
 double now_since(std::chrono::steady_clock::time_point t0) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -59,9 +69,17 @@ struct phfem_server_s {
   int64_t next_id = 1;
   bool stop = false;
   std::vector<std::thread> workers;
+  // per slot, kPrioClasses contexts, each on a stream of its own priority:
+  // [slot * kPrioClasses + class]
   std::vector<phfem_ctx> ctxs;
   std::vector<cudaStream_t> streams;
-  cudaEvent_t ref = nullptr;  // device-time origin of the requests' event windows
+  // device-time windows of the requests: the global timer (ns) written by a
+  // one-thread kernel at the start and end of each request, per context
+  // [2 * context], read back through pinned host memory; ref_ns is the
+  // timer when the server was created
+  uint64_t ref_ns = 0;
+  uint64_t* stamp_dev = nullptr;
+  uint64_t* stamp_host = nullptr;
   int64_t completed = 0;
   // largest device bytes per finest-mesh triangle that finished requests
   // allocated, by kind (elliptic, Crank-Nicolson) and refinement (none, some);
@@ -74,6 +92,17 @@ namespace {
 
 double fine_triangles(const phfem_request& r) {
   return (double)r.nT * std::pow(4.0, (double)std::max(0, r.levels));
+}
+
+// Stream priority classes by request size: a small request's many short
+// kernels would otherwise wait behind the full-GPU grids of a large one (a
+// 50k-triangle multigrid solve took 36 ms beside a level-5 Jacobi solve on
+// another stream, 5.5 ms on a higher-priority stream, 1.8 ms alone), so the
+// block scheduler serves small requests first.
+constexpr int kPrioClasses = 3;
+int prio_class(const phfem_request& r) {
+  const double fine = fine_triangles(r);
+  return fine < 131072.0 ? 0 : (fine < 1048576.0 ? 1 : 2);
 }
 
 // The reservation of a request (the server's lock held): the measured bytes
@@ -180,7 +209,6 @@ int run_request(phfem_ctx ctx, const phfem_request& r, const phfem_solve_opts& o
 
 void worker(phfem_server S, int slot) {
   cudaSetDevice(S->device);
-  phfem_ctx ctx = S->ctxs[slot];
   for (;;) {
     std::pair<int64_t, phfem_request> job;
     double est = 0.0;
@@ -202,23 +230,22 @@ void worker(phfem_server S, int slot) {
       S->results[job.first].slot = slot;
       S->results[job.first].bytes_reserved = est;
     }
+    const int cls = prio_class(job.second);
+    phfem_ctx ctx = S->ctxs[slot * kPrioClasses + cls];
     phfem_result res{};
-    // the request's device-time window: events on the slot's stream around its work
-    cudaEvent_t ev[2] = {nullptr, nullptr};
-    const bool timed = cudaEventCreate(&ev[0]) == cudaSuccess && cudaEventCreate(&ev[1]) == cudaSuccess;
-    if (timed) cudaEventRecord(ev[0], ctx->stream);
+    res.priority_class = cls;
+    // the request's device-time window: timer stamps on its stream around its work
+    const int ci = slot * kPrioClasses + cls;
+    uint64_t* sd = S->stamp_dev + 2 * ci;
+    uint64_t* sh = S->stamp_host + 2 * ci;
+    k_stamp<<<1, 1, 0, ctx->stream>>>(sd);
     int st = run_request(ctx, job.second, S->opts, res);
-    if (timed) {
-      float a = 0.f, b = 0.f;
-      if (cudaEventRecord(ev[1], ctx->stream) == cudaSuccess && cudaEventSynchronize(ev[1]) == cudaSuccess &&
-          cudaEventElapsedTime(&a, S->ref, ev[0]) == cudaSuccess &&
-          cudaEventElapsedTime(&b, S->ref, ev[1]) == cudaSuccess) {
-        res.t_dev_start = 1e-3 * a;
-        res.t_dev_end = 1e-3 * b;
-      }
+    k_stamp<<<1, 1, 0, ctx->stream>>>(sd + 1);
+    if (cudaMemcpyAsync(sh, sd, 2 * sizeof(uint64_t), cudaMemcpyDeviceToHost, ctx->stream) == cudaSuccess &&
+        cudaStreamSynchronize(ctx->stream) == cudaSuccess) {
+      res.t_dev_start = 1e-9 * (double)(int64_t)(sh[0] - S->ref_ns);
+      res.t_dev_end = 1e-9 * (double)(int64_t)(sh[1] - S->ref_ns);
     }
-    for (cudaEvent_t e : ev)
-      if (e) cudaEventDestroy(e);
     cudaGetLastError();
     {
       std::lock_guard<std::mutex> lock(S->mu);
@@ -231,6 +258,7 @@ void worker(phfem_server S, int slot) {
       R.nL = res.nL;
       R.nE = res.nE;
       R.bytes_peak = res.bytes_peak;
+      R.priority_class = res.priority_class;
       R.t_dev_start = res.t_dev_start;
       R.t_dev_end = res.t_dev_end;
       R.t_finish = now_since(S->t0);
@@ -262,22 +290,38 @@ PHFEM_API int phfem_server_create(int32_t slots, double hbm_budget_bytes, const 
   S->budget = hbm_budget_bytes;
   S->opts = opts ? *opts : phfem_solve_opts{};
   S->t0 = std::chrono::steady_clock::now();
-  if (cudaEventCreate(&S->ref) != cudaSuccess || cudaEventRecord(S->ref, 0) != cudaSuccess ||
-      cudaEventSynchronize(S->ref) != cudaSuccess) {
-    if (S->ref) cudaEventDestroy(S->ref);
+  if (cudaMalloc((void**)&S->stamp_dev, sizeof(uint64_t) * 2 * (slots * kPrioClasses + 1)) != cudaSuccess ||
+      cudaMallocHost((void**)&S->stamp_host, sizeof(uint64_t) * 2 * (slots * kPrioClasses + 1)) != cudaSuccess) {
+    cudaGetLastError();
+    if (S->stamp_dev) cudaFree(S->stamp_dev);
     delete S;
-    return fail(PHFEM_ECUDA, "phfem_server_create: reference event");
+    return fail(PHFEM_ENOMEM, "phfem_server_create: timer stamps");
   }
-  for (int i = 0; i < slots; ++i) {
+  {  // the device-time origin, taken next to the host one
+    uint64_t* last = S->stamp_dev + 2 * slots * kPrioClasses;
+    k_stamp<<<1, 1>>>(last);
+    if (cudaMemcpy(&S->ref_ns, last, sizeof(uint64_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+      cudaFree(S->stamp_dev);
+      cudaFreeHost(S->stamp_host);
+      delete S;
+      return fail(PHFEM_ECUDA, "phfem_server_create: timer origin");
+    }
+    S->t0 = std::chrono::steady_clock::now();
+  }
+  int least = 0, greatest = 0;  // numerically: greatest < least
+  if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) least = greatest = 0;
+  const int prio[kPrioClasses] = {greatest, (least + greatest) / 2, least};
+  for (int i = 0; i < slots * kPrioClasses; ++i) {
     cudaStream_t s;
-    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    cudaError_t e = cudaStreamCreateWithPriority(&s, cudaStreamNonBlocking, prio[i % kPrioClasses]);
     phfem_ctx c = nullptr;
     if (e != cudaSuccess || phfem_ctx_create(s, &c) != PHFEM_OK || phfem_ctx_set_l2_window(c, 0) != PHFEM_OK) {
       for (size_t j = 0; j < S->ctxs.size(); ++j) {
         phfem_ctx_destroy(S->ctxs[j]);
         cudaStreamDestroy(S->streams[j]);
       }
-      cudaEventDestroy(S->ref);
+      cudaFree(S->stamp_dev);
+      cudaFreeHost(S->stamp_host);
       delete S;
       return fail(PHFEM_ECUDA, "phfem_server_create: stream or context creation failed");
     }
@@ -342,7 +386,8 @@ PHFEM_API int phfem_server_destroy(phfem_server S) {
     phfem_ctx_destroy(S->ctxs[j]);
     cudaStreamDestroy(S->streams[j]);
   }
-  cudaEventDestroy(S->ref);
+  cudaFree(S->stamp_dev);
+  cudaFreeHost(S->stamp_host);
   delete S;
   return PHFEM_OK;
 }

@@ -74,7 +74,7 @@ class Result(C.Structure):
                 ("slot", C.c_int32), ("nE", C.c_int32), ("nL", C.c_int32), ("rel_residual", C.c_double),
                 ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_finish", C.c_double),
                 ("bytes_reserved", C.c_double), ("bytes_peak", C.c_int64), ("t_dev_start", C.c_double),
-                ("t_dev_end", C.c_double)]
+                ("t_dev_end", C.c_double), ("priority_class", C.c_int32), ("pad", C.c_int32)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}

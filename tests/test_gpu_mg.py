@@ -310,3 +310,32 @@ def test_full_size_lshape_multigrid(ctx):
     P.phfem_sys_destroy(sysh)
     for h in reversed(hs):
         P.phfem_mesh_destroy(h)
+
+
+@pytest.mark.parametrize("n0", [3, 30, 60], ids=["one_block", "cluster4", "cluster8"])
+def test_coarse_iteration_in_one_launch(ctx, n0):
+    """The coarsest Chebyshev iteration in one launch (one block for a few
+    hundred rows, a cluster of 4 or 8 CTAs reading neighbours across them for
+    thousands) against the step-per-launch iteration: bitwise the same solve."""
+    H = Hierarchy(ctx, I.square_mesh(n0), 2)
+    P = H.P
+    pb = I.problem_sine_exp()
+    pb.delta = 0.5
+    mesh = H.meshes[-1]
+    sysh = _system(H, pb, np.ones(mesh.nT), P.PHFEM_FP32_IR)
+    info = P.phfem_mesh_info_get(H.handles[-1])
+    coarse = P.phfem_mesh_info_get(H.handles[0])["nE"]
+    assert coarse == 3 * n0 * n0 + 2 * n0
+    ws, its = [], []
+    for flags in (0, P.PHFEM_MG_COARSE_STEPWISE):
+        mg = P.phfem_mg_create(sysh, H.handles, flags=flags)
+        P.phfem_sys_set_mg(sysh, mg)
+        st, _, _, w = _solve(P, sysh, info)
+        assert st["converged"] == 1 and st["rel_residual"] <= 1e-10, st
+        ws.append(w)
+        its.append(st["iterations"])
+        P.phfem_sys_set_mg(sysh, None)
+        P.phfem_mg_destroy(mg)
+    assert np.array_equal(ws[0], ws[1]) and its[0] == its[1]
+    P.phfem_sys_destroy(sysh)
+    H.close()

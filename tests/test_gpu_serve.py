@@ -244,6 +244,8 @@ def test_memory_accounting_and_measured_admission():
     (n1, r1), (n2, r2) = res
     assert r1["status"] == 0 and r2["status"] == 0
     assert r1["bytes_peak"] > 0 and r2["bytes_peak"] > 0
+    # stream priority by size: 131,072 triangles run in the middle class, 80,000 in the highest
+    assert r1["priority_class"] == 1 and r2["priority_class"] == 0
     assert r1["bytes_reserved"] == pytest.approx(400.0 * n1 + 4 * 2 ** 20)  # nothing measured yet
     assert r2["bytes_reserved"] == pytest.approx(1.1 * r1["bytes_peak"] / n1 * n2 + 4 * 2 ** 20)
     assert r2["bytes_peak"] <= r2["bytes_reserved"]
